@@ -37,6 +37,8 @@ Readings where the paper is silent (each is listed in the design notes):
   info is 2.
 * TRQRCP builds the selected columns on all m rows; W2 is formed only on
   columns that are still trailing.
+* Alg. 4 runs k/b blocks, so b <= k is implied: a block size above the rank
+  is clamped to k before the sample rank l = b + p is formed.
 """
 
 import numpy as np
@@ -182,6 +184,7 @@ def rqrcp(A, b, p, seed=0, k=None, omega=None, replay_jpvt=None, tie_rtol=1e-8,
     m, n = F.shape
     kmax = min(m, n)
     k = kmax if k is None else int(k)
+    b = min(b, k)
     if omega is None:
         ell = b + p
         omega = gaussian_omega(seed, ell, m)
@@ -258,6 +261,7 @@ def trqrcp(A, k, b, p, seed=0, omega=None, replay_jpvt=None, tie_rtol=1e-8, ties
     A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
     k = int(k)
+    b = min(b, k)
     if omega is None:
         ell = b + p
         omega = gaussian_omega(seed, ell, m)
