@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark: randomized QR with column pivoting (Alg. 4) on a GB300.
+
+Workload: one 16384 x 16384 FP64 matrix A = U diag(sigma) V^T with Haar U, V
+(QR of seeded Gaussians) and sigma_i = 10^(-12 (i-1)/(n-1)); block b = 64,
+oversampling p = 8, Omega from Philox seed 1.  A step is one full
+factorization (sketch, and per block: sample QRCP, column permutation,
+panel + T, trailing update, sample update) after restoring A from a
+resident copy.  The same matrix is also factored by the project's own
+unpivoted blocked QR, the paper's baseline for the cost of pivoting.
+
+Flop convention (LAPACK dgeqrf count, used for both routines so that the
+rate ratio is the time ratio): 2 m n^2 - 2 n^3 / 3.
+
+Multi-GPU: every rank factors its own matrix (replicas, no collective on
+the data path); value = all ranks' flops / the slowest rank's time.
+
+--impl reference times the CPU oracle (numpy float64) on the host cores on
+a bounded sample of the same workload: the first blocks of the same
+factorization, scaled by their algorithmic flops.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RQRCP GFLOP/s & time vs own unpivoted QR at 16384^2 FP64"
+UNIT = "GFLOP/s"
+
+
+def flops_geqrf(m, n):
+    k = min(m, n)
+    if m >= n:
+        return 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
+    return 2.0 * n * m * m - 2.0 * m ** 3 / 3.0
+
+
+def block_flops(m, n, b, p, nblocks):
+    """Algorithmic flops of the first `nblocks` blocks of Alg. 4 (sketch,
+    sample QRCP, panel + T, trailing update, sample update)."""
+    ell = b + p
+    k = min(m, n)
+    fl = 2.0 * ell * m * n
+    j0 = 0
+    for _ in range(nblocks):
+        if j0 >= k:
+            break
+        bJ = min(b, k - j0)
+        mJ, nc = m - j0, n - j0
+        n2 = nc - bJ
+        fl += sum(4.0 * (ell - i) * (nc - i - 1) for i in range(min(bJ, ell)))
+        fl += 2.0 * mJ * bJ * bJ - 2.0 * bJ ** 3 / 3.0
+        fl += 4.0 * mJ * n2 * bJ
+        fl += 2.0 * bJ * bJ * n2
+        j0 += bJ
+    return fl
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--b", type=int, default=64)
+    ap.add_argument("--p", type=int, default=8)
+    ap.add_argument("--cpu-blocks", type=int, default=6,
+                    help="blocks of the factorization in the oracle's bounded sample")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the QR baseline, e2e and cpu_baseline legs")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [t.strip() for t in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ oracle legs
+def cpu_sample(A_host, b, p, nblocks):
+    """Time the oracle on the first `nblocks` blocks of the factorization."""
+    import numpy as np
+    import oracle
+    k = nblocks * b
+    t0 = time.perf_counter()
+    oracle.rqrcp(A_host, b, p, seed=1, k=k)
+    dt = time.perf_counter() - t0
+    m, n = A_host.shape
+    fl = block_flops(m, n, b, p, nblocks)
+    return fl / dt / 1e9, dt
+
+
+def host_matrix(n):
+    import torch
+    import synth
+    if torch.cuda.is_available():
+        A = synth.graded_device(n, "cuda")
+        return A.cpu().numpy().T.copy().T  # column-major host copy
+    return synth.graded(n)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    n, b, p = args.n, args.b, args.p
+    A = np.asfortranarray(host_matrix(n))
+    for _ in range(args.warmup):
+        cpu_sample(A, b, p, max(1, args.cpu_blocks // 2))
+    rates, secs = [], []
+    for _ in range(args.steps):
+        r, dt = cpu_sample(A, b, p, max(1, args.cpu_blocks // 2))
+        rates.append(r)
+        secs.append(dt)
+    value = statistics.mean(rates)
+    full_s = flops_geqrf(n, n) / (value * 1e9)
+    sample = (f"first {max(1, args.cpu_blocks // 2)} blocks (b={b}) of the {n}x{n} factorization "
+              f"per step, rate scaled by algorithmic flops")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * full_s,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"rqrcp_graded_{n}x{n}_b{b}_p{p}", "m": n, "n": n, "b": b, "p": p,
+                   "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1509_06820_gb300 as rq
+    import synth
+
+    n, b, p = args.n, args.b, args.p
+    m = n
+    A0 = synth.graded_device(n, dev)                 # column-major, resident
+    A = rq.empty_colmajor(m, n, dev)
+    h = rq.Handle(dev)
+    stream = torch.cuda.current_stream(dev)
+    h.reserve("R", m, n, n, b, p)
+    h.reserve("Q", m, n, n, b, 0)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def step():
+        A.copy_(A0)
+        rq.rqrcp_factor(A, b, p, 1, handle=h)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize(dev)
+    info_warm = h.sync_info()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize(dev)
+    h.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = h.profile_read()
+    h.profile(False)
+    info = h.sync_info()
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    fl = flops_geqrf(m, n)
+    value = world * fl / (ms / 1e3) / 1e9
+    gpu_launches = sum(v[2] for v in prof.values())
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
+    fp64_peak = bf16 * 1.25 / 2250.0      # nominal FP64 : BF16 dense ratio
+    tr_ms, tr_fl, tr_launch = prof["trailing_update"]
+    achieved = tr_fl / (tr_ms / 1e3) / 1e12 if tr_ms > 0 else None
+    roofline = {"bound": "alu", "kernel": "trailing update (gemm_kernel FP64 FFMA)",
+                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak if achieved else None, "traffic": None,
+                "peak_source": "MEASURED_PEAKS bf16_tflops_sustained x 1.25/2250 (nominal FP64/BF16)",
+                "launch_ms_avg": tr_ms / max(tr_launch, 1)}
+    phases = {k: {"ms": v[0], "gflop": v[1] / 1e9, "launches": v[2]} for k, v in prof.items()}
+
+    extras = {}
+    if not args.no_extras:
+        # the project's own unpivoted blocked QR on the same matrix
+        def qstep():
+            A.copy_(A0)
+            rq.qr_factor(A, b, handle=h)
+        qstep()
+        torch.cuda.synchronize(dev)
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(args.steps):
+            qstep()
+        q1.record(stream)
+        torch.cuda.synchronize(dev)
+        qr_ms = q0.elapsed_time(q1) / args.steps
+        extras["qr_ms_per_step"] = qr_ms
+        extras["qr_gflops"] = fl / (qr_ms / 1e3) / 1e9
+        extras["rqrcp_over_qr_time"] = ms / qr_ms
+
+        # end to end through the public call with host buffers
+        Ah = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+        Ah.copy_(A0)
+        Ah_out = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+        jh = torch.empty(n, dtype=torch.int64, pin_memory=True)
+        th = torch.empty(min(m, n), dtype=torch.float64, pin_memory=True)
+        torch.cuda.synchronize(dev)
+
+        def estep():
+            A.copy_(Ah, non_blocking=True)
+            jp, tau = rq.rqrcp_factor(A, b, p, 1, handle=h)
+            Ah_out.copy_(A, non_blocking=True)
+            jh.copy_(jp, non_blocking=True)
+            th.copy_(tau, non_blocking=True)
+        estep()
+        torch.cuda.synchronize(dev)
+        barrier()
+        x0 = torch.cuda.Event(enable_timing=True)
+        x1 = torch.cuda.Event(enable_timing=True)
+        x0.record(stream)
+        for _ in range(args.steps):
+            estep()
+        x1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = x0.elapsed_time(x1) / args.steps
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        extras["e2e"] = {"value": world * fl / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
+                         "ms_per_step": e2e_ms, "h2d_bytes_per_step": m * n * 8,
+                         "d2h_bytes_per_step": m * n * 8 + n * 8 + min(m, n) * 8}
+        del Ah, Ah_out
+
+        if rank == 0:
+            import numpy as np
+            A_host = np.asfortranarray(A0.cpu().numpy())
+            rate, dt = cpu_sample(A_host, b, p, args.cpu_blocks)
+            extras["cpu_baseline"] = {
+                "value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                "sample": (f"first {args.cpu_blocks} blocks (b={b}) of the same {n}x{n} "
+                           f"factorization, {dt:.1f} s, rate from their algorithmic flops"),
+                "threads": "numpy BLAS default (all host cores)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"rqrcp_graded_{n}x{n}_b{b}_p{p}", "m": m, "n": n, "b": b,
+                       "p": p, "sigma": "10^(-12 (i-1)/(n-1))", "omega_seed": 1,
+                       "l2": "inputs larger than L2 (2.1 GB matrix)",
+                       "parallelism": f"replicas x{world}"},
+            "gpu_launches": gpu_launches,
+            "device_info": info | info_warm,
+            "clocks": clk,
+            "roofline": roofline,
+            "phases": phases,
+        }
+        line.update({k: v for k, v in extras.items()})
+        line.setdefault("e2e", None)
+        line.setdefault("cpu_baseline", None)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

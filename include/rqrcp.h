@@ -1,0 +1,179 @@
+/*
+ * rqrcp.h -- C ABI of the GB300 (sm_103a) implementation of randomized QR
+ * with column pivoting, its truncated form and the TUXV approximate SVD
+ * (Duersch & Gu, "Randomized QR with Column Pivoting").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices are column-major FP64 in device memory; element (i, j) of a
+ *   matrix X with leading dimension ldx lives at X[i + j * ldx].
+ * - All matrix/vector pointers are DEVICE pointers owned by the caller.  They
+ *   must stay valid until the work enqueued on the handle's stream has run.
+ * - Every call is asynchronous on the handle's stream (the stream passed to
+ *   rqrcp_create or rqrcp_set_stream; NULL means the legacy default stream).
+ *   It validates its arguments on the host, enqueues kernels and returns.
+ * - Return value: RQRCP_OK when the work was enqueued.  A negative value -i
+ *   names the invalid argument i (1-based, the handle is argument 1).
+ *   RQRCP_ERR_CUDA reports a CUDA runtime error at enqueue time
+ *   (rqrcp_last_error gives the text), RQRCP_ERR_ALLOC a failed workspace
+ *   allocation, RQRCP_ERR_UNSUPPORTED a size outside the limits stated below.
+ * - Numerical status is a device word, read with rqrcp_sync_info (which
+ *   synchronises the stream): 0, or an OR of the RQRCP_INFO_* bits.
+ * - Column indices in jpvt are 0-based: jpvt[c] is the original index of the
+ *   column that ends up in position c (A[:, jpvt] = Q R).
+ * - Omega, the Gaussian compression matrix, is generated on the device from
+ *   `seed` by Philox4x32-10 (Salmon et al., SC'11): entry (i, r) of the
+ *   l x m matrix uses key (seed mod 2^32, seed >> 32) and counter
+ *   (r mod 2^32, r >> 32, i / 2, 1); words (x0,x1) and (x2,x3) give
+ *   u = (top 52 bits + 1/2) * 2^-52 and Box-Muller gives rows 2q (cosine)
+ *   and 2q+1 (sine).
+ * - The handle owns all scratch memory (grown on demand with cudaMalloc;
+ *   rqrcp_reserve pre-allocates it).  One handle must not be used from two
+ *   host threads at once, and two calls on one handle must not overlap on
+ *   the device (they share the scratch); calls on one stream never do.
+ *
+ * Size limits of this build (RQRCP_ERR_UNSUPPORTED beyond them): b <= 128,
+ * l = b + p <= 192; the sample of one block (l x (n - j0)) and the panel of
+ * one block ((m - j0) x b) are held in the shared memory of at most one
+ * cooperative CTA per SM, which bounds l * n <= 152 * 25000 and
+ * m * b <= 152 * 25000 (FP64 elements).
+ */
+#ifndef RQRCP_H_
+#define RQRCP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RQRCP_OK 0
+#define RQRCP_ERR_CUDA 1000
+#define RQRCP_ERR_ALLOC 1001
+#define RQRCP_ERR_UNSUPPORTED 1002
+
+#define RQRCP_INFO_NONFINITE 1  /* the sample held NaN/Inf: A is not finite */
+#define RQRCP_INFO_RESAMPLED 2  /* exactly singular R11: trailing sample re-drawn */
+#define RQRCP_INFO_TIMEOUT 4    /* a device-side wait gave up; results invalid */
+
+typedef struct rqrcp_handle_s* rqrcp_handle_t;
+
+/* Create a handle bound to `cuda_stream` (a cudaStream_t, may be NULL) on the
+ * current CUDA device.  Allocates a few kilobytes of device state. */
+int rqrcp_create(rqrcp_handle_t* handle, void* cuda_stream);
+
+/* Free the handle and its scratch memory (synchronises its stream first). */
+int rqrcp_destroy(rqrcp_handle_t handle);
+
+/* Rebind the handle to another stream. */
+int rqrcp_set_stream(rqrcp_handle_t handle, void* cuda_stream);
+
+/* Scratch bytes a call needs: op = 'R' (rqrcp_factor), 'Q' (qr_factor),
+ * 'T' (trqrcp), 'U' (tuxv).  k is ignored for 'R' and 'Q'. */
+size_t rqrcp_workspace_bytes(char op, int64_t m, int64_t n, int64_t k, int b, int p);
+
+/* Allocate the scratch for a later call now (so that the call itself does
+ * not allocate, e.g. before stream capture). */
+int rqrcp_reserve(rqrcp_handle_t handle, char op, int64_t m, int64_t n, int64_t k, int b, int p);
+
+/* Wait for the handle's stream, then return the device status word in *info
+ * and clear it. */
+int rqrcp_sync_info(rqrcp_handle_t handle, int* info);
+
+/* Text of the last CUDA error seen by the handle ("" if none). */
+const char* rqrcp_last_error(rqrcp_handle_t handle);
+
+/* Text for a return code or info bit. */
+const char* rqrcp_status_string(int code);
+
+/*
+ * Full randomized QR with column pivoting -- Alg. 4 (RQRCP) of the paper with
+ * the sample update of Eq. (3), k = min(m, n).
+ *   m, n   : matrix size, m >= 1, n >= 1
+ *   dA     : in/out, m x n, lda >= max(1, m).  On exit R is on and above the
+ *            diagonal and the Householder vectors (unit leading entry
+ *            implied) below it, LAPACK dgeqp3 layout.
+ *   b      : block size (pivots per block), 1 <= b <= 128; clamped to k
+ *   p      : oversampling, p >= 0; sample rank l = b + p
+ *   seed   : Philox seed of Omega
+ *   d_jpvt : out, n int64 (0-based permutation, see above)
+ *   d_tau  : out, min(m, n) reflector coefficients (H = I - tau v v^T)
+ */
+int rqrcp_factor(rqrcp_handle_t handle, int64_t m, int64_t n, double* dA, int64_t lda, int b,
+                 int p, uint64_t seed, int64_t* d_jpvt, double* d_tau);
+
+/*
+ * Unpivoted blocked Householder QR: Alg. 4 with every sample operation and
+ * pivot removed (the paper's `qr`, note to Table 3).  dA in/out as in
+ * rqrcp_factor (LAPACK dgeqrf layout); d_tau out, min(m, n).
+ */
+int qr_factor(rqrcp_handle_t handle, int64_t m, int64_t n, double* dA, int64_t lda, int b,
+              double* d_tau);
+
+/*
+ * Truncated RQRCP without trailing update -- Alg. 6 (TRQRCP).  A is read
+ * only; its columns are gathered through the permutation instead of moved
+ * (the same result as permuting A in place, Alg. 6, without the copy).
+ *   k      : rank, 1 <= k <= min(m, n)
+ *   d_jpvt : out, n int64; the first k entries are the selected columns
+ *   d_tau  : out, k
+ *   dY     : out, m x k, ldy >= m: reflectors, unit diagonal and zeros above
+ *            it stored explicitly
+ *   dR     : out, k x n, ldr >= k: upper trapezoidal R in the permuted column
+ *            order, A[:, jpvt] ~= (I - Y T Y^T)[:, :k] R
+ */
+int trqrcp(rqrcp_handle_t handle, int64_t m, int64_t n, const double* dA, int64_t lda, int64_t k,
+           int b, int p, uint64_t seed, int64_t* d_jpvt, double* d_tau, double* dY, int64_t ldy,
+           double* dR, int64_t ldr);
+
+/*
+ * Approximate truncated SVD -- Alg. 7 (TUXV) with j_max = 1:
+ * TRQRCP, Z0 = R P^T, V from the QR of Z0^T, Z1 = A V, [U, X] = qr(Z1).
+ *   dU : out, m x k, ldu >= m, orthonormal columns
+ *   dX : out, k x k, ldx >= k, upper triangular (zeros below stored)
+ *   dV : out, n x k, ldv >= n, orthonormal columns;  A ~= U X V^T
+ */
+int tuxv(rqrcp_handle_t handle, int64_t m, int64_t n, const double* dA, int64_t lda, int64_t k,
+         int b, int p, uint64_t seed, double* dU, int64_t ldu, double* dX, int64_t ldx,
+         double* dV, int64_t ldv);
+
+/*
+ * The Gaussian compression matrix of Alg. 4 (first steps): writes the
+ * rows x cols block of the seeded GIID matrix for Philox stream `stream_id`
+ * (1 = Omega) into dOut (column-major, ldo >= rows).
+ */
+int rqrcp_gaussian(rqrcp_handle_t handle, uint64_t seed, uint32_t stream_id, int64_t rows,
+                   int64_t cols, double* dOut, int64_t ldo);
+
+/*
+ * The initial sample of Alg. 4: B = Omega A with Omega = rqrcp_gaussian(seed,
+ * 1, l, m).  dB out, l x n, ldb >= l.
+ */
+int rqrcp_sketch(rqrcp_handle_t handle, int64_t m, int64_t n, const double* dA, int64_t lda,
+                 int ell, uint64_t seed, double* dB, int64_t ldb);
+
+/*
+ * Instrumentation (no counterpart in the paper).  While enabled, every phase
+ * of a call is bracketed by CUDA events recorded on the handle's stream, and
+ * the algorithmic FLOP count and the number of kernel launches of each phase
+ * are accumulated:
+ *   0 Omega generation and sketch B = Omega A      4 trailing update (W, A2 -= Y W)
+ *   1 sample QRCP                                  5 sample update (Eq. 3)
+ *   2 column permutation                           6 TRQRCP/TUXV products
+ *   3 panel QR and T factor                        7 other (fills, copies)
+ * rqrcp_profile(h, 1) clears the totals and starts recording; (h, 0) stops.
+ * rqrcp_profile_read synchronises the stream and writes, for each of the
+ * first nphase phases (<= 8), the device milliseconds, algorithmic FLOPs and
+ * kernel launches since the last enable; any pointer may be NULL.
+ */
+#define RQRCP_NPHASE 8
+int rqrcp_profile(rqrcp_handle_t handle, int enable);
+int rqrcp_profile_read(rqrcp_handle_t handle, int nphase, double* ms, double* flops,
+                       int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RQRCP_H_ */

@@ -1,0 +1,260 @@
+"""Python binding of librqrcp (randomized QR with column pivoting on GB300).
+
+Argument marshalling only: every numerical step runs in the CUDA kernels of
+``csrc/`` behind the C ABI of ``include/rqrcp.h``.  PyTorch supplies device
+memory and the current stream.  There is no CPU fallback: if the library
+cannot be loaded the calls raise.
+
+Matrices are column-major float64 CUDA tensors, i.e. tensors with
+``stride(0) == 1`` (the transpose of a contiguous tensor); ``colmajor``
+converts, ``empty_colmajor`` allocates.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "librqrcp.so")
+
+RQRCP_OK = 0
+RQRCP_ERR_CUDA = 1000
+RQRCP_ERR_ALLOC = 1001
+RQRCP_ERR_UNSUPPORTED = 1002
+INFO_NONFINITE = 1
+INFO_RESAMPLED = 2
+INFO_TIMEOUT = 4
+
+# (name, restype, argtypes) of every symbol declared in include/rqrcp.h
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I = ctypes.c_int
+_U64 = ctypes.c_uint64
+SIGNATURES = [
+    ("rqrcp_create", _I, [ctypes.POINTER(_P), _P]),
+    ("rqrcp_destroy", _I, [_P]),
+    ("rqrcp_set_stream", _I, [_P, _P]),
+    ("rqrcp_workspace_bytes", ctypes.c_size_t, [ctypes.c_char, _I64, _I64, _I64, _I, _I]),
+    ("rqrcp_reserve", _I, [_P, ctypes.c_char, _I64, _I64, _I64, _I, _I]),
+    ("rqrcp_sync_info", _I, [_P, ctypes.POINTER(_I)]),
+    ("rqrcp_last_error", ctypes.c_char_p, [_P]),
+    ("rqrcp_status_string", ctypes.c_char_p, [_I]),
+    ("rqrcp_factor", _I, [_P, _I64, _I64, _P, _I64, _I, _I, _U64, _P, _P]),
+    ("qr_factor", _I, [_P, _I64, _I64, _P, _I64, _I, _P]),
+    ("trqrcp", _I, [_P, _I64, _I64, _P, _I64, _I64, _I, _I, _U64, _P, _P, _P, _I64, _P, _I64]),
+    ("tuxv", _I, [_P, _I64, _I64, _P, _I64, _I64, _I, _I, _U64, _P, _I64, _P, _I64, _P, _I64]),
+    ("rqrcp_gaussian", _I, [_P, _U64, ctypes.c_uint32, _I64, _I64, _P, _I64]),
+    ("rqrcp_sketch", _I, [_P, _I64, _I64, _P, _I64, _I, _U64, _P, _I64]),
+    ("rqrcp_profile", _I, [_P, _I]),
+    ("rqrcp_profile_read", _I, [_P, _I, _P, _P, _P]),
+]
+
+PHASES = ["sketch", "sample_qrcp", "permute", "panel", "trailing_update", "sample_update",
+          "trqrcp_products", "other"]
+
+_lib = None
+
+
+class RqrcpError(RuntimeError):
+    pass
+
+
+def load(path=None):
+    """Load librqrcp.so (building it first is the job of ``build.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RqrcpError(f"librqrcp.so not found at {path}; run paper_1509_06820_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class Handle:
+    """Owns an rqrcp handle (scratch memory, status word) on one device."""
+
+    def __init__(self, device=None):
+        lib = load()
+        self.device = torch.device(device or "cuda")
+        with torch.cuda.device(self.device):
+            h = _P()
+            _check(lib.rqrcp_create(ctypes.byref(h), None), None)
+        self.h = h
+
+    def bind(self, stream=None):
+        stream = stream or torch.cuda.current_stream(self.device)
+        load().rqrcp_set_stream(self.h, _P(stream.cuda_stream))
+        return self.h
+
+    def sync_info(self):
+        info = _I(0)
+        _check(load().rqrcp_sync_info(self.bind(), ctypes.byref(info)), self.h)
+        return info.value
+
+    def reserve(self, op, m, n, k, b, p):
+        _check(load().rqrcp_reserve(self.bind(), op.encode(), m, n, k, b, p), self.h)
+
+    def profile(self, enable=True):
+        _check(load().rqrcp_profile(self.h, 1 if enable else 0), self.h)
+
+    def profile_read(self):
+        """{phase: (ms, flops, launches)} since the last profile(True)."""
+        n = len(PHASES)
+        ms = (ctypes.c_double * n)()
+        fl = (ctypes.c_double * n)()
+        ln = (ctypes.c_int64 * n)()
+        self.bind()
+        _check(load().rqrcp_profile_read(self.h, n, ctypes.cast(ms, _P), ctypes.cast(fl, _P),
+                                         ctypes.cast(ln, _P)), self.h)
+        return {p: (ms[i], fl[i], ln[i]) for i, p in enumerate(PHASES)}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().rqrcp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_handles = {}
+
+
+def default_handle(device=None):
+    dev = torch.device(device or "cuda")
+    if dev.index is None:
+        dev = torch.device("cuda", torch.cuda.current_device())
+    if dev not in _handles:
+        _handles[dev] = Handle(dev)
+    return _handles[dev]
+
+
+def _check(code, h):
+    if code == RQRCP_OK:
+        return
+    lib = load()
+    msg = lib.rqrcp_status_string(code).decode()
+    if h is not None and code in (RQRCP_ERR_CUDA, RQRCP_ERR_ALLOC):
+        msg += ": " + lib.rqrcp_last_error(h).decode()
+    if code < 0:
+        msg = f"argument {-code} invalid"
+    raise RqrcpError(f"rqrcp call failed ({code}): {msg}")
+
+
+def _is_colmajor(x):
+    if x.dim() != 2:
+        return False
+    rows, cols = x.shape
+    ok_rows = rows <= 1 or x.stride(0) == 1
+    ok_cols = cols <= 1 or x.stride(1) >= max(1, rows)
+    return ok_rows and ok_cols
+
+
+def _ld(x):
+    rows, cols = x.shape
+    return x.stride(1) if cols > 1 else max(1, rows)
+
+
+def colmajor(x):
+    """x itself if it is column-major, else a column-major copy."""
+    if _is_colmajor(x):
+        return x
+    out = empty_colmajor(x.shape[0], x.shape[1], x.device, x.dtype)
+    out.copy_(x)
+    return out
+
+
+def empty_colmajor(rows, cols, device, dtype=torch.float64):
+    return torch.empty((cols, rows), device=device, dtype=dtype).t()
+
+
+def _cm(x, name):
+    if x.device.type != "cuda" or x.dtype != torch.float64:
+        raise TypeError(f"{name} must be a float64 CUDA tensor")
+    if not _is_colmajor(x):
+        raise ValueError(f"{name} must be column-major (stride(0) == 1)")
+    return x.data_ptr(), _ld(x)
+
+
+def _ptr(x):
+    return _P(x.data_ptr())
+
+
+def rqrcp_factor(A, b, p, seed, handle=None):
+    """Alg. 4 in place on column-major A; returns (jpvt, tau)."""
+    h = handle or default_handle(A.device)
+    pa, lda = _cm(A, "A")
+    m, n = A.shape
+    jpvt = torch.empty(n, dtype=torch.int64, device=A.device)
+    tau = torch.empty(min(m, n), dtype=torch.float64, device=A.device)
+    _check(load().rqrcp_factor(h.bind(), m, n, _P(pa), lda, b, p, seed, _ptr(jpvt), _ptr(tau)), h.h)
+    return jpvt, tau
+
+
+def qr_factor(A, b, handle=None):
+    """Unpivoted blocked QR in place; returns tau."""
+    h = handle or default_handle(A.device)
+    pa, lda = _cm(A, "A")
+    m, n = A.shape
+    tau = torch.empty(min(m, n), dtype=torch.float64, device=A.device)
+    _check(load().qr_factor(h.bind(), m, n, _P(pa), lda, b, _ptr(tau)), h.h)
+    return tau
+
+
+def trqrcp(A, k, b, p, seed, handle=None):
+    """Alg. 6; returns (jpvt, tau, Y (m x k), R (k x n, permuted order))."""
+    h = handle or default_handle(A.device)
+    pa, lda = _cm(A, "A")
+    m, n = A.shape
+    jpvt = torch.empty(n, dtype=torch.int64, device=A.device)
+    tau = torch.empty(k, dtype=torch.float64, device=A.device)
+    Y = empty_colmajor(m, k, A.device)
+    R = empty_colmajor(k, n, A.device)
+    _check(load().trqrcp(h.bind(), m, n, _P(pa), lda, k, b, p, seed, _ptr(jpvt), _ptr(tau),
+                         _ptr(Y), _ld(Y), _ptr(R), _ld(R)), h.h)
+    return jpvt, tau, Y, R
+
+
+def tuxv(A, k, b, p, seed, handle=None):
+    """Alg. 7 with j_max = 1; returns (U (m x k), X (k x k), V (n x k))."""
+    h = handle or default_handle(A.device)
+    pa, lda = _cm(A, "A")
+    m, n = A.shape
+    U = empty_colmajor(m, k, A.device)
+    X = empty_colmajor(k, k, A.device)
+    V = empty_colmajor(n, k, A.device)
+    _check(load().tuxv(h.bind(), m, n, _P(pa), lda, k, b, p, seed, _ptr(U), _ld(U),
+                       _ptr(X), _ld(X), _ptr(V), _ld(V)), h.h)
+    return U, X, V
+
+
+def gaussian(seed, stream_id, rows, cols, device="cuda", handle=None):
+    """The rows x cols seeded GIID block (stream 1 = Omega)."""
+    h = handle or default_handle(device)
+    out = empty_colmajor(rows, cols, device)
+    _check(load().rqrcp_gaussian(h.bind(), seed, stream_id, rows, cols, _ptr(out), _ld(out)),
+           h.h)
+    return out
+
+
+def sketch(A, ell, seed, handle=None):
+    """B = Omega A with the seeded l x m Omega."""
+    h = handle or default_handle(A.device)
+    pa, lda = _cm(A, "A")
+    m, n = A.shape
+    B = empty_colmajor(ell, n, A.device)
+    _check(load().rqrcp_sketch(h.bind(), m, n, _P(pa), lda, ell, seed, _ptr(B), _ld(B)), h.h)
+    return B
+
+
+def sync_info(device=None):
+    return default_handle(device).sync_info()

@@ -1,0 +1,114 @@
+// Launchers of the device kernels (internal interface between the .cu files
+// and the host orchestrator in rqrcp.cu).  All launches are asynchronous on
+// `st` and return the cudaError_t of the launch.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace rq {
+
+// ---- philox.cu: seeded GIID matrix (Omega and re-samples)
+// Writes rows x cols into out (ld >= rows).  When gate != nullptr the kernel
+// does nothing unless *gate != 0.
+cudaError_t launch_gaussian(uint64_t seed, uint32_t stream_id, int64_t rows, int64_t cols,
+                            double* out, int64_t ld, const int* gate, cudaStream_t st);
+
+// ---- gemm_f64.cu: C = alpha op(A) op(B) + beta C (column-major FP64).
+// amode: how A is read -- 0 plain, 1 unit-lower-trapezoidal (entries above the
+// diagonal read as 0, diagonal as 1: a Householder block Y stored in place),
+// 2 upper-triangular (entries below the diagonal read as 0).
+// transA/transB: 'N' or 'T'.  gate: if non-null the kernel runs only when
+// *gate == gate_run.  Split-K uses `partial` scratch (splits * M * N doubles)
+// when splits > 1.
+struct GemmArgs {
+  char transA, transB;
+  int amode;
+  int64_t M, N, K;
+  double alpha;
+  const double* A;
+  int64_t lda;
+  const double* B;
+  int64_t ldb;
+  double beta;
+  double* C;
+  int64_t ldc;
+  const int* gate;
+  int gate_run;
+  const int64_t* bcols;  // transB == 'N' only: column j of op(B) is stored column bcols[j]
+};
+cudaError_t launch_gemm(const GemmArgs& g, int splits, double* partial, cudaStream_t st);
+int gemm_pick_splits(int64_t M, int64_t N, int64_t K, int num_sms);
+
+// ---- sample_qrcp.cu: partial QRCP (Alg. 1, b steps) on the l x nc sample.
+struct SampleQrcpArgs {
+  double* B;          // l x nc, ld = l; overwritten by S in the permuted order
+  int ell;
+  int64_t nc;
+  int steps;          // bJ
+  int64_t* swaps;     // out: steps entries, partner position of each swap
+  double* cand;       // scratch: 2 * grid * 2 doubles (value, position)
+  double* candcol;    // scratch: 2 * grid * l doubles
+  GridBarrier* bar;
+  int* status;
+};
+cudaError_t launch_sample_qrcp(const SampleQrcpArgs& a, int num_sms, cudaStream_t st);
+bool sample_qrcp_fits(int ell, int64_t nc, int num_sms);
+
+// ---- permute.cu: apply the swap sequence of one block to whole columns.
+// A: m rows, columns col0 + (0..nc); swaps relative to col0.  jpvt (may be
+// null) moves alongside.  `map` scratch: 1 + 10 * steps int64, `buf` scratch:
+// m * 2 * steps doubles.  m may be 0 (then only jpvt moves).
+cudaError_t launch_apply_swaps(double* A, int64_t lda, int64_t m, int64_t col0,
+                               const int64_t* swaps, int steps, int64_t* jpvt, int64_t* map,
+                               double* buf, cudaStream_t st);
+cudaError_t launch_iota(int64_t* v, int64_t n, cudaStream_t st);
+// dst(:, t) = src(r0:r0+rows, idx[t]) for t < ncols (column gather through a map)
+cudaError_t launch_gather_cols(const double* src, int64_t lds, int64_t r0, int64_t rows,
+                               const int64_t* idx, int64_t ncols, double* dst, int64_t ldd,
+                               cudaStream_t st);
+// dst(idx[c], r) = src(r, c): scatter-transpose of a rows x ncols block
+cudaError_t launch_scatter_transpose(const double* src, int64_t lds, int64_t rows,
+                                     const int64_t* idx, int64_t ncols, double* dst, int64_t ldd,
+                                     cudaStream_t st);
+// Y(:, c) explicit from in-place storage F (rows x cols): unit diagonal,
+// zeros above, F below; R part (upper triangle, zeros below) into Rout.
+cudaError_t launch_split_qr(const double* F, int64_t ldf, int64_t rows, int64_t cols, int64_t yrow0,
+                            double* Y, int64_t ldy, double* Rout, int64_t ldr, cudaStream_t st);
+
+// ---- panel.cu: Householder panel QR (unblocked, cooperative) of the
+// mJ x bJ panel P (ld), tau out, T (bJ x bJ, ld bJ) the compact-WY factor.
+struct PanelArgs {
+  double* P;
+  int64_t ld;
+  int64_t mJ;
+  int bJ;
+  double* tau;
+  double* T;          // out, bJ x bJ, column-major, zeros below the diagonal
+  double* partial;    // scratch: grid * (bJ + 1) * 2 doubles + grid * bJ * bJ
+  double* rowj;       // scratch: bJ doubles
+  GridBarrier* bar;
+  int* status;
+};
+cudaError_t launch_panel(const PanelArgs& a, int num_sms, cudaStream_t st);
+size_t panel_partial_doubles(int grid, int bJ);
+int panel_grid(int64_t mJ, int bJ, int num_sms);
+bool panel_fits(int64_t mJ, int bJ, int num_sms);
+
+// ---- sample_update.cu: W11 = S11 R11^{-1} (bJ x bJ, ld bJ).  Sets *flag to 1
+// (and ORs RQRCP_INFO_RESAMPLED into status) when R11 has an exact zero
+// diagonal entry, else 0.
+cudaError_t launch_w11(const double* S, int ell, const double* R11, int64_t ldr, int bJ,
+                       double* W11, int* flag, int* status, cudaStream_t st);
+
+// Q = first cols columns of the rows x rows identity
+cudaError_t launch_eye(double* Q, int64_t rows, int64_t cols, int64_t ld, cudaStream_t st);
+// Fill / copy helpers
+cudaError_t launch_fill(double* X, int64_t rows, int64_t cols, int64_t ld, double v,
+                        cudaStream_t st);
+cudaError_t launch_copy2d(const double* src, int64_t lds, double* dst, int64_t ldd,
+                          int64_t rows, int64_t cols, cudaStream_t st);
+
+}  // namespace rq

@@ -1,0 +1,219 @@
+// Householder panel QR of the m_J x b_J leading columns of the trailing
+// matrix (the reflector-construction step of Alg. 4 and Alg. 6) and the
+// upper-triangular compact-WY factor T with Q = I - Y T Y^T (Sec. 2.2).
+//
+// One cooperative launch.  CTA g keeps a contiguous range of panel rows in
+// shared memory.  Column j costs one grid barrier: before it every CTA
+// publishes, over its rows below row j, the dot products of column j with
+// columns j..b_J-1 (the j-th entry is the squared tail norm), and the owner
+// of row j publishes that row.  After it every CTA adds the partial sums in
+// the same fixed order, so all CTAs derive the same reflector
+//   beta = -sign(alpha) ||x||, tau = (beta - alpha)/beta, v = x/(alpha - beta),
+// and the same w_c = tau v^T a_c = tau (a_jc + (x^T a_c)_tail/(alpha - beta)),
+// update their rows, and compute the partial sums of the next column.
+// Finally the CTAs publish partial Gram matrices Y^T Y of their rows, CTA 0
+// adds them and builds T column by column:
+//   T(i,i) = tau_i,  T(0:i, i) = -tau_i T(0:i,0:i) (Y^T Y)(0:i, i).
+#include "kernels.cuh"
+
+namespace rq {
+namespace {
+
+constexpr int NT = 256;
+constexpr int MAXB = 128;
+constexpr int PARTS = 4;
+
+__global__ void __launch_bounds__(NT, 1) panel_kernel(PanelArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int bJ = a.bJ;
+  const int G = gridDim.x, g = blockIdx.x;
+  const int64_t chunk = (a.mJ + G - 1) / G;
+  const int64_t r_lo = (int64_t)g * chunk;
+  const int nrow = (int)imax64(0, imin64(a.mJ, r_lo + chunk) - r_lo);
+  double* Ps = reinterpret_cast<double*>(smem_raw);  // chunk x bJ, ld = chunk
+  __shared__ double s_tot[MAXB];
+  __shared__ double s_w[MAXB];
+  __shared__ double s_part[PARTS][MAXB];
+  __shared__ double s_scal[4];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = NT / 32;
+
+  for (int64_t e = tid; e < (int64_t)nrow * bJ; e += NT) {
+    const int64_t r = e % nrow, c = e / nrow;
+    Ps[r + c * chunk] = a.P[(r_lo + r) + c * a.ld];
+  }
+  __syncthreads();
+
+  double* part_base = a.partial;  // 2 x G x bJ (column dots), then G x bJ x bJ (Gram)
+  // partial dots of column j with columns j..bJ-1 over owned rows below row j
+  auto publish = [&](int j) {
+    double* part = part_base + (size_t)(j & 1) * G * bJ + (size_t)g * bJ;
+    const int64_t rstart = imax64(0, (int64_t)j + 1 - r_lo);  // local first row > j
+    for (int c = j + warp; c < bJ; c += nwarps) {
+      double s = 0.0;
+      for (int64_t r = rstart + lane; r < nrow; r += 32) s = fma(Ps[r + j * chunk], Ps[r + c * chunk], s);
+      s = warp_sum(s);
+      if (lane == 0) part[c] = s;
+    }
+    if (j >= r_lo && j < r_lo + nrow) {
+      double* rowj = a.rowj + (size_t)(j & 1) * bJ;
+      for (int c = j + tid; c < bJ; c += NT) rowj[c] = Ps[(j - r_lo) + c * chunk];
+    }
+  };
+
+  publish(0);
+  for (int j = 0; j < bJ; ++j) {
+    if (!grid_barrier(a.bar, G, a.status)) return;
+    // fixed-order reduction of the partial dots
+    const double* part = part_base + (size_t)(j & 1) * G * bJ;
+    for (int e = tid; e < PARTS * bJ; e += NT) {
+      const int c = e % bJ, pp = e / bJ;
+      double s = 0.0;
+      if (c >= j)
+        for (int q = pp; q < G; q += PARTS) s += __ldcg(part + (size_t)q * bJ + c);
+      s_part[pp][c] = s;
+    }
+    __syncthreads();
+    const double* rowj = a.rowj + (size_t)(j & 1) * bJ;
+    for (int c = j + tid; c < bJ; c += NT) {
+      double s = 0.0;
+#pragma unroll
+      for (int pp = 0; pp < PARTS; ++pp) s += s_part[pp][c];
+      s_tot[c] = s;
+      s_w[c] = __ldcg(rowj + c);  // row j of the panel before this step
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double beta, tau, scale;
+      house_scalars(s_w[j], sqrt(s_tot[j]), &beta, &tau, &scale);
+      s_scal[0] = beta;
+      s_scal[1] = tau;
+      s_scal[2] = scale;
+      if (g == 0) a.tau[j] = tau;
+    }
+    __syncthreads();
+    const double beta = s_scal[0], tau = s_scal[1], scale = s_scal[2];
+    // w_c = tau * v^T a_c for c > j (v_j = 1, v_r = scale x_r below)
+    for (int c = j + 1 + tid; c < bJ; c += NT) s_w[c] = tau * (s_w[c] + scale * s_tot[c]);
+    __syncthreads();
+    const int64_t jl = (int64_t)j - r_lo;  // local index of row j (may be outside)
+    const int64_t rstart = imax64(0, jl + 1);
+    // scale column j into v, then a_rc -= v_r w_c on owned rows below j
+    for (int64_t r = rstart + tid; r < nrow; r += NT) Ps[r + j * chunk] *= scale;
+    __syncthreads();
+    if (tau != 0.0) {
+      const int ncols = bJ - j - 1;
+      const int64_t rows = nrow - rstart;
+      for (int64_t e = tid; e < rows * ncols; e += NT) {
+        const int64_t r = rstart + e % rows;
+        const int c = j + 1 + (int)(e / rows);
+        Ps[r + c * chunk] = fma(-Ps[r + j * chunk], s_w[c], Ps[r + c * chunk]);
+      }
+    }
+    if (jl >= 0 && jl < nrow) {
+      // row j: R entries
+      for (int c = j + 1 + tid; c < bJ; c += NT) Ps[jl + c * chunk] -= (tau != 0.0) ? s_w[c] : 0.0;
+      if (tid == 0) Ps[jl + j * chunk] = beta;
+    }
+    __syncthreads();
+    if (j + 1 < bJ) publish(j + 1);
+  }
+
+  // write the factored rows back
+  for (int64_t e = tid; e < (int64_t)nrow * bJ; e += NT) {
+    const int64_t r = e % nrow, c = e / nrow;
+    a.P[(r_lo + r) + c * a.ld] = Ps[r + c * chunk];
+  }
+  // partial Gram Y^T Y over owned rows (upper triangle, Y unit lower)
+  double* gram = part_base + (size_t)2 * G * bJ + (size_t)g * bJ * bJ;
+  for (int e = tid; e < bJ * bJ; e += NT) {
+    const int c1 = e % bJ, c2 = e / bJ;  // entry (c1, c2), c1 <= c2
+    if (c1 > c2) continue;
+    double s = 0.0;
+    for (int64_t r = 0; r < nrow; ++r) {
+      const int64_t R = r_lo + r;
+      if (R < c2) continue;
+      const double y2 = (R == c2) ? 1.0 : Ps[r + c2 * chunk];
+      const double y1 = (R == c1) ? 1.0 : Ps[r + c1 * chunk];
+      s = fma(y1, y2, s);
+    }
+    gram[c1 + c2 * bJ] = s;
+  }
+  if (!grid_barrier(a.bar, G, a.status)) return;
+  if (g != 0) return;
+  // CTA 0: add the Gram partials in fixed order (reuse the panel smem), build T
+  double* Gs = Ps;  // bJ x bJ
+  for (int e = tid; e < bJ * bJ; e += NT) {
+    const int c1 = e % bJ, c2 = e / bJ;
+    double s = 0.0;
+    if (c1 <= c2)
+      for (int q = 0; q < G; ++q) s += __ldcg(part_base + (size_t)2 * G * bJ + (size_t)q * bJ * bJ + e);
+    Gs[e] = s;
+  }
+  __syncthreads();
+  double* T = a.T;
+  for (int e = tid; e < bJ * bJ; e += NT) T[e] = 0.0;
+  __syncthreads();
+  for (int i = 0; i < bJ; ++i) {
+    const double ti = __ldcg(a.tau + i);
+    // T(0:i, i) = -tau_i T(0:i, 0:i) G(0:i, i)
+    if (tid < i) {
+      double s = 0.0;
+      for (int t = tid; t < i; ++t) s = fma(T[tid + t * bJ], Gs[t + i * bJ], s);
+      s_w[tid] = -ti * s;
+    }
+    __syncthreads();
+    if (tid < i) T[tid + i * bJ] = s_w[tid];
+    if (tid == 0) T[i + i * bJ] = ti;
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+int panel_grid(int64_t mJ, int bJ, int num_sms) {
+  int64_t G = (mJ + 31) / 32;
+  if (G > num_sms) G = num_sms;
+  if (G < 1) G = 1;
+  return (int)G;
+}
+
+size_t panel_partial_doubles(int grid, int bJ) {
+  return (size_t)2 * grid * bJ + (size_t)grid * bJ * bJ;
+}
+
+static size_t panel_smem(int64_t chunk, int bJ) {
+  size_t a = (size_t)chunk * bJ * 8;
+  size_t b = (size_t)bJ * bJ * 8;
+  return a > b ? a : b;
+}
+
+bool panel_fits(int64_t mJ, int bJ, int num_sms) {
+  if (bJ < 1 || bJ > MAXB) return false;
+  const int G = panel_grid(mJ, bJ, num_sms);
+  const int64_t chunk = (mJ + G - 1) / G;
+  return panel_smem(chunk, bJ) <= 216 * 1024;
+}
+
+cudaError_t launch_panel(const PanelArgs& a, int num_sms, cudaStream_t st) {
+  if (a.bJ > MAXB || a.bJ < 1) return cudaErrorInvalidValue;
+  const int G = panel_grid(a.mJ, a.bJ, num_sms);
+  const int64_t chunk = (a.mJ + G - 1) / G;
+  const size_t smem = panel_smem(chunk, a.bJ);
+  if (smem > 216 * 1024) return cudaErrorInvalidValue;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         216 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  cudaError_t e = cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), st);
+  if (e != cudaSuccess) return e;
+  PanelArgs args = a;
+  void* params[] = {&args};
+  return cudaLaunchCooperativeKernel((const void*)panel_kernel, dim3((unsigned)G), dim3(NT), params,
+                                     smem, st);
+}
+
+}  // namespace rq

@@ -1,0 +1,250 @@
+// Column permutation of one block (Alg. 4: permute A^[J-1] and the completed
+// rows of R with P_b^[J]) plus small utility kernels.
+//
+// The b swaps chosen on the sample (position i <-> swaps[i], in order) are
+// composed on the device into at most 2b (destination, source) moves; whole
+// columns (all m rows, so completed rows of R move too) are gathered into
+// scratch and scattered back, 16-byte vectorised when the layout allows.
+// jpvt moves alongside.  The pivot list never leaves the device.
+#include "kernels.cuh"
+
+namespace rq {
+namespace {
+
+// map layout: map[0] = number of moves; moves at map[1 + 2t] (dest), map[2 + 2t] (src);
+// work area for the composition follows at map[1 + 4*steps].
+__global__ void compose_swaps(const int64_t* __restrict__ swaps, int steps, int64_t* map) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int64_t* pos = map + 1 + 4 * steps;      // touched positions
+  int64_t* content = pos + 2 * steps;      // original position held there
+  int ntouch = 0;
+  for (int i = 0; i < steps; ++i) {
+    const int64_t s = swaps[i];
+    if (s == i) continue;
+    int ia = -1, ib = -1;
+    for (int t = 0; t < ntouch; ++t) {
+      if (pos[t] == i) ia = t;
+      if (pos[t] == s) ib = t;
+    }
+    if (ia < 0) { pos[ntouch] = i; content[ntouch] = i; ia = ntouch++; }
+    if (ib < 0) { pos[ntouch] = s; content[ntouch] = s; ib = ntouch++; }
+    int64_t tmp = content[ia];
+    content[ia] = content[ib];
+    content[ib] = tmp;
+  }
+  int nm = 0;
+  for (int t = 0; t < ntouch; ++t) {
+    if (content[t] != pos[t]) {
+      map[1 + 2 * nm] = pos[t];
+      map[2 + 2 * nm] = content[t];
+      ++nm;
+    }
+  }
+  map[0] = nm;
+}
+
+// gather (dir = 0): buf[:, t] = A[:, col0 + src_t]; scatter (dir = 1):
+// A[:, col0 + dest_t] = buf[:, t].  blockIdx.y = move index.
+template <bool VEC>
+__global__ void move_columns(double* __restrict__ A, int64_t lda, int64_t m, int64_t col0,
+                             const int64_t* __restrict__ map, double* __restrict__ buf,
+                             int64_t* __restrict__ jpvt, int64_t* __restrict__ jbuf, int dir) {
+  const int t = blockIdx.y;
+  if (t >= map[0]) return;
+  const int64_t dest = map[1 + 2 * t], src = map[2 + 2 * t];
+  const int64_t acol = col0 + (dir == 0 ? src : dest);
+  double* a = A + acol * lda;
+  double* bb = buf + (int64_t)t * m;
+  if (VEC) {
+    const int64_t m2 = m / 2;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m2;
+         r += (int64_t)gridDim.x * blockDim.x) {
+      if (dir == 0) reinterpret_cast<double2*>(bb)[r] = reinterpret_cast<const double2*>(a)[r];
+      else reinterpret_cast<double2*>(a)[r] = reinterpret_cast<const double2*>(bb)[r];
+    }
+    if ((m & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+      if (dir == 0) bb[m - 1] = a[m - 1];
+      else a[m - 1] = bb[m - 1];
+    }
+  } else {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m;
+         r += (int64_t)gridDim.x * blockDim.x) {
+      if (dir == 0) bb[r] = a[r];
+      else a[r] = bb[r];
+    }
+  }
+  if (jpvt != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (dir == 0) jbuf[t] = jpvt[col0 + src];
+    else jpvt[col0 + dest] = jbuf[t];
+  }
+}
+
+__global__ void iota_kernel(int64_t* v, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = i;
+}
+
+__global__ void fill_kernel(double* X, int64_t rows, int64_t cols, int64_t ld, double v) {
+  const int64_t total = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x)
+    X[(e % rows) + (e / rows) * ld] = v;
+}
+
+__global__ void copy2d_kernel(const double* __restrict__ src, int64_t lds, double* __restrict__ dst,
+                              int64_t ldd, int64_t rows, int64_t cols) {
+  const int64_t total = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % rows, c = e / rows;
+    dst[r + c * ldd] = src[r + c * lds];
+  }
+}
+
+unsigned grid_for(int64_t work, int threads, int64_t cap) {
+  int64_t b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+cudaError_t launch_apply_swaps(double* A, int64_t lda, int64_t m, int64_t col0,
+                               const int64_t* swaps, int steps, int64_t* jpvt, int64_t* map,
+                               double* buf, cudaStream_t st) {
+  if (steps <= 0) return cudaSuccess;
+  compose_swaps<<<1, 32, 0, st>>>(swaps, steps, map);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int64_t* jbuf = map + 1 + 8 * (int64_t)steps;
+  const bool vec = (lda % 2 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
+                   ((reinterpret_cast<uintptr_t>(buf) & 15) == 0) && (m % 2 == 0);
+  const int threads = 256;
+  dim3 grid(grid_for(vec ? m / 2 : m, threads, 64), (unsigned)(2 * steps));
+  for (int dir = 0; dir < 2; ++dir) {
+    if (vec) move_columns<true><<<grid, threads, 0, st>>>(A, lda, m, col0, map, buf, jpvt, jbuf, dir);
+    else move_columns<false><<<grid, threads, 0, st>>>(A, lda, m, col0, map, buf, jpvt, jbuf, dir);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_iota(int64_t* v, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  iota_kernel<<<grid_for(n, 256, 1024), 256, 0, st>>>(v, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill(double* X, int64_t rows, int64_t cols, int64_t ld, double v,
+                        cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  fill_kernel<<<grid_for(rows * cols, 256, 152 * 16), 256, 0, st>>>(X, rows, cols, ld, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy2d(const double* src, int64_t lds, double* dst, int64_t ldd,
+                          int64_t rows, int64_t cols, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  copy2d_kernel<<<grid_for(rows * cols, 256, 152 * 16), 256, 0, st>>>(src, lds, dst, ldd, rows,
+                                                                        cols);
+  return cudaGetLastError();
+}
+
+}  // namespace rq
+
+namespace rq {
+namespace {
+
+__global__ void gather_cols_kernel(const double* __restrict__ src, int64_t lds, int64_t r0,
+                                   int64_t rows, const int64_t* __restrict__ idx, int64_t ncols,
+                                   double* __restrict__ dst, int64_t ldd) {
+  const int64_t total = rows * ncols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % rows, t = e / rows;
+    dst[r + t * ldd] = src[(r0 + r) + idx[t] * lds];
+  }
+}
+
+__global__ void scatter_transpose_kernel(const double* __restrict__ src, int64_t lds, int64_t rows,
+                                         const int64_t* __restrict__ idx, int64_t ncols,
+                                         double* __restrict__ dst, int64_t ldd) {
+  const int64_t total = rows * ncols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % rows, c = e / rows;
+    dst[idx[c] + r * ldd] = src[r + c * lds];
+  }
+}
+
+__global__ void split_qr_kernel(const double* __restrict__ F, int64_t ldf, int64_t rows,
+                                int64_t cols, int64_t yrow0, double* __restrict__ Y, int64_t ldy,
+                                double* __restrict__ R, int64_t ldr) {
+  const int64_t total = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % rows, c = e / rows;
+    const double f = F[r + c * ldf];
+    if (Y != nullptr) Y[(yrow0 + r) + c * ldy] = (r > c) ? f : (r == c ? 1.0 : 0.0);
+    if (R != nullptr && r < cols) R[r + c * ldr] = (r <= c) ? f : 0.0;
+  }
+}
+
+unsigned grid2(int64_t work) {
+  int64_t b = (work + 255) / 256;
+  if (b < 1) b = 1;
+  if (b > 152 * 16) b = 152 * 16;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+cudaError_t launch_gather_cols(const double* src, int64_t lds, int64_t r0, int64_t rows,
+                               const int64_t* idx, int64_t ncols, double* dst, int64_t ldd,
+                               cudaStream_t st) {
+  if (rows <= 0 || ncols <= 0) return cudaSuccess;
+  gather_cols_kernel<<<grid2(rows * ncols), 256, 0, st>>>(src, lds, r0, rows, idx, ncols, dst, ldd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_transpose(const double* src, int64_t lds, int64_t rows,
+                                     const int64_t* idx, int64_t ncols, double* dst, int64_t ldd,
+                                     cudaStream_t st) {
+  if (rows <= 0 || ncols <= 0) return cudaSuccess;
+  scatter_transpose_kernel<<<grid2(rows * ncols), 256, 0, st>>>(src, lds, rows, idx, ncols, dst,
+                                                                 ldd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_qr(const double* F, int64_t ldf, int64_t rows, int64_t cols, int64_t yrow0,
+                            double* Y, int64_t ldy, double* Rout, int64_t ldr, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  split_qr_kernel<<<grid2(rows * cols), 256, 0, st>>>(F, ldf, rows, cols, yrow0, Y, ldy, Rout, ldr);
+  return cudaGetLastError();
+}
+
+}  // namespace rq
+
+namespace rq {
+namespace {
+__global__ void eye_kernel(double* Q, int64_t rows, int64_t cols, int64_t ld) {
+  const int64_t total = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % rows, c = e / rows;
+    Q[r + c * ld] = (r == c) ? 1.0 : 0.0;
+  }
+}
+}  // namespace
+
+cudaError_t launch_eye(double* Q, int64_t rows, int64_t cols, int64_t ld, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  int64_t b = (rows * cols + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  eye_kernel<<<(unsigned)b, 256, 0, st>>>(Q, rows, cols, ld);
+  return cudaGetLastError();
+}
+}  // namespace rq

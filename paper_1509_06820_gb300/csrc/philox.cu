@@ -1,0 +1,77 @@
+// Seeded Gaussian i.i.d. matrix: the compression matrix Omega of Alg. 4
+// (and re-samples of Alg. 5), from Philox4x32-10 (Salmon, Moraes, Dror and
+// Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11) and the
+// Box-Muller transform.  One thread per (column r, row pair q): a single
+// Philox block gives the two normals of rows 2q and 2q+1.
+#include "kernels.cuh"
+
+namespace rq {
+namespace {
+
+// Philox4x32 round multipliers and Weyl key increments (Salmon et al. SC'11).
+constexpr uint32_t kM0 = 0xD2511F53u;
+constexpr uint32_t kM1 = 0xCD9E8D57u;
+constexpr uint32_t kW0 = 0x9E3779B9u;
+constexpr uint32_t kW1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k.x += kW0;
+      k.y += kW1;
+    }
+    uint32_t hi0 = __umulhi(kM0, c.x), lo0 = kM0 * c.x;
+    uint32_t hi1 = __umulhi(kM1, c.z), lo1 = kM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// (top 52 bits of hi:lo + 1/2) * 2^-52, strictly inside (0, 1).
+__device__ __forceinline__ double unit_open(uint32_t lo, uint32_t hi) {
+  uint64_t t = ((uint64_t)hi << 20) | (uint64_t)(lo >> 12);
+  return ((double)t + 0.5) * 0x1.0p-52;
+}
+
+__global__ void gaussian_kernel(uint2 key, uint32_t stream_id, int64_t rows, int64_t cols,
+                                int64_t npairs, double* __restrict__ out, int64_t ld,
+                                const int* gate) {
+  if (gate != nullptr && *gate == 0) return;
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t total = npairs * cols;
+  for (; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    // pairs fastest so that a warp writes neighbouring rows of one column
+    int64_t q = idx % npairs;
+    int64_t r = idx / npairs;
+    uint4 c = make_uint4((uint32_t)(uint64_t)r, (uint32_t)((uint64_t)r >> 32), (uint32_t)q,
+                         stream_id);
+    uint4 x = philox10(c, key);
+    double u1 = unit_open(x.x, x.y);
+    double u2 = unit_open(x.z, x.w);
+    double rho = sqrt(-2.0 * log(u1));
+    double s, co;
+    sincospi(2.0 * u2, &s, &co);
+    int64_t i0 = 2 * q;
+    out[i0 + r * ld] = rho * co;
+    if (i0 + 1 < rows) out[i0 + 1 + r * ld] = rho * s;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gaussian(uint64_t seed, uint32_t stream_id, int64_t rows, int64_t cols,
+                            double* out, int64_t ld, const int* gate, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  int64_t npairs = (rows + 1) / 2;
+  int64_t total = npairs * cols;
+  int threads = 256;
+  int64_t blocks = (total + threads - 1) / threads;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  gaussian_kernel<<<(unsigned)blocks, threads, 0, st>>>(key, stream_id, rows, cols, npairs, out,
+                                                         ld, gate);
+  return cudaGetLastError();
+}
+
+}  // namespace rq

@@ -1,0 +1,725 @@
+// Host orchestrator and C ABI (include/rqrcp.h).
+//
+// Every public call validates its arguments, takes its scratch from the
+// handle and enqueues kernels on the handle's stream; nothing waits for the
+// device inside a call, the pivot list never travels to the host, and the
+// launch sequence depends only on (m, n, k, b, p), so a whole factorization
+// can be captured in a CUDA graph once its scratch is reserved.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+struct rqrcp_handle_s {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 1;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  int* state = nullptr;  // [0] status word, [1] re-sample flag; barrier at byte 64
+  std::string err;
+  // instrumentation
+  bool prof = false;
+  std::vector<cudaEvent_t> events;  // pool, pairs (2i, 2i+1)
+  std::vector<int> ev_phase;
+  size_t ev_used = 0;
+  double flops[RQRCP_NPHASE] = {};
+  int64_t launches[RQRCP_NPHASE] = {};
+  int64_t launch_total = 0;
+  int cur_phase = 7;
+};
+
+namespace {
+
+using rq::GemmArgs;
+
+constexpr int kMaxB = 128;
+constexpr int kMaxEll = 192;
+constexpr uint32_t kOmegaStream = 1;
+constexpr uint32_t kResampleStreamBase = 0x100;
+
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Scratch layout of one call; a sizing pass runs with base == nullptr.
+struct Work {
+  double* omega = nullptr;    // l x m (also the re-sample matrix)
+  double* B = nullptr;        // l x n sample
+  int64_t* swaps = nullptr;   // b
+  int64_t* map = nullptr;     // 1 + 10 b
+  double* permbuf = nullptr;  // rows x 2b (column moves)
+  double* cand = nullptr;     // 2 x sms x 2
+  double* candcol = nullptr;  // 2 x sms x l
+  double* ppart = nullptr;    // panel partial sums
+  double* rowj = nullptr;     // 2 b
+  double* T = nullptr;        // b x b
+  double* Z = nullptr;        // b x n
+  double* W = nullptr;        // b x n
+  double* skpart = nullptr;   // split-K partial sums
+  size_t skcap = 0;
+  double* W11 = nullptr;      // b x b
+  // TRQRCP / TUXV
+  double* Wt = nullptr;       // k x n
+  double* Ahat = nullptr;     // m x b
+  double* YY = nullptr;       // b x k
+  double* OY = nullptr;       // l x k
+  // TUXV
+  double* Yk = nullptr;       // m x k
+  double* Rk = nullptr;       // k x n
+  int64_t* jpvt = nullptr;    // n
+  double* tau = nullptr;      // k
+  double* tau2 = nullptr;     // k
+  double* Tall = nullptr;     // ceil(k/b) x b x b
+  double* F = nullptr;        // max(m, n) x k copy of reflectors
+  size_t bytes = 0;
+};
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    off = align_up(off);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+Work carve(char op, int64_t m, int64_t n, int64_t k, int b, int p, int sms, char* base) {
+  Work w;
+  Carver c{base};
+  const int64_t ell = b + p;
+  const int64_t bb = b;
+  if (op != 'Q') {
+    w.omega = c.take<double>((size_t)ell * m);
+    w.B = c.take<double>((size_t)ell * n);
+    w.swaps = c.take<int64_t>(bb);
+    w.map = c.take<int64_t>(1 + 10 * bb);
+    const int64_t prow = (op == 'R') ? m : k;
+    w.permbuf = c.take<double>((size_t)std::max<int64_t>(prow, 1) * 2 * bb);
+    w.cand = c.take<double>((size_t)2 * sms * 2);
+    w.candcol = c.take<double>((size_t)2 * sms * ell);
+    w.W11 = c.take<double>((size_t)bb * bb);
+  }
+  w.ppart = c.take<double>(rq::panel_partial_doubles(sms, b));
+  w.rowj = c.take<double>(2 * bb);
+  w.T = c.take<double>((size_t)bb * bb);
+  const int64_t zc = std::max(n, k);
+  w.Z = c.take<double>((size_t)bb * zc);
+  w.W = c.take<double>((size_t)bb * zc);
+  w.skcap = (size_t)4 * sms * 4096 + 4096;
+  w.skpart = c.take<double>(w.skcap);
+  if (op == 'T' || op == 'U') {
+    w.Wt = c.take<double>((size_t)k * n);
+    w.Ahat = c.take<double>((size_t)m * bb);
+    w.YY = c.take<double>((size_t)bb * k);
+    w.OY = c.take<double>((size_t)ell * k);
+  }
+  if (op == 'U') {
+    w.Yk = c.take<double>((size_t)m * k);
+    w.Rk = c.take<double>((size_t)k * n);
+    w.jpvt = c.take<int64_t>(n);
+    w.tau = c.take<double>(k);
+    w.tau2 = c.take<double>(k);
+    w.Tall = c.take<double>((size_t)((k + b - 1) / b) * bb * bb);
+    w.F = c.take<double>((size_t)std::max(m, n) * k);
+  } else if (op == 'Q') {
+    w.Tall = nullptr;
+  }
+  w.bytes = align_up(c.off) + 256;
+  return w;
+}
+
+struct Call {
+  rqrcp_handle_t h;
+  Work w;
+  cudaStream_t st;
+  int* status;
+  int* flag;
+  rq::GridBarrier* bar;
+};
+
+enum Phase { PH_SKETCH = 0, PH_SAMPLE, PH_PERM, PH_PANEL, PH_TRAIL, PH_SUPD, PH_TRQ, PH_OTHER };
+
+// Brackets a phase region with CUDA events when profiling is on and makes it
+// the phase that launch counts are charged to.
+struct PhaseScope {
+  rqrcp_handle_t h;
+  int prev;
+  size_t pair = (size_t)-1;
+  PhaseScope(rqrcp_handle_t hh, int ph, double flops) : h(hh), prev(hh->cur_phase) {
+    h->cur_phase = ph;
+    if (!h->prof) return;
+    h->flops[ph] += flops;
+    if (h->events.size() < 2 * (h->ev_used + 1)) {
+      cudaEvent_t a, b;
+      if (cudaEventCreate(&a) != cudaSuccess) return;
+      if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return;
+      }
+      h->events.push_back(a);
+      h->events.push_back(b);
+      h->ev_phase.push_back(ph);
+    }
+    pair = h->ev_used++;
+    h->ev_phase[pair] = ph;
+    cudaEventRecord(h->events[2 * pair], h->stream);
+  }
+  ~PhaseScope() {
+    if (pair != (size_t)-1) cudaEventRecord(h->events[2 * pair + 1], h->stream);
+    h->cur_phase = prev;
+  }
+};
+
+void count_launch(rqrcp_handle_t h, int n) {
+  h->launch_total += n;
+  if (h->prof) h->launches[h->cur_phase] += n;
+}
+
+#define CK(expr)                                              \
+  do {                                                        \
+    cudaError_t e_ = (expr);                                  \
+    if (e_ != cudaSuccess) {                                  \
+      cl.h->err = std::string(#expr) + ": " + cudaGetErrorString(e_); \
+      return RQRCP_ERR_CUDA;                                  \
+    }                                                         \
+  } while (0)
+
+// CK for a launcher that enqueues n kernels
+#define CKL(n, expr)                 \
+  do {                               \
+    CK(expr);                        \
+    count_launch(cl.h, (n));         \
+  } while (0)
+
+cudaError_t gemm(Call& cl, char ta, char tb, int amode, int64_t M, int64_t N, int64_t K,
+                 double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+                 double beta, double* C, int64_t ldc, const int* gate = nullptr, int gate_run = 0,
+                 const int64_t* bcols = nullptr) {
+  GemmArgs g{ta, tb, amode, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, gate, gate_run, bcols};
+  int s = rq::gemm_pick_splits(M, N, K, cl.h->num_sms);
+  while (s > 1 && (size_t)s * M * N > cl.w.skcap) --s;
+  if (M > 0 && N > 0) count_launch(cl.h, s > 1 && K > 0 ? 2 : 1);
+  return rq::launch_gemm(g, s, cl.w.skpart, cl.st);
+}
+
+int ensure(rqrcp_handle_t h, size_t bytes) {
+  if (h->ws_bytes >= bytes) return RQRCP_OK;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess && h->ws) e = cudaFree(h->ws);
+  h->ws = nullptr;
+  h->ws_bytes = 0;
+  if (e == cudaSuccess) e = cudaMalloc(&h->ws, bytes);
+  if (e != cudaSuccess) {
+    h->ws = nullptr;
+    h->err = std::string("workspace: ") + cudaGetErrorString(e);
+    return RQRCP_ERR_ALLOC;
+  }
+  h->ws_bytes = bytes;
+  return RQRCP_OK;
+}
+
+int begin(rqrcp_handle_t h, char op, int64_t m, int64_t n, int64_t k, int b, int p, Call* cl) {
+  Work sz = carve(op, m, n, k, b, p, h->num_sms, nullptr);
+  int r = ensure(h, sz.bytes);
+  if (r != RQRCP_OK) return r;
+  cl->h = h;
+  cl->w = carve(op, m, n, k, b, p, h->num_sms, h->ws);
+  cl->st = h->stream;
+  cl->status = h->state;
+  cl->flag = h->state + 1;
+  cl->bar = reinterpret_cast<rq::GridBarrier*>(reinterpret_cast<char*>(h->state) + 64);
+  return RQRCP_OK;
+}
+
+// ---------------------------------------------------------------- blocks
+int sample_step(Call& cl, double* Bblk, int ell, int64_t nc, int bJ) {
+  double fl = 0.0;
+  for (int i = 0; i < bJ && i < ell; ++i) fl += 4.0 * (ell - i) * (double)(nc - i - 1);
+  PhaseScope ps(cl.h, PH_SAMPLE, fl);
+  rq::SampleQrcpArgs a{Bblk, ell, nc, bJ, cl.w.swaps, cl.w.cand, cl.w.candcol, cl.bar, cl.status};
+  CKL(1, rq::launch_sample_qrcp(a, cl.h->num_sms, cl.st));
+  return RQRCP_OK;
+}
+
+int panel_step(Call& cl, double* P, int64_t ld, int64_t mJ, int bJ, double* tau, double* T) {
+  const double b = bJ, m = (double)mJ;
+  PhaseScope ps(cl.h, PH_PANEL, 2.0 * m * b * b - 2.0 * b * b * b / 3.0 + m * b * b + b * b * b / 3.0);
+  rq::PanelArgs a{P, ld, mJ, bJ, tau, T, cl.w.ppart, cl.w.rowj, cl.bar, cl.status};
+  CKL(1, rq::launch_panel(a, cl.h->num_sms, cl.st));
+  return RQRCP_OK;
+}
+
+int swaps_step(Call& cl, double* A, int64_t lda, int64_t rows, int64_t col0, int bJ, int64_t* jpvt) {
+  PhaseScope ps(cl.h, PH_PERM, 0.0);
+  CKL(3, rq::launch_apply_swaps(A, lda, rows, col0, cl.w.swaps, bJ, jpvt, cl.w.map, cl.w.permbuf,
+                                cl.st));
+  return RQRCP_OK;
+}
+
+// A2 <- Q^T A2 with Q = I - Y T Y^T; Y = unit-lower part of P (mJ x bJ, ld),
+// A2 mJ x n2 (ld).  Rows 0..bJ-1 of the result are R12.
+int trailing_update(Call& cl, const double* P, int64_t ld, int64_t mJ, int bJ, const double* T,
+                    double* A2, int64_t n2) {
+  if (n2 <= 0) return RQRCP_OK;
+  PhaseScope ps(cl.h, PH_TRAIL, 4.0 * (double)mJ * (double)n2 * bJ + 2.0 * bJ * bJ * (double)n2);
+  CK(gemm(cl, 'T', 'N', 1, bJ, n2, mJ, 1.0, P, ld, A2, ld, 0.0, cl.w.Z, bJ));
+  CK(gemm(cl, 'T', 'N', 0, bJ, n2, bJ, 1.0, T, bJ, cl.w.Z, bJ, 0.0, cl.w.W, bJ));
+  CK(gemm(cl, 'N', 'N', 1, mJ, n2, bJ, -1.0, P, ld, cl.w.W, bJ, 1.0, A2, ld));
+  return RQRCP_OK;
+}
+
+// Unpivoted blocked QR of F (M x N, ldf) in place; T of block J stored at
+// Tall + J*b*b when Tall != nullptr.
+int qr_core(Call& cl, int64_t M, int64_t N, double* F, int64_t ldf, int b, double* tau,
+            double* Tall) {
+  const int64_t k = std::min(M, N);
+  int J = 0;
+  for (int64_t j0 = 0; j0 < k; j0 += b, ++J) {
+    const int bJ = (int)std::min<int64_t>(b, k - j0);
+    double* P = F + j0 + j0 * ldf;
+    double* T = Tall ? Tall + (size_t)J * b * b : cl.w.T;
+    int r = panel_step(cl, P, ldf, M - j0, bJ, tau + j0, T);
+    if (r) return r;
+    r = trailing_update(cl, P, ldf, M - j0, bJ, T, F + j0 + (j0 + bJ) * ldf, N - j0 - bJ);
+    if (r) return r;
+  }
+  return RQRCP_OK;
+}
+
+// Q (M x K, ldq) = first K columns of H_0 ... H_{K-1} from reflectors in F
+// (M x K, ldf) and the block factors Tall.
+int orgqr_core(Call& cl, int64_t M, int64_t K, const double* F, int64_t ldf, int b,
+               const double* Tall, double* Q, int64_t ldq) {
+  // Q starts as the first K columns of the identity
+  {
+    PhaseScope ps(cl.h, PH_OTHER, 0.0);
+    CKL(1, rq::launch_eye(Q, M, K, ldq, cl.st));
+  }
+  PhaseScope ps(cl.h, PH_TRQ, 4.0 * (double)M * (double)K * (double)K);
+  const int nblk = (int)((K + b - 1) / b);
+  for (int J = nblk - 1; J >= 0; --J) {
+    const int64_t j0 = (int64_t)J * b;
+    const int bJ = (int)std::min<int64_t>(b, K - j0);
+    const double* P = F + j0 + j0 * ldf;
+    const double* T = Tall + (size_t)J * b * b;  // ld bJ
+    const int64_t nc = K - j0;                   // columns < j0 of Q are still e_i
+    double* Qb = Q + j0 + j0 * ldq;
+    CK(gemm(cl, 'T', 'N', 1, bJ, nc, M - j0, 1.0, P, ldf, Qb, ldq, 0.0, cl.w.Z, bJ));
+    CK(gemm(cl, 'N', 'N', 0, bJ, nc, bJ, 1.0, T, bJ, cl.w.Z, bJ, 0.0, cl.w.W, bJ));
+    CK(gemm(cl, 'N', 'N', 1, M - j0, nc, bJ, -1.0, P, ldf, cl.w.W, bJ, 1.0, Qb, ldq));
+  }
+  return RQRCP_OK;
+}
+
+int check_handle(rqrcp_handle_t h) { return h ? RQRCP_OK : -1; }
+
+bool sizes_fit(int num_sms, int64_t m, int64_t n, int b, int ell) {
+  if (b > kMaxB || ell > kMaxEll) return false;
+  if (ell > 0 && !rq::sample_qrcp_fits(ell, n, num_sms)) return false;
+  if (!rq::panel_fits(m, b, num_sms)) return false;
+  return true;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+int rqrcp_create(rqrcp_handle_t* handle, void* cuda_stream) {
+  if (!handle) return -1;
+  *handle = nullptr;
+  rqrcp_handle_s* h = new rqrcp_handle_s();
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess) e = cudaMalloc(&h->state, 256);
+  if (e == cudaSuccess) e = cudaMemset(h->state, 0, 256);
+  if (e != cudaSuccess) {
+    if (h->state) cudaFree(h->state);
+    delete h;
+    return RQRCP_ERR_CUDA;
+  }
+  *handle = h;
+  return RQRCP_OK;
+}
+
+int rqrcp_destroy(rqrcp_handle_t h) {
+  if (!h) return -1;
+  cudaStreamSynchronize(h->stream);
+  for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  if (h->ws) cudaFree(h->ws);
+  if (h->state) cudaFree(h->state);
+  delete h;
+  return RQRCP_OK;
+}
+
+int rqrcp_set_stream(rqrcp_handle_t h, void* cuda_stream) {
+  if (!h) return -1;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  return RQRCP_OK;
+}
+
+size_t rqrcp_workspace_bytes(char op, int64_t m, int64_t n, int64_t k, int b, int p) {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (op == 'R' || op == 'Q') k = std::min(m, n);
+  if (b > k) b = (int)std::max<int64_t>(k, 1);
+  return carve(op, m, n, k, b, p, sms, nullptr).bytes;
+}
+
+int rqrcp_reserve(rqrcp_handle_t h, char op, int64_t m, int64_t n, int64_t k, int b, int p) {
+  if (!h) return -1;
+  if (op == 'R' || op == 'Q') k = std::min(m, n);
+  if (b > k) b = (int)std::max<int64_t>(k, 1);
+  return ensure(h, carve(op, m, n, k, b, p, h->num_sms, nullptr).bytes);
+}
+
+int rqrcp_sync_info(rqrcp_handle_t h, int* info) {
+  if (!h) return -1;
+  if (!info) return -2;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(info, h->state, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(h->state, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    h->err = std::string("sync_info: ") + cudaGetErrorString(e);
+    return RQRCP_ERR_CUDA;
+  }
+  return RQRCP_OK;
+}
+
+const char* rqrcp_last_error(rqrcp_handle_t h) { return h ? h->err.c_str() : ""; }
+
+const char* rqrcp_status_string(int code) {
+  switch (code) {
+    case RQRCP_OK: return "ok";
+    case RQRCP_ERR_CUDA: return "CUDA runtime error";
+    case RQRCP_ERR_ALLOC: return "workspace allocation failed";
+    case RQRCP_ERR_UNSUPPORTED: return "size outside the supported limits";
+    case RQRCP_INFO_NONFINITE: return "non-finite input";
+    case RQRCP_INFO_RESAMPLED: return "singular R11: sample re-drawn";
+    case RQRCP_INFO_TIMEOUT: return "device wait timed out";
+    default: return code < 0 ? "invalid argument" : "unknown";
+  }
+}
+
+int rqrcp_gaussian(rqrcp_handle_t h, uint64_t seed, uint32_t stream_id, int64_t rows, int64_t cols,
+                   double* dOut, int64_t ldo) {
+  if (!h) return -1;
+  if (rows < 0) return -4;
+  if (cols < 0) return -5;
+  if (!dOut && rows * cols > 0) return -6;
+  if (ldo < std::max<int64_t>(1, rows)) return -7;
+  Call cl{};
+  cl.h = h;
+  cl.st = h->stream;
+  PhaseScope ps(h, PH_SKETCH, 0.0);
+  CKL(1, rq::launch_gaussian(seed, stream_id, rows, cols, dOut, ldo, nullptr, cl.st));
+  return RQRCP_OK;
+}
+
+int rqrcp_sketch(rqrcp_handle_t h, int64_t m, int64_t n, const double* dA, int64_t lda, int ell,
+                 uint64_t seed, double* dB, int64_t ldb) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (n < 1) return -3;
+  if (!dA) return -4;
+  if (lda < m) return -5;
+  if (ell < 1) return -6;
+  if (!dB) return -8;
+  if (ldb < ell) return -9;
+  Call cl;
+  int r = begin(h, 'S', m, n, 1, 1, ell - 1, &cl);
+  if (r) return r;
+  PhaseScope ps(h, PH_SKETCH, 2.0 * ell * (double)m * (double)n);
+  CKL(1, rq::launch_gaussian(seed, kOmegaStream, ell, m, cl.w.omega, ell, nullptr, cl.st));
+  CK(gemm(cl, 'N', 'N', 0, ell, n, m, 1.0, cl.w.omega, ell, dA, lda, 0.0, dB, ldb));
+  return RQRCP_OK;
+}
+
+int rqrcp_factor(rqrcp_handle_t h, int64_t m, int64_t n, double* dA, int64_t lda, int b, int p,
+                 uint64_t seed, int64_t* d_jpvt, double* d_tau) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (n < 1) return -3;
+  if (!dA) return -4;
+  if (lda < m) return -5;
+  if (b < 1) return -6;
+  if (p < 0) return -7;
+  if (!d_jpvt) return -9;
+  if (!d_tau) return -10;
+  const int64_t k = std::min(m, n);
+  if (b > k) b = (int)k;
+  const int ell = b + p;
+  if (!sizes_fit(h->num_sms, m, n, b, ell)) return RQRCP_ERR_UNSUPPORTED;
+  Call cl;
+  int r = begin(h, 'R', m, n, k, b, p, &cl);
+  if (r) return r;
+  Work& w = cl.w;
+  // Alg. 4: Omega^[0] and the initial sample B^[0] = Omega^[0] A^[0]
+  {
+    PhaseScope ps(cl.h, PH_SKETCH, 2.0 * ell * (double)m * (double)n);
+    CKL(1, rq::launch_gaussian(seed, kOmegaStream, ell, m, w.omega, ell, nullptr, cl.st));
+    CK(gemm(cl, 'N', 'N', 0, ell, n, m, 1.0, w.omega, ell, dA, lda, 0.0, w.B, ell));
+    CKL(1, rq::launch_iota(d_jpvt, n, cl.st));
+  }
+  int J = 0;
+  for (int64_t j0 = 0; j0 < k; j0 += b) {
+    ++J;
+    const int bJ = (int)std::min<int64_t>(b, k - j0);
+    const int64_t nc = n - j0, n2 = nc - bJ, mJ = m - j0;
+    double* Bblk = w.B + j0 * ell;
+    // b pivots from the sample; S left in B in the permuted order
+    if ((r = sample_step(cl, Bblk, ell, nc, bJ))) return r;
+    // permute whole columns of the A/R array and jpvt
+    if ((r = swaps_step(cl, dA, lda, m, j0, bJ, d_jpvt))) return r;
+    // reflectors and R11 from the new leading columns, then T
+    double* P = dA + j0 + j0 * lda;
+    if ((r = panel_step(cl, P, lda, mJ, bJ, d_tau + j0, w.T))) return r;
+    // R12 and the trailing matrix A^[J]
+    if ((r = trailing_update(cl, P, lda, mJ, bJ, w.T, dA + j0 + (j0 + bJ) * lda, n2))) return r;
+    if (j0 + bJ < k) {
+      PhaseScope ps(cl.h, PH_SUPD, (double)bJ * bJ * bJ / 3.0 + 2.0 * bJ * bJ * (double)n2);
+      // Eq. (3): B1 = S12 - S11 R11^{-1} R12, B2 = S22 (in place)
+      CKL(1, rq::launch_w11(Bblk, ell, P, lda, bJ, w.W11, cl.flag, cl.status, cl.st));
+      double* Bnext = Bblk + (int64_t)bJ * ell;
+      CK(gemm(cl, 'N', 'N', 2, bJ, n2, bJ, -1.0, w.W11, bJ, dA + j0 + (j0 + bJ) * lda, lda, 1.0,
+              Bnext, ell, cl.flag, 0));
+      // exactly singular R11: fresh sample of the trailing matrix (Alg. 5 step)
+      const int64_t mt = m - j0 - bJ;
+      CKL(1, rq::launch_gaussian(seed, kResampleStreamBase + J, ell, mt, w.omega, ell, cl.flag, cl.st));
+      CK(gemm(cl, 'N', 'N', 0, ell, n2, mt, 1.0, w.omega, ell, dA + (j0 + bJ) + (j0 + bJ) * lda,
+              lda, 0.0, Bnext, ell, cl.flag, 1));
+    }
+  }
+  return RQRCP_OK;
+}
+
+int qr_factor(rqrcp_handle_t h, int64_t m, int64_t n, double* dA, int64_t lda, int b,
+              double* d_tau) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (n < 1) return -3;
+  if (!dA) return -4;
+  if (lda < m) return -5;
+  if (b < 1) return -6;
+  if (!d_tau) return -7;
+  const int64_t k = std::min(m, n);
+  if (b > k) b = (int)k;
+  if (!sizes_fit(h->num_sms, m, n, b, 0)) return RQRCP_ERR_UNSUPPORTED;
+  Call cl;
+  int r = begin(h, 'Q', m, n, k, b, 0, &cl);
+  if (r) return r;
+  return qr_core(cl, m, n, dA, lda, b, d_tau, nullptr);
+}
+
+namespace {
+
+// Alg. 6 on device buffers; Y (m x k, ldy) and R (k x n, ldr) outputs.
+int trqrcp_core(Call& cl, int64_t m, int64_t n, const double* dA, int64_t lda, int64_t k, int b,
+                int ell, uint64_t seed, int64_t* jpvt, double* tau, double* Y, int64_t ldy,
+                double* R, int64_t ldr) {
+  Work& w = cl.w;
+  int r;
+  {
+    PhaseScope ps(cl.h, PH_SKETCH, 2.0 * ell * (double)m * (double)n);
+    CKL(1, rq::launch_gaussian(seed, kOmegaStream, ell, m, w.omega, ell, nullptr, cl.st));
+    CK(gemm(cl, 'N', 'N', 0, ell, n, m, 1.0, w.omega, ell, dA, lda, 0.0, w.B, ell));
+  }
+  {
+    PhaseScope ps(cl.h, PH_OTHER, 0.0);
+    CKL(1, rq::launch_iota(jpvt, n, cl.st));
+    CKL(1, rq::launch_fill(Y, m, k, ldy, 0.0, cl.st));
+    CKL(1, rq::launch_fill(R, k, n, ldr, 0.0, cl.st));
+    CKL(1, rq::launch_fill(w.Wt, k, n, k, 0.0, cl.st));
+  }
+  int J = 0;
+  for (int64_t j0 = 0; j0 < k; j0 += b) {
+    ++J;
+    const int bJ = (int)std::min<int64_t>(b, k - j0);
+    const int64_t nc = n - j0, n2 = nc - bJ, mJ = m - j0;
+    double* Bblk = w.B + j0 * ell;
+    if ((r = sample_step(cl, Bblk, ell, nc, bJ))) return r;
+    // permute jpvt, prior inner products W^T and completed rows of R
+    if ((r = swaps_step(cl, w.Wt, k, j0, j0, bJ, jpvt))) return r;
+    if ((r = swaps_step(cl, R, ldr, j0, j0, bJ, nullptr))) return r;
+    {
+      // selected columns A_hat = A(:, sel) - Y1 W1^T(:, sel), rows j0..m-1
+      PhaseScope ps(cl.h, PH_TRQ, 2.0 * (double)mJ * bJ * (double)j0);
+      CKL(1, rq::launch_gather_cols(dA, lda, j0, mJ, jpvt + j0, bJ, w.Ahat, m, cl.st));
+      if (j0 > 0)
+        CK(gemm(cl, 'N', 'N', 0, mJ, bJ, j0, -1.0, Y + j0, ldy, w.Wt + j0 * k, k, 1.0, w.Ahat, m));
+    }
+    if ((r = panel_step(cl, w.Ahat, m, mJ, bJ, tau + j0, w.T))) return r;
+    {
+      PhaseScope ps(cl.h, PH_OTHER, 0.0);
+      CKL(1, rq::launch_split_qr(w.Ahat, m, mJ, bJ, j0, Y + j0 * ldy, ldy, R + j0 + j0 * ldr, ldr,
+                                 cl.st));
+    }
+    if (n2 > 0) {
+      PhaseScope ps(cl.h, PH_TRQ,
+                    2.0 * bJ * (double)mJ * (double)n2 + 2.0 * bJ * (double)mJ * j0 +
+                        2.0 * bJ * (double)j0 * (double)n2 + 2.0 * bJ * bJ * (double)n2 +
+                        2.0 * bJ * (double)(j0 + bJ) * (double)n2);
+      const int64_t* tcols = jpvt + j0 + bJ;
+      double* Y2 = Y + j0 + j0 * ldy;  // rows j0.., explicit unit lower
+      // W2^T = T2^T (Y2^T A(:, trailing) - (Y2^T Y1) W1^T(:, trailing))
+      CK(gemm(cl, 'T', 'N', 0, bJ, n2, mJ, 1.0, Y2, ldy, dA + j0, lda, 0.0, w.Z, bJ, nullptr, 0,
+              tcols));
+      if (j0 > 0) {
+        CK(gemm(cl, 'T', 'N', 0, bJ, j0, mJ, 1.0, Y2, ldy, Y + j0, ldy, 0.0, w.YY, bJ));
+        CK(gemm(cl, 'N', 'N', 0, bJ, n2, j0, -1.0, w.YY, bJ, w.Wt + (j0 + bJ) * k, k, 1.0, w.Z, bJ));
+      }
+      CK(gemm(cl, 'T', 'N', 0, bJ, n2, bJ, 1.0, w.T, bJ, w.Z, bJ, 0.0, w.Wt + j0 + (j0 + bJ) * k, k));
+      // new rows of R: A(rows J, trailing) - Y(rows J, :) W^T(:, trailing)
+      double* Rrows = R + j0 + (j0 + bJ) * ldr;
+      CKL(1, rq::launch_gather_cols(dA, lda, j0, bJ, tcols, n2, Rrows, ldr, cl.st));
+      CK(gemm(cl, 'N', 'N', 0, bJ, n2, j0 + bJ, -1.0, Y + j0, ldy, w.Wt + (j0 + bJ) * k, k, 1.0,
+              Rrows, ldr));
+    }
+    if (j0 + bJ < k) {
+      PhaseScope ps(cl.h, PH_SUPD, (double)bJ * bJ * bJ / 3.0 + 2.0 * bJ * bJ * (double)n2);
+      const double* R11 = R + j0 + j0 * ldr;
+      CKL(1, rq::launch_w11(Bblk, ell, R11, ldr, bJ, w.W11, cl.flag, cl.status, cl.st));
+      double* Bnext = Bblk + (int64_t)bJ * ell;
+      CK(gemm(cl, 'N', 'N', 2, bJ, n2, bJ, -1.0, w.W11, bJ, R + j0 + (j0 + bJ) * ldr, ldr, 1.0,
+              Bnext, ell, cl.flag, 0));
+      // re-sample: Omega' (A(rows > j0+bJ, trailing) - Y W^T)
+      const int64_t mt = m - j0 - bJ;
+      const int64_t kk = j0 + bJ;
+      const int64_t* tcols = jpvt + j0 + bJ;
+      CKL(1, rq::launch_gaussian(seed, kResampleStreamBase + J, ell, mt, w.omega, ell, cl.flag, cl.st));
+      CK(gemm(cl, 'N', 'N', 0, ell, n2, mt, 1.0, w.omega, ell, dA + kk, lda, 0.0, Bnext, ell,
+              cl.flag, 1, tcols));
+      CK(gemm(cl, 'N', 'N', 0, ell, kk, mt, 1.0, w.omega, ell, Y + kk, ldy, 0.0, w.OY, ell, cl.flag,
+              1));
+      CK(gemm(cl, 'N', 'N', 0, ell, n2, kk, -1.0, w.OY, ell, w.Wt + kk * k, k, 1.0, Bnext, ell,
+              cl.flag, 1));
+    }
+  }
+  return RQRCP_OK;
+}
+
+}  // namespace
+
+int trqrcp(rqrcp_handle_t h, int64_t m, int64_t n, const double* dA, int64_t lda, int64_t k, int b,
+           int p, uint64_t seed, int64_t* d_jpvt, double* d_tau, double* dY, int64_t ldy,
+           double* dR, int64_t ldr) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (n < 1) return -3;
+  if (!dA) return -4;
+  if (lda < m) return -5;
+  if (k < 1 || k > std::min(m, n)) return -6;
+  if (b < 1) return -7;
+  if (p < 0) return -8;
+  if (!d_jpvt) return -10;
+  if (!d_tau) return -11;
+  if (!dY) return -12;
+  if (ldy < m) return -13;
+  if (!dR) return -14;
+  if (ldr < k) return -15;
+  if (b > k) b = (int)k;
+  const int ell = b + p;
+  if (!sizes_fit(h->num_sms, m, n, b, ell)) return RQRCP_ERR_UNSUPPORTED;
+  Call cl;
+  int r = begin(h, 'T', m, n, k, b, p, &cl);
+  if (r) return r;
+  return trqrcp_core(cl, m, n, dA, lda, k, b, ell, seed, d_jpvt, d_tau, dY, ldy, dR, ldr);
+}
+
+int tuxv(rqrcp_handle_t h, int64_t m, int64_t n, const double* dA, int64_t lda, int64_t k, int b,
+         int p, uint64_t seed, double* dU, int64_t ldu, double* dX, int64_t ldx, double* dV,
+         int64_t ldv) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (n < 1) return -3;
+  if (!dA) return -4;
+  if (lda < m) return -5;
+  if (k < 1 || k > std::min(m, n)) return -6;
+  if (b < 1) return -7;
+  if (p < 0) return -8;
+  if (!dU) return -10;
+  if (ldu < m) return -11;
+  if (!dX) return -12;
+  if (ldx < k) return -13;
+  if (!dV) return -14;
+  if (ldv < n) return -15;
+  if (b > k) b = (int)k;
+  const int ell = b + p;
+  if (!sizes_fit(h->num_sms, m, n, b, ell) || !rq::panel_fits(n, b, h->num_sms))
+    return RQRCP_ERR_UNSUPPORTED;
+  Call cl;
+  int r = begin(h, 'U', m, n, k, b, p, &cl);
+  if (r) return r;
+  Work& w = cl.w;
+  // Alg. 7: TRQRCP, then Z0 = R P^T
+  if ((r = trqrcp_core(cl, m, n, dA, lda, k, b, ell, seed, w.jpvt, w.tau, w.Yk, m, w.Rk, k))) return r;
+  // Z0^T (n x k) into V's storage: V(jpvt[c], :) = R(:, c)^T
+  {
+    PhaseScope ps(cl.h, PH_OTHER, 0.0);
+    CKL(1, rq::launch_scatter_transpose(w.Rk, k, k, w.jpvt, n, dV, ldv, cl.st));
+  }
+  // LQ of Z0 as the QR of Z0^T; V1 = leading k columns of its Q
+  if ((r = qr_core(cl, n, k, dV, ldv, b, w.tau2, w.Tall))) return r;
+  {
+    PhaseScope ps(cl.h, PH_OTHER, 0.0);
+    CKL(1, rq::launch_copy2d(dV, ldv, w.F, n, n, k, cl.st));
+  }
+  if ((r = orgqr_core(cl, n, k, w.F, n, b, w.Tall, dV, ldv))) return r;
+  // Z1 = A V1, then [U, X] = qr(Z1)
+  {
+    PhaseScope ps(cl.h, PH_TRQ, 2.0 * (double)m * (double)n * (double)k);
+    CK(gemm(cl, 'N', 'N', 0, m, k, n, 1.0, dA, lda, dV, ldv, 0.0, dU, ldu));
+  }
+  if ((r = qr_core(cl, m, k, dU, ldu, b, w.tau2, w.Tall))) return r;
+  {
+    PhaseScope ps(cl.h, PH_OTHER, 0.0);
+    CKL(1, rq::launch_split_qr(dU, ldu, k, k, 0, nullptr, 0, dX, ldx, cl.st));
+    CKL(1, rq::launch_copy2d(dU, ldu, w.F, m, m, k, cl.st));
+  }
+  if ((r = orgqr_core(cl, m, k, w.F, m, b, w.Tall, dU, ldu))) return r;
+  return RQRCP_OK;
+}
+
+int rqrcp_profile(rqrcp_handle_t h, int enable) {
+  if (!h) return -1;
+  if (enable) {
+    h->ev_used = 0;
+    for (int i = 0; i < RQRCP_NPHASE; ++i) {
+      h->flops[i] = 0.0;
+      h->launches[i] = 0;
+    }
+  }
+  h->prof = enable != 0;
+  return RQRCP_OK;
+}
+
+int rqrcp_profile_read(rqrcp_handle_t h, int nphase, double* ms, double* flops, int64_t* launches) {
+  if (!h) return -1;
+  if (nphase < 0 || nphase > RQRCP_NPHASE) return -2;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    h->err = std::string("profile_read: ") + cudaGetErrorString(e);
+    return RQRCP_ERR_CUDA;
+  }
+  double acc[RQRCP_NPHASE] = {};
+  for (size_t i = 0; i < h->ev_used; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, h->events[2 * i], h->events[2 * i + 1]) == cudaSuccess)
+      acc[h->ev_phase[i]] += t;
+  }
+  for (int i = 0; i < nphase; ++i) {
+    if (ms) ms[i] = acc[i];
+    if (flops) flops[i] = h->flops[i];
+    if (launches) launches[i] = h->launches[i];
+  }
+  return RQRCP_OK;
+}
+
+}  // extern "C"

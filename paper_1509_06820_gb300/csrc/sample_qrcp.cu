@@ -1,0 +1,265 @@
+// Partial QRCP on the sample matrix: Alg. 1 halted after b pivots, applied to
+// the l x n_J sample B (the qrcp(B, b) step of Alg. 4 and Alg. 6).
+//
+// One cooperative launch per block of pivots.  CTA g owns a contiguous range
+// of sample columns and keeps them in shared memory for the whole launch;
+// columns never move between CTAs.  Each pivot step costs one grid barrier:
+//   1. every CTA publishes its best trailing column (norm, logical position)
+//      and that column's values;
+//   2. after the barrier every CTA picks the same winner (largest norm, lowest
+//      logical position on a tie), builds the same Householder reflector from
+//      the published column, records the swap in its own bookkeeping, applies
+//      the reflector to its trailing columns (8 lanes per column, shuffle
+//      reductions), downdates their norms and computes its next candidate.
+// Swaps are tracked as logical positions; at the end every column is written
+// back to B at its final logical position, so B holds S = [S11 S12; 0 S22]
+// in the permuted order and `swaps` the partner position of each step.
+//
+// Norm update (reading of Alg. 1's trailing-norm step once row j is final):
+// nrm *= sqrt(max(0, 1 - (|s_ij|/nrm)^2)), recomputed exactly from rows
+// j+1.. when f * (nrm/nrm_ref)^2 <= sqrt(eps); identical to the oracle.
+#include <climits>
+
+#include "kernels.cuh"
+
+namespace rq {
+namespace {
+
+constexpr int NT = 256;
+constexpr int LPC = 8;                 // lanes per column
+constexpr int GROUPS = NT / LPC;       // columns processed concurrently
+constexpr int MAX_ELL = 192;
+constexpr double TOL3Z = 1.4901161193847656e-08;  // sqrt(2^-52)
+
+struct Cand {
+  double key;    // norm; -1 for NaN, -2 when the CTA has no trailing column
+  long long pos; // logical position
+  int who;       // CTA index or local column index
+};
+
+__device__ __forceinline__ bool better(const Cand& a, const Cand& b) {
+  return a.key > b.key || (a.key == b.key && a.pos < b.pos);
+}
+
+__device__ Cand block_argmax(Cand c, Cand* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Cand d;
+    d.key = __shfl_xor_sync(0xffffffffu, c.key, o);
+    d.pos = __shfl_xor_sync(0xffffffffu, c.pos, o);
+    d.who = __shfl_xor_sync(0xffffffffu, c.who, o);
+    if (better(d, c)) c = d;
+  }
+  if (lane == 0) red[warp] = c;
+  __syncthreads();
+  if (warp == 0) {
+    c = (lane < NT / 32) ? red[lane] : Cand{-3.0, LLONG_MAX, -1};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      Cand d;
+      d.key = __shfl_xor_sync(0xffffffffu, c.key, o);
+      d.pos = __shfl_xor_sync(0xffffffffu, c.pos, o);
+      d.who = __shfl_xor_sync(0xffffffffu, c.who, o);
+      if (better(d, c)) c = d;
+    }
+    if (lane == 0) red[0] = c;
+  }
+  __syncthreads();
+  Cand r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(NT, 1) sample_qrcp_kernel(SampleQrcpArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ell = a.ell;
+  const int G = gridDim.x, g = blockIdx.x;
+  const int64_t chunk = (a.nc + G - 1) / G;
+  const int64_t c_lo = (int64_t)g * chunk;
+  const int ncol = (int)imax64(0, imin64(a.nc, c_lo + chunk) - c_lo);
+
+  double* col = reinterpret_cast<double*>(smem_raw);          // ell x chunk
+  double* vn = col + (size_t)ell * chunk;                       // chunk
+  double* vn0 = vn + chunk;                                     // chunk
+  long long* lpos = reinterpret_cast<long long*>(vn0 + chunk);  // chunk
+  double* xv = reinterpret_cast<double*>(lpos + chunk);         // MAX_ELL (reflector v)
+  int* done = reinterpret_cast<int*>(xv + MAX_ELL);             // chunk
+  __shared__ Cand red[NT / 32];
+  __shared__ double s_scal[4];
+
+  const int tid = threadIdx.x;
+  const int grp = tid / LPC, lig = tid % LPC;
+
+  // load the owned columns (contiguous in B), logical position = index
+  for (int64_t e = tid; e < (int64_t)ncol * ell; e += NT) col[e] = a.B[c_lo * ell + e];
+  for (int c = tid; c < ncol; c += NT) {
+    lpos[c] = c_lo + c;
+    done[c] = 0;
+  }
+  __syncthreads();
+  // exact initial norms (rounds of GROUPS columns keep the shuffles warp-uniform)
+  for (int base = 0; base < ncol; base += GROUPS) {
+    const int c = base + grp;
+    const bool act = c < ncol;
+    double s = 0.0;
+    if (act)
+      for (int r = lig; r < ell; r += LPC) s = fma(col[r + c * ell], col[r + c * ell], s);
+    s = group_sum<LPC>(s);
+    if (act && lig == 0) {
+      double nv = sqrt(s);
+      if (!isfinite(nv)) atomicOr(a.status, RQRCP_INFO_NONFINITE);
+      vn[c] = nv;
+      vn0[c] = nv;
+    }
+  }
+  __syncthreads();
+
+  for (int i = 0; i < a.steps; ++i) {
+    // ---- local candidate
+    Cand mine{-2.0, LLONG_MAX, -1};
+    for (int c = tid; c < ncol; c += NT) {
+      if (done[c]) continue;
+      Cand t{isnan(vn[c]) ? -1.0 : vn[c], lpos[c], c};
+      if (better(t, mine)) mine = t;
+    }
+    Cand best = block_argmax(mine, red);
+    const int my_pivot = best.who;  // local column index of this CTA's candidate
+    double* cand = a.cand + (size_t)(i & 1) * G * 2;
+    double* ccol = a.candcol + (size_t)(i & 1) * G * ell;
+    if (tid == 0) {
+      cand[2 * g] = best.key;
+      cand[2 * g + 1] = (double)best.pos;  // positions < 2^53: exact
+    }
+    if (my_pivot >= 0)
+      for (int r = tid; r < ell; r += NT) ccol[(size_t)g * ell + r] = col[r + my_pivot * ell];
+    if (!grid_barrier(a.bar, G, a.status)) return;
+
+    // ---- global winner (identical in every CTA)
+    Cand w{-3.0, LLONG_MAX, -1};
+    for (int q = tid; q < G; q += NT) {
+      Cand t{__ldcg(cand + 2 * q), (long long)__ldcg(cand + 2 * q + 1), q};
+      if (better(t, w)) w = t;
+    }
+    w = block_argmax(w, red);
+    const long long Lstar = w.pos;
+    // reflector from the winner's rows i..ell-1 (warp 0, fixed order)
+    for (int r = tid; r < ell; r += NT) xv[r] = (r >= i) ? __ldcg(ccol + (size_t)w.who * ell + r) : 0.0;
+    __syncthreads();
+    if (tid < 32) {
+      double s = 0.0;
+      for (int r = i + 1 + tid; r < ell; r += 32) s = fma(xv[r], xv[r], s);
+      s = warp_sum(s);
+      if (tid == 0) {
+        double beta, tau, scale;
+        house_scalars(xv[i], sqrt(s), &beta, &tau, &scale);
+        s_scal[0] = beta;
+        s_scal[1] = tau;
+        s_scal[2] = scale;
+      }
+    }
+    __syncthreads();
+    const double beta = s_scal[0], tau = s_scal[1], scale = s_scal[2];
+    for (int r = i + 1 + tid; r < ell; r += NT) xv[r] *= scale;
+    if (tid == 0) xv[i] = 1.0;
+    if (g == 0 && tid == 0) a.swaps[i] = Lstar;
+    // the trailing column at logical position i moves to Lstar (the pivot
+    // itself sits at Lstar != i, so it is not matched here)
+    if (Lstar != i) {
+      for (int c = tid; c < ncol; c += NT)
+        if (!done[c] && lpos[c] == i) lpos[c] = Lstar;
+    }
+    __syncthreads();
+    if (g == w.who && my_pivot >= 0) {
+      // finish the pivot column: S(i, i) = beta, zeros below, position i
+      for (int r = i + 1 + tid; r < ell; r += NT) col[r + my_pivot * ell] = 0.0;
+      if (tid == 0) {
+        col[i + my_pivot * ell] = beta;
+        done[my_pivot] = 1;
+        lpos[my_pivot] = i;
+      }
+    }
+    __syncthreads();
+    // ---- apply H = I - tau v v^T to the trailing columns, downdate norms
+    for (int base = 0; base < ncol; base += GROUPS) {
+      const int c = base + grp;
+      const bool act = c < ncol && !done[c];
+      double* cc = col + (size_t)(act ? c : 0) * ell;
+      if (tau != 0.0) {
+        double s = 0.0;
+        if (act)
+          for (int r = i + lig; r < ell; r += LPC) s = fma(xv[r], cc[r], s);
+        s = group_sum<LPC>(s) * tau;
+        if (act)
+          for (int r = i + lig; r < ell; r += LPC) cc[r] = fma(-s, xv[r], cc[r]);
+      }
+      double t = 0.0;
+      if (act)
+        for (int r = i + 1 + lig; r < ell; r += LPC) t = fma(cc[r], cc[r], t);
+      t = group_sum<LPC>(t);
+      if (act && lig == 0 && vn[c] != 0.0) {
+        double rr = fabs(cc[i]) / vn[c];
+        double f = fmax(0.0, (1.0 - rr) * (1.0 + rr));
+        double q = vn[c] / vn0[c];
+        if (f * q * q <= TOL3Z) {
+          vn[c] = sqrt(t);
+          vn0[c] = vn[c];
+        } else {
+          vn[c] *= sqrt(f);
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // every CTA finished loading before the first barrier: write S back in the
+  // permuted (logical) order
+  for (int c = 0; c < ncol; ++c) {
+    const long long L = lpos[c];
+    for (int r = tid; r < ell; r += NT) a.B[L * ell + r] = col[r + (size_t)c * ell];
+  }
+}
+
+size_t smem_bytes(int ell, int64_t chunk) {
+  return (size_t)chunk * ((size_t)ell * 8 + 8 + 8 + 8 + 4) + MAX_ELL * 8 + 16;
+}
+
+constexpr size_t kSmemLimit = 216 * 1024;
+
+int sample_grid(int64_t nc, int num_sms) {
+  int64_t G = (nc + 63) / 64;
+  if (G > num_sms) G = num_sms;
+  if (G < 1) G = 1;
+  return (int)G;
+}
+
+}  // namespace
+
+bool sample_qrcp_fits(int ell, int64_t nc, int num_sms) {
+  const int G = sample_grid(nc, num_sms);
+  const int64_t chunk = (nc + G - 1) / G;
+  return ell <= MAX_ELL && smem_bytes(ell, chunk) <= kSmemLimit;
+}
+
+cudaError_t launch_sample_qrcp(const SampleQrcpArgs& a, int num_sms, cudaStream_t st) {
+  const int G = sample_grid(a.nc, num_sms);
+  const int64_t chunk = (a.nc + G - 1) / G;
+  const size_t smem = smem_bytes(a.ell, chunk);
+  if (a.ell > MAX_ELL || smem > kSmemLimit) return cudaErrorInvalidValue;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(sample_qrcp_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSmemLimit);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  cudaError_t e = cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), st);
+  if (e != cudaSuccess) return e;
+  SampleQrcpArgs args = a;
+  void* params[] = {&args};
+  return cudaLaunchCooperativeKernel((const void*)sample_qrcp_kernel, dim3((unsigned)G),
+                                     dim3(NT), params, smem, st);
+}
+
+}  // namespace rq
