@@ -304,9 +304,10 @@ def main():
         torch.cuda.synchronize(dev)
 
         def estep():
-            A.copy_(Ah, non_blocking=True)
+            # .t() views of contiguous buffers: one flat pinned copy each way
+            A.t().copy_(Ah.t(), non_blocking=True)
             jp, tau = rq.rqrcp_factor(A, b, p, 1, handle=h)
-            Ah_out.copy_(A, non_blocking=True)
+            Ah_out.t().copy_(A.t(), non_blocking=True)
             jh.copy_(jp, non_blocking=True)
             th.copy_(tau, non_blocking=True)
         estep()

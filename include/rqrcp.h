@@ -104,6 +104,23 @@ int rqrcp_factor(rqrcp_handle_t handle, int64_t m, int64_t n, double* dA, int64_
                  int p, uint64_t seed, int64_t* d_jpvt, double* d_tau);
 
 /*
+ * Mixed-precision RQRCP (Alg. 4 with Eq. 3) on an FP32 matrix.
+ * The sketch B = Omega A is a BF16 product with FP32 accumulation (it only
+ * steers pivots); the trailing update W = T^T Y^T A2, A2 -= Y W runs as
+ * split-BF16 x3 tensor-core products (rqrcp_gemm_bf16x, FP32-level); the
+ * sample QRCP with its norm downdates, the Householder panel, T and the
+ * sample update stay in FP64, and R's diagonal is returned in FP64.
+ *   dA     : in/out, m x n FP32, lda >= m; on exit R (FP32-rounded) on and
+ *            above the diagonal and the reflectors below it
+ *   d_jpvt : out, n int64;  d_tau : out, min(m, n) FP64
+ *   d_rdiag: out, min(m, n) FP64 diagonal of R
+ * Exactly singular R11 sets RQRCP_INFO_RESAMPLED and keeps S12 as the next
+ * sample rows (this mode does not re-draw the sample).
+ */
+int rqrcp_factor_mixed(rqrcp_handle_t handle, int64_t m, int64_t n, float* dA, int64_t lda, int b,
+                       int p, uint64_t seed, int64_t* d_jpvt, double* d_tau, double* d_rdiag);
+
+/*
  * Unpivoted blocked Householder QR: Alg. 4 with every sample operation and
  * pivot removed (the paper's `qr`, note to Table 3).  dA in/out as in
  * rqrcp_factor (LAPACK dgeqrf layout); d_tau out, min(m, n).
@@ -126,6 +143,16 @@ int qr_factor(rqrcp_handle_t handle, int64_t m, int64_t n, double* dA, int64_t l
 int trqrcp(rqrcp_handle_t handle, int64_t m, int64_t n, const double* dA, int64_t lda, int64_t k,
            int b, int p, uint64_t seed, int64_t* d_jpvt, double* d_tau, double* dY, int64_t ldy,
            double* dR, int64_t ldr);
+
+/*
+ * Mixed-precision TRQRCP (Alg. 6) on an FP32 matrix: BF16 sketch, the
+ * products with A, Y and W^T as split-BF16 x3 tensor-core GEMMs, FP64 sample
+ * QRCP, panel, T and R diagonal.  Outputs as in trqrcp with dY (m x k, ldy)
+ * and dR (k x n, ldr) in FP32, d_tau and d_rdiag (k) in FP64.
+ */
+int trqrcp_mixed(rqrcp_handle_t handle, int64_t m, int64_t n, const float* dA, int64_t lda,
+                 int64_t k, int b, int p, uint64_t seed, int64_t* d_jpvt, double* d_tau,
+                 float* dY, int64_t ldy, float* dR, int64_t ldr, double* d_rdiag);
 
 /*
  * Approximate truncated SVD -- Alg. 7 (TUXV) with j_max = 1:
@@ -152,6 +179,29 @@ int rqrcp_gaussian(rqrcp_handle_t handle, uint64_t seed, uint32_t stream_id, int
  */
 int rqrcp_sketch(rqrcp_handle_t handle, int64_t m, int64_t n, const double* dA, int64_t lda,
                  int ell, uint64_t seed, double* dB, int64_t ldb);
+
+/*
+ * Split-BF16 tensor-core GEMM, the contraction engine of the mixed-precision
+ * path: C = alpha op(A) op(B) + beta C with FP32 operands and result
+ * (column-major; transA/transB 'N' or 'T').  slices = 3 splits each operand
+ * element into three bfloat16 parts and sums the six largest slice products
+ * with FP32 accumulation in tensor memory (FP32-level accuracy); slices = 1
+ * rounds the operands to bfloat16 (one product, FP32 accumulation).
+ */
+int rqrcp_gemm_bf16x(rqrcp_handle_t handle, char transA, char transB, int64_t m, int64_t n,
+                     int64_t k, float alpha, const float* dA, int64_t lda, const float* dB,
+                     int64_t ldb, float beta, float* dC, int64_t ldc, int slices);
+
+/*
+ * The pivot-selection step of Alg. 4 on its own: partial QRCP (Alg. 1 halted
+ * after `steps` pivots) of the ell x nc sample dB (ldb >= ell), in place.
+ * On exit dB holds S = Q_b^T B P in the permuted column order (S11 upper
+ * triangular with exact zeros below its diagonal, then S12 over S22) and
+ * d_swaps[i] (0-based) is the column exchanged with column i at step i.
+ * 1 <= steps <= min(ell, nc); ell <= 192.
+ */
+int rqrcp_sample_qrcp(rqrcp_handle_t handle, int ell, int64_t nc, int steps, double* dB,
+                      int64_t ldb, int64_t* d_swaps);
 
 /*
  * Instrumentation (no counterpart in the paper).  While enabled, every phase

@@ -41,10 +41,16 @@ SIGNATURES = [
     ("rqrcp_status_string", ctypes.c_char_p, [_I]),
     ("rqrcp_factor", _I, [_P, _I64, _I64, _P, _I64, _I, _I, _U64, _P, _P]),
     ("qr_factor", _I, [_P, _I64, _I64, _P, _I64, _I, _P]),
+    ("rqrcp_factor_mixed", _I, [_P, _I64, _I64, _P, _I64, _I, _I, _U64, _P, _P, _P]),
     ("trqrcp", _I, [_P, _I64, _I64, _P, _I64, _I64, _I, _I, _U64, _P, _P, _P, _I64, _P, _I64]),
+    ("trqrcp_mixed", _I, [_P, _I64, _I64, _P, _I64, _I64, _I, _I, _U64, _P, _P, _P, _I64, _P, _I64,
+                          _P]),
     ("tuxv", _I, [_P, _I64, _I64, _P, _I64, _I64, _I, _I, _U64, _P, _I64, _P, _I64, _P, _I64]),
     ("rqrcp_gaussian", _I, [_P, _U64, ctypes.c_uint32, _I64, _I64, _P, _I64]),
     ("rqrcp_sketch", _I, [_P, _I64, _I64, _P, _I64, _I, _U64, _P, _I64]),
+    ("rqrcp_gemm_bf16x", _I, [_P, ctypes.c_char, ctypes.c_char, _I64, _I64, _I64, ctypes.c_float,
+                          _P, _I64, _P, _I64, ctypes.c_float, _P, _I64, _I]),
+    ("rqrcp_sample_qrcp", _I, [_P, _I, _I64, _I, _P, _I64, _P]),
     ("rqrcp_profile", _I, [_P, _I]),
     ("rqrcp_profile_read", _I, [_P, _I, _P, _P, _P]),
 ]
@@ -200,6 +206,22 @@ def rqrcp_factor(A, b, p, seed, handle=None):
     return jpvt, tau
 
 
+def rqrcp_factor_mixed(A, b, p, seed, handle=None):
+    """Mixed-precision Alg. 4 in place on a column-major float32 A;
+    returns (jpvt, tau (float64), rdiag (float64))."""
+    h = handle or default_handle(A.device)
+    if A.device.type != "cuda" or A.dtype != torch.float32 or not _is_colmajor(A):
+        raise ValueError("A must be a column-major float32 CUDA tensor")
+    m, n = A.shape
+    k = min(m, n)
+    jpvt = torch.empty(n, dtype=torch.int64, device=A.device)
+    tau = torch.empty(k, dtype=torch.float64, device=A.device)
+    rdiag = torch.empty(k, dtype=torch.float64, device=A.device)
+    _check(load().rqrcp_factor_mixed(h.bind(), m, n, _ptr(A), _ld(A), b, p, seed, _ptr(jpvt),
+                                     _ptr(tau), _ptr(rdiag)), h.h)
+    return jpvt, tau, rdiag
+
+
 def qr_factor(A, b, handle=None):
     """Unpivoted blocked QR in place; returns tau."""
     h = handle or default_handle(A.device)
@@ -222,6 +244,25 @@ def trqrcp(A, k, b, p, seed, handle=None):
     _check(load().trqrcp(h.bind(), m, n, _P(pa), lda, k, b, p, seed, _ptr(jpvt), _ptr(tau),
                          _ptr(Y), _ld(Y), _ptr(R), _ld(R)), h.h)
     return jpvt, tau, Y, R
+
+
+def trqrcp_mixed(A, k, b, p, seed, handle=None, out=None):
+    """Mixed-precision Alg. 6 on a column-major float32 A; returns
+    (jpvt, tau (f64), Y (f32, m x k), R (f32, k x n), rdiag (f64))."""
+    h = handle or default_handle(A.device)
+    if A.device.type != "cuda" or A.dtype != torch.float32 or not _is_colmajor(A):
+        raise ValueError("A must be a column-major float32 CUDA tensor")
+    m, n = A.shape
+    if out is None:
+        out = (torch.empty(n, dtype=torch.int64, device=A.device),
+               torch.empty(k, dtype=torch.float64, device=A.device),
+               empty_colmajor(m, k, A.device, torch.float32),
+               empty_colmajor(k, n, A.device, torch.float32),
+               torch.empty(k, dtype=torch.float64, device=A.device))
+    jpvt, tau, Y, R, rdiag = out
+    _check(load().trqrcp_mixed(h.bind(), m, n, _ptr(A), _ld(A), k, b, p, seed, _ptr(jpvt),
+                               _ptr(tau), _ptr(Y), _ld(Y), _ptr(R), _ld(R), _ptr(rdiag)), h.h)
+    return jpvt, tau, Y, R, rdiag
 
 
 def tuxv(A, k, b, p, seed, handle=None):
@@ -254,6 +295,34 @@ def sketch(A, ell, seed, handle=None):
     B = empty_colmajor(ell, n, A.device)
     _check(load().rqrcp_sketch(h.bind(), m, n, _P(pa), lda, ell, seed, _ptr(B), _ld(B)), h.h)
     return B
+
+
+def gemm_bf16x(A, B, transA="N", transB="N", alpha=1.0, beta=0.0, C=None, slices=3, handle=None):
+    """C = alpha op(A) op(B) + beta C on the tensor cores (FP32, column-major)."""
+    h = handle or default_handle(A.device)
+    for x, nm in ((A, "A"), (B, "B")):
+        if x.dtype != torch.float32 or not _is_colmajor(x):
+            raise ValueError(f"{nm} must be a column-major float32 CUDA tensor")
+    m = A.shape[0] if transA == "N" else A.shape[1]
+    k = A.shape[1] if transA == "N" else A.shape[0]
+    n = B.shape[1] if transB == "N" else B.shape[0]
+    if C is None:
+        C = empty_colmajor(m, n, A.device, torch.float32)
+        beta = 0.0
+    _check(load().rqrcp_gemm_bf16x(h.bind(), transA.encode(), transB.encode(), m, n, k, alpha,
+                                   _ptr(A), _ld(A), _ptr(B), _ld(B), beta, _ptr(C), _ld(C),
+                                   slices), h.h)
+    return C
+
+
+def sample_qrcp(B, steps, handle=None):
+    """Partial QRCP of the column-major float64 sample B in place; returns swaps."""
+    h = handle or default_handle(B.device)
+    pb, ldb = _cm(B, "B")
+    ell, nc = B.shape
+    swaps = torch.empty(steps, dtype=torch.int64, device=B.device)
+    _check(load().rqrcp_sample_qrcp(h.bind(), ell, nc, steps, _P(pb), ldb, _ptr(swaps)), h.h)
+    return swaps
 
 
 def sync_info(device=None):

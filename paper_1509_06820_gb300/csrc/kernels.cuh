@@ -42,9 +42,33 @@ struct GemmArgs {
 cudaError_t launch_gemm(const GemmArgs& g, int splits, double* partial, cudaStream_t st);
 int gemm_pick_splits(int64_t M, int64_t N, int64_t K, int num_sms);
 
+// ---- tc_gemm.cu: split-BF16 tensor-core GEMM (tcgen05), FP32 operands.
+struct TcGemmArgs {
+  char transA, transB;
+  int64_t M, N, K;
+  float alpha;
+  const float* A;
+  int64_t lda;
+  const float* B;
+  int64_t ldb;
+  float beta;
+  float* C;
+  int64_t ldc;
+  int* status;
+  bool vecA, vecB;      // set by the launcher
+  int splits;           // split-K factor (1: none)
+  float* partial;       // splits * M * N floats when splits > 1
+  int kt_per_split;     // set by the launcher
+  const int64_t* bcols; // transB == 'N' only: column j of op(B) is stored column bcols[j]
+};
+// slices = 1 (plain BF16) or 3 (FP32-level split, six products)
+cudaError_t launch_tc_gemm(TcGemmArgs g, int slices, cudaStream_t st);
+int tc_pick_splits(int64_t M, int64_t N, int64_t K, int num_sms, size_t cap_floats);
+
 // ---- sample_qrcp.cu: partial QRCP (Alg. 1, b steps) on the l x nc sample.
 struct SampleQrcpArgs {
-  double* B;          // l x nc, ld = l; overwritten by S in the permuted order
+  double* B;          // l x nc, leading dimension ldb; overwritten by S in the permuted order
+  int64_t ldb;        // >= ell
   int ell;
   int64_t nc;
   int steps;          // bJ
@@ -64,7 +88,23 @@ bool sample_qrcp_fits(int ell, int64_t nc, int num_sms);
 cudaError_t launch_apply_swaps(double* A, int64_t lda, int64_t m, int64_t col0,
                                const int64_t* swaps, int steps, int64_t* jpvt, int64_t* map,
                                double* buf, cudaStream_t st);
+cudaError_t launch_apply_swaps_f32(float* A, int64_t lda, int64_t m, int64_t col0,
+                                   const int64_t* swaps, int steps, int64_t* jpvt, int64_t* map,
+                                   float* buf, cudaStream_t st);
 cudaError_t launch_iota(int64_t* v, int64_t n, cudaStream_t st);
+cudaError_t launch_convert_f32_f64(const float* src, int64_t lds, double* dst, int64_t ldd,
+                                   int64_t rows, int64_t cols, cudaStream_t st);
+cudaError_t launch_convert_f64_f32(const double* src, int64_t lds, float* dst, int64_t ldd,
+                                   int64_t rows, int64_t cols, cudaStream_t st);
+cudaError_t launch_gather_cols_f32(const float* src, int64_t lds, int64_t r0, int64_t rows,
+                                   const int64_t* idx, int64_t ncols, float* dst, int64_t ldd,
+                                   cudaStream_t st);
+// dst (cols x cols, ldd) = upper triangle of src (zeros below)
+cudaError_t launch_copy_upper_f32(const float* src, int64_t lds, int64_t cols, float* dst,
+                                  int64_t ldd, cudaStream_t st);
+cudaError_t launch_panel_writeback(const double* P, int64_t ldp, int64_t rows, int64_t cols,
+                                   float* A, int64_t lda, float* Y, int64_t ldy, double* rdiag,
+                                   cudaStream_t st);
 // dst(:, t) = src(r0:r0+rows, idx[t]) for t < ncols (column gather through a map)
 cudaError_t launch_gather_cols(const double* src, int64_t lds, int64_t r0, int64_t rows,
                                const int64_t* idx, int64_t ncols, double* dst, int64_t ldd,

@@ -44,27 +44,30 @@ __global__ void compose_swaps(const int64_t* __restrict__ swaps, int steps, int6
 }
 
 // gather (dir = 0): buf[:, t] = A[:, col0 + src_t]; scatter (dir = 1):
-// A[:, col0 + dest_t] = buf[:, t].  blockIdx.y = move index.
-template <bool VEC>
-__global__ void move_columns(double* __restrict__ A, int64_t lda, int64_t m, int64_t col0,
-                             const int64_t* __restrict__ map, double* __restrict__ buf,
+// A[:, col0 + dest_t] = buf[:, t].  blockIdx.y = move index.  V is a 16-byte
+// vector of T (double2 or float4) used when the layout allows.
+template <typename T, typename V, bool VEC>
+__global__ void move_columns(T* __restrict__ A, int64_t lda, int64_t m, int64_t col0,
+                             const int64_t* __restrict__ map, T* __restrict__ buf,
                              int64_t* __restrict__ jpvt, int64_t* __restrict__ jbuf, int dir) {
+  constexpr int W = sizeof(V) / sizeof(T);
   const int t = blockIdx.y;
   if (t >= map[0]) return;
   const int64_t dest = map[1 + 2 * t], src = map[2 + 2 * t];
   const int64_t acol = col0 + (dir == 0 ? src : dest);
-  double* a = A + acol * lda;
-  double* bb = buf + (int64_t)t * m;
+  T* a = A + acol * lda;
+  T* bb = buf + (int64_t)t * m;
   if (VEC) {
-    const int64_t m2 = m / 2;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m2;
+    const int64_t mv = m / W;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < mv;
          r += (int64_t)gridDim.x * blockDim.x) {
-      if (dir == 0) reinterpret_cast<double2*>(bb)[r] = reinterpret_cast<const double2*>(a)[r];
-      else reinterpret_cast<double2*>(a)[r] = reinterpret_cast<const double2*>(bb)[r];
+      if (dir == 0) reinterpret_cast<V*>(bb)[r] = reinterpret_cast<const V*>(a)[r];
+      else reinterpret_cast<V*>(a)[r] = reinterpret_cast<const V*>(bb)[r];
     }
-    if ((m & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-      if (dir == 0) bb[m - 1] = a[m - 1];
-      else a[m - 1] = bb[m - 1];
+    if (blockIdx.x == 0 && threadIdx.x < (unsigned)(m - mv * W)) {
+      const int64_t r = mv * W + threadIdx.x;
+      if (dir == 0) bb[r] = a[r];
+      else a[r] = bb[r];
     }
   } else {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m;
@@ -109,27 +112,40 @@ unsigned grid_for(int64_t work, int threads, int64_t cap) {
   return (unsigned)b;
 }
 
+template <typename T, typename V>
+cudaError_t apply_swaps_t(T* A, int64_t lda, int64_t m, int64_t col0, const int64_t* swaps,
+                          int steps, int64_t* jpvt, int64_t* map, T* buf, cudaStream_t st) {
+  if (steps <= 0) return cudaSuccess;
+  compose_swaps<<<1, 32, 0, st>>>(swaps, steps, map);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  constexpr int W = sizeof(V) / sizeof(T);
+  int64_t* jbuf = map + 1 + 8 * (int64_t)steps;
+  const bool vec = (lda % W == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
+                   ((reinterpret_cast<uintptr_t>(buf) & 15) == 0) && (m % W == 0);
+  const int threads = 256;
+  dim3 grid(grid_for(vec ? m / W : m, threads, 64), (unsigned)(2 * steps));
+  for (int dir = 0; dir < 2; ++dir) {
+    if (vec) move_columns<T, V, true><<<grid, threads, 0, st>>>(A, lda, m, col0, map, buf, jpvt, jbuf, dir);
+    else move_columns<T, V, false><<<grid, threads, 0, st>>>(A, lda, m, col0, map, buf, jpvt, jbuf, dir);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 }  // namespace
 
 cudaError_t launch_apply_swaps(double* A, int64_t lda, int64_t m, int64_t col0,
                                const int64_t* swaps, int steps, int64_t* jpvt, int64_t* map,
                                double* buf, cudaStream_t st) {
-  if (steps <= 0) return cudaSuccess;
-  compose_swaps<<<1, 32, 0, st>>>(swaps, steps, map);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  int64_t* jbuf = map + 1 + 8 * (int64_t)steps;
-  const bool vec = (lda % 2 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
-                   ((reinterpret_cast<uintptr_t>(buf) & 15) == 0) && (m % 2 == 0);
-  const int threads = 256;
-  dim3 grid(grid_for(vec ? m / 2 : m, threads, 64), (unsigned)(2 * steps));
-  for (int dir = 0; dir < 2; ++dir) {
-    if (vec) move_columns<true><<<grid, threads, 0, st>>>(A, lda, m, col0, map, buf, jpvt, jbuf, dir);
-    else move_columns<false><<<grid, threads, 0, st>>>(A, lda, m, col0, map, buf, jpvt, jbuf, dir);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  return apply_swaps_t<double, double2>(A, lda, m, col0, swaps, steps, jpvt, map, buf, st);
+}
+
+cudaError_t launch_apply_swaps_f32(float* A, int64_t lda, int64_t m, int64_t col0,
+                                   const int64_t* swaps, int steps, int64_t* jpvt, int64_t* map,
+                                   float* buf, cudaStream_t st) {
+  return apply_swaps_t<float, float4>(A, lda, m, col0, swaps, steps, jpvt, map, buf, st);
 }
 
 cudaError_t launch_iota(int64_t* v, int64_t n, cudaStream_t st) {
@@ -245,6 +261,98 @@ cudaError_t launch_eye(double* Q, int64_t rows, int64_t cols, int64_t ld, cudaSt
   int64_t b = (rows * cols + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
   eye_kernel<<<(unsigned)b, 256, 0, st>>>(Q, rows, cols, ld);
+  return cudaGetLastError();
+}
+}  // namespace rq
+
+namespace rq {
+namespace {
+template <typename TI, typename TO>
+__global__ void convert_kernel(const TI* __restrict__ src, int64_t lds, TO* __restrict__ dst,
+                               int64_t ldd, int64_t rows, int64_t cols) {
+  const int64_t total = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % rows, c = e / rows;
+    dst[r + c * ldd] = (TO)src[r + c * lds];
+  }
+}
+
+// Mixed-precision panel write-back: P64 (rows x cols, ld ldp) holds the FP64
+// factored panel; its R part and reflectors go to the FP32 array (ld lda),
+// the explicit unit-lower reflector block to Y32 (ld ldy) and R's diagonal
+// to rdiag in FP64.
+__global__ void panel_writeback_kernel(const double* __restrict__ P, int64_t ldp, int64_t rows,
+                                       int64_t cols, float* __restrict__ A, int64_t lda,
+                                       float* __restrict__ Y, int64_t ldy, double* __restrict__ rdiag) {
+  const int64_t total = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % rows, c = e / rows;
+    const double v = P[r + c * ldp];
+    A[r + c * lda] = (float)v;
+    Y[r + c * ldy] = (r > c) ? (float)v : (r == c ? 1.0f : 0.0f);
+    if (r == c) rdiag[c] = v;
+  }
+}
+__global__ void gather_cols_f32_kernel(const float* __restrict__ src, int64_t lds, int64_t r0,
+                                       int64_t rows, const int64_t* __restrict__ idx, int64_t ncols,
+                                       float* __restrict__ dst, int64_t ldd) {
+  const int64_t total = rows * ncols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % rows, t = e / rows;
+    dst[r + t * ldd] = src[(r0 + r) + idx[t] * lds];
+  }
+}
+
+__global__ void copy_upper_f32_kernel(const float* __restrict__ src, int64_t lds, int64_t cols,
+                                      float* __restrict__ dst, int64_t ldd) {
+  const int64_t total = cols * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % cols, c = e / cols;
+    dst[r + c * ldd] = (r <= c) ? src[r + c * lds] : 0.0f;
+  }
+}
+}  // namespace
+
+cudaError_t launch_gather_cols_f32(const float* src, int64_t lds, int64_t r0, int64_t rows,
+                                   const int64_t* idx, int64_t ncols, float* dst, int64_t ldd,
+                                   cudaStream_t st) {
+  if (rows <= 0 || ncols <= 0) return cudaSuccess;
+  gather_cols_f32_kernel<<<grid2(rows * ncols), 256, 0, st>>>(src, lds, r0, rows, idx, ncols, dst,
+                                                               ldd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_upper_f32(const float* src, int64_t lds, int64_t cols, float* dst,
+                                  int64_t ldd, cudaStream_t st) {
+  if (cols <= 0) return cudaSuccess;
+  copy_upper_f32_kernel<<<grid2(cols * cols), 256, 0, st>>>(src, lds, cols, dst, ldd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_f32_f64(const float* src, int64_t lds, double* dst, int64_t ldd,
+                                   int64_t rows, int64_t cols, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  convert_kernel<float, double><<<grid2(rows * cols), 256, 0, st>>>(src, lds, dst, ldd, rows, cols);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_f64_f32(const double* src, int64_t lds, float* dst, int64_t ldd,
+                                   int64_t rows, int64_t cols, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  convert_kernel<double, float><<<grid2(rows * cols), 256, 0, st>>>(src, lds, dst, ldd, rows, cols);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_panel_writeback(const double* P, int64_t ldp, int64_t rows, int64_t cols,
+                                   float* A, int64_t lda, float* Y, int64_t ldy, double* rdiag,
+                                   cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  panel_writeback_kernel<<<grid2(rows * cols), 256, 0, st>>>(P, ldp, rows, cols, A, lda, Y, ldy,
+                                                              rdiag);
   return cudaGetLastError();
 }
 }  // namespace rq

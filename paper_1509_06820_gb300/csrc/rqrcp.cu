@@ -73,6 +73,18 @@ struct Work {
   double* tau2 = nullptr;     // k
   double* Tall = nullptr;     // ceil(k/b) x b x b
   double* F = nullptr;        // max(m, n) x k copy of reflectors
+  // mixed precision (FP32 storage)
+  float* omega32 = nullptr;   // l x m
+  float* B32 = nullptr;       // l x n
+  float* permbuf32 = nullptr; // m x 2b
+  double* P64 = nullptr;      // m x b FP64 panel
+  float* Y32 = nullptr;       // m x b explicit reflectors
+  float* T32 = nullptr;       // b x b
+  float* Z32 = nullptr;       // b x n
+  float* W32 = nullptr;       // b x n
+  double* R12 = nullptr;      // b x n FP64 copy of the new rows of R
+  float* tcpart = nullptr;    // split-K partial sums
+  size_t tccap = 0;
   size_t bytes = 0;
 };
 
@@ -128,6 +140,32 @@ Work carve(char op, int64_t m, int64_t n, int64_t k, int b, int p, int sms, char
     w.F = c.take<double>((size_t)std::max(m, n) * k);
   } else if (op == 'Q') {
     w.Tall = nullptr;
+  } else if (op == 'V') {
+    // mixed-precision TRQRCP
+    w.omega32 = c.take<float>((size_t)ell * m);
+    w.B32 = c.take<float>((size_t)ell * n);
+    w.permbuf32 = c.take<float>((size_t)std::max<int64_t>(k, 1) * 2 * bb);
+    w.P64 = c.take<double>((size_t)m * bb);
+    w.Y32 = c.take<float>((size_t)m * bb);  // A_hat
+    w.T32 = c.take<float>((size_t)bb * bb);
+    w.Z32 = c.take<float>((size_t)bb * n);
+    w.W32 = c.take<float>((size_t)k * n);   // W^T
+    w.Wt = c.take<double>((size_t)bb * k);  // Y2^T Y1 as floats (reinterpreted)
+    w.R12 = c.take<double>((size_t)bb * n);
+    w.tccap = (size_t)8 * bb * n;
+    w.tcpart = c.take<float>(w.tccap);
+  } else if (op == 'M') {
+    w.omega32 = c.take<float>((size_t)ell * m);
+    w.B32 = c.take<float>((size_t)ell * n);
+    w.permbuf32 = c.take<float>((size_t)m * 2 * bb);
+    w.P64 = c.take<double>((size_t)m * bb);
+    w.Y32 = c.take<float>((size_t)m * bb);
+    w.T32 = c.take<float>((size_t)bb * bb);
+    w.Z32 = c.take<float>((size_t)bb * n);
+    w.W32 = c.take<float>((size_t)bb * n);
+    w.R12 = c.take<double>((size_t)bb * n);
+    w.tccap = (size_t)8 * bb * n;
+    w.tcpart = c.take<float>(w.tccap);
   }
   w.bytes = align_up(c.off) + 256;
   return w;
@@ -207,6 +245,19 @@ cudaError_t gemm(Call& cl, char ta, char tb, int amode, int64_t M, int64_t N, in
   return rq::launch_gemm(g, s, cl.w.skpart, cl.st);
 }
 
+cudaError_t tcgemm(Call& cl, char ta, char tb, int64_t M, int64_t N, int64_t K, float alpha,
+                   const float* A, int64_t lda, const float* B, int64_t ldb, float beta, float* C,
+                   int64_t ldc, int slices, const int64_t* bcols = nullptr) {
+  rq::TcGemmArgs g{ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, cl.status, false, false,
+                   1, nullptr, 0, bcols};
+  if (cl.w.tcpart != nullptr) {
+    g.splits = rq::tc_pick_splits(M, N, K, cl.h->num_sms, cl.w.tccap);
+    g.partial = g.splits > 1 ? cl.w.tcpart : nullptr;
+  }
+  if (M > 0 && N > 0) count_launch(cl.h, g.splits > 1 ? 2 : 1);
+  return rq::launch_tc_gemm(g, slices, cl.st);
+}
+
 int ensure(rqrcp_handle_t h, size_t bytes) {
   if (h->ws_bytes >= bytes) return RQRCP_OK;
   cudaError_t e = cudaStreamSynchronize(h->stream);
@@ -241,7 +292,8 @@ int sample_step(Call& cl, double* Bblk, int ell, int64_t nc, int bJ) {
   double fl = 0.0;
   for (int i = 0; i < bJ && i < ell; ++i) fl += 4.0 * (ell - i) * (double)(nc - i - 1);
   PhaseScope ps(cl.h, PH_SAMPLE, fl);
-  rq::SampleQrcpArgs a{Bblk, ell, nc, bJ, cl.w.swaps, cl.w.cand, cl.w.candcol, cl.bar, cl.status};
+  rq::SampleQrcpArgs a{Bblk, ell, ell, nc, bJ, cl.w.swaps, cl.w.cand, cl.w.candcol, cl.bar,
+                       cl.status};
   CKL(1, rq::launch_sample_qrcp(a, cl.h->num_sms, cl.st));
   return RQRCP_OK;
 }
@@ -439,6 +491,28 @@ int rqrcp_sketch(rqrcp_handle_t h, int64_t m, int64_t n, const double* dA, int64
   PhaseScope ps(h, PH_SKETCH, 2.0 * ell * (double)m * (double)n);
   CKL(1, rq::launch_gaussian(seed, kOmegaStream, ell, m, cl.w.omega, ell, nullptr, cl.st));
   CK(gemm(cl, 'N', 'N', 0, ell, n, m, 1.0, cl.w.omega, ell, dA, lda, 0.0, dB, ldb));
+  return RQRCP_OK;
+}
+
+int rqrcp_sample_qrcp(rqrcp_handle_t h, int ell, int64_t nc, int steps, double* dB, int64_t ldb,
+                      int64_t* d_swaps) {
+  if (!h) return -1;
+  if (ell < 1 || ell > kMaxEll) return -2;
+  if (nc < 1) return -3;
+  if (steps < 1 || steps > ell || steps > nc) return -4;
+  if (!dB) return -5;
+  if (ldb < ell) return -6;
+  if (!d_swaps) return -7;
+  if (!rq::sample_qrcp_fits(ell, nc, h->num_sms)) return RQRCP_ERR_UNSUPPORTED;
+  Call cl;
+  int r = begin(h, 'S', ell, nc, 1, 1, ell - 1, &cl);
+  if (r) return r;
+  double fl = 0.0;
+  for (int i = 0; i < steps; ++i) fl += 4.0 * (ell - i) * (double)(nc - i - 1);
+  PhaseScope ps(cl.h, PH_SAMPLE, fl);
+  rq::SampleQrcpArgs a{dB, ldb, ell, nc, steps, d_swaps, cl.w.cand, cl.w.candcol, cl.bar,
+                       cl.status};
+  CKL(1, rq::launch_sample_qrcp(a, cl.h->num_sms, cl.st));
   return RQRCP_OK;
 }
 
@@ -684,6 +758,208 @@ int tuxv(rqrcp_handle_t h, int64_t m, int64_t n, const double* dA, int64_t lda, 
     CKL(1, rq::launch_copy2d(dU, ldu, w.F, m, m, k, cl.st));
   }
   if ((r = orgqr_core(cl, m, k, w.F, m, b, w.Tall, dU, ldu))) return r;
+  return RQRCP_OK;
+}
+
+int rqrcp_factor_mixed(rqrcp_handle_t h, int64_t m, int64_t n, float* dA, int64_t lda, int b,
+                       int p, uint64_t seed, int64_t* d_jpvt, double* d_tau, double* d_rdiag) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (n < 1) return -3;
+  if (!dA) return -4;
+  if (lda < m) return -5;
+  if (b < 1) return -6;
+  if (p < 0) return -7;
+  if (!d_jpvt) return -9;
+  if (!d_tau) return -10;
+  if (!d_rdiag) return -11;
+  const int64_t k = std::min(m, n);
+  if (b > k) b = (int)k;
+  const int ell = b + p;
+  if (!sizes_fit(h->num_sms, m, n, b, ell)) return RQRCP_ERR_UNSUPPORTED;
+  Call cl;
+  int r = begin(h, 'M', m, n, k, b, p, &cl);
+  if (r) return r;
+  Work& w = cl.w;
+  {
+    // Omega in FP64 from Philox, rounded for the BF16 sketch B = Omega A
+    PhaseScope ps(cl.h, PH_SKETCH, 2.0 * ell * (double)m * (double)n);
+    CKL(1, rq::launch_gaussian(seed, kOmegaStream, ell, m, w.omega, ell, nullptr, cl.st));
+    CKL(1, rq::launch_convert_f64_f32(w.omega, ell, w.omega32, ell, ell, m, cl.st));
+    CK(tcgemm(cl, 'N', 'N', ell, n, m, 1.0f, w.omega32, ell, dA, lda, 0.0f, w.B32, ell, 1));
+    CKL(1, rq::launch_convert_f32_f64(w.B32, ell, w.B, ell, ell, n, cl.st));
+    CKL(1, rq::launch_iota(d_jpvt, n, cl.st));
+  }
+  for (int64_t j0 = 0; j0 < k; j0 += b) {
+    const int bJ = (int)std::min<int64_t>(b, k - j0);
+    const int64_t nc = n - j0, n2 = nc - bJ, mJ = m - j0;
+    double* Bblk = w.B + j0 * ell;
+    if ((r = sample_step(cl, Bblk, ell, nc, bJ))) return r;
+    {
+      PhaseScope ps(cl.h, PH_PERM, 0.0);
+      CKL(3, rq::launch_apply_swaps_f32(dA, lda, m, j0, w.swaps, bJ, d_jpvt, w.map, w.permbuf32,
+                                        cl.st));
+    }
+    // FP64 panel, T and R diagonal; FP32 copies back into A and Y32
+    float* P = dA + j0 + j0 * lda;
+    {
+      PhaseScope ps(cl.h, PH_OTHER, 0.0);
+      CKL(1, rq::launch_convert_f32_f64(P, lda, w.P64, m, mJ, bJ, cl.st));
+    }
+    if ((r = panel_step(cl, w.P64, m, mJ, bJ, d_tau + j0, w.T))) return r;
+    {
+      PhaseScope ps(cl.h, PH_OTHER, 0.0);
+      CKL(1, rq::launch_panel_writeback(w.P64, m, mJ, bJ, P, lda, w.Y32, m, d_rdiag + j0, cl.st));
+    }
+    float* A2 = dA + j0 + (j0 + bJ) * lda;
+    if (n2 > 0) {
+      // trailing update with split-BF16 x3 tensor-core products
+      PhaseScope ps(cl.h, PH_TRAIL, 4.0 * (double)mJ * (double)n2 * bJ + 2.0 * bJ * bJ * (double)n2);
+      CKL(1, rq::launch_convert_f64_f32(w.T, bJ, w.T32, bJ, bJ, bJ, cl.st));
+      CK(tcgemm(cl, 'T', 'N', bJ, n2, mJ, 1.0f, w.Y32, m, A2, lda, 0.0f, w.Z32, bJ, 3));
+      CK(tcgemm(cl, 'T', 'N', bJ, n2, bJ, 1.0f, w.T32, bJ, w.Z32, bJ, 0.0f, w.W32, bJ, 3));
+      CK(tcgemm(cl, 'N', 'N', mJ, n2, bJ, -1.0f, w.Y32, m, w.W32, bJ, 1.0f, A2, lda, 3));
+    }
+    if (j0 + bJ < k) {
+      // Eq. (3) in FP64 with R11 from the FP64 panel and R12 widened from FP32;
+      // an exactly singular R11 keeps S12 (no re-sample in this mode)
+      PhaseScope ps(cl.h, PH_SUPD, (double)bJ * bJ * bJ / 3.0 + 2.0 * bJ * bJ * (double)n2);
+      CKL(1, rq::launch_w11(Bblk, ell, w.P64, m, bJ, w.W11, cl.flag, cl.status, cl.st));
+      CKL(1, rq::launch_convert_f32_f64(A2, lda, w.R12, bJ, bJ, n2, cl.st));
+      CK(gemm(cl, 'N', 'N', 2, bJ, n2, bJ, -1.0, w.W11, bJ, w.R12, bJ, 1.0,
+              Bblk + (int64_t)bJ * ell, ell, cl.flag, 0));
+    }
+  }
+  return RQRCP_OK;
+}
+
+int trqrcp_mixed(rqrcp_handle_t h, int64_t m, int64_t n, const float* dA, int64_t lda, int64_t k,
+                 int b, int p, uint64_t seed, int64_t* d_jpvt, double* d_tau, float* dY,
+                 int64_t ldy, float* dR, int64_t ldr, double* d_rdiag) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (n < 1) return -3;
+  if (!dA) return -4;
+  if (lda < m) return -5;
+  if (k < 1 || k > std::min(m, n)) return -6;
+  if (b < 1) return -7;
+  if (p < 0) return -8;
+  if (!d_jpvt) return -10;
+  if (!d_tau) return -11;
+  if (!dY) return -12;
+  if (ldy < m) return -13;
+  if (!dR) return -14;
+  if (ldr < k) return -15;
+  if (!d_rdiag) return -16;
+  if (b > k) b = (int)k;
+  const int ell = b + p;
+  if (!sizes_fit(h->num_sms, m, n, b, ell)) return RQRCP_ERR_UNSUPPORTED;
+  Call cl;
+  int r = begin(h, 'V', m, n, k, b, p, &cl);
+  if (r) return r;
+  Work& w = cl.w;
+  float* Ahat = w.Y32;
+  float* Wt = w.W32;                                   // k x n, ld k
+  float* YY = reinterpret_cast<float*>(w.Wt);          // b x k, ld b
+  {
+    PhaseScope ps(cl.h, PH_SKETCH, 2.0 * ell * (double)m * (double)n);
+    CKL(1, rq::launch_gaussian(seed, kOmegaStream, ell, m, w.omega, ell, nullptr, cl.st));
+    CKL(1, rq::launch_convert_f64_f32(w.omega, ell, w.omega32, ell, ell, m, cl.st));
+    CK(tcgemm(cl, 'N', 'N', ell, n, m, 1.0f, w.omega32, ell, dA, lda, 0.0f, w.B32, ell, 1));
+    CKL(1, rq::launch_convert_f32_f64(w.B32, ell, w.B, ell, ell, n, cl.st));
+  }
+  {
+    PhaseScope ps(cl.h, PH_OTHER, 0.0);
+    CKL(1, rq::launch_iota(d_jpvt, n, cl.st));
+    CK(cudaMemset2DAsync(dY, ldy * sizeof(float), 0, m * sizeof(float), k, cl.st));
+    CK(cudaMemset2DAsync(dR, ldr * sizeof(float), 0, k * sizeof(float), n, cl.st));
+    CK(cudaMemsetAsync(Wt, 0, sizeof(float) * k * n, cl.st));
+  }
+  for (int64_t j0 = 0; j0 < k; j0 += b) {
+    const int bJ = (int)std::min<int64_t>(b, k - j0);
+    const int64_t nc = n - j0, n2 = nc - bJ, mJ = m - j0;
+    double* Bblk = w.B + j0 * ell;
+    if ((r = sample_step(cl, Bblk, ell, nc, bJ))) return r;
+    {
+      PhaseScope ps(cl.h, PH_PERM, 0.0);
+      CKL(3, rq::launch_apply_swaps_f32(Wt, k, j0, j0, w.swaps, bJ, d_jpvt, w.map, w.permbuf32, cl.st));
+      CKL(3, rq::launch_apply_swaps_f32(dR, ldr, j0, j0, w.swaps, bJ, nullptr, w.map, w.permbuf32,
+                                        cl.st));
+    }
+    {
+      // selected columns A_hat = A(:, sel) - Y1 W1^T(:, sel) on rows j0..m-1
+      PhaseScope ps(cl.h, PH_TRQ, 2.0 * (double)mJ * bJ * (double)j0);
+      CKL(1, rq::launch_gather_cols_f32(dA, lda, j0, mJ, d_jpvt + j0, bJ, Ahat, m, cl.st));
+      if (j0 > 0)
+        CK(tcgemm(cl, 'N', 'N', mJ, bJ, j0, -1.0f, dY + j0, ldy, Wt + j0 * k, k, 1.0f, Ahat, m, 3));
+      CKL(1, rq::launch_convert_f32_f64(Ahat, m, w.P64, m, mJ, bJ, cl.st));
+    }
+    if ((r = panel_step(cl, w.P64, m, mJ, bJ, d_tau + j0, w.T))) return r;
+    {
+      PhaseScope ps(cl.h, PH_OTHER, 0.0);
+      // Y (explicit, FP32) and R11 (FP32, diagonal also in FP64)
+      CKL(1, rq::launch_panel_writeback(w.P64, m, mJ, bJ, Ahat, m, dY + j0 + j0 * ldy, ldy,
+                                        d_rdiag + j0, cl.st));
+      CKL(1, rq::launch_copy_upper_f32(Ahat, m, bJ, dR + j0 + j0 * ldr, ldr, cl.st));
+      CKL(1, rq::launch_convert_f64_f32(w.T, bJ, w.T32, bJ, bJ, bJ, cl.st));
+    }
+    if (n2 > 0) {
+      PhaseScope ps(cl.h, PH_TRQ,
+                    2.0 * bJ * (double)mJ * (double)n2 + 2.0 * bJ * (double)mJ * j0 +
+                        2.0 * bJ * (double)j0 * (double)n2 + 2.0 * bJ * bJ * (double)n2 +
+                        2.0 * bJ * (double)(j0 + bJ) * (double)n2);
+      const int64_t* tcols = d_jpvt + j0 + bJ;
+      const float* Y2 = dY + j0 + j0 * ldy;
+      // W2^T = T2^T (Y2^T A(:, trailing) - (Y2^T Y1) W1^T(:, trailing))
+      CK(tcgemm(cl, 'T', 'N', bJ, n2, mJ, 1.0f, Y2, ldy, dA + j0, lda, 0.0f, w.Z32, bJ, 3, tcols));
+      if (j0 > 0) {
+        CK(tcgemm(cl, 'T', 'N', bJ, j0, mJ, 1.0f, Y2, ldy, dY + j0, ldy, 0.0f, YY, bJ, 3));
+        CK(tcgemm(cl, 'N', 'N', bJ, n2, j0, -1.0f, YY, bJ, Wt + (j0 + bJ) * k, k, 1.0f, w.Z32, bJ,
+                  3));
+      }
+      CK(tcgemm(cl, 'T', 'N', bJ, n2, bJ, 1.0f, w.T32, bJ, w.Z32, bJ, 0.0f, Wt + j0 + (j0 + bJ) * k,
+                k, 3));
+      // new rows of R: A(rows J, trailing) - Y(rows J, :) W^T(:, trailing)
+      float* Rrows = dR + j0 + (j0 + bJ) * ldr;
+      CKL(1, rq::launch_gather_cols_f32(dA, lda, j0, bJ, tcols, n2, Rrows, ldr, cl.st));
+      CK(tcgemm(cl, 'N', 'N', bJ, n2, j0 + bJ, -1.0f, dY + j0, ldy, Wt + (j0 + bJ) * k, k, 1.0f,
+                Rrows, ldr, 3));
+    }
+    if (j0 + bJ < k) {
+      PhaseScope ps(cl.h, PH_SUPD, (double)bJ * bJ * bJ / 3.0 + 2.0 * bJ * bJ * (double)n2);
+      CKL(1, rq::launch_w11(Bblk, ell, w.P64, m, bJ, w.W11, cl.flag, cl.status, cl.st));
+      CKL(1, rq::launch_convert_f32_f64(dR + j0 + (j0 + bJ) * ldr, ldr, w.R12, bJ, bJ, n2, cl.st));
+      CK(gemm(cl, 'N', 'N', 2, bJ, n2, bJ, -1.0, w.W11, bJ, w.R12, bJ, 1.0,
+              Bblk + (int64_t)bJ * ell, ell, cl.flag, 0));
+    }
+  }
+  return RQRCP_OK;
+}
+
+int rqrcp_gemm_bf16x(rqrcp_handle_t h, char transA, char transB, int64_t m, int64_t n, int64_t k,
+                     float alpha, const float* dA, int64_t lda, const float* dB, int64_t ldb,
+                     float beta, float* dC, int64_t ldc, int slices) {
+  if (!h) return -1;
+  if (transA != 'N' && transA != 'T') return -2;
+  if (transB != 'N' && transB != 'T') return -3;
+  if (m < 0) return -4;
+  if (n < 0) return -5;
+  if (k < 0) return -6;
+  const int64_t arows = transA == 'N' ? m : k, brows = transB == 'N' ? k : n;
+  if (!dA && m * k > 0) return -8;
+  if (lda < std::max<int64_t>(1, arows)) return -9;
+  if (!dB && n * k > 0) return -10;
+  if (ldb < std::max<int64_t>(1, brows)) return -11;
+  if (!dC && m * n > 0) return -13;
+  if (ldc < std::max<int64_t>(1, m)) return -14;
+  if (slices != 1 && slices != 3) return -15;
+  Call cl{};
+  cl.h = h;
+  cl.st = h->stream;
+  PhaseScope ps(h, PH_TRAIL, 2.0 * (double)m * (double)n * (double)k);
+  rq::TcGemmArgs g{transA, transB, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc, h->state,
+                   false, false, 1, nullptr, 0, nullptr};
+  CKL(1, rq::launch_tc_gemm(g, slices, cl.st));
   return RQRCP_OK;
 }
 

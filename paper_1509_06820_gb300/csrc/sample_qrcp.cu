@@ -91,8 +91,11 @@ __global__ void __launch_bounds__(NT, 1) sample_qrcp_kernel(SampleQrcpArgs a) {
   const int tid = threadIdx.x;
   const int grp = tid / LPC, lig = tid % LPC;
 
-  // load the owned columns (contiguous in B), logical position = index
-  for (int64_t e = tid; e < (int64_t)ncol * ell; e += NT) col[e] = a.B[c_lo * ell + e];
+  // load the owned columns, logical position = index
+  for (int64_t e = tid; e < (int64_t)ncol * ell; e += NT) {
+    const int64_t c = e / ell, r = e % ell;
+    col[e] = a.B[(c_lo + c) * a.ldb + r];
+  }
   for (int c = tid; c < ncol; c += NT) {
     lpos[c] = c_lo + c;
     done[c] = 0;
@@ -216,7 +219,7 @@ __global__ void __launch_bounds__(NT, 1) sample_qrcp_kernel(SampleQrcpArgs a) {
   // permuted (logical) order
   for (int c = 0; c < ncol; ++c) {
     const long long L = lpos[c];
-    for (int r = tid; r < ell; r += NT) a.B[L * ell + r] = col[r + (size_t)c * ell];
+    for (int r = tid; r < ell; r += NT) a.B[L * a.ldb + r] = col[r + (size_t)c * ell];
   }
 }
 

@@ -187,3 +187,105 @@ def test_tuxv_matches_oracle(lib, m, n, k, b, p):
     approx_o = Uo @ Xo @ Vo.T
     assert np.linalg.norm(approx_g - approx_o) <= 1e-10 * np.linalg.norm(approx_o)
     np.testing.assert_allclose(np.abs(np.diag(Xg)), np.abs(np.diag(Xo)), rtol=1e-9)
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
+@pytest.mark.parametrize("m,n,k", [(128, 128, 64), (300, 200, 150), (64, 700, 1000), (129, 1, 7)])
+def test_tc_gemm_bf16x3(lib, ta, tb, m, n, k):
+    """Split-BF16 x3 tensor-core GEMM against an FP64 product: FP32-level error."""
+    g = torch.Generator().manual_seed(m + n + k)
+    Af = torch.randn((m, k) if ta == "N" else (k, m), generator=g, dtype=torch.float64)
+    Bf = torch.randn((k, n) if tb == "N" else (n, k), generator=g, dtype=torch.float64)
+    A32, B32 = Af.float(), Bf.float()
+    A = lib.colmajor(A32.cuda())
+    B = lib.colmajor(B32.cuda())
+    C0 = lib.colmajor(torch.randn((m, n), generator=g, dtype=torch.float32).cuda())
+    C = C0.clone()
+    lib.gemm_bf16x(A, B, ta, tb, alpha=-1.0, beta=1.0, C=C, slices=3)
+    assert lib.sync_info() == 0
+    opA = A32.double() if ta == "N" else A32.double().t()
+    opB = B32.double() if tb == "N" else B32.double().t()
+    ref = C0.cpu().double() - opA @ opB
+    err = (C.cpu().double() - ref).abs().max().item()
+    scale = (opA.abs() @ opB.abs()).max().item() + C0.abs().max().item()
+    # FP32 GEMM bound: K accumulations plus the dropped slice products
+    assert err <= max(8, k) * 2.0 ** -24 * scale, err / scale
+
+
+@pytest.mark.parametrize("m,n,k", [(256, 256, 128), (100, 300, 70)])
+def test_tc_gemm_bf16x1(lib, m, n, k):
+    """One-slice mode: the product of the bf16-rounded operands, FP32 accumulation."""
+    g = torch.Generator().manual_seed(7)
+    A32 = torch.randn((m, k), generator=g)
+    B32 = torch.randn((k, n), generator=g)
+    C = lib.gemm_bf16x(lib.colmajor(A32.cuda()), lib.colmajor(B32.cuda()), slices=1)
+    assert lib.sync_info() == 0
+    ref = A32.bfloat16().double() @ B32.bfloat16().double()
+    err = (C.cpu().double() - ref).abs().max().item()
+    assert err <= 2.0 ** -22 * (A32.abs().double() @ B32.abs().double()).max().item()
+
+
+def _mixed_errors(A, A32, jp, t, rdiag):
+    """Reconstruction and orthogonality of the mixed-precision factors in FP64."""
+    m, n = A.shape
+    k = min(m, n)
+    F = A32.astype(np.float64)
+    Q = hh.form_q(F, t, m)
+    R = np.triu(F)
+    R[np.arange(k), np.arange(k)] = rdiag
+    rec = np.linalg.norm(A[:, jp] - Q @ R) / np.linalg.norm(A)
+    orth = np.abs(Q.T @ Q - np.eye(m)).max()
+    return rec, orth, R
+
+
+@pytest.mark.parametrize("m,n,b,p", [(1000, 1000, 128, 16), (700, 400, 64, 8), (300, 900, 128, 16)])
+def test_rqrcp_mixed_reconstruction(lib, m, n, b, p):
+    """Mixed precision (BF16 sketch, split-BF16 x3 trailing update, FP64
+    panel/T/R-diagonal): reconstruction <= 1e-6 against the FP64 input; its
+    R stated against the FP64 oracle replayed on the same pivots."""
+    A = synth.spiked(m, n, rank=min(m, n) // 4, scale=1e3)
+    A32 = A.astype(np.float32)
+    dA = lib.colmajor(torch.from_numpy(A32).cuda())
+    jpvt, tau, rdiag = lib.rqrcp_factor_mixed(dA, b, p, 1)
+    assert lib.sync_info() == 0
+    jp = host(jpvt)
+    assert sorted(jp.tolist()) == list(range(n))
+    rec, orth, R = _mixed_errors(A32.astype(np.float64), host(dA), jp, host(tau), host(rdiag))
+    assert rec <= 1e-6, rec
+    assert orth <= 1e-5, orth
+    # the FP64 oracle on the same pivots (replay with a loose tie window: the
+    # BF16 sample may legitimately reorder close columns)
+    Fo, jo, to, _ = oracle.rqrcp(A32.astype(np.float64), b, p, seed=1, replay_jpvt=jp,
+                                 tie_rtol=1.0)
+    k = min(m, n)
+    rel = np.linalg.norm(R[:k] - np.triu(Fo[:k])) / np.linalg.norm(np.triu(Fo[:k]))
+    print(f"mixed {m}x{n}: recon {rec:.2e} orth {orth:.2e} R vs FP64 oracle {rel:.2e}")
+    assert rel <= 1e-5
+
+
+def _swaps_to_ids(swaps, nc):
+    perm = np.arange(nc)
+    for i, s in enumerate(swaps):
+        perm[[i, s]] = perm[[s, i]]
+    return perm
+
+
+@pytest.mark.parametrize("ell,nc,steps,ldpad", [(72, 5000, 64, 0), (40, 333, 32, 5), (9, 20, 9, 0),
+                                                (144, 3000, 128, 3)])
+def test_sample_qrcp_matches_oracle(lib, ell, nc, steps, ldpad):
+    """Alg. 1 halted after `steps` pivots on an l x n sample (row a3 alone)."""
+    from oracle.rqrcp import sample_qrcp
+    r = np.random.default_rng(ell + nc)
+    B = r.standard_normal((ell, nc)) * np.exp(r.standard_normal(nc))[None, :]
+    store = torch.zeros((nc, ell + ldpad), dtype=torch.float64)
+    store[:, :ell] = torch.from_numpy(B.T)
+    dB_full = store.cuda().t()               # (ell + ldpad) x nc column-major
+    dB = dB_full[:ell]
+    swaps = host(lib.sample_qrcp(dB, steps))
+    assert lib.sync_info() == 0
+    ids = _swaps_to_ids(swaps, nc)
+    S = B.copy()
+    sample_qrcp(S, steps, ids=np.arange(nc), forced_ids=ids[:steps])
+    Sg = host(dB)
+    assert np.abs(Sg - S).max() <= 1e-12 * np.abs(B).max()
+    assert np.all(np.tril(Sg[:, :steps], -1) == 0.0)
