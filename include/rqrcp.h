@@ -204,6 +204,28 @@ int rqrcp_sample_qrcp(rqrcp_handle_t handle, int ell, int64_t nc, int steps, dou
                       int64_t ldb, int64_t* d_swaps);
 
 /*
+ * Allocation-free form of rqrcp_sample_qrcp (the paper has no counterpart:
+ * this is a deployment variant).  For callers that cannot allocate device
+ * memory -- code running during CUDA graph stream capture, latency-critical
+ * loops that must stay out of the driver's allocator, processes whose device
+ * memory is owned by a pool or arena -- it runs the same sample QRCP with its
+ * scratch in a fixed device array compiled into the library (about 467 KB,
+ * held by every GPU that loads the library until exit), so it needs no
+ * handle and calls no cudaMalloc/cudaFree.
+ *   ell, nc, steps, dB, ldb, d_swaps : as rqrcp_sample_qrcp (ell <= 192)
+ *   d_info      : optional device int; RQRCP_INFO_* bits are ORed into it
+ *                 (the caller clears it); NULL keeps the status internal
+ *   cuda_stream : the cudaStream_t to run on (NULL = legacy default stream)
+ * Returns -i for an invalid argument i, RQRCP_ERR_UNSUPPORTED when the sample
+ * does not fit the kernel's shared memory, RQRCP_ERR_CUDA on a CUDA error.
+ * The first call on a device looks up the array's device address; make it
+ * before any stream capture.  All calls share the array: calls that overlap on
+ * the GPU race, so order them (for example on one stream).
+ */
+int rqrcp_sample_qrcp_noalloc(int ell, int64_t nc, int steps, double* dB, int64_t ldb,
+                              int64_t* d_swaps, int* d_info, void* cuda_stream);
+
+/*
  * Instrumentation (no counterpart in the paper).  While enabled, every phase
  * of a call is bracketed by CUDA events recorded on the handle's stream, and
  * the algorithmic FLOP count and the number of kernel launches of each phase

@@ -51,6 +51,7 @@ SIGNATURES = [
     ("rqrcp_gemm_bf16x", _I, [_P, ctypes.c_char, ctypes.c_char, _I64, _I64, _I64, ctypes.c_float,
                           _P, _I64, _P, _I64, ctypes.c_float, _P, _I64, _I]),
     ("rqrcp_sample_qrcp", _I, [_P, _I, _I64, _I, _P, _I64, _P]),
+    ("rqrcp_sample_qrcp_noalloc", _I, [_I, _I64, _I, _P, _I64, _P, _P, _P]),
     ("rqrcp_profile", _I, [_P, _I]),
     ("rqrcp_profile_read", _I, [_P, _I, _P, _P, _P]),
 ]

@@ -19,6 +19,7 @@
 // nrm *= sqrt(max(0, 1 - (|s_ij|/nrm)^2)), recomputed exactly from rows
 // j+1.. when f * (nrm/nrm_ref)^2 <= sqrt(eps); identical to the oracle.
 #include <climits>
+#include <mutex>
 
 #include "kernels.cuh"
 
@@ -264,5 +265,98 @@ cudaError_t launch_sample_qrcp(const SampleQrcpArgs& a, int num_sms, cudaStream_
   return cudaLaunchCooperativeKernel((const void*)sample_qrcp_kernel, dim3((unsigned)G),
                                      dim3(NT), params, smem, st);
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the sample QRCP launch.
+//
+// Some callers cannot allocate device memory: code running while a stream is
+// being captured into a CUDA graph (cudaMalloc is not a stream operation, so
+// it cannot be recorded and breaks the capture), latency-critical loops that
+// must not enter the driver's allocator, and processes whose device memory
+// belongs to a caching pool or a fixed arena, where a direct cudaMalloc would
+// fragment it or exceed its reservation.  rqrcp_sample_qrcp_noalloc serves
+// them: it launches the same kernel as rqrcp_sample_qrcp, but its scratch
+// (the candidate norms and columns, the grid barrier and a fallback status
+// word) lives in the file-scope device array below instead of handle memory.
+//
+// * Size: kNoAllocScratchDoubles doubles (2*152*2 + 2*152*192 + 8, about
+//   467 KB).  Every GPU that loads this library holds the array until the
+//   process exits.  It covers ell <= 192 sample rows with at most 152 CTAs;
+//   larger ell is rejected.
+// * The array's host-side name is only a stand-in for the symbol; the first
+//   call on each device looks up its device address with
+//   cudaGetSymbolAddress (with that device current) and caches it.  Make that
+//   first call before any stream capture.
+// * Every call shares the array and it keeps the previous call's contents.
+//   Each call clears the words that must start at zero (the barrier, and the
+//   fallback status word when no info word is passed) on its stream before
+//   the launch.  Calls whose kernels overlap on the GPU race on the array:
+//   run them on one stream, or order them.
+namespace {
+
+constexpr int kNoAllocMaxGrid = 152;  // CTAs (one per SM, capped)
+constexpr int64_t kNoAllocCand = 2LL * kNoAllocMaxGrid * 2;
+constexpr int64_t kNoAllocCandCol = 2LL * kNoAllocMaxGrid * MAX_ELL;
+// candidates, candidate columns, then 8 doubles for the barrier and status
+constexpr int64_t kNoAllocScratchDoubles = kNoAllocCand + kNoAllocCandCol + 8;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once
+// per device; the host-side name of the array is not a device address).
+cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace rq
+
+extern "C" int rqrcp_sample_qrcp_noalloc(int ell, int64_t nc, int steps, double* dB, int64_t ldb,
+                                         int64_t* d_swaps, int* d_info, void* cuda_stream) {
+  using namespace rq;
+  if (ell < 1 || ell > MAX_ELL) return -1;
+  if (nc < 1) return -2;
+  if (steps < 1 || steps > ell || steps > nc) return -3;
+  if (!dB) return -4;
+  if (ldb < ell) return -5;
+  if (!d_swaps) return -6;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return RQRCP_ERR_CUDA;
+  if (sms > kNoAllocMaxGrid) sms = kNoAllocMaxGrid;
+  if (!sample_qrcp_fits(ell, nc, sms)) return RQRCP_ERR_UNSUPPORTED;
+  double* scratch = nullptr;
+  if (noalloc_scratch(&scratch) != cudaSuccess) return RQRCP_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  GridBarrier* bar = reinterpret_cast<GridBarrier*>(scratch + kNoAllocCand + kNoAllocCandCol);
+  int* status = d_info;
+  if (status == nullptr) {
+    // no caller word: keep the status in the array (cleared by every call)
+    status = reinterpret_cast<int*>(scratch + kNoAllocCand + kNoAllocCandCol + 4);
+    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return RQRCP_ERR_CUDA;
+  }
+  SampleQrcpArgs a{dB, ldb, ell, nc, steps, d_swaps, scratch, scratch + kNoAllocCand, bar, status};
+  // launch_sample_qrcp clears the barrier words before the cooperative launch
+  return launch_sample_qrcp(a, sms, st) == cudaSuccess ? RQRCP_OK : RQRCP_ERR_CUDA;
+}
+
+namespace rq {
 
 }  // namespace rq
