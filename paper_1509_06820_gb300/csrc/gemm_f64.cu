@@ -139,15 +139,26 @@ cudaError_t dispatch_amode(const GemmArgs& g, dim3 grid, int64_t kchunk, double*
 
 }  // namespace
 
+// Split-K factor: the FP64 pipe is the bottleneck, so pick the factor whose
+// CTA count fills whole waves of the resident slots (4 CTAs per SM at 64
+// registers x 256 threads) best, keeping at least 256 of K per split.
 int gemm_pick_splits(int64_t M, int64_t N, int64_t K, int num_sms) {
-  int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
-  int64_t want = 2LL * num_sms;
-  if (tiles >= want) return 1;
-  int64_t s = (want + tiles - 1) / tiles;
-  int64_t kmax = (K + 255) / 256;  // keep at least 256 of K per split
-  if (s > kmax) s = kmax;
-  if (s > 64) s = 64;
-  return (int)(s < 1 ? 1 : s);
+  const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  const int64_t slots = 4LL * num_sms;
+  if (tiles >= 8 * slots) return 1;
+  const int64_t kmax = std::max<int64_t>(1, std::min<int64_t>(64, K / 256));
+  int best = 1;
+  double best_eff = 0.0;
+  for (int64_t s = 1; s <= kmax; ++s) {
+    const int64_t ctas = tiles * s;
+    const int64_t waves = (ctas + slots - 1) / slots;
+    const double eff = (double)ctas / (double)(waves * slots);
+    if (eff > best_eff + 0.02) {
+      best_eff = eff;
+      best = (int)s;
+    }
+  }
+  return best;
 }
 
 cudaError_t launch_gemm(const GemmArgs& g, int splits, double* partial, cudaStream_t st) {

@@ -122,7 +122,8 @@ Work carve(char op, int64_t m, int64_t n, int64_t k, int b, int p, int sms, char
   const int64_t zc = std::max(n, k);
   w.Z = c.take<double>((size_t)bb * zc);
   w.W = c.take<double>((size_t)bb * zc);
-  w.skcap = (size_t)4 * sms * 4096 + 4096;
+  // split-K partial sums: up to ~20 splits of a b x max(n, k) product
+  w.skcap = std::max((size_t)4 * sms * 4096, (size_t)20 * bb * (size_t)zc) + 4096;
   w.skpart = c.take<double>(w.skcap);
   if (op == 'T' || op == 'U') {
     w.Wt = c.take<double>((size_t)k * n);
@@ -810,6 +811,8 @@ int rqrcp_factor_mixed(rqrcp_handle_t h, int64_t m, int64_t n, float* dA, int64_
     {
       PhaseScope ps(cl.h, PH_OTHER, 0.0);
       CKL(1, rq::launch_panel_writeback(w.P64, m, mJ, bJ, P, lda, w.Y32, m, d_rdiag + j0, cl.st));
+      CKL(2, rq::launch_tau_t_from_f32(w.Y32, m, mJ, bJ, d_tau + j0, w.T, w.ppart, cl.h->num_sms,
+                                       cl.st));
     }
     float* A2 = dA + j0 + (j0 + bJ) * lda;
     if (n2 > 0) {
@@ -900,6 +903,8 @@ int trqrcp_mixed(rqrcp_handle_t h, int64_t m, int64_t n, const float* dA, int64_
       // Y (explicit, FP32) and R11 (FP32, diagonal also in FP64)
       CKL(1, rq::launch_panel_writeback(w.P64, m, mJ, bJ, Ahat, m, dY + j0 + j0 * ldy, ldy,
                                         d_rdiag + j0, cl.st));
+      CKL(2, rq::launch_tau_t_from_f32(dY + j0 + j0 * ldy, ldy, mJ, bJ, d_tau + j0, w.T, w.ppart,
+                                       cl.h->num_sms, cl.st));
       CKL(1, rq::launch_copy_upper_f32(Ahat, m, bJ, dR + j0 + j0 * ldr, ldr, cl.st));
       CKL(1, rq::launch_convert_f64_f32(w.T, bJ, w.T32, bJ, bJ, bJ, cl.st));
     }

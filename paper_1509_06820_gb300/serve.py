@@ -1,0 +1,272 @@
+"""Continuous-batching server for low-rank approximation requests.
+
+Each request asks for the rank-k TRQRCP factorization (Alg. 6, mixed
+precision: FP32 storage, split-BF16 tensor-core products, FP64 sample QRCP,
+panels and T) of an m x n matrix.  The server keeps a pool of slots; a slot
+owns a CUDA stream and an rqrcp handle whose scratch holds the request's
+sample, reflector and inner-product state on the device while it runs.
+
+* Admission: requests wait in FIFO order; one is admitted when a slot is free
+  and its HBM footprint (input, outputs) fits in what is left of the budget
+  after the slots' reserved scratch.  Requests that arrive while others run
+  are admitted as soon as a slot and memory free up, so their kernels overlap
+  on the device with the ones already in flight (continuous batching).
+* Launch: a request is enqueued on its slot's stream as one CUDA graph: the
+  first request of each (slot, size bucket) is captured (shapes rounded up to
+  the bucket, A zero-padded -- zero columns are never pivoted and zero rows
+  leave the reflectors unchanged, and the Philox compression matrix is
+  prefix-stable in m), later ones replay it.  With graphs off the calls are
+  enqueued eagerly.
+* Completion is polled with CUDA events; latency = completion - arrival.
+* b and p per size bucket come from the autotuner table (autotune.py).
+
+Only host-side scheduling lives here: every numerical step runs in the CUDA
+kernels behind the C ABI.
+"""
+import collections
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import _ld, _ptr, empty_colmajor, Handle, trqrcp_mixed, load
+
+
+def request_flops(m, n, k, ell):
+    """Algorithmic flops of one TRQRCP request: sketch 2 l m n plus the
+    inner products with A, 2 m n k (the same count for every (b, p))."""
+    return 2.0 * ell * m * n + 2.0 * m * n * k
+
+
+class Request:
+    __slots__ = ("rid", "m", "n", "k", "seed", "t_arrival", "t_admit", "t_done", "result",
+                 "bucket", "b", "p", "slot")
+
+    def __init__(self, rid, m, n, k, seed=None, t_arrival=0.0):
+        self.rid = rid
+        self.m, self.n, self.k = int(m), int(n), int(k)
+        self.seed = rid if seed is None else seed
+        self.t_arrival = t_arrival
+        self.t_admit = None
+        self.t_done = None
+        self.result = None
+        self.bucket = None
+        self.b = self.p = None
+        self.slot = None
+
+
+def factors(req):
+    """(jpvt[:k], tau, Y (m x k), R (k x n), rdiag) of a finished request, on
+    the device.  R keeps the columns of the original matrix in pivot order:
+    padding columns of the size bucket (index >= n) are dropped."""
+    jpvt, tau, Y, R, rdiag = req.result
+    keep = jpvt < req.n
+    return jpvt[keep][: req.n], tau, Y, R[:, keep], rdiag
+
+
+def make_input(req, out, stream):
+    """The request's matrix A = X Y^T (X: m x k, Y: n x k, N(0,1) from the
+    request's seed) written into the column-major FP32 view `out`."""
+    with torch.cuda.stream(stream):
+        g = torch.Generator(device=out.device)
+        g.manual_seed(int(req.seed))
+        X = torch.randn((req.m, req.k), generator=g, device=out.device, dtype=torch.float32)
+        Y = torch.randn((req.n, req.k), generator=g, device=out.device, dtype=torch.float32)
+        out[: req.m, : req.n].t().copy_(Y @ X.t())
+
+
+class Slot:
+    def __init__(self, device, max_m, max_n, max_k, use_graphs):
+        self.device = device
+        self.stream = torch.cuda.Stream(device)
+        self.handle = Handle(device)
+        self.event = torch.cuda.Event()
+        self.req = None
+        self.use_graphs = use_graphs
+        self.graphs = {}  # bucket -> (graph, A view, outputs)
+        self.max = (max_m, max_n, max_k)
+
+    def _buffers(self, bucket):
+        M, N, K = bucket
+        A = empty_colmajor(M, N, self.device, torch.float32)
+        outs = (torch.empty(N, dtype=torch.int64, device=self.device),
+                torch.empty(K, dtype=torch.float64, device=self.device),
+                empty_colmajor(M, K, self.device, torch.float32),
+                empty_colmajor(K, N, self.device, torch.float32),
+                torch.empty(K, dtype=torch.float64, device=self.device))
+        return A, outs
+
+    def launch(self, req):
+        M, N, K = req.bucket
+        entry = self.graphs.get((req.bucket, req.b, req.p))
+        if entry is None:
+            A, outs = self._buffers(req.bucket)
+            graph = None
+            with torch.cuda.stream(self.stream):
+                self.handle.reserve("V", M, N, K, req.b, req.p)
+                A.zero_()
+                # eager run first: sets kernel attributes and sizes the scratch
+                trqrcp_mixed(A, K, req.b, req.p, 1, handle=self.handle, out=outs)
+            if self.use_graphs:
+                self.stream.synchronize()
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph, stream=self.stream):
+                    trqrcp_mixed(A, K, req.b, req.p, 1, handle=self.handle, out=outs)
+            entry = (graph, A, outs)
+            self.graphs[(req.bucket, req.b, req.p)] = entry
+        graph, A, outs = entry
+        self.req = req
+        req.slot = self
+        with torch.cuda.stream(self.stream):
+            if req.m < M or req.n < N:
+                A.zero_()
+            make_input(req, A, self.stream)
+            if graph is not None:
+                graph.replay()
+            else:
+                trqrcp_mixed(A, K, req.b, req.p, 1, handle=self.handle, out=outs)
+            # the request keeps its own copy of the factors; the slot's
+            # buffers are reused by the next request
+            jpvt, tau, Y, R, rdiag = outs
+            k, m = req.k, req.m
+            req.result = (jpvt.clone(), tau[:k].clone(), Y[:m, :k].clone(), R[:k, :].clone(),
+                          rdiag[:k].clone())
+            self.event.record(self.stream)
+
+    def done(self):
+        return self.req is not None and self.event.query()
+
+
+class Server:
+    """Continuous-batching TRQRCP server on one GPU.
+
+    `slots` are Slot objects (or any object with launch(req), done() and a
+    `req` attribute); `Server.on_gpu` builds real ones.
+    """
+
+    def __init__(self, slots, hbm_budget=16 << 30, tuner=None, bucket=512, kbucket=32,
+                 footprint_fn=None, clock=time.perf_counter):
+        self.bucket = bucket
+        self.kbucket = kbucket
+        self.tuner = tuner
+        self.slots = list(slots)
+        self.free = collections.deque(self.slots)
+        self.pending = collections.deque()
+        self.running = []
+        self.done = []
+        self.hbm_budget = hbm_budget
+        self.in_flight_bytes = 0
+        self.max_in_flight = 0
+        self.footprint_fn = footprint_fn
+        self.clock = clock
+
+    @classmethod
+    def on_gpu(cls, device="cuda", slots=8, use_graphs=True, max_m=4096, max_n=4096, max_k=128,
+               **kw):
+        dev = torch.device(device)
+        return cls([Slot(dev, max_m, max_n, max_k, use_graphs) for _ in range(slots)], **kw)
+
+    # ---------------------------------------------------------------- sizing
+    def plan(self, req):
+        M = int(math.ceil(req.m / self.bucket) * self.bucket)
+        N = int(math.ceil(req.n / self.bucket) * self.bucket)
+        K = int(min(math.ceil(req.k / self.kbucket) * self.kbucket, min(M, N)))
+        req.bucket = (M, N, K)
+        b, p = (self.tuner.choose(M, N, K) if self.tuner else (min(K, 64), 8))
+        req.b, req.p = b, p
+        return req
+
+    def footprint(self, req):
+        """HBM bytes the request holds while in flight: its padded input and
+        outputs plus the handle scratch of its bucket."""
+        if self.footprint_fn is not None:
+            return self.footprint_fn(req)
+        M, N, K = req.bucket
+        io = M * N * 4 + N * 8 + K * 16 + (M * K + K * N) * 4
+        ws = load().rqrcp_workspace_bytes(b"V", M, N, K, req.b, req.p)
+        return io + int(ws)
+
+    # ---------------------------------------------------------------- loop
+    def submit(self, req):
+        self.pending.append(self.plan(req))
+
+    def poll(self):
+        """Retire finished requests, then admit waiting ones (FIFO) while a
+        slot is free and the budget allows."""
+        still = []
+        for req in self.running:
+            if req.slot.done():
+                req.t_done = self.clock()
+                self.in_flight_bytes -= self.footprint(req)
+                req.slot.req = None
+                self.free.append(req.slot)
+                self.done.append(req)
+            else:
+                still.append(req)
+        self.running = still
+        while self.pending and self.free:
+            req = self.pending[0]
+            fp = self.footprint(req)
+            if self.in_flight_bytes + fp > self.hbm_budget and self.running:
+                break
+            self.pending.popleft()
+            slot = self.free.popleft()
+            req.t_admit = self.clock()
+            self.in_flight_bytes += fp
+            req.slot = slot
+            slot.launch(req)
+            self.running.append(req)
+            self.max_in_flight = max(self.max_in_flight, len(self.running))
+
+    def drain(self):
+        while self.pending or self.running:
+            self.poll()
+            if self.running and not any(r.slot.done() for r in self.running):
+                time.sleep(20e-6)
+
+    # ---------------------------------------------------------------- workload
+    def run_poisson(self, rate, duration, warmup=0.0, seed=7, size_range=(256, 4096),
+                    k_range=(16, 128)):
+        """Serve a Poisson stream at `rate` req/s for warmup + duration seconds;
+        statistics cover requests that arrived after the warm-up."""
+        rng = np.random.default_rng(seed)
+        total = warmup + duration
+        t = 0.0
+        arrivals = []
+        rid = 0
+        while True:
+            t += rng.exponential(1.0 / rate)
+            if t > total:
+                break
+            m = int(rng.integers(size_range[0], size_range[1] + 1))
+            n = int(rng.integers(size_range[0], size_range[1] + 1))
+            k = int(rng.integers(k_range[0], k_range[1] + 1))
+            arrivals.append((t, Request(rid, m, n, min(k, m, n))))
+            rid += 1
+        t0 = time.perf_counter()
+        i = 0
+        while i < len(arrivals) or self.pending or self.running:
+            now = time.perf_counter() - t0
+            while i < len(arrivals) and arrivals[i][0] <= now:
+                req = arrivals[i][1]
+                req.t_arrival = t0 + arrivals[i][0]
+                self.submit(req)
+                i += 1
+            self.poll()
+            if i < len(arrivals) and not self.pending:
+                wait = arrivals[i][0] - (time.perf_counter() - t0)
+                if wait > 50e-6:
+                    time.sleep(min(wait, 200e-6))
+        t_end = time.perf_counter()
+        measured = [r for r in self.done if r.t_arrival - t0 >= warmup]
+        lat = np.array([r.t_done - r.t_arrival for r in measured]) * 1e3
+        span = max(r.t_done for r in measured) - min(r.t_arrival for r in measured)
+        flops = sum(request_flops(r.m, r.n, r.k, r.b + r.p) for r in measured)
+        return {
+            "requests": len(measured), "offered_rate": rate,
+            "throughput_rps": len(measured) / span, "gflops": flops / span / 1e9,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+            "wall_s": t_end - t0, "slots": len(self.slots),
+        }
