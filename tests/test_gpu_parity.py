@@ -320,3 +320,36 @@ def test_trqrcp_mixed_lowrank(lib, m, n, k, b, p):
     rel = np.linalg.norm(Rg - Ro) / np.linalg.norm(Ro)
     print(f"trqrcp_mixed {m}x{n} k={k}: rank-k recon {rec:.2e}, R vs FP64 oracle {rel:.2e}")
     assert rel <= 1e-4
+
+
+def test_tc_gemm_accumulation_profile(lib):
+    """Error of the split-BF16 x3 tensor-core GEMM against K (per entry, in
+    units of u = 2^-24 of sum_k |a||b|) next to cuBLAS FP32 SGEMM; prints the
+    table and pins the short-reduction bound (K = 64 within 8 u)."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    g = torch.Generator().manual_seed(0)
+    u = 2.0 ** -24
+    try:
+        for K in [64, 256, 1024, 4096, 16384]:
+            for kind in ["gauss", "pos"]:
+                A = torch.randn(128, K, generator=g, dtype=torch.float64)
+                B = torch.randn(K, 256, generator=g, dtype=torch.float64)
+                if kind == "pos":
+                    A, B = A.abs(), B.abs()
+                A32, B32 = A.float(), B.float()
+                ref = A32.double() @ B32.double()
+                scale = A32.double().abs() @ B32.double().abs()
+                C3 = lib.gemm_bf16x(lib.colmajor(A32.cuda()), lib.colmajor(B32.cuda()),
+                                    slices=3).cpu().double()
+                Cf = (A32.cuda() @ B32.cuda()).cpu().double()
+                e3 = (C3 - ref) / scale
+                ef = (Cf - ref) / scale
+                print(f"K={K:6d} {kind:5s} bf16x3 max {e3.abs().max().item() / u:8.2f}u "
+                      f"mean {e3.abs().mean().item() / u:7.2f}u signed {e3.mean().item() / u:8.2f}u"
+                      f" | sgemm max {ef.abs().max().item() / u:6.2f}u "
+                      f"mean {ef.abs().mean().item() / u:5.2f}u")
+                if K == 64:
+                    assert e3.abs().max().item() <= 8 * u
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
