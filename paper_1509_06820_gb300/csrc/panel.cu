@@ -44,7 +44,8 @@ __global__ void __launch_bounds__(NT, 1) panel_kernel(PanelArgs a) {
   }
   __syncthreads();
 
-  double* part_base = a.partial;  // 2 x G x bJ (column dots), then G x bJ x bJ (Gram)
+  // 2 x G x bJ (column dots), G x bJ x bJ (Gram partials), bJ x bJ (Gram)
+  double* part_base = a.partial;
   // partial dots of column j with columns j..bJ-1 over owned rows below row j
   auto publish = [&](int j) {
     double* part = part_base + (size_t)(j & 1) * G * bJ + (size_t)g * bJ;
@@ -69,8 +70,20 @@ __global__ void __launch_bounds__(NT, 1) panel_kernel(PanelArgs a) {
     for (int e = tid; e < PARTS * bJ; e += NT) {
       const int c = e % bJ, pp = e / bJ;
       double s = 0.0;
-      if (c >= j)
-        for (int q = pp; q < G; q += PARTS) s += __ldcg(part + (size_t)q * bJ + c);
+      if (c >= j) {
+        // q = pp, pp + PARTS, ... in increasing order; loads issued in batches
+        // of 8 so that their L2 latencies overlap
+        for (int q0 = pp; q0 < G; q0 += 8 * PARTS) {
+          double v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u * PARTS;
+            v[u] = (q < G) ? __ldcg(part + (size_t)q * bJ + c) : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) s += v[u];
+        }
+      }
       s_part[pp][c] = s;
     }
     __syncthreads();
@@ -140,15 +153,51 @@ __global__ void __launch_bounds__(NT, 1) panel_kernel(PanelArgs a) {
     gram[c1 + c2 * bJ] = s;
   }
   if (!grid_barrier(a.bar, G, a.status)) return;
+  // every CTA adds the partials of the Gram entries e = g, g + G, ... over all
+  // CTAs q in increasing order (PP threads per entry, then a fixed-order
+  // combine), so the reduction is spread over the grid
+  {
+    const double* gp = part_base + (size_t)2 * G * bJ;
+    double* gtot = part_base + (size_t)2 * G * bJ + (size_t)G * bJ * bJ;
+    const int nent = (bJ * bJ - g + G - 1) / G;   // entries owned by this CTA
+    const int PP = nent >= NT ? 1 : (nent * 8 <= NT ? 8 : (nent * 4 <= NT ? 4 : (nent * 2 <= NT ? 2 : 1)));
+    __shared__ double s_g[NT];
+    for (int i0 = 0; i0 < nent; i0 += NT / PP) {
+      const int i = i0 + tid / PP, sub = tid % PP;
+      double s = 0.0;
+      if (i < nent) {
+        const int e = g + i * G;
+        for (int q0 = sub; q0 < G; q0 += 8 * PP) {
+          double v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u * PP;
+            v[u] = (q < G) ? __ldcg(gp + (size_t)q * bJ * bJ + e) : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) s += v[u];
+        }
+      }
+      s_g[tid] = s;
+      __syncthreads();
+      if (sub == 0 && i < nent) {
+        double t = 0.0;
+        for (int u = 0; u < PP; ++u) t += s_g[tid + u];
+        gtot[g + i * G] = t;
+      }
+      __syncthreads();
+    }
+  }
+  if (!grid_barrier(a.bar, G, a.status)) return;
   if (g != 0) return;
-  // CTA 0: add the Gram partials in fixed order (reuse the panel smem), build T
+  // CTA 0: the reduced Gram (upper triangle) into shared memory, then T
   double* Gs = Ps;  // bJ x bJ
-  for (int e = tid; e < bJ * bJ; e += NT) {
-    const int c1 = e % bJ, c2 = e / bJ;
-    double s = 0.0;
-    if (c1 <= c2)
-      for (int q = 0; q < G; ++q) s += __ldcg(part_base + (size_t)2 * G * bJ + (size_t)q * bJ * bJ + e);
-    Gs[e] = s;
+  {
+    const double* gtot = part_base + (size_t)2 * G * bJ + (size_t)G * bJ * bJ;
+    for (int e = tid; e < bJ * bJ; e += NT) {
+      const int c1 = e % bJ, c2 = e / bJ;
+      Gs[e] = (c1 <= c2) ? __ldcg(gtot + e) : 0.0;
+    }
   }
   __syncthreads();
   double* T = a.T;
@@ -179,7 +228,7 @@ int panel_grid(int64_t mJ, int bJ, int num_sms) {
 }
 
 size_t panel_partial_doubles(int grid, int bJ) {
-  return (size_t)2 * grid * bJ + (size_t)grid * bJ * bJ;
+  return (size_t)2 * grid * bJ + (size_t)grid * bJ * bJ + (size_t)bJ * bJ;
 }
 
 static size_t panel_smem(int64_t chunk, int bJ) {

@@ -12,11 +12,12 @@ namespace rq {
 namespace {
 
 // map layout: map[0] = number of moves; moves at map[1 + 2t] (dest), map[2 + 2t] (src);
-// work area for the composition follows at map[1 + 4*steps].
+// the jpvt staging buffer follows at map[1 + 8*steps].
 __global__ void compose_swaps(const int64_t* __restrict__ swaps, int steps, int64_t* map) {
+  // touched positions and the original position each holds, in shared memory
+  __shared__ int64_t pos[256];
+  __shared__ int64_t content[256];
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int64_t* pos = map + 1 + 4 * steps;      // touched positions
-  int64_t* content = pos + 2 * steps;      // original position held there
   int ntouch = 0;
   for (int i = 0; i < steps; ++i) {
     const int64_t s = swaps[i];
@@ -28,7 +29,7 @@ __global__ void compose_swaps(const int64_t* __restrict__ swaps, int steps, int6
     }
     if (ia < 0) { pos[ntouch] = i; content[ntouch] = i; ia = ntouch++; }
     if (ib < 0) { pos[ntouch] = s; content[ntouch] = s; ib = ntouch++; }
-    int64_t tmp = content[ia];
+    const int64_t tmp = content[ia];
     content[ia] = content[ib];
     content[ib] = tmp;
   }

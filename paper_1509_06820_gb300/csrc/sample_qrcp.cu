@@ -184,7 +184,10 @@ __global__ void __launch_bounds__(NT, 1) sample_qrcp_kernel(SampleQrcpArgs a) {
       }
     }
     __syncthreads();
-    // ---- apply H = I - tau v v^T to the trailing columns, downdate norms
+    // ---- apply H = I - tau v v^T to the trailing columns, downdate norms;
+    // a column whose downdated norm lost too many digits is marked for an
+    // exact recompute, done in a second pass only when some column needs it
+    int need_any = 0;
     for (int base = 0; base < ncol; base += GROUPS) {
       const int c = base + grp;
       const bool act = c < ncol && !done[c];
@@ -197,19 +200,31 @@ __global__ void __launch_bounds__(NT, 1) sample_qrcp_kernel(SampleQrcpArgs a) {
         if (act)
           for (int r = i + lig; r < ell; r += LPC) cc[r] = fma(-s, xv[r], cc[r]);
       }
-      double t = 0.0;
-      if (act)
-        for (int r = i + 1 + lig; r < ell; r += LPC) t = fma(cc[r], cc[r], t);
-      t = group_sum<LPC>(t);
       if (act && lig == 0 && vn[c] != 0.0) {
         double rr = fabs(cc[i]) / vn[c];
         double f = fmax(0.0, (1.0 - rr) * (1.0 + rr));
         double q = vn[c] / vn0[c];
         if (f * q * q <= TOL3Z) {
-          vn[c] = sqrt(t);
-          vn0[c] = vn[c];
+          vn[c] = -1.0;  // recompute below
+          need_any = 1;
         } else {
           vn[c] *= sqrt(f);
+        }
+      }
+    }
+    if (__syncthreads_or(need_any)) {
+      for (int base = 0; base < ncol; base += GROUPS) {
+        const int c = base + grp;
+        const bool act = c < ncol && !done[c] && vn[c] < 0.0;
+        double t = 0.0;
+        if (act) {
+          const double* cc = col + (size_t)c * ell;
+          for (int r = i + 1 + lig; r < ell; r += LPC) t = fma(cc[r], cc[r], t);
+        }
+        t = group_sum<LPC>(t);
+        if (act && lig == 0) {
+          vn[c] = sqrt(t);
+          vn0[c] = vn[c];
         }
       }
     }

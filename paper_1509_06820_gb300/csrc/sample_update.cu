@@ -11,36 +11,65 @@
 namespace rq {
 namespace {
 
+constexpr int W11_ROWS = 8;  // rows of W11 per CTA, one warp each
+
+// W11 = S11 R11^{-1}: CTA c owns rows 8c..8c+7 of W11; R11 (columns >= the
+// CTA's first row) is staged in shared memory; warp w computes row r of W11
+// left to right, W(r, j) = (S(r, j) - sum_{r <= t < j} W(r, t) R(t, j)) / R(j, j),
+// its lanes splitting the sum over t (fixed-order shuffle reduction).
 __global__ void w11_kernel(const double* __restrict__ S, int ell, const double* __restrict__ R,
                            int64_t ldr, int bJ, double* __restrict__ W, int* flag, int* status) {
+  extern __shared__ double sm[];
+  double* Rs = sm;                    // bJ x bJ, ld bJ
+  double* Wr = sm + bJ * bJ;          // W11_ROWS x bJ
   __shared__ int s_sing;
-  if (threadIdx.x == 0) s_sing = 0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_sing = 0;
   __syncthreads();
-  for (int j = threadIdx.x; j < bJ; j += blockDim.x)
+  for (int e = tid; e < bJ * bJ; e += blockDim.x) {
+    const int r = e % bJ, c = e / bJ;
+    Rs[e] = (r <= c) ? R[r + c * ldr] : 0.0;
+  }
+  for (int j = tid; j < bJ; j += blockDim.x)
     if (R[j + j * ldr] == 0.0) s_sing = 1;
   __syncthreads();
   if (s_sing) {
-    if (threadIdx.x == 0) {
+    if (blockIdx.x == 0 && tid == 0) {
       *flag = 1;
       atomicOr(status, RQRCP_INFO_RESAMPLED);
     }
     return;
   }
-  if (threadIdx.x == 0) *flag = 0;
-  for (int r = threadIdx.x; r < bJ; r += blockDim.x) {
-    for (int j = 0; j < bJ; ++j) {
-      double s = (r <= j) ? S[r + (int64_t)j * ell] : 0.0;
-      for (int t = r; t < j; ++t) s = fma(-W[r + t * bJ], R[t + j * ldr], s);
-      W[r + j * bJ] = (r <= j) ? s / R[j + j * ldr] : 0.0;
-    }
+  if (blockIdx.x == 0 && tid == 0) *flag = 0;
+  const int r = blockIdx.x * W11_ROWS + warp;
+  if (r >= bJ) return;
+  double* wrow = Wr + warp * bJ;
+  for (int j = lane; j < bJ; j += 32) wrow[j] = 0.0;
+  __syncwarp();
+  for (int j = r; j < bJ; ++j) {
+    double s = 0.0;
+    for (int t = r + lane; t < j; t += 32) s = fma(wrow[t], Rs[t + j * bJ], s);
+    s = warp_sum(s);
+    if (lane == 0) wrow[j] = (S[r + (int64_t)j * ell] - s) / Rs[j + j * bJ];
+    __syncwarp();
   }
+  for (int j = lane; j < bJ; j += 32) W[r + j * bJ] = wrow[j];
 }
 
 }  // namespace
 
 cudaError_t launch_w11(const double* S, int ell, const double* R11, int64_t ldr, int bJ,
                        double* W11, int* flag, int* status, cudaStream_t st) {
-  w11_kernel<<<1, 128, 0, st>>>(S, ell, R11, ldr, bJ, W11, flag, status);
+  const size_t smem = ((size_t)bJ * bJ + (size_t)W11_ROWS * bJ) * sizeof(double);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(w11_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (128 * 128 + W11_ROWS * 128) * (int)sizeof(double));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int grid = (bJ + W11_ROWS - 1) / W11_ROWS;
+  w11_kernel<<<grid, 32 * W11_ROWS, smem, st>>>(S, ell, R11, ldr, bJ, W11, flag, status);
   return cudaGetLastError();
 }
 

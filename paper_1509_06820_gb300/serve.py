@@ -77,25 +77,45 @@ def make_input(req, out, stream):
 
 
 class Slot:
-    def __init__(self, device, max_m, max_n, max_k, use_graphs):
+    """One concurrent request: a stream, a handle and cached per-bucket graphs.
+
+    Captured graphs hold the handle's scratch pointers, so the scratch is
+    reserved once for the largest bucket and never moves; if a bucket ever
+    needs more, the slot's graphs are dropped before the scratch grows.
+    """
+
+    def __init__(self, device, max_m, max_n, max_k, use_graphs, bp_choices=((128, 16), (64, 16))):
         self.device = device
         self.stream = torch.cuda.Stream(device)
         self.handle = Handle(device)
         self.event = torch.cuda.Event()
         self.req = None
         self.use_graphs = use_graphs
-        self.graphs = {}  # bucket -> (graph, A view, outputs)
+        self.graphs = {}  # (bucket, b, p) -> (graph, A view, outputs)
         self.max = (max_m, max_n, max_k)
+        self.reserved = 0
+        for b, p in bp_choices:
+            self._reserve(max_m, max_n, max_k, min(b, max_k), p)
+        # one buffer set of the largest size; buckets use leading-dimension views
+        self.bufA = empty_colmajor(max_m, max_n, device, torch.float32)
+        self.bufs = (torch.empty(max_n, dtype=torch.int64, device=device),
+                     torch.empty(max_k, dtype=torch.float64, device=device),
+                     empty_colmajor(max_m, max_k, device, torch.float32),
+                     empty_colmajor(max_k, max_n, device, torch.float32),
+                     torch.empty(max_k, dtype=torch.float64, device=device))
+
+    def _reserve(self, M, N, K, b, p):
+        need = int(load().rqrcp_workspace_bytes(b"V", M, N, K, b, p))
+        if need > self.reserved:
+            self.graphs.clear()   # their scratch pointers are about to move
+            with torch.cuda.stream(self.stream):
+                self.handle.reserve("V", M, N, K, b, p)
+            self.reserved = need
 
     def _buffers(self, bucket):
         M, N, K = bucket
-        A = empty_colmajor(M, N, self.device, torch.float32)
-        outs = (torch.empty(N, dtype=torch.int64, device=self.device),
-                torch.empty(K, dtype=torch.float64, device=self.device),
-                empty_colmajor(M, K, self.device, torch.float32),
-                empty_colmajor(K, N, self.device, torch.float32),
-                torch.empty(K, dtype=torch.float64, device=self.device))
-        return A, outs
+        jp, tau, Y, R, rd = self.bufs
+        return self.bufA[:M, :N], (jp[:N], tau[:K], Y[:M, :K], R[:K, :N], rd[:K])
 
     def launch(self, req):
         M, N, K = req.bucket
@@ -103,8 +123,8 @@ class Slot:
         if entry is None:
             A, outs = self._buffers(req.bucket)
             graph = None
+            self._reserve(M, N, K, req.b, req.p)
             with torch.cuda.stream(self.stream):
-                self.handle.reserve("V", M, N, K, req.b, req.p)
                 A.zero_()
                 # eager run first: sets kernel attributes and sizes the scratch
                 trqrcp_mixed(A, K, req.b, req.p, 1, handle=self.handle, out=outs)
