@@ -131,15 +131,15 @@ struct PanelArgs {
   double* rowj;       // scratch: bJ doubles
   GridBarrier* bar;
   int* status;
+  // mixed precision: round the reflectors below the diagonal to FP32 values
+  // before the Gram, and set tau_i = 2 / v_i^T v_i (kept 0 where the column
+  // had a zero tail), so that T and tau describe exactly the stored vectors
+  int round_f32;
 };
 cudaError_t launch_panel(const PanelArgs& a, int num_sms, cudaStream_t st);
 size_t panel_partial_doubles(int grid, int bJ);
 int panel_grid(int64_t mJ, int bJ, int num_sms);
 bool panel_fits(int64_t mJ, int bJ, int num_sms);
-// tau_i = 2 / v_i^T v_i (0 kept) and T recomputed in FP64 from the explicit
-// FP32 reflector block Y (mJ x bJ, ld); partial: num_sms * bJ * bJ doubles.
-cudaError_t launch_tau_t_from_f32(const float* Y, int64_t ld, int64_t mJ, int bJ, double* tau,
-                                  double* T, double* partial, int num_sms, cudaStream_t st);
 
 // ---- sample_update.cu: W11 = S11 R11^{-1} (bJ x bJ, ld bJ).  Sets *flag to 1
 // (and ORs RQRCP_INFO_RESAMPLED into status) when R11 has an exact zero

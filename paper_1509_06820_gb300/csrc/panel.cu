@@ -132,6 +132,14 @@ __global__ void __launch_bounds__(NT, 1) panel_kernel(PanelArgs a) {
     if (j + 1 < bJ) publish(j + 1);
   }
 
+  // mixed precision: the stored reflectors are the FP32-rounded ones
+  if (a.round_f32) {
+    for (int64_t e = tid; e < (int64_t)nrow * bJ; e += NT) {
+      const int64_t r = e % nrow, c = e / nrow;
+      if (r_lo + r > c) Ps[r + c * chunk] = (double)(float)Ps[r + c * chunk];
+    }
+    __syncthreads();
+  }
   // write the factored rows back
   for (int64_t e = tid; e < (int64_t)nrow * bJ; e += NT) {
     const int64_t r = e % nrow, c = e / nrow;
@@ -203,6 +211,12 @@ __global__ void __launch_bounds__(NT, 1) panel_kernel(PanelArgs a) {
   double* T = a.T;
   for (int e = tid; e < bJ * bJ; e += NT) T[e] = 0.0;
   __syncthreads();
+  if (a.round_f32) {
+    // tau_i = 2 / v_i^T v_i for the stored (rounded) v_i; zero stays zero
+    for (int i = tid; i < bJ; i += NT)
+      if (__ldcg(a.tau + i) != 0.0) a.tau[i] = 2.0 / Gs[i + i * bJ];
+    __syncthreads();
+  }
   for (int i = 0; i < bJ; ++i) {
     const double ti = __ldcg(a.tau + i);
     // T(0:i, i) = -tau_i T(0:i, 0:i) G(0:i, i)
@@ -263,92 +277,6 @@ cudaError_t launch_panel(const PanelArgs& a, int num_sms, cudaStream_t st) {
   void* params[] = {&args};
   return cudaLaunchCooperativeKernel((const void*)panel_kernel, dim3((unsigned)G), dim3(NT), params,
                                      smem, st);
-}
-
-}  // namespace rq
-
-// ---------------------------------------------------------------------------
-// Compact-WY factor of reflectors stored in FP32 (mixed-precision path).
-// The panel computes v in FP64; once v is rounded to FP32 for storage and for
-// the tensor-core products, tau and T are recomputed in FP64 from the stored
-// vectors so that each H_i = I - tau_i v_i v_i^T is orthogonal for exactly
-// the stored v_i (tau_i = 2 / v_i^T v_i, kept 0 where the panel found a zero
-// tail) and I - Y T Y^T is exactly their product.
-namespace rq {
-namespace {
-
-constexpr int GNT = 256;
-
-// partial Gram Y^T Y (upper triangle) over rows [r0, r1) of the explicit
-// unit-lower FP32 block Y (mJ x bJ, ld)
-__global__ void gram_f32_partial(const float* __restrict__ Y, int64_t ld, int64_t mJ, int bJ,
-                                 int64_t chunk, double* __restrict__ partial) {
-  const int64_t r0 = (int64_t)blockIdx.x * chunk;
-  const int64_t r1 = imin64(mJ, r0 + chunk);
-  double* out = partial + (size_t)blockIdx.x * bJ * bJ;
-  for (int e = threadIdx.x; e < bJ * bJ; e += GNT) {
-    const int c1 = e % bJ, c2 = e / bJ;
-    double s = 0.0;
-    if (c1 <= c2)
-      for (int64_t r = imax64(r0, c2); r < r1; ++r)
-        s = fma((double)Y[r + c1 * ld], (double)Y[r + c2 * ld], s);
-    out[e] = s;
-  }
-}
-
-__global__ void tau_t_from_gram(const double* __restrict__ partial, int G, int bJ,
-                                double* __restrict__ tau, double* __restrict__ T) {
-  extern __shared__ double Gs[];  // bJ x bJ
-  __shared__ double s_t[128];
-  for (int e = threadIdx.x; e < bJ * bJ; e += GNT) {
-    double s = 0.0;
-    for (int q = 0; q < G; ++q) s += partial[(size_t)q * bJ * bJ + e];
-    Gs[e] = s;
-    T[e] = 0.0;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < bJ; i += GNT)
-    if (tau[i] != 0.0) tau[i] = 2.0 / Gs[i + i * bJ];
-  __syncthreads();
-  for (int i = 0; i < bJ; ++i) {
-    const double ti = tau[i];
-    if (threadIdx.x < i) {
-      double s = 0.0;
-      for (int t = threadIdx.x; t < i; ++t) s = fma(T[threadIdx.x + t * bJ], Gs[t + i * bJ], s);
-      s_t[threadIdx.x] = -ti * s;
-    }
-    __syncthreads();
-    if (threadIdx.x < i) T[threadIdx.x + i * bJ] = s_t[threadIdx.x];
-    if (threadIdx.x == 0) T[i + i * bJ] = ti;
-    __syncthreads();
-  }
-}
-
-}  // namespace
-
-int tau_t_grid(int64_t mJ, int num_sms) {
-  int64_t G = (mJ + 255) / 256;
-  if (G > num_sms) G = num_sms;
-  return (int)(G < 1 ? 1 : G);
-}
-
-cudaError_t launch_tau_t_from_f32(const float* Y, int64_t ld, int64_t mJ, int bJ, double* tau,
-                                  double* T, double* partial, int num_sms, cudaStream_t st) {
-  if (bJ < 1 || bJ > MAXB) return cudaErrorInvalidValue;
-  const int G = tau_t_grid(mJ, num_sms);
-  const int64_t chunk = (mJ + G - 1) / G;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(tau_t_from_gram, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         MAXB * MAXB * (int)sizeof(double));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  gram_f32_partial<<<G, GNT, 0, st>>>(Y, ld, mJ, bJ, chunk, partial);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  tau_t_from_gram<<<1, GNT, (size_t)bJ * bJ * sizeof(double), st>>>(partial, G, bJ, tau, T);
-  return cudaGetLastError();
 }
 
 }  // namespace rq

@@ -299,10 +299,11 @@ int sample_step(Call& cl, double* Bblk, int ell, int64_t nc, int bJ) {
   return RQRCP_OK;
 }
 
-int panel_step(Call& cl, double* P, int64_t ld, int64_t mJ, int bJ, double* tau, double* T) {
+int panel_step(Call& cl, double* P, int64_t ld, int64_t mJ, int bJ, double* tau, double* T,
+               int round_f32 = 0) {
   const double b = bJ, m = (double)mJ;
   PhaseScope ps(cl.h, PH_PANEL, 2.0 * m * b * b - 2.0 * b * b * b / 3.0 + m * b * b + b * b * b / 3.0);
-  rq::PanelArgs a{P, ld, mJ, bJ, tau, T, cl.w.ppart, cl.w.rowj, cl.bar, cl.status};
+  rq::PanelArgs a{P, ld, mJ, bJ, tau, T, cl.w.ppart, cl.w.rowj, cl.bar, cl.status, round_f32};
   CKL(1, rq::launch_panel(a, cl.h->num_sms, cl.st));
   return RQRCP_OK;
 }
@@ -807,12 +808,10 @@ int rqrcp_factor_mixed(rqrcp_handle_t h, int64_t m, int64_t n, float* dA, int64_
       PhaseScope ps(cl.h, PH_OTHER, 0.0);
       CKL(1, rq::launch_convert_f32_f64(P, lda, w.P64, m, mJ, bJ, cl.st));
     }
-    if ((r = panel_step(cl, w.P64, m, mJ, bJ, d_tau + j0, w.T))) return r;
+    if ((r = panel_step(cl, w.P64, m, mJ, bJ, d_tau + j0, w.T, 1))) return r;
     {
       PhaseScope ps(cl.h, PH_OTHER, 0.0);
       CKL(1, rq::launch_panel_writeback(w.P64, m, mJ, bJ, P, lda, w.Y32, m, d_rdiag + j0, cl.st));
-      CKL(2, rq::launch_tau_t_from_f32(w.Y32, m, mJ, bJ, d_tau + j0, w.T, w.ppart, cl.h->num_sms,
-                                       cl.st));
     }
     float* A2 = dA + j0 + (j0 + bJ) * lda;
     if (n2 > 0) {
@@ -897,14 +896,12 @@ int trqrcp_mixed(rqrcp_handle_t h, int64_t m, int64_t n, const float* dA, int64_
         CK(tcgemm(cl, 'N', 'N', mJ, bJ, j0, -1.0f, dY + j0, ldy, Wt + j0 * k, k, 1.0f, Ahat, m, 3));
       CKL(1, rq::launch_convert_f32_f64(Ahat, m, w.P64, m, mJ, bJ, cl.st));
     }
-    if ((r = panel_step(cl, w.P64, m, mJ, bJ, d_tau + j0, w.T))) return r;
+    if ((r = panel_step(cl, w.P64, m, mJ, bJ, d_tau + j0, w.T, 1))) return r;
     {
       PhaseScope ps(cl.h, PH_OTHER, 0.0);
       // Y (explicit, FP32) and R11 (FP32, diagonal also in FP64)
       CKL(1, rq::launch_panel_writeback(w.P64, m, mJ, bJ, Ahat, m, dY + j0 + j0 * ldy, ldy,
                                         d_rdiag + j0, cl.st));
-      CKL(2, rq::launch_tau_t_from_f32(dY + j0 + j0 * ldy, ldy, mJ, bJ, d_tau + j0, w.T, w.ppart,
-                                       cl.h->num_sms, cl.st));
       CKL(1, rq::launch_copy_upper_f32(Ahat, m, bJ, dR + j0 + j0 * ldr, ldr, cl.st));
       CKL(1, rq::launch_convert_f64_f32(w.T, bJ, w.T32, bJ, bJ, bJ, cl.st));
     }
