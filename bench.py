@@ -246,6 +246,51 @@ def mixed_leg(args, dev, fp64_ms, stream):
             "phases": {kk: {"ms": v[0], "launches": v[2]} for kk, v in prof.items()}}
 
 
+def truncated_leg(args, dev):
+    """TRQRCP and TUXV (FP64) at rank 512 on a 50000 x 20000 matrix
+    U_r diag(i^-2) V_r^T (rank 2048) + N(0, 1e-8^2), b = 64, p = 8."""
+    import torch
+    import paper_1509_06820_gb300 as rq
+    import synth
+    m, n, k, b, p = 50000, 20000, 512, 64, 8
+    A = rq.colmajor(synth.decaying_lowrank_device(m, n, dev, rank=2048, noise=1e-8))
+    h = rq.Handle(dev)
+    h.reserve("U", m, n, k, b, p)
+    ell = b + p
+    out = {}
+    for name, fn, extra in (("trqrcp", lambda: rq.trqrcp(A, k, b, p, 1, handle=h), 0.0),
+                            ("tuxv", lambda: rq.tuxv(A, k, b, p, 1, handle=h), 2.0 * m * n * k)):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        steps = max(1, min(args.steps, 2))
+        for _ in range(steps):
+            res = fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        fl = 2.0 * m * n * k + 2.0 * ell * m * n + extra
+        out[name] = {"ms": ms, "gflops": fl / (ms / 1e3) / 1e9, "flop_count": "2mnk + 2lmn (+2mnk)"}
+    info = h.sync_info()
+    U, X, V = res
+    # ||A - U X V^T||_F^2 = ||A||^2 - 2 <U^T A V, X> + ||X||^2 (U, V orthonormal)
+    a2 = (A.double() ** 2).sum().item()
+    UtAV = (U.t() @ A) @ V
+    err2 = a2 - 2.0 * (UtAV * X).sum().item() + (X ** 2).sum().item()
+    sig = torch.arange(1, 2049, dtype=torch.float64) ** -2.0
+    tail = float((sig[k:] ** 2).sum() + (1e-8) ** 2 * m * n)
+    out["tuxv_rel_err"] = (max(err2, 0.0) / a2) ** 0.5
+    out["optimum_rel_err_approx"] = (tail / a2) ** 0.5
+    out["orth_U"] = (U.t() @ U - torch.eye(k, device=dev, dtype=torch.float64)).abs().max().item()
+    out["device_info"] = info
+    out["workload"] = f"trqrcp_tuxv_{m}x{n}_k{k}_b{b}_p{p}_decay2_noise1e-8"
+    del A, U, X, V, UtAV
+    h.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def serving_leg(args, dev):
     """Served TRQRCP: Poisson arrivals, m, n ~ U{256..4096}, k ~ U{16..128},
     A = X Y^T (FP32), continuous batching over 8 slots, autotuned b/p."""
@@ -257,6 +302,11 @@ def serving_leg(args, dev):
     tune_s = time.perf_counter() - t0
     srv = Server.on_gpu(dev, slots=8, tuner=tuner)
     stats = srv.run_poisson(rate=args.serve_rate, duration=args.serve_seconds, warmup=1.0, seed=7)
+    # the same server below saturation, for the service-time latency
+    low = srv.run_poisson(rate=args.serve_rate / 5, duration=min(5.0, args.serve_seconds),
+                          warmup=0.5, seed=8)
+    stats["below_saturation"] = {k: low[k] for k in ("offered_rate", "requests", "throughput_rps",
+                                                     "p50_ms", "p99_ms", "gflops")}
     stats["autotune_s"] = tune_s
     stats["autotune_table"] = tuner.table
     stats["graphs_captured"] = sum(len(s.graphs) for s in srv.slots)
@@ -420,6 +470,7 @@ def main():
 
     if not args.no_extras:
         extras["mixed"] = mixed_leg(args, dev, ms, stream)
+        extras["truncated"] = truncated_leg(args, dev)
         if rank == 0:
             extras["serving"] = serving_leg(args, dev)
 

@@ -264,6 +264,7 @@ class Server:
             k = int(rng.integers(k_range[0], k_range[1] + 1))
             arrivals.append((t, Request(rid, m, n, min(k, m, n))))
             rid += 1
+        self.done = []
         t0 = time.perf_counter()
         i = 0
         while i < len(arrivals) or self.pending or self.running:
