@@ -77,6 +77,14 @@ size_t rqrcp_workspace_bytes(char op, int64_t m, int64_t n, int64_t k, int b, in
  * not allocate, e.g. before stream capture). */
 int rqrcp_reserve(rqrcp_handle_t handle, char op, int64_t m, int64_t n, int64_t k, int b, int p);
 
+/* Handle options.  RQRCP_OPT_FP64_EMULATION (value 0/1, default 0): run the
+ * two large products of the FP64 trailing update (rqrcp_factor, qr_factor;
+ * blocks of b <= 64) on the BF16 tensor cores with the FP64-accurate slicing
+ * of rqrcp_gemm_f64x instead of the FP64 pipe.  Its scratch adds 14 bytes
+ * per element of A. */
+#define RQRCP_OPT_FP64_EMULATION 1
+int rqrcp_set_option(rqrcp_handle_t handle, int option, int value);
+
 /* Wait for the handle's stream, then return the device status word in *info
  * and clear it. */
 int rqrcp_sync_info(rqrcp_handle_t handle, int* info);
@@ -224,6 +232,19 @@ int rqrcp_sample_qrcp(rqrcp_handle_t handle, int ell, int64_t nc, int steps, dou
  */
 int rqrcp_sample_qrcp_noalloc(int ell, int64_t nc, int steps, double* dB, int64_t ldb,
                               int64_t* d_swaps, int* d_info, void* cuda_stream);
+
+/*
+ * FP64-accurate GEMM on the BF16 tensor cores: C = alpha op(A) op(B) + beta C
+ * in FP64 (column-major, transA/transB 'N' or 'T').  Each row of op(A) and
+ * column of op(B) is scaled by a power of two and cut into seven exact 8-bit
+ * BF16 slices; the 28 significant slice products are accumulated on the
+ * tensor cores in exact per-diagonal FP32 sums (drained every 64 k into
+ * error-free double-FP32 running sums), so the result carries about 48
+ * significant bits relative to sum_k |a_ik b_kj|.
+ */
+int rqrcp_gemm_f64x(rqrcp_handle_t handle, char transA, char transB, int64_t m, int64_t n,
+                    int64_t k, double alpha, const double* dA, int64_t lda, const double* dB,
+                    int64_t ldb, double beta, double* dC, int64_t ldc);
 
 /*
  * Instrumentation (no counterpart in the paper).  While enabled, every phase

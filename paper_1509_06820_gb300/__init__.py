@@ -36,6 +36,7 @@ SIGNATURES = [
     ("rqrcp_set_stream", _I, [_P, _P]),
     ("rqrcp_workspace_bytes", ctypes.c_size_t, [ctypes.c_char, _I64, _I64, _I64, _I, _I]),
     ("rqrcp_reserve", _I, [_P, ctypes.c_char, _I64, _I64, _I64, _I, _I]),
+    ("rqrcp_set_option", _I, [_P, _I, _I]),
     ("rqrcp_sync_info", _I, [_P, ctypes.POINTER(_I)]),
     ("rqrcp_last_error", ctypes.c_char_p, [_P]),
     ("rqrcp_status_string", ctypes.c_char_p, [_I]),
@@ -50,6 +51,8 @@ SIGNATURES = [
     ("rqrcp_sketch", _I, [_P, _I64, _I64, _P, _I64, _I, _U64, _P, _I64]),
     ("rqrcp_gemm_bf16x", _I, [_P, ctypes.c_char, ctypes.c_char, _I64, _I64, _I64, ctypes.c_float,
                           _P, _I64, _P, _I64, ctypes.c_float, _P, _I64, _I]),
+    ("rqrcp_gemm_f64x", _I, [_P, ctypes.c_char, ctypes.c_char, _I64, _I64, _I64, ctypes.c_double,
+                         _P, _I64, _P, _I64, ctypes.c_double, _P, _I64]),
     ("rqrcp_sample_qrcp", _I, [_P, _I, _I64, _I, _P, _I64, _P]),
     ("rqrcp_sample_qrcp_noalloc", _I, [_I, _I64, _I, _P, _I64, _P, _P, _P]),
     ("rqrcp_profile", _I, [_P, _I]),
@@ -106,6 +109,10 @@ class Handle:
 
     def reserve(self, op, m, n, k, b, p):
         _check(load().rqrcp_reserve(self.bind(), op.encode(), m, n, k, b, p), self.h)
+
+    def set_fp64_emulation(self, on=True):
+        """Run the FP64 trailing update on the BF16 tensor cores (exact slicing)."""
+        _check(load().rqrcp_set_option(self.h, 1, 1 if on else 0), self.h)
 
     def profile(self, enable=True):
         _check(load().rqrcp_profile(self.h, 1 if enable else 0), self.h)
@@ -324,6 +331,23 @@ def sample_qrcp(B, steps, handle=None):
     swaps = torch.empty(steps, dtype=torch.int64, device=B.device)
     _check(load().rqrcp_sample_qrcp(h.bind(), ell, nc, steps, _P(pb), ldb, _ptr(swaps)), h.h)
     return swaps
+
+
+def gemm_f64x(A, B, transA="N", transB="N", alpha=1.0, beta=0.0, C=None, handle=None):
+    """C = alpha op(A) op(B) + beta C in FP64 on the tensor cores (exact slicing)."""
+    h = handle or default_handle(A.device)
+    pa, lda = _cm(A, "A")
+    pb, ldb = _cm(B, "B")
+    m = A.shape[0] if transA == "N" else A.shape[1]
+    k = A.shape[1] if transA == "N" else A.shape[0]
+    n = B.shape[1] if transB == "N" else B.shape[0]
+    if C is None:
+        C = empty_colmajor(m, n, A.device)
+        beta = 0.0
+    pc, ldc = _cm(C, "C")
+    _check(load().rqrcp_gemm_f64x(h.bind(), transA.encode(), transB.encode(), m, n, k, alpha,
+                                  _P(pa), lda, _P(pb), ldb, beta, _P(pc), ldc), h.h)
+    return C
 
 
 def sync_info(device=None):

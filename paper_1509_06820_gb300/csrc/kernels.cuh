@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -64,6 +65,29 @@ struct TcGemmArgs {
 // slices = 1 (plain BF16) or 3 (FP32-level split, six products)
 cudaError_t launch_tc_gemm(TcGemmArgs g, int slices, cudaStream_t st);
 int tc_pick_splits(int64_t M, int64_t N, int64_t K, int num_sms, size_t cap_floats);
+
+// ---- oz_gemm.cu: FP64-accurate GEMM on the BF16 tensor cores by exact
+// slicing.  C (M x N, FP64, ldc) = alpha * 2^(expA_i + expB_j) * (A_sl B_sl^T)
+// + beta * C, where A_sl (7 x M x Kp bf16) and B_sl (7 x N x Kp bf16) are the
+// slices written by launch_oz_slice (rows of op(A) and columns of op(B)).
+struct OzGemmArgs {
+  int64_t M, N, Kp;
+  const __nv_bfloat16* As;
+  const int* expA;
+  const __nv_bfloat16* Bs;
+  const int* expB;
+  double alpha, beta;
+  double* C;
+  int64_t ldc;
+  int* status;
+};
+// Slices of the R rows of op(X) (K values each): kc -> row r is stored column
+// r (X[k + r ld]), else stored row r (X[r + k ld]); amode 1 reads X as a
+// unit-lower reflector block.  slices: 7 * R * Kp bf16, exps: R ints.
+cudaError_t launch_oz_slice(const double* X, int64_t ld, bool kc, int amode, int64_t R, int64_t K,
+                            __nv_bfloat16* slices, int* exps, cudaStream_t st);
+cudaError_t launch_oz_gemm(const OzGemmArgs& g, cudaStream_t st);
+int64_t oz_kpad(int64_t K);
 
 // ---- sample_qrcp.cu: partial QRCP (Alg. 1, b steps) on the l x nc sample.
 struct SampleQrcpArgs {

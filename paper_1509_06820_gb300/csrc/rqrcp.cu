@@ -30,6 +30,7 @@ struct rqrcp_handle_s {
   int64_t launches[RQRCP_NPHASE] = {};
   int64_t launch_total = 0;
   int cur_phase = 7;
+  int fp64_emulation = 0;  // RQRCP_OPT_FP64_EMULATION
 };
 
 namespace {
@@ -85,6 +86,11 @@ struct Work {
   double* R12 = nullptr;      // b x n FP64 copy of the new rows of R
   float* tcpart = nullptr;    // split-K partial sums
   size_t tccap = 0;
+  // FP64 emulation on the tensor cores: operand slices and exponents
+  __nv_bfloat16* slA = nullptr;
+  __nv_bfloat16* slB = nullptr;
+  int* exA = nullptr;
+  int* exB = nullptr;
   size_t bytes = 0;
 };
 
@@ -100,12 +106,13 @@ struct Carver {
   }
 };
 
-Work carve(char op, int64_t m, int64_t n, int64_t k, int b, int p, int sms, char* base) {
+Work carve(char op, int64_t m, int64_t n, int64_t k, int b, int p, int sms, char* base,
+           bool emul = false) {
   Work w;
   Carver c{base};
   const int64_t ell = b + p;
   const int64_t bb = b;
-  if (op != 'Q') {
+  if (op != 'Q' && op != 'X') {
     w.omega = c.take<double>((size_t)ell * m);
     w.B = c.take<double>((size_t)ell * n);
     w.swaps = c.take<int64_t>(bb);
@@ -155,6 +162,13 @@ Work carve(char op, int64_t m, int64_t n, int64_t k, int b, int p, int sms, char
     w.R12 = c.take<double>((size_t)bb * n);
     w.tccap = (size_t)8 * bb * n;
     w.tcpart = c.take<float>(w.tccap);
+  } else if (op == 'X') {
+    // slices of op(A) (m rows) and op(B)^T (n rows), K = k
+    const int64_t Kp = rq::oz_kpad(k);
+    w.slA = c.take<__nv_bfloat16>((size_t)7 * m * Kp);
+    w.slB = c.take<__nv_bfloat16>((size_t)7 * n * Kp);
+    w.exA = c.take<int>(m);
+    w.exB = c.take<int>(n);
   } else if (op == 'M') {
     w.omega32 = c.take<float>((size_t)ell * m);
     w.B32 = c.take<float>((size_t)ell * n);
@@ -167,6 +181,16 @@ Work carve(char op, int64_t m, int64_t n, int64_t k, int b, int p, int sms, char
     w.R12 = c.take<double>((size_t)bb * n);
     w.tccap = (size_t)8 * bb * n;
     w.tcpart = c.take<float>(w.tccap);
+  }
+  if (emul && (op == 'R' || op == 'Q')) {
+    // slices of the trailing matrix A2^T (n rows of m) and of Y, W^T, and W^T itself
+    const int64_t Kp = rq::oz_kpad(m);
+    w.slA = c.take<__nv_bfloat16>((size_t)7 * n * Kp);
+    // Y sliced twice: b rows of m (as op(B) of Z^T), m rows of b (as op(A) of the update)
+    w.slB = c.take<__nv_bfloat16>(
+        (size_t)7 * std::max<int64_t>(bb * Kp, m * rq::oz_kpad(bb)));
+    w.exA = c.take<int>(std::max(n, m));
+    w.exB = c.take<int>(std::max(n, m));
   }
   w.bytes = align_up(c.off) + 256;
   return w;
@@ -276,11 +300,12 @@ int ensure(rqrcp_handle_t h, size_t bytes) {
 }
 
 int begin(rqrcp_handle_t h, char op, int64_t m, int64_t n, int64_t k, int b, int p, Call* cl) {
-  Work sz = carve(op, m, n, k, b, p, h->num_sms, nullptr);
+  const bool emul = h->fp64_emulation != 0;
+  Work sz = carve(op, m, n, k, b, p, h->num_sms, nullptr, emul);
   int r = ensure(h, sz.bytes);
   if (r != RQRCP_OK) return r;
   cl->h = h;
-  cl->w = carve(op, m, n, k, b, p, h->num_sms, h->ws);
+  cl->w = carve(op, m, n, k, b, p, h->num_sms, h->ws, emul);
   cl->st = h->stream;
   cl->status = h->state;
   cl->flag = h->state + 1;
@@ -315,12 +340,35 @@ int swaps_step(Call& cl, double* A, int64_t lda, int64_t rows, int64_t col0, int
   return RQRCP_OK;
 }
 
+// The trailing update with its two large products on the BF16 tensor cores
+// (FP64-accurate slicing, oz_gemm.cu): Z^T = A2^T Y (K = mJ), W^T = Z^T T in
+// native FP64 (small), A2 -= Y (W^T)^T (K = bJ).
+int trailing_update_emulated(Call& cl, const double* P, int64_t ld, int64_t mJ, int bJ,
+                             const double* T, double* A2, int64_t n2) {
+  Work& w = cl.w;
+  double* Zt = w.Z;  // n2 x bJ, ld n2
+  double* Wt = w.W;  // n2 x bJ, ld n2
+  CKL(1, rq::launch_oz_slice(A2, ld, true, 0, n2, mJ, w.slA, w.exA, cl.st));
+  CKL(1, rq::launch_oz_slice(P, ld, true, 1, bJ, mJ, w.slB, w.exB, cl.st));
+  rq::OzGemmArgs z{n2, bJ, rq::oz_kpad(mJ), w.slA, w.exA, w.slB, w.exB, 1.0, 0.0, Zt, n2,
+                   cl.status};
+  CKL(1, rq::launch_oz_gemm(z, cl.st));
+  CK(gemm(cl, 'N', 'N', 0, n2, bJ, bJ, 1.0, Zt, n2, T, bJ, 0.0, Wt, n2));
+  CKL(1, rq::launch_oz_slice(P, ld, false, 1, mJ, bJ, w.slB, w.exB, cl.st));
+  CKL(1, rq::launch_oz_slice(Wt, n2, false, 0, n2, bJ, w.slA, w.exA, cl.st));
+  rq::OzGemmArgs u{mJ, n2, rq::oz_kpad(bJ), w.slB, w.exB, w.slA, w.exA, -1.0, 1.0, A2, ld,
+                   cl.status};
+  CKL(1, rq::launch_oz_gemm(u, cl.st));
+  return RQRCP_OK;
+}
+
 // A2 <- Q^T A2 with Q = I - Y T Y^T; Y = unit-lower part of P (mJ x bJ, ld),
 // A2 mJ x n2 (ld).  Rows 0..bJ-1 of the result are R12.
 int trailing_update(Call& cl, const double* P, int64_t ld, int64_t mJ, int bJ, const double* T,
                     double* A2, int64_t n2) {
   if (n2 <= 0) return RQRCP_OK;
   PhaseScope ps(cl.h, PH_TRAIL, 4.0 * (double)mJ * (double)n2 * bJ + 2.0 * bJ * bJ * (double)n2);
+  if (cl.w.slA != nullptr && bJ <= 64) return trailing_update_emulated(cl, P, ld, mJ, bJ, T, A2, n2);
   CK(gemm(cl, 'T', 'N', 1, bJ, n2, mJ, 1.0, P, ld, A2, ld, 0.0, cl.w.Z, bJ));
   CK(gemm(cl, 'T', 'N', 0, bJ, n2, bJ, 1.0, T, bJ, cl.w.Z, bJ, 0.0, cl.w.W, bJ));
   CK(gemm(cl, 'N', 'N', 1, mJ, n2, bJ, -1.0, P, ld, cl.w.W, bJ, 1.0, A2, ld));
@@ -431,7 +479,16 @@ int rqrcp_reserve(rqrcp_handle_t h, char op, int64_t m, int64_t n, int64_t k, in
   if (!h) return -1;
   if (op == 'R' || op == 'Q') k = std::min(m, n);
   if (b > k) b = (int)std::max<int64_t>(k, 1);
-  return ensure(h, carve(op, m, n, k, b, p, h->num_sms, nullptr).bytes);
+  return ensure(h, carve(op, m, n, k, b, p, h->num_sms, nullptr, h->fp64_emulation != 0).bytes);
+}
+
+int rqrcp_set_option(rqrcp_handle_t h, int option, int value) {
+  if (!h) return -1;
+  if (option == RQRCP_OPT_FP64_EMULATION) {
+    h->fp64_emulation = value != 0;
+    return RQRCP_OK;
+  }
+  return -2;
 }
 
 int rqrcp_sync_info(rqrcp_handle_t h, int* info) {
@@ -962,6 +1019,37 @@ int rqrcp_gemm_bf16x(rqrcp_handle_t h, char transA, char transB, int64_t m, int6
   rq::TcGemmArgs g{transA, transB, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc, h->state,
                    false, false, 1, nullptr, 0, nullptr};
   CKL(1, rq::launch_tc_gemm(g, slices, cl.st));
+  return RQRCP_OK;
+}
+
+int rqrcp_gemm_f64x(rqrcp_handle_t h, char transA, char transB, int64_t m, int64_t n, int64_t k,
+                    double alpha, const double* dA, int64_t lda, const double* dB, int64_t ldb,
+                    double beta, double* dC, int64_t ldc) {
+  if (!h) return -1;
+  if (transA != 'N' && transA != 'T') return -2;
+  if (transB != 'N' && transB != 'T') return -3;
+  if (m < 0) return -4;
+  if (n < 0) return -5;
+  if (k < 0) return -6;
+  const int64_t arows = transA == 'N' ? m : k, brows = transB == 'N' ? k : n;
+  if (!dA && m * k > 0) return -8;
+  if (lda < std::max<int64_t>(1, arows)) return -9;
+  if (!dB && n * k > 0) return -10;
+  if (ldb < std::max<int64_t>(1, brows)) return -11;
+  if (!dC && m * n > 0) return -13;
+  if (ldc < std::max<int64_t>(1, m)) return -14;
+  if (m == 0 || n == 0) return RQRCP_OK;
+  Call cl;
+  int r = begin(h, 'X', m, n, std::max<int64_t>(k, 1), 1, 0, &cl);
+  if (r) return r;
+  PhaseScope ps(h, PH_TRAIL, 2.0 * (double)m * (double)n * (double)k);
+  // rows of op(A): stored columns when transposed; columns of op(B): stored
+  // columns when not transposed
+  CKL(1, rq::launch_oz_slice(dA, lda, transA == 'T', 0, m, k, cl.w.slA, cl.w.exA, cl.st));
+  CKL(1, rq::launch_oz_slice(dB, ldb, transB == 'N', 0, n, k, cl.w.slB, cl.w.exB, cl.st));
+  rq::OzGemmArgs g{m, n, rq::oz_kpad(k), cl.w.slA, cl.w.exA, cl.w.slB, cl.w.exB, alpha, beta,
+                   dC, ldc, cl.status};
+  CKL(1, rq::launch_oz_gemm(g, cl.st));
   return RQRCP_OK;
 }
 

@@ -353,3 +353,45 @@ def test_tc_gemm_accumulation_profile(lib):
                     assert e3.abs().max().item() <= 8 * u
     finally:
         torch.backends.cuda.matmul.allow_tf32 = prev
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T")])
+@pytest.mark.parametrize("m,n,k", [(128, 64, 64), (300, 200, 150), (200, 70, 1000), (1, 1, 1)])
+def test_gemm_f64x_accuracy(lib, ta, tb, m, n, k):
+    """FP64 GEMM emulated on the BF16 tensor cores: error at FP64 level
+    (<= 64 * 2^-53 of sum_k |a||b|), on data spanning 12 decades per row."""
+    r = np.random.default_rng(m + 3 * n + 7 * k)
+    A = r.standard_normal((m, k) if ta == "N" else (k, m)) * 10.0 ** r.uniform(-6, 6, ((m, k) if ta == "N" else (k, m)))
+    B = r.standard_normal((k, n) if tb == "N" else (n, k))
+    C0 = r.standard_normal((m, n))
+    opA = A if ta == "N" else A.T
+    opB = B if tb == "N" else B.T
+    C = to_dev(C0)
+    lib.gemm_f64x(to_dev(A), to_dev(B), ta, tb, alpha=-1.0, beta=1.0, C=C)
+    assert lib.sync_info() == 0
+    ref = C0 - opA @ opB
+    scale = np.abs(opA) @ np.abs(opB) + np.abs(C0)
+    err = (np.abs(host(C) - ref) / scale).max()
+    assert err <= 64 * 2.0 ** -53, err
+
+
+@pytest.mark.parametrize("m,n,b,p", [(300, 200, 32, 8), (1000, 1000, 32, 8), (520, 700, 64, 8)])
+def test_rqrcp_fp64_emulated_trailing(lib, m, n, b, p):
+    """RQRCP with the trailing update on the BF16 tensor cores (FP64-accurate
+    slicing) meets the same FP64 parity bar against the oracle."""
+    h = lib.Handle()
+    h.set_fp64_emulation(True)
+    try:
+        A = synth.gaussian(m, n, seed=m + n)
+        dA = to_dev(A)
+        jpvt, tau = lib.rqrcp_factor(dA, b, p, 1, handle=h)
+        assert h.sync_info() == 0
+        F, jp, t = host(dA), host(jpvt), host(tau)
+        Fo, jo, to, _ = oracle.rqrcp(A, b, p, seed=1, replay_jpvt=jp)
+        k = min(m, n)
+        Ro = np.triu(Fo[:k])
+        assert np.linalg.norm(np.triu(F[:k]) - Ro) <= RTOL_R * np.linalg.norm(Ro)
+        Q = hh.form_q(F, t, m)
+        assert np.linalg.norm(A[:, jp] - Q @ np.triu(F)) <= RTOL_REC * np.linalg.norm(A)
+    finally:
+        h.close()
