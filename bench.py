@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the QR baseline, e2e, cpu_baseline, mixed and serving legs")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--only-emulated", action="store_true",
+                    help="time only the native and emulated FP64 legs (development aid)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     return ap.parse_args()
 
@@ -244,6 +246,50 @@ def mixed_leg(args, dev, fp64_ms, stream):
             "trailing_update": {"ms": tr_ms, "bf16_tflops": 6 * tr_fl / (tr_ms / 1e3) / 1e12,
                                 "tf32_equiv_tflops": tr_fl / (tr_ms / 1e3) / 1e12},
             "phases": {kk: {"ms": v[0], "launches": v[2]} for kk, v in prof.items()}}
+
+
+def emulated_leg(args, dev, A0, fp64_ms, qr_ms, stream):
+    """The same FP64 factorization with the trailing update on the BF16
+    tensor cores (FP64-accurate slicing, rqrcp_set_option), and the same for
+    the unpivoted QR."""
+    import torch
+    import paper_1509_06820_gb300 as rq
+    n, b, p = args.n, args.b, args.p
+    h = rq.Handle(dev)
+    h.set_fp64_emulation(True)
+    h.reserve("R", n, n, n, b, p)
+    A = rq.empty_colmajor(n, n, dev)
+    out = {}
+    for name, call in (("rqrcp", lambda: rq.rqrcp_factor(A, b, p, 1, handle=h)),
+                       ("qr", lambda: rq.qr_factor(A, b, handle=h))):
+        for _ in range(max(1, args.warmup)):
+            A.copy_(A0)
+            call()
+        torch.cuda.synchronize(dev)
+        h.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            A.copy_(A0)
+            call()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / args.steps
+        prof = h.profile_read()
+        h.profile(False)
+        tr_ms, tr_fl, tr_l = prof["trailing_update"]
+        out[name] = {"ms_per_step": ms, "gflops": flops_geqrf(n, n) / (ms / 1e3) / 1e9,
+                     "trailing_update_fp64_equiv_tflops": tr_fl / (tr_ms / 1e3) / 1e12,
+                     "trailing_update_bf16_tflops": 28 * tr_fl / (tr_ms / 1e3) / 1e12,
+                     "phases": {k: round(v[0] / args.steps, 2) for k, v in prof.items()}}
+    out["device_info"] = h.sync_info()
+    out["rqrcp_over_qr_time"] = out["rqrcp"]["ms_per_step"] / out["qr"]["ms_per_step"]
+    out["speedup_vs_fp64_pipe"] = fp64_ms / out["rqrcp"]["ms_per_step"]
+    out["note"] = ("28 BF16 slice products per FP64 multiply-add, exact per-diagonal FP32 sums, "
+                   "double-FP32 running sums; parity vs the FP64 oracle in tests")
+    h.close()
+    del A
+    return out
 
 
 def truncated_leg(args, dev):
@@ -468,7 +514,10 @@ def main():
                            f"factorization, {dt:.1f} s, rate from their algorithmic flops"),
                 "threads": "numpy BLAS default (all host cores)"}
 
-    if not args.no_extras:
+    if args.only_emulated:
+        extras["fp64_emulated"] = emulated_leg(args, dev, A0, ms, None, stream)
+    elif not args.no_extras:
+        extras["fp64_emulated"] = emulated_leg(args, dev, A0, ms, extras["qr_ms_per_step"], stream)
         extras["mixed"] = mixed_leg(args, dev, ms, stream)
         extras["truncated"] = truncated_leg(args, dev)
         if rank == 0:

@@ -10,22 +10,23 @@
 // each slice value y_s 2^{-8s} exactly representable in BF16.
 //
 // Products.  C_ij = 2^{e_i + f_j} sum_{s,t} sum_k a_s(i,k) b_t(k,j).  The pairs
-// with s + t = d carry the common grid 2^{-8d}; with K <= 64 per accumulation
-// their sum is an integer multiple of that grid below (d-1) 64 255^2 < 2^24
-// units for d <= 5, hence EXACT in an FP32 accumulator whatever the tensor
-// core's rounding.  d = 2, 3, 4, 5 get one accumulator each; d = 6, 7, 8 share
-// one (their FP32 rounding is below 2^-53 of the leading term); pairs with
-// s + t > 8 are dropped (below 2^-56).  28 BF16 MMAs per k-step.
+// with s + t = d carry the common grid 2^{-8d}; with K <= 32 per accumulation
+// their sum is an integer multiple of that grid below (d-1) 32 255^2 < 2^24
+// units for d <= 6, hence EXACT in an FP32 accumulator whatever the tensor
+// core's rounding (it truncates).  d = 2..6 get one accumulator each; d = 7, 8
+// share one (at most 2^-40 of the leading term, so even a truncating FP32 sum
+// of its 416 products errs below 2^-54); pairs with s + t > 8 are dropped
+// (below 2^-56).  28 BF16 MMAs per k-step.
 //
 // Kernel (oz_gemm_kernel): one 128 x 64 output tile per CTA, 256 threads.
 // Per 64-wide k-stage the slices are copied (16-byte chunks) into the
-// 128-byte-swizzled K-major layout, thread 0 issues the 28 x 4 tcgen05.mma
-// into the five tensor-memory accumulators (5 x 64 columns), commits to an
-// mbarrier, and the eight warps (two per accumulator lane quadrant, one per
-// 32-column half) drain the accumulators into running
-// double-FP32 sums (error-free TwoSum), so the exactness bound never needs
-// K > 64.  The epilogue forms 2^{e_i + f_j} (hi + lo) in FP64 and writes
-// C = alpha * that + beta * C.
+// 128-byte-swizzled K-major layout; for each 32-wide half of the stage,
+// thread 0 issues the 28 x 2 tcgen05.mma into the six tensor-memory
+// accumulators (6 x 64 columns), commits to an mbarrier, and the eight warps
+// (two per accumulator lane quadrant, one per 32-column half) drain the
+// accumulators into running double-FP32 sums (error-free TwoSum), so the
+// exactness bound never needs K > 32.  The epilogue forms
+// 2^{e_i + f_j} (hi + lo) in FP64 and writes C = alpha * that + beta * C.
 #include <cuda_bf16.h>
 
 #include "kernels.cuh"
@@ -35,7 +36,8 @@ namespace {
 
 constexpr int OZ_S = 7;        // slices per operand
 constexpr int OZ_BITS = 8;     // bits per slice
-constexpr int OZ_NG = 5;       // accumulators: d = 2, 3, 4, 5 and d >= 6
+constexpr int OZ_NG = 6;       // accumulators: d = 2, 3, 4, 5, 6 and d >= 7
+constexpr int OZ_KH = 32;      // k per exact accumulation (one drain)
 constexpr int OZ_BM = 128;
 constexpr int OZ_BN = 64;
 constexpr int OZ_BK = 64;
@@ -256,65 +258,69 @@ __global__ void __launch_bounds__(OZ_NT, 1) oz_gemm_kernel(OzGemmArgs g) {
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = su32(As), b0 = su32(Bs);
-      uint32_t started = 0;  // bit g: accumulator g written in this stage
+    for (int half = 0; half < OZ_BK / OZ_KH; ++half) {
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = su32(As), b0 = su32(Bs);
+        uint32_t started = 0;  // bit g: accumulator g written in this half
 #pragma unroll
-      for (int d = OZ_S + 1; d >= 2; --d) {
-        const int grp = oz_group(d);
+        for (int d = OZ_S + 1; d >= 2; --d) {
+          const int grp = oz_group(d);
 #pragma unroll
-        for (int s = 1; s <= OZ_S; ++s) {
-          const int t = d - s;
-          if (t < 1 || t > OZ_S) continue;
+          for (int s = 1; s <= OZ_S; ++s) {
+            const int t = d - s;
+            if (t < 1 || t > OZ_S) continue;
 #pragma unroll
-          for (int kk = 0; kk < OZ_BK / 16; ++kk) {
-            const uint32_t acc = (started >> grp) & 1u;
-            oz_mma(tmem + (uint32_t)(grp * OZ_BN),
-                   oz_desc(a0 + (uint32_t)((s - 1) * A_SL) + kk * 32),
-                   oz_desc(b0 + (uint32_t)((t - 1) * B_SL) + kk * 32), acc);
-            started |= 1u << grp;
+            for (int kq = 0; kq < OZ_KH / 16; ++kq) {
+              const int kk = half * (OZ_KH / 16) + kq;
+              const uint32_t acc = (started >> grp) & 1u;
+              oz_mma(tmem + (uint32_t)(grp * OZ_BN),
+                     oz_desc(a0 + (uint32_t)((s - 1) * A_SL) + kk * 32),
+                     oz_desc(b0 + (uint32_t)((t - 1) * B_SL) + kk * 32), acc);
+              started |= 1u << grp;
+            }
           }
         }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                su32(&mbar))
+            : "memory");
+        if (!oz_mbar_wait(&mbar, (uint32_t)((kt * (OZ_BK / OZ_KH) + half) & 1))) s_fail = 1;
       }
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              su32(&mbar))
-          : "memory");
-      if (!oz_mbar_wait(&mbar, (uint32_t)(kt & 1))) s_fail = 1;
-    }
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (s_fail) break;
-    // ---- drain: add the five exact group sums of this stage (smallest
-    // first) into the running double-FP32 sums of row 32 warp + lane
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)cbase;
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (s_fail) break;
+      // ---- drain: add the exact group sums (smallest first) into the
+      // running double-FP32 sums of row 32 quad + lane, columns cbase..
+      const uint32_t lane_base = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)cbase;
 #pragma unroll
-    for (int c0 = 0; c0 < CPT; c0 += 16) {
-      float v[16], part_hi[16], part_lo[16];
+      for (int c0 = 0; c0 < CPT; c0 += 16) {
+        float v[16], part_hi[16], part_lo[16];
 #pragma unroll
-      for (int e = 0; e < 16; ++e) part_hi[e] = part_lo[e] = 0.0f;
+        for (int e = 0; e < 16; ++e) part_hi[e] = part_lo[e] = 0.0f;
 #pragma unroll
-      for (int grp = OZ_NG - 1; grp >= 0; --grp) {
-        oz_ld16(lane_base + (uint32_t)(grp * OZ_BN + c0), v);
+        for (int grp = OZ_NG - 1; grp >= 0; --grp) {
+          oz_ld16(lane_base + (uint32_t)(grp * OZ_BN + c0), v);
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            float sm, err;
+            two_sum(part_hi[e], v[e], sm, err);
+            part_hi[e] = sm;
+            part_lo[e] += err;
+          }
+        }
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-          float s, err;
-          two_sum(part_hi[e], v[e], s, err);
-          part_hi[e] = s;
-          part_lo[e] += err;
+          float sm, err;
+          two_sum(hi[c0 + e], part_hi[e], sm, err);
+          hi[c0 + e] = sm;
+          lo[c0 + e] += err + part_lo[e];
         }
       }
-#pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        float s, err;
-        two_sum(hi[c0 + e], part_hi[e], s, err);
-        hi[c0 + e] = s;
-        lo[c0 + e] += err + part_lo[e];
-      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();  // accumulators read before the next MMAs overwrite them
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();  // accumulators read before the next stage's MMAs
+    if (s_fail) break;
   }
 
   if (s_fail) {
