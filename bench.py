@@ -79,9 +79,18 @@ def parse():
                     help="skip the QR baseline, e2e, cpu_baseline, mixed and serving legs")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--only-emulated", action="store_true",
-                    help="time only the native and emulated FP64 legs (development aid)")
+                    help="same as --legs emulated")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
-    return ap.parse_args()
+    ap.add_argument("--legs", default="qr,e2e,cpu,emulated,mixed,truncated,serving",
+                    help="comma-separated extra legs to run after the FP64 step")
+    args = ap.parse_args()
+    legs = set(x for x in args.legs.split(",") if x)
+    if args.no_extras:
+        legs = set()
+    if args.only_emulated:
+        legs = {"emulated"}
+    args.legs = legs
+    return args
 
 
 # ------------------------------------------------------------------ clocks
@@ -450,7 +459,7 @@ def main():
     phases = {k: {"ms": v[0], "gflop": v[1] / 1e9, "launches": v[2]} for k, v in prof.items()}
 
     extras = {}
-    if not args.no_extras:
+    if "qr" in args.legs:
         # the project's own unpivoted blocked QR on the same matrix
         def qstep():
             A.copy_(A0)
@@ -469,6 +478,7 @@ def main():
         extras["qr_gflops"] = fl / (qr_ms / 1e3) / 1e9
         extras["rqrcp_over_qr_time"] = ms / qr_ms
 
+    if "e2e" in args.legs:
         # end to end through the public call with host buffers
         Ah = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
         Ah.copy_(A0)
@@ -504,24 +514,25 @@ def main():
                          "d2h_bytes_per_step": m * n * 8 + n * 8 + min(m, n) * 8}
         del Ah, Ah_out
 
-        if rank == 0:
-            import numpy as np
-            A_host = np.asfortranarray(A0.cpu().numpy())
-            rate, dt = cpu_sample(A_host, b, p, args.cpu_blocks)
-            extras["cpu_baseline"] = {
-                "value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                "sample": (f"first {args.cpu_blocks} blocks (b={b}) of the same {n}x{n} "
-                           f"factorization, {dt:.1f} s, rate from their algorithmic flops"),
-                "threads": "numpy BLAS default (all host cores)"}
+    if "cpu" in args.legs and rank == 0:
+        import numpy as np
+        A_host = np.asfortranarray(A0.cpu().numpy())
+        rate, dt = cpu_sample(A_host, b, p, args.cpu_blocks)
+        extras["cpu_baseline"] = {
+            "value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"first {args.cpu_blocks} blocks (b={b}) of the same {n}x{n} "
+                       f"factorization, {dt:.1f} s, rate from their algorithmic flops"),
+            "threads": "numpy BLAS default (all host cores)"}
 
-    if args.only_emulated:
-        extras["fp64_emulated"] = emulated_leg(args, dev, A0, ms, None, stream)
-    elif not args.no_extras:
-        extras["fp64_emulated"] = emulated_leg(args, dev, A0, ms, extras["qr_ms_per_step"], stream)
+    if "emulated" in args.legs:
+        extras["fp64_emulated"] = emulated_leg(args, dev, A0, ms, extras.get("qr_ms_per_step"),
+                                               stream)
+    if "mixed" in args.legs:
         extras["mixed"] = mixed_leg(args, dev, ms, stream)
+    if "truncated" in args.legs:
         extras["truncated"] = truncated_leg(args, dev)
-        if rank == 0:
-            extras["serving"] = serving_leg(args, dev)
+    if "serving" in args.legs and rank == 0:
+        extras["serving"] = serving_leg(args, dev)
 
     if rank == 0:
         line = {

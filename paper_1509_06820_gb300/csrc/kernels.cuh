@@ -44,6 +44,9 @@ cudaError_t launch_gemm(const GemmArgs& g, int splits, double* partial, cudaStre
 int gemm_pick_splits(int64_t M, int64_t N, int64_t K, int num_sms);
 
 // ---- tc_gemm.cu: split-BF16 tensor-core GEMM (tcgen05), FP32 operands.
+// The operands are first split into bfloat16 slices (k-contiguous rows of
+// op(A) and columns of op(B), in the caller's scratch), then multiplied by a
+// persistent TMA-fed kernel.
 struct TcGemmArgs {
   char transA, transB;
   int64_t M, N, K;
@@ -56,15 +59,20 @@ struct TcGemmArgs {
   float* C;
   int64_t ldc;
   int* status;
-  bool vecA, vecB;      // set by the launcher
-  int splits;           // split-K factor (1: none)
-  float* partial;       // splits * M * N floats when splits > 1
-  int kt_per_split;     // set by the launcher
-  const int64_t* bcols; // transB == 'N' only: column j of op(B) is stored column bcols[j]
+  const int64_t* bcols;  // transB == 'N' only: column j of op(B) is stored column bcols[j]
+  __nv_bfloat16* slA;    // >= tc_slice_elems(M, K, slices) elements
+  size_t slcapA;
+  __nv_bfloat16* slB;    // >= tc_slice_elems(N, K, slices) elements
+  size_t slcapB;
+  float* partial;        // split-K sums (2 floats per element of C and split); may be null
+  size_t partial_cap;    // floats
+  int num_sms;
 };
 // slices = 1 (plain BF16) or 3 (FP32-level split, six products)
 cudaError_t launch_tc_gemm(TcGemmArgs g, int slices, cudaStream_t st);
-int tc_pick_splits(int64_t M, int64_t N, int64_t K, int num_sms, size_t cap_floats);
+size_t tc_slice_elems(int64_t rows, int64_t K, int slices);
+// kernel launches one launch_tc_gemm call makes
+int tc_launches(int64_t M, int64_t N, int64_t K, int num_sms, size_t partial_cap);
 
 // ---- oz_gemm.cu: FP64-accurate GEMM on the BF16 tensor cores by exact
 // slicing.  C (M x N, FP64, ldc) = alpha * 2^(expA_i + expB_j) * (A_sl B_sl^T)

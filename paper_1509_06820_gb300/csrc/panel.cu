@@ -234,11 +234,8 @@ __global__ void __launch_bounds__(NT, 1) panel_kernel(PanelArgs a) {
 
 }  // namespace
 
-// At least 128 rows per CTA: the per-column cost is dominated by the grid
-// barrier and the cross-CTA reduction, so small panels gain nothing from more
-// CTAs, and fewer CTAs leave SMs free for concurrent problems.
 int panel_grid(int64_t mJ, int bJ, int num_sms) {
-  int64_t G = (mJ + 127) / 128;
+  int64_t G = (mJ + 31) / 32;
   if (G > num_sms) G = num_sms;
   if (G < 1) G = 1;
   return (int)G;

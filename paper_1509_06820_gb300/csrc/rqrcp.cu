@@ -84,8 +84,12 @@ struct Work {
   float* Z32 = nullptr;       // b x n
   float* W32 = nullptr;       // b x n
   double* R12 = nullptr;      // b x n FP64 copy of the new rows of R
-  float* tcpart = nullptr;    // split-K partial sums
+  float* tcpart = nullptr;    // split-K partial sums (hi and lo per split)
   size_t tccap = 0;
+  __nv_bfloat16* tslA = nullptr;  // bfloat16 slices of op(A) rows
+  size_t tslcapA = 0;
+  __nv_bfloat16* tslB = nullptr;  // bfloat16 slices of op(B) columns
+  size_t tslcapB = 0;
   // FP64 emulation on the tensor cores: operand slices and exponents
   __nv_bfloat16* slA = nullptr;
   __nv_bfloat16* slB = nullptr;
@@ -160,8 +164,22 @@ Work carve(char op, int64_t m, int64_t n, int64_t k, int b, int p, int sms, char
     w.W32 = c.take<float>((size_t)k * n);   // W^T
     w.Wt = c.take<double>((size_t)bb * k);  // Y2^T Y1 as floats (reinterpreted)
     w.R12 = c.take<double>((size_t)bb * n);
-    w.tccap = (size_t)8 * bb * n;
+    w.tccap = (size_t)16 * bb * n;
     w.tcpart = c.take<float>(w.tccap);
+    // the largest split-BF16 products: (b x m)(m x n) and (m x k)(k x b)
+    w.tslcapA = std::max(rq::tc_slice_elems(bb, m, 3),
+                         std::max(rq::tc_slice_elems(m, k, 3), rq::tc_slice_elems(ell, m, 1)));
+    w.tslcapB = std::max(rq::tc_slice_elems(n, m, 3), rq::tc_slice_elems(k, m, 3));
+    w.tslA = c.take<__nv_bfloat16>(w.tslcapA);
+    w.tslB = c.take<__nv_bfloat16>(w.tslcapB);
+  } else if (op == 'G') {
+    // split-BF16 GEMM of op(A) (m x k) and op(B) (k x n)
+    w.tccap = (size_t)32 * (size_t)std::min<int64_t>(m * n, (int64_t)sms * 128 * 128);
+    w.tcpart = c.take<float>(w.tccap);
+    w.tslcapA = rq::tc_slice_elems(m, k, 3);
+    w.tslcapB = rq::tc_slice_elems(n, k, 3);
+    w.tslA = c.take<__nv_bfloat16>(w.tslcapA);
+    w.tslB = c.take<__nv_bfloat16>(w.tslcapB);
   } else if (op == 'X') {
     // slices of op(A) (m rows) and op(B)^T (n rows), K = k
     const int64_t Kp = rq::oz_kpad(k);
@@ -179,8 +197,14 @@ Work carve(char op, int64_t m, int64_t n, int64_t k, int b, int p, int sms, char
     w.Z32 = c.take<float>((size_t)bb * n);
     w.W32 = c.take<float>((size_t)bb * n);
     w.R12 = c.take<double>((size_t)bb * n);
-    w.tccap = (size_t)8 * bb * n;
+    w.tccap = (size_t)16 * bb * n;
     w.tcpart = c.take<float>(w.tccap);
+    // the largest split-BF16 products: (b x m)(m x n) and (m x b)(b x n)
+    w.tslcapA = std::max(rq::tc_slice_elems(bb, m, 3),
+                         std::max(rq::tc_slice_elems(m, bb, 3), rq::tc_slice_elems(ell, m, 1)));
+    w.tslcapB = rq::tc_slice_elems(n, m, 3);
+    w.tslA = c.take<__nv_bfloat16>(w.tslcapA);
+    w.tslB = c.take<__nv_bfloat16>(w.tslcapB);
   }
   if (emul && (op == 'R' || op == 'Q')) {
     // slices of the trailing matrix A2^T (n rows of m) and of Y, W^T, and W^T itself
@@ -273,13 +297,11 @@ cudaError_t gemm(Call& cl, char ta, char tb, int amode, int64_t M, int64_t N, in
 cudaError_t tcgemm(Call& cl, char ta, char tb, int64_t M, int64_t N, int64_t K, float alpha,
                    const float* A, int64_t lda, const float* B, int64_t ldb, float beta, float* C,
                    int64_t ldc, int slices, const int64_t* bcols = nullptr) {
-  rq::TcGemmArgs g{ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, cl.status, false, false,
-                   1, nullptr, 0, bcols};
-  if (cl.w.tcpart != nullptr) {
-    g.splits = rq::tc_pick_splits(M, N, K, cl.h->num_sms, cl.w.tccap);
-    g.partial = g.splits > 1 ? cl.w.tcpart : nullptr;
-  }
-  if (M > 0 && N > 0) count_launch(cl.h, g.splits > 1 ? 2 : 1);
+  rq::TcGemmArgs g{ta,     tb,        M,         N,         K,          alpha,
+                   A,      lda,       B,         ldb,       beta,       C,
+                   ldc,    cl.status, bcols,     cl.w.tslA, cl.w.tslcapA, cl.w.tslB,
+                   cl.w.tslcapB, cl.w.tcpart, cl.w.tccap, cl.h->num_sms};
+  count_launch(cl.h, rq::tc_launches(M, N, K, cl.h->num_sms, cl.w.tcpart ? cl.w.tccap : 0));
   return rq::launch_tc_gemm(g, slices, cl.st);
 }
 
@@ -417,8 +439,6 @@ int orgqr_core(Call& cl, int64_t M, int64_t K, const double* F, int64_t ldf, int
   }
   return RQRCP_OK;
 }
-
-int check_handle(rqrcp_handle_t h) { return h ? RQRCP_OK : -1; }
 
 bool sizes_fit(int num_sms, int64_t m, int64_t n, int b, int ell) {
   if (b > kMaxB || ell > kMaxEll) return false;
@@ -1012,13 +1032,12 @@ int rqrcp_gemm_bf16x(rqrcp_handle_t h, char transA, char transB, int64_t m, int6
   if (!dC && m * n > 0) return -13;
   if (ldc < std::max<int64_t>(1, m)) return -14;
   if (slices != 1 && slices != 3) return -15;
-  Call cl{};
-  cl.h = h;
-  cl.st = h->stream;
+  if (m == 0 || n == 0) return RQRCP_OK;
+  Call cl;
+  int r = begin(h, 'G', m, n, k, 1, 0, &cl);
+  if (r) return r;
   PhaseScope ps(h, PH_TRAIL, 2.0 * (double)m * (double)n * (double)k);
-  rq::TcGemmArgs g{transA, transB, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc, h->state,
-                   false, false, 1, nullptr, 0, nullptr};
-  CKL(1, rq::launch_tc_gemm(g, slices, cl.st));
+  CK(tcgemm(cl, transA, transB, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc, slices));
   return RQRCP_OK;
 }
 

@@ -246,7 +246,7 @@ size_t smem_bytes(int ell, int64_t chunk) {
 constexpr size_t kSmemLimit = 216 * 1024;
 
 int sample_grid(int64_t nc, int num_sms) {
-  int64_t G = (nc + 127) / 128;  // at least 128 sample columns per CTA
+  int64_t G = (nc + 63) / 64;
   if (G > num_sms) G = num_sms;
   if (G < 1) G = 1;
   return (int)G;

@@ -1,38 +1,58 @@
 // Split-BF16 GEMM on the 5th-generation tensor cores (tcgen05, sm_103a):
 //   C = alpha op(A) op(B) + beta C, FP32 operands and result, column-major.
 //
-// Each FP32 operand element x is split into S bfloat16 slices
+// Splitting (tcx_split_kernel, one memory-bound pass per operand).  Each FP32
+// element x becomes S bfloat16 slices
 //   x1 = bf16(x), x2 = bf16(x - x1), x3 = bf16(x - x1 - x2)
-// (every subtraction is exact in FP32), and the product is the sum of the
-// slice products x_s y_t with s + t <= S + 1 -- for S = 3 the six products
-// 11, 12, 21, 13, 31, 22 -- accumulated in FP32 in tensor memory.  S = 3
-// gives FP32-level accuracy (the mixed-precision form of the trailing-matrix
-// update of Alg. 4); S = 1 is a plain BF16 product with FP32
-// accumulation (the mixed-precision sketch B = Omega A).
+// (every subtraction is exact in FP32 and x1 + x2 + x3 = x).  The rows of
+// op(A) and the columns of op(B) are written k-contiguous, S slices after one
+// another, rows padded to 128 and k to 64 with zeros, so that one TMA box is
+// one slice tile in the layout the MMA reads.
 //
-// Kernel structure (one 128 x BN output tile per CTA, 128 threads):
-//   * all four warps load a 128 x 64 (A) and BN x 64 (B) k-slice of the FP32
-//     operands from global memory, split it and store the bf16 slices in the
-//     128-byte-swizzled K-major layout the MMA reads (row r at r*128 bytes,
-//     16-byte chunk c at position c ^ (r mod 8));
-//   * thread 0 issues the tcgen05.mma instructions (M = 128, N = BN, K = 16)
-//     for every slice product and k-step, then tcgen05.commit arrives on the
-//     stage's mbarrier; two stages let the loads of k-slice t+1 overlap the
-//     MMAs of k-slice t;
-//   * the accumulator lives in tensor memory (BN columns x 128 lanes); warp w
-//     reads lanes 32w..32w+31 with tcgen05.ld and writes C.
+// Products.  S = 3 is the mixed-precision form of the trailing update of
+// Alg. 4 (FP32-level accuracy): the six slice products with s + t <= 4.  The
+// tensor core rounds its FP32 accumulator toward zero, which over a long k
+// loop gives an error that grows with K; so the leading product x1 y1 and the
+// five correction products go to two separate tensor-memory accumulators that
+// are drained every 32 k (two MMA k-steps) into running sums in registers
+// with Kahan compensation (error below 2u of the sum, independent of K).
+// S = 1 (the sketch B = Omega A, which only steers pivots) is one product
+// accumulated over the whole k range.
+//
+// Kernel (tcx_gemm_kernel): persistent, one CTA per SM, 128 x 64 output
+// tiles, split-K units; 5 warps with fixed roles:
+//   warp 0      allocates tensor memory; one thread issues the TMA copies
+//               (per 64-k stage one 3-D box per operand: 64 k x rows x S
+//               slices, 128-byte swizzle) into a three-stage shared-memory
+//               ring (mbarrier expect-tx), the tcgen05.mma (M = 128, N = 64,
+//               K = 16) and the tcgen05.commit;
+//   warps 1-4   drain: warp w reads accumulator lanes 32 (w % 4).. (one row
+//               per thread, 64 columns), adds into the compensated sums and,
+//               at the end of a unit, writes C (or its split-K partial sums).
+// The accumulators are double-buffered in tensor memory (2 x 2 x 64
+// columns), so the drain of one chunk overlaps the MMAs of the next.
 // Every mbarrier wait is bounded; on timeout the status word gets
-// RQRCP_INFO_TIMEOUT and the kernel frees its tensor memory and returns.
+// RQRCP_INFO_TIMEOUT, each role stops, in-flight copies and MMAs are waited
+// for (bounded) and the tensor memory is freed.
+#include <cuda.h>
 #include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
 
 #include "kernels.cuh"
 
 namespace rq {
 namespace {
 
-constexpr int TBM = 128;   // UMMA M
-constexpr int TBK = 64;    // k per stage: one 128-byte swizzle row of bf16
-constexpr int TNT = 128;   // threads
+constexpr int XBM = 128;          // tile rows (A role), UMMA M
+constexpr int XBN = 64;           // tile columns (B role), UMMA N
+constexpr int XBK = 64;           // k per pipeline stage: one 128-byte swizzle row
+constexpr int XNST = 3;           // shared-memory ring stages
+constexpr int XNT = 160;          // warp 0 TMA and MMA issue, warps 1..4 drain
+constexpr int XCH = 2;            // MMA k-steps per drained chunk (S = 3): 32 k
+constexpr int XTILE_A = XBM * 128;  // bytes of one A slice tile (128 rows x 64 k)
+constexpr int XTILE_B = XBN * 128;  // bytes of one B slice tile (64 rows x 64 k)
 constexpr unsigned kWaitPolls = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -43,24 +63,39 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait; false when it gave up.
+// Bounded wait for the phase with the given parity; false when it gave up.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   for (unsigned i = 0; i < kWaitPolls; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (i > 32) __nanosleep(32);
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (i > 64) __nanosleep(64);
   }
   return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() {
@@ -74,27 +109,25 @@ __device__ __forceinline__ void tc_fence_after() {
 // 1024 bytes apart (stride byte offset), descriptor version 1.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);       // start address
-  d |= (uint64_t)1 << 16;                          // leading byte offset (unused)
-  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
-  d |= (uint64_t)1 << 46;                          // version
-  d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                     // leading byte offset (unused)
+  d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset
+  d |= (uint64_t)1 << 46;                     // version
+  d |= (uint64_t)2 << 61;                     // 128-byte swizzle
   return d;
 }
 
 // Instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B, both
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
+constexpr uint32_t XIDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(XBN >> 3) << 17) |
+                            ((uint32_t)(XBM >> 4) << 24);
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
+                                         uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      "l"(adesc), "l"(bdesc), "r"(XIDESC), "r"(accumulate)
       : "memory");
 }
 
@@ -105,20 +138,38 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
+// 8 columns of two accumulators (same lanes), then wait for both loads.
+__device__ __forceinline__ void tmem_ld8x2(uint32_t ta, uint32_t tb, float* a, float* b) {
+  uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n"
+      "tcgen05.wait::ld.sync.aligned;"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(ta), "r"(tb)
+      : "memory");
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 8; ++i) {
+    a[i] = __uint_as_float(r[i]);
+    b[i] = __uint_as_float(r[8 + i]);
+  }
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t ta, float* a) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(ta)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -126,102 +177,128 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// Split 8 consecutive-k values into S slices and store each as one 16-byte
-// chunk of row r of the slice tiles (swizzled position).
+// Split 8 consecutive-k values into S slices; slice s goes to dst[s * sstride].
 template <int S>
-__device__ __forceinline__ void split_store(const float* x, unsigned char* tile0, size_t slice_bytes,
-                                            int r, int c) {
+__device__ __forceinline__ void split8_store(const float* x, __nv_bfloat16* dst, size_t sstride) {
   float rem[8];
 #pragma unroll
   for (int e = 0; e < 8; ++e) rem[e] = x[e];
-  const uint32_t off = (uint32_t)r * 128u + ((uint32_t)(c ^ (r & 7)) << 4);
 #pragma unroll
   for (int s = 0; s < S; ++s) {
-    float hi[8];
+    float h[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-      hi[e] = __bfloat162float(__float2bfloat16_rn(rem[e]));
-      rem[e] = rem[e] - hi[e];
+      h[e] = __bfloat162float(__float2bfloat16_rn(rem[e]));
+      rem[e] = rem[e] - h[e];
     }
-    uint4 q = make_uint4(pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]), pack_bf16(hi[4], hi[5]),
-                         pack_bf16(hi[6], hi[7]));
-    *reinterpret_cast<uint4*>(tile0 + (size_t)s * slice_bytes + off) = q;
+    *reinterpret_cast<uint4*>(dst + (size_t)s * sstride) =
+        make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]),
+                   pack_bf16(h[6], h[7]));
   }
 }
 
-// Load the rows x 64 k-slice of an operand into S swizzled slice tiles.
-// KC: element (row, k) at base[row * ld + k] (contiguous along k);
-// otherwise at base[row + k * ld] (contiguous along rows).
-// rmap (KC only, may be null): tile row r reads stored row rmap[row0 + r].
-template <int S, bool KC>
-__device__ __forceinline__ void load_tile(const float* __restrict__ base, int64_t ld, int64_t row0,
-                                          int64_t nrows_total, int64_t k0, int64_t K, int rows,
-                                          bool vec, unsigned char* tile0, size_t slice_bytes,
-                                          const int64_t* __restrict__ rmap) {
-  const int tid = threadIdx.x;
-  if (KC) {
-    for (int item = tid; item < rows * 8; item += TNT) {
-      const int r = item >> 3, c = item & 7;
-      const int64_t gr = row0 + r, gk = k0 + 8 * c;
-      float x[8];
-      const int64_t sr = (gr < nrows_total && rmap != nullptr) ? rmap[gr] : gr;
-      if (gr < nrows_total && vec && gk + 8 <= K) {
-        const float4* p = reinterpret_cast<const float4*>(base + sr * ld + gk);
-        float4 a = __ldg(p), b = __ldg(p + 1);
+// ---------------------------------------------------------------- splitting
+// Rows r < Rp of op(X), K values each (k-contiguous source: element (r, k) at
+// X[row(r) * ld + k], row(r) = rmap ? rmap[r] : r).  Output slice s of row r
+// at out[s * Rp * Kp + r * Kp + k]; zeros for r >= R or k >= K.
+template <int S>
+__global__ void tcx_split_kc(const float* __restrict__ X, int64_t ld, int64_t R, int64_t K,
+                             int64_t Rp, int64_t Kp, const int64_t* __restrict__ rmap, bool vec,
+                             __nv_bfloat16* __restrict__ out) {
+  const int64_t chunks = Kp / 8, items = Rp * chunks;
+  const size_t sstride = (size_t)Rp * Kp;
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < items;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = it / chunks, k0 = (it % chunks) * 8;
+    float x[8];
+    if (r < R && k0 < K) {
+      const float* src = X + (rmap ? rmap[r] : r) * ld + k0;
+      if (vec && k0 + 8 <= K) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(src));
+        const float4 b = __ldg(reinterpret_cast<const float4*>(src) + 1);
         x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
         x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
       } else {
 #pragma unroll
-        for (int e = 0; e < 8; ++e)
-          x[e] = (gr < nrows_total && gk + e < K) ? __ldg(base + sr * ld + gk + e) : 0.0f;
+        for (int e = 0; e < 8; ++e) x[e] = (k0 + e < K) ? __ldg(src + e) : 0.0f;
       }
-      split_store<S>(x, tile0, slice_bytes, r, c);
-    }
-  } else {
-    for (int item = tid; item < rows * 8; item += TNT) {
-      const int r = item % rows, c = item / rows;
-      const int64_t gr = row0 + r, gk = k0 + 8 * c;
-      float x[8];
+    } else {
 #pragma unroll
-      for (int e = 0; e < 8; ++e)
-        x[e] = (gr < nrows_total && gk + e < K) ? __ldg(base + gr + (gk + e) * ld) : 0.0f;
-      split_store<S>(x, tile0, slice_bytes, r, c);
+      for (int e = 0; e < 8; ++e) x[e] = 0.0f;
     }
+    split8_store<S>(x, out + r * Kp + k0, sstride);
   }
 }
 
-template <int S, int BN, char TA, char TB>
-__global__ void __launch_bounds__(TNT, 1) tc_gemm_kernel(TcGemmArgs g) {
+// Same output from a row-contiguous source: element (r, k) at X[r + k * ld].
+// A 32-row x 64-k tile is transposed through shared memory (256 threads).
+template <int S>
+__global__ void tcx_split_rc(const float* __restrict__ X, int64_t ld, int64_t R, int64_t K,
+                             int64_t Rp, int64_t Kp, __nv_bfloat16* __restrict__ out) {
+  __shared__ float tile[64][33];
+  const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
+  const int64_t r0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 64;
+#pragma unroll
+  for (int kk = 0; kk < 64; kk += 8) {
+    const int64_t r = r0 + tx, k = k0 + kk + ty;
+    tile[kk + ty][tx] = (r < R && k < K) ? __ldg(X + r + k * ld) : 0.0f;
+  }
+  __syncthreads();
+  const int row = t >> 3, c = t & 7;
+  const int64_t r = r0 + row;
+  if (r >= Rp) return;
+  float x[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) x[e] = tile[8 * c + e][row];
+  split8_store<S>(x, out + r * Kp + k0 + 8 * c, (size_t)Rp * Kp);
+}
+
+// ---------------------------------------------------------------- GEMM
+struct TcxArgs {
+  int64_t M, N;       // rows of the A-role and B-role operands (C is M x N)
+  int KT;             // 64-k stages
+  int kt_per_split;   // stages per split-K unit
+  int tiles_m, tiles_n, units;
+  float alpha, beta;
+  float* C;
+  int64_t ldc;
+  float* part;        // splits > 1: hi at part[2z MN + r + c M], lo at part[(2z+1) MN + ...]
+  int* status;
+};
+
+template <int S>
+__global__ void __launch_bounds__(XNT, 1)
+    tcx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    TcxArgs g) {
+  constexpr int NACC = (S == 3) ? 2 : 1;
+  constexpr uint32_t TCOLS = (S == 3) ? 256u : 128u;
+  constexpr uint32_t STAGE_A = (uint32_t)S * XTILE_A;
+  constexpr uint32_t STAGE_TX = (uint32_t)S * (XTILE_A + XTILE_B);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1024-byte aligned stage buffers
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  constexpr size_t A_SLICE = (size_t)TBM * 128;
-  constexpr size_t B_SLICE = (size_t)BN * 128;
-  constexpr size_t STAGE = S * (A_SLICE + B_SLICE);
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t full[XNST], empty[XNST], tfull[2], tempty[2], done;
   __shared__ uint32_t s_tmem;
-  __shared__ int s_fail;
+  __shared__ volatile int s_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t i0 = (int64_t)blockIdx.x * TBM;
-  const int64_t j0 = (int64_t)blockIdx.y * BN;
-  // split-K: this CTA covers k-slices [kt_beg, kt_end)
-  const int KT_all = (int)((g.K + TBK - 1) / TBK);
-  const int kt_beg = (int)blockIdx.z * g.kt_per_split;
-  const int kt_end = min(KT_all, kt_beg + g.kt_per_split);
-  const int KT = max(0, kt_end - kt_beg);
-
   if (tid == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    for (int i = 0; i < XNST; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 4);
+    }
+    mbar_init(&done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&s_tmem)),
-                 "r"((uint32_t)BN)
+                 "r"(TCOLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -229,175 +306,373 @@ __global__ void __launch_bounds__(TNT, 1) tc_gemm_kernel(TcGemmArgs g) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
-  constexpr uint32_t IDESC = idesc_bf16(TBM, BN);
 
-  int issued = 0;  // k-slices whose MMAs were committed (same count in every thread)
-  for (int kt = 0; kt < KT; ++kt) {
-    const int st = kt & 1;
-    unsigned char* a_tile = smem + (size_t)st * STAGE;
-    unsigned char* b_tile = a_tile + S * A_SLICE;
-    if (kt >= 2) {
-      // the MMAs of k-slice kt-2 (commit number (kt-2)/2 on this stage) read this buffer
-      if (tid == 0 && !mbar_wait(&mbar[st], (uint32_t)(((kt - 2) >> 1) & 1))) s_fail = 1;
-      __syncthreads();
-      if (s_fail) break;
-    }
-    const int64_t k0 = (int64_t)(kt_beg + kt) * TBK;
-    // op(A)(i, k): 'N' -> A[i + k lda] (contiguous along rows), 'T' -> A[k + i lda]
-    load_tile<S, TA == 'T'>(g.A, g.lda, i0, g.M, k0, g.K, TBM, g.vecA, a_tile, A_SLICE, nullptr);
-    // op(B)(k, j): 'N' -> B[k + j ldb] (contiguous along k), 'T' -> B[j + k ldb]
-    load_tile<S, TB == 'N'>(g.B, g.ldb, j0, g.N, k0, g.K, BN, g.vecB, b_tile, B_SLICE,
-                            TB == 'N' ? g.bcols : nullptr);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t a0 = smem_u32(a_tile), b0 = smem_u32(b_tile);
-      // slice products with s + t <= S + 1, smallest terms first
-      uint32_t acc = kt > 0 ? 1u : 0u;
-#pragma unroll
-      for (int d = S + 1; d >= 2; --d) {
-#pragma unroll
-        for (int s = 1; s <= S; ++s) {
-          const int t = d - s;
-          if (t < 1 || t > S) continue;
-#pragma unroll
-          for (int kk = 0; kk < TBK / 16; ++kk) {
-            const uint64_t ad = sw128_desc(a0 + (uint32_t)((s - 1) * A_SLICE) + kk * 32);
-            const uint64_t bd = sw128_desc(b0 + (uint32_t)((t - 1) * B_SLICE) + kk * 32);
-            mma_bf16(tmem, ad, bd, IDESC, acc);
-            acc = 1u;
-          }
+  auto stage_a = [&](int st) { return smem + (size_t)st * STAGE_TX; };
+  auto stage_b = [&](int st) { return smem + (size_t)st * STAGE_TX + STAGE_A; };
+
+  if (warp == 0) {
+    // ------------------------------------------------ TMA + MMA issue
+    // One thread walks the stages of its units in order.  It keeps XNST - 1
+    // copies ahead: after issuing the MMAs of stage i it refills the ring slot
+    // of stage i - 1 (once those MMAs have completed) with stage i + XNST - 1.
+    if (lane == 0) {
+      int lu = 0, lkt = 0, lke = 0, ltm = 0, ltn = 0;  // cursor of the next copy
+      auto cursor_unit = [&](int u) {
+        lu = u;
+        if (lu < g.units) {
+          ltm = lu % g.tiles_m;
+          const int rest = lu / g.tiles_m;
+          ltn = rest % g.tiles_n;
+          lkt = (rest / g.tiles_n) * g.kt_per_split;
+          lke = min(g.KT, lkt + g.kt_per_split);
         }
-      }
-      mma_commit(&mbar[st]);
-    }
-    ++issued;
-  }
-  // wait for the last commit (it tracks every earlier MMA of this thread);
-  // after a failed wait this is the bounded wait for the MMAs still in flight
-  if (issued > 0 && tid == 0) {
-    const int last = issued - 1;
-    if (!mbar_wait(&mbar[last & 1], (uint32_t)((last >> 1) & 1))) s_fail = 1;
-  }
-  __syncthreads();
-  tc_fence_after();
-  if (s_fail) {
-    if (tid == 0) atomicOr(g.status, RQRCP_INFO_TIMEOUT);
-  } else {
-    // epilogue: warp w owns accumulator lanes (rows) 32w..32w+31
-    const int64_t i = i0 + 32 * warp + lane;
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      float v[32];
-      if (issued > 0) {
-        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
-      } else {
-#pragma unroll
-        for (int e = 0; e < 32; ++e) v[e] = 0.0f;
-      }
-      if (i < g.M) {
-        if (g.partial != nullptr) {
-          float* pp = g.partial + (int64_t)blockIdx.z * g.M * g.N;
-#pragma unroll
-          for (int e = 0; e < 32; ++e) {
-            const int64_t j = j0 + c0 + e;
-            if (j < g.N) pp[i + j * g.M] = v[e];
+      };
+      cursor_unit(blockIdx.x);
+      int lst = 0;
+      uint32_t luse[XNST] = {};
+      auto issue_load = [&]() -> bool {
+        if (lu >= g.units) return true;
+        if (!mbar_wait(&empty[lst], (luse[lst] & 1u) ^ 1u)) return false;
+        mbar_expect_tx(&full[lst], STAGE_TX);
+        tma_load_3d(stage_a(lst), &tmA, lkt * XBK, ltm * XBM, 0, &full[lst]);
+        tma_load_3d(stage_b(lst), &tmB, lkt * XBK, ltn * XBN, 0, &full[lst]);
+        ++luse[lst];
+        lst = (lst + 1 == XNST) ? 0 : lst + 1;
+        if (++lkt >= lke) cursor_unit(lu + gridDim.x);
+        return true;
+      };
+      bool ok = true;
+      for (int i = 0; i < XNST - 1 && ok; ++i) ok = issue_load();
+      int st = 0, buf = 0;
+      uint32_t fuse[XNST] = {}, tuse[2] = {0u, 0u};
+      bool any = false;
+      for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
+        const int z = u / (g.tiles_m * g.tiles_n);
+        const int kb = z * g.kt_per_split, ke = min(g.KT, kb + g.kt_per_split);
+        const int nks = (ke - kb) * (XBK / 16);
+        for (int q = 0; q < nks; ++q) {
+          const int sq = q & 3;
+          if (sq == 0) {
+            if (!mbar_wait(&full[st], fuse[st] & 1u) || s_fail) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
           }
-        } else {
-#pragma unroll
-          for (int e = 0; e < 32; ++e) {
-            const int64_t j = j0 + c0 + e;
-            if (j < g.N) {
-              float* cp = g.C + i + j * g.ldc;
-              float out = g.alpha * v[e];
-              if (g.beta != 0.0f) out = fmaf(g.beta, *cp, out);
-              *cp = out;
+          const bool cstart = (S == 3) ? (q % XCH == 0) : (q == 0);
+          const bool cend = (S == 3) ? (q % XCH == XCH - 1) : (q == nks - 1);
+          if (cstart) {
+            if (!mbar_wait(&tempty[buf], (tuse[buf] & 1u) ^ 1u) || s_fail) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+          }
+          const uint32_t acc = cstart ? 0u : 1u;
+          const uint32_t a0 = smem_u32(stage_a(st)) + (uint32_t)sq * 32u;
+          const uint32_t b0 = smem_u32(stage_b(st)) + (uint32_t)sq * 32u;
+          const uint32_t d_big = tmem + (uint32_t)(buf * NACC * XBN);
+          mma_bf16(d_big, sw128_desc(a0), sw128_desc(b0), acc);  // x1 y1
+          if (S == 3) {
+            const uint32_t d_small = d_big + XBN;
+            // correction products (s, t) with 2 < s + t <= 4
+            mma_bf16(d_small, sw128_desc(a0 + 2 * XTILE_A), sw128_desc(b0), acc);        // x3 y1
+            mma_bf16(d_small, sw128_desc(a0 + XTILE_A), sw128_desc(b0 + XTILE_B), 1u);   // x2 y2
+            mma_bf16(d_small, sw128_desc(a0), sw128_desc(b0 + 2 * XTILE_B), 1u);         // x1 y3
+            mma_bf16(d_small, sw128_desc(a0 + XTILE_A), sw128_desc(b0), 1u);             // x2 y1
+            mma_bf16(d_small, sw128_desc(a0), sw128_desc(b0 + XTILE_B), 1u);             // x1 y2
+          }
+          any = true;
+          if (cend) {
+            mma_commit(&tfull[buf]);
+            ++tuse[buf];
+            buf ^= 1;
+          }
+          if (sq == 3) {
+            mma_commit(&empty[st]);
+            ++fuse[st];
+            st = (st + 1 == XNST) ? 0 : st + 1;
+            if (!issue_load()) {
+              ok = false;
+              break;
             }
           }
         }
       }
+      if (!ok) {
+        s_fail = 1;
+        // wait (bounded) for the last copy issued on each slot
+        for (int i = 0; i < XNST; ++i)
+          if (luse[i] > 0) mbar_wait(&full[i], (luse[i] - 1u) & 1u);
+      }
+      if (any) {
+        // every MMA of this thread has completed once this commit arrives
+        mma_commit(&done);
+        mbar_wait(&done, 0u);
+      }
     }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------ drain and epilogue
+    const int quad = warp & 3;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * quad) << 16);
+    const int64_t MN = g.M * g.N;
+    int buf = 0;
+    uint32_t tuse[2] = {0u, 0u};
+    bool ok = true;
+    for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
+      const int tm = u % g.tiles_m, rest = u / g.tiles_m;
+      const int tn = rest % g.tiles_n, z = rest / g.tiles_n;
+      const int kb = z * g.kt_per_split, ke = min(g.KT, kb + g.kt_per_split);
+      const int nch = (S == 3) ? (ke - kb) * (XBK / 16) / XCH : (ke > kb ? 1 : 0);
+      // compensated sums: value = hi - cc
+      float hi[XBN], cc[XBN];
+#pragma unroll
+      for (int c = 0; c < XBN; ++c) hi[c] = cc[c] = 0.0f;
+      for (int ch = 0; ch < nch; ++ch) {
+        if (!mbar_wait(&tfull[buf], tuse[buf] & 1u) || s_fail) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tb = lane_base + (uint32_t)(buf * NACC * XBN);
+        if (S == 3) {
+#pragma unroll
+          for (int c0 = 0; c0 < XBN; c0 += 8) {
+            float v[8], w[8];
+            tmem_ld8x2(tb + c0, tb + XBN + c0, v, w);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              // Kahan step with the chunk's leading and correction parts
+              const float y = (v[e] - cc[c0 + e]) + w[e];
+              const float t = hi[c0 + e] + y;
+              cc[c0 + e] = (t - hi[c0 + e]) - y;
+              hi[c0 + e] = t;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int c0 = 0; c0 < XBN; c0 += 16) {
+            float v[16];
+            tmem_ld16(tb + c0, v);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) hi[c0 + e] = v[e];
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
+        ++tuse[buf];
+        buf ^= 1;
+      }
+      if (!ok) break;
+      const int64_t r = (int64_t)tm * XBM + 32 * quad + lane;
+      const int64_t c0 = (int64_t)tn * XBN;
+      const int nval = (int)imin64(XBN, g.N - c0);
+      if (r < g.M) {
+        if (g.part != nullptr) {
+          float* ph = g.part + (int64_t)(2 * z) * MN + r + c0 * g.M;
+#pragma unroll
+          for (int c = 0; c < XBN; ++c) {
+            if (c < nval) {
+              ph[0] = hi[c];
+              ph[MN] = -cc[c];
+            }
+            ph += g.M;
+          }
+        } else {
+          float* cp = g.C + r + c0 * g.ldc;
+          const float alpha = g.alpha, beta = g.beta;
+#pragma unroll
+          for (int c = 0; c < XBN; ++c) {
+            if (c < nval) {
+              const float out = beta != 0.0f ? fmaf(alpha, hi[c], beta * *cp) : alpha * hi[c];
+              *cp = fmaf(-alpha, cc[c], out);
+            }
+            cp += g.ldc;
+          }
+        }
+      }
+    }
+    if (!ok) s_fail = 1;
   }
+
+  if (tid == 0 && s_fail) atomicOr(g.status, RQRCP_INFO_TIMEOUT);
   tc_fence_before();
   __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"((uint32_t)BN)
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS)
                  : "memory");
-}
-
-// C = alpha * sum_z partial[z] + beta C, in a fixed order
-__global__ void tc_splitk_reduce(TcGemmArgs g, int splits) {
-  const int64_t total = g.M * g.N;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    float s = 0.0f;
-    for (int z = 0; z < splits; ++z) s += g.partial[(int64_t)z * total + e];
-    const int64_t i = e % g.M, j = e / g.M;
-    float* cp = g.C + i + j * g.ldc;
-    float out = g.alpha * s;
-    if (g.beta != 0.0f) out = fmaf(g.beta, *cp, out);
-    *cp = out;
   }
 }
 
-template <int S, int BN>
-size_t tc_smem() {
-  return 2 * (size_t)S * ((size_t)TBM * 128 + (size_t)BN * 128) + 1024;
+// C = alpha * sum_z (hi_z + lo_z) + beta C, the sum in FP64 in a fixed order;
+// splits = 0 gives C = beta C.
+__global__ void tcx_reduce(const float* __restrict__ part, int splits, int64_t M, int64_t N,
+                           float alpha, float beta, float* __restrict__ C, int64_t ldc) {
+  const int64_t MN = M * N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < MN;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int z = 0; z < splits; ++z)
+      s += (double)part[(int64_t)(2 * z) * MN + e] + (double)part[(int64_t)(2 * z + 1) * MN + e];
+    const int64_t i = e % M, j = e / M;
+    float* cp = C + i + j * ldc;
+    const float v = alpha * (float)s;
+    *cp = beta != 0.0f ? fmaf(beta, *cp, v) : v;
+  }
 }
 
-template <int S, int BN, char TA, char TB>
-cudaError_t launch_variant(const TcGemmArgs& g, cudaStream_t st) {
-  auto kern = tc_gemm_kernel<S, BN, TA, TB>;
-  const size_t smem = tc_smem<S, BN>();
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const int KT_all = (int)((g.K + TBK - 1) / TBK);
-  const int splits = KT_all > 0 ? (KT_all + g.kt_per_split - 1) / g.kt_per_split : 1;
-  dim3 grid((unsigned)((g.M + TBM - 1) / TBM), (unsigned)((g.N + BN - 1) / BN), (unsigned)splits);
-  kern<<<grid, TNT, smem, st>>>(g);
-  e = cudaGetLastError();
-  if (e != cudaSuccess || g.partial == nullptr) return e;
-  const int64_t total = g.M * g.N;
-  int64_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  tc_splitk_reduce<<<(unsigned)blocks, 256, 0, st>>>(g, splits);
+// ---------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+int64_t rpad(int64_t R, int tile) { return (R + tile - 1) / tile * tile; }
+int64_t kpad(int64_t K) { return (K + XBK - 1) / XBK * XBK; }
+
+// 3-D map over S slices of Rp rows x Kp k: box = 64 k x `rows` rows x S slices.
+cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t Rp, int64_t Kp, int S,
+                     int rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (fn == nullptr) return cudaErrorNotSupported;
+  const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)Rp, (cuuint64_t)S};
+  const cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Rp * Kp * 2};
+  const cuuint32_t box[3] = {(cuuint32_t)XBK, (cuuint32_t)rows, (cuuint32_t)S};
+  const cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(base), dims,
+                  strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int S>
+cudaError_t split_operand(const float* X, int64_t ld, bool kc, int64_t R, int64_t K, int64_t Rp,
+                          int64_t Kp, const int64_t* rmap, __nv_bfloat16* out, int num_sms,
+                          cudaStream_t st) {
+  if (kc) {
+    const bool vec = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    const int64_t items = Rp * (Kp / 8);
+    int64_t blocks = (items + 255) / 256;
+    if (blocks > (int64_t)num_sms * 16) blocks = (int64_t)num_sms * 16;
+    tcx_split_kc<S><<<(unsigned)blocks, 256, 0, st>>>(X, ld, R, K, Rp, Kp, rmap, vec, out);
+  } else {
+    dim3 grid((unsigned)(Rp / 32), (unsigned)(Kp / 64));
+    tcx_split_rc<S><<<grid, 256, 0, st>>>(X, ld, R, K, Rp, Kp, out);
+  }
   return cudaGetLastError();
 }
 
-template <int S, int BN>
-cudaError_t dispatch_trans(const TcGemmArgs& g, cudaStream_t st) {
-  if (g.transA == 'N' && g.transB == 'N') return launch_variant<S, BN, 'N', 'N'>(g, st);
-  if (g.transA == 'N') return launch_variant<S, BN, 'N', 'T'>(g, st);
-  if (g.transB == 'N') return launch_variant<S, BN, 'T', 'N'>(g, st);
-  return launch_variant<S, BN, 'T', 'T'>(g, st);
+template <int S>
+size_t gemm_smem() {
+  return (size_t)XNST * S * (XTILE_A + XTILE_B) + 1024;
+}
+
+template <int S>
+cudaError_t run(TcGemmArgs g, cudaStream_t st) {
+  const int64_t Rm = rpad(g.M, XBM), Rn = rpad(g.N, XBN), Kp = kpad(g.K);
+  const int KT = (int)(Kp / XBK);
+  const int nsm = g.num_sms > 0 ? g.num_sms : 1;
+  if (KT == 0) {
+    // C = beta C
+    int64_t blocks = (g.M * g.N + 255) / 256;
+    if (blocks > (int64_t)nsm * 16) blocks = (int64_t)nsm * 16;
+    tcx_reduce<<<(unsigned)blocks, 256, 0, st>>>(nullptr, 0, g.M, g.N, g.alpha, g.beta, g.C, g.ldc);
+    return cudaGetLastError();
+  }
+  if ((size_t)S * Rm * Kp > g.slcapA || (size_t)S * Rn * Kp > g.slcapB || g.slA == nullptr ||
+      g.slB == nullptr)
+    return cudaErrorInvalidValue;
+  // rows of op(A): stored columns when transposed (k-contiguous); columns of
+  // op(B): stored columns when not transposed (k-contiguous)
+  cudaError_t e = split_operand<S>(g.A, g.lda, g.transA == 'T', g.M, g.K, Rm, Kp, nullptr, g.slA,
+                                   nsm, st);
+  if (e != cudaSuccess) return e;
+  e = split_operand<S>(g.B, g.ldb, g.transB == 'N', g.N, g.K, Rn, Kp,
+                       g.transB == 'N' ? g.bcols : nullptr, g.slB, nsm, st);
+  if (e != cudaSuccess) return e;
+  CUtensorMap ma, mb;
+  if ((e = make_map(&ma, g.slA, Rm, Kp, S, XBM)) != cudaSuccess) return e;
+  if ((e = make_map(&mb, g.slB, Rn, Kp, S, XBN)) != cudaSuccess) return e;
+
+  TcxArgs x{};
+  x.M = g.M;
+  x.N = g.N;
+  x.KT = KT;
+  x.tiles_m = (int)(Rm / XBM);
+  x.tiles_n = (int)(Rn / XBN);
+  const int64_t tiles = (int64_t)x.tiles_m * x.tiles_n;
+  int splits = 1;
+  if (g.partial != nullptr && tiles < nsm && KT > 1) {
+    splits = (int)std::min<int64_t>((nsm + tiles - 1) / tiles, KT);
+    while (splits > 1 && (size_t)2 * splits * g.M * g.N > g.partial_cap) --splits;
+  }
+  x.kt_per_split = (KT + splits - 1) / splits;
+  splits = (KT + x.kt_per_split - 1) / x.kt_per_split;
+  x.units = (int)(tiles * splits);
+  x.alpha = g.alpha;
+  x.beta = g.beta;
+  x.C = g.C;
+  x.ldc = g.ldc;
+  x.part = splits > 1 ? g.partial : nullptr;
+  x.status = g.status;
+
+  auto kern = tcx_gemm_kernel<S>;
+  const size_t smem = gemm_smem<S>();
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = (int)std::min<int64_t>(x.units, nsm);
+  kern<<<grid, XNT, smem, st>>>(ma, mb, x);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || splits == 1) return e;
+  int64_t blocks = (g.M * g.N + 255) / 256;
+  if (blocks > (int64_t)nsm * 16) blocks = (int64_t)nsm * 16;
+  tcx_reduce<<<(unsigned)blocks, 256, 0, st>>>(g.partial, splits, g.M, g.N, g.alpha, g.beta, g.C,
+                                               g.ldc);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
-int tc_pick_splits(int64_t M, int64_t N, int64_t K, int num_sms, size_t cap_floats) {
-  const int64_t tiles = ((M + TBM - 1) / TBM) * ((N + 127) / 128);
-  const int64_t kts = (K + TBK - 1) / TBK;
-  int64_t s = 1;
-  while (tiles * s < num_sms && s * 2 <= kts / 2 && (size_t)(s * 2) * M * N <= cap_floats) s *= 2;
-  return (int)s;
+size_t tc_slice_elems(int64_t rows, int64_t K, int slices) {
+  return (size_t)slices * rpad(rows, XBM) * kpad(K);
+}
+
+int tc_launches(int64_t M, int64_t N, int64_t K, int num_sms, size_t partial_cap) {
+  if (M <= 0 || N <= 0) return 0;
+  if (K <= 0) return 1;
+  const int64_t tiles = (rpad(M, XBM) / XBM) * (rpad(N, XBN) / XBN);
+  const int KT = (int)(kpad(K) / XBK);
+  int splits = 1;
+  if (partial_cap > 0 && tiles < num_sms && KT > 1) {
+    splits = (int)std::min<int64_t>((num_sms + tiles - 1) / tiles, KT);
+    while (splits > 1 && (size_t)2 * splits * M * N > partial_cap) --splits;
+  }
+  const int per = (KT + splits - 1) / splits;
+  splits = (KT + per - 1) / per;
+  return splits > 1 ? 4 : 3;
 }
 
 cudaError_t launch_tc_gemm(TcGemmArgs g, int slices, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
-  // splits > 1 needs the partial buffer; kt_per_split is derived here
-  const int KT_all = (int)((g.K + TBK - 1) / TBK);
-  if (g.splits <= 1 || g.partial == nullptr || KT_all <= 1) {
-    g.splits = 1;
-    g.partial = nullptr;
-    g.kt_per_split = KT_all > 0 ? KT_all : 1;
-  } else {
-    g.kt_per_split = (KT_all + g.splits - 1) / g.splits;
-  }
-  g.vecA = (g.transA == 'T') && (g.lda % 4 == 0) && ((reinterpret_cast<uintptr_t>(g.A) & 15) == 0);
-  g.vecB = (g.transB == 'N') && (g.ldb % 4 == 0) && ((reinterpret_cast<uintptr_t>(g.B) & 15) == 0);
-  if (slices == 1) return dispatch_trans<1, 128>(g, st);
-  if (slices == 3) return dispatch_trans<3, 128>(g, st);
+  if (slices == 1) return run<1>(g, st);
+  if (slices == 3) return run<3>(g, st);
   return cudaErrorInvalidValue;
 }
 

@@ -192,7 +192,9 @@ def test_tuxv_matches_oracle(lib, m, n, k, b, p):
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
 @pytest.mark.parametrize("m,n,k", [(128, 128, 64), (300, 200, 150), (64, 700, 1000), (129, 1, 7)])
 def test_tc_gemm_bf16x3(lib, ta, tb, m, n, k):
-    """Split-BF16 x3 tensor-core GEMM against an FP64 product: FP32-level error."""
+    """Split-BF16 x3 tensor-core GEMM against an FP64 product: FP32-level error
+    independent of K (exact three-slice split, the leading product drained
+    every 32 k into compensated register sums)."""
     g = torch.Generator().manual_seed(m + n + k)
     Af = torch.randn((m, k) if ta == "N" else (k, m), generator=g, dtype=torch.float64)
     Bf = torch.randn((k, n) if tb == "N" else (n, k), generator=g, dtype=torch.float64)
@@ -208,8 +210,10 @@ def test_tc_gemm_bf16x3(lib, ta, tb, m, n, k):
     ref = C0.cpu().double() - opA @ opB
     err = (C.cpu().double() - ref).abs().max().item()
     scale = (opA.abs() @ opB.abs()).max().item() + C0.abs().max().item()
-    # FP32 GEMM bound: K accumulations plus the dropped slice products
-    assert err <= max(8, k) * 2.0 ** -24 * scale, err / scale
+    # a few u of sum_k |a||b|: two truncating MMA additions per 32-k chunk,
+    # the dropped slice products (below 2^-25 each), the compensated sum and
+    # the final FP32 rounding
+    assert err <= 8 * 2.0 ** -24 * scale, err / scale
 
 
 @pytest.mark.parametrize("m,n,k", [(256, 256, 128), (100, 300, 70)])
@@ -242,11 +246,10 @@ def _mixed_errors(A, A32, jp, t, rdiag):
 def test_rqrcp_mixed_reconstruction(lib, m, n, b, p):
     """Mixed precision (FP32 storage, BF16 sketch, split-BF16 x3 trailing
     update, FP64 panel/T/R-diagonal) is FP32-level: its reconstruction error
-    is within 6x of LAPACK's own FP32 pivoted QR (sgeqp3) on the same matrix
-    (the tensor core's truncating FP32 accumulation costs ~4x over long
-    reductions), Q is orthogonal to FP64 level (tau and T are recomputed
-    from the stored FP32 reflectors), and R is stated against the FP64
-    oracle replayed on the same pivots."""
+    is within 2x of LAPACK's own FP32 pivoted QR (sgeqp3) on the same matrix,
+    Q is orthogonal to FP64 level (tau and T are recomputed from the stored
+    FP32 reflectors), and R is stated against the FP64 oracle replayed on the
+    same pivots."""
     import scipy.linalg as sla
     A = synth.spiked(m, n, rank=min(m, n) // 4, scale=1e3)
     A32 = A.astype(np.float32)
@@ -264,7 +267,7 @@ def test_rqrcp_mixed_reconstruction(lib, m, n, b, p):
     rel = np.linalg.norm(R[:k] - np.triu(Fo[:k])) / np.linalg.norm(np.triu(Fo[:k]))
     print(f"mixed {m}x{n}: recon {rec:.2e} (sgeqp3 {rec32:.2e}) orth {orth:.2e} "
           f"R vs FP64 oracle {rel:.2e}")
-    assert rec <= 6 * rec32, (rec, rec32)
+    assert rec <= 2 * rec32, (rec, rec32)
     assert orth <= 1e-5, orth
     assert rel <= 1e-5
 
@@ -325,7 +328,9 @@ def test_trqrcp_mixed_lowrank(lib, m, n, k, b, p):
 def test_tc_gemm_accumulation_profile(lib):
     """Error of the split-BF16 x3 tensor-core GEMM against K (per entry, in
     units of u = 2^-24 of sum_k |a||b|) next to cuBLAS FP32 SGEMM; prints the
-    table and pins the short-reduction bound (K = 64 within 8 u)."""
+    table and pins the bound: within 8 u at every K, with a mean signed error
+    below 1 u (the tensor core truncates inside each 32-k chunk, which on
+    all-positive data leaves a bias of under 1 u that does not grow with K)."""
     prev = torch.backends.cuda.matmul.allow_tf32
     torch.backends.cuda.matmul.allow_tf32 = False
     g = torch.Generator().manual_seed(0)
@@ -349,8 +354,8 @@ def test_tc_gemm_accumulation_profile(lib):
                       f"mean {e3.abs().mean().item() / u:7.2f}u signed {e3.mean().item() / u:8.2f}u"
                       f" | sgemm max {ef.abs().max().item() / u:6.2f}u "
                       f"mean {ef.abs().mean().item() / u:5.2f}u")
-                if K == 64:
-                    assert e3.abs().max().item() <= 8 * u
+                assert e3.abs().max().item() <= 8 * u
+                assert abs(e3.mean().item()) <= 1.0 * u
     finally:
         torch.backends.cuda.matmul.allow_tf32 = prev
 
