@@ -16,10 +16,12 @@ namespace rq {
 //   RQRCP_INFO_NONFINITE    -> the sample held NaN or Inf
 // Several conditions OR together.
 
-// Grid barrier state; one per concurrently running cooperative kernel.
+// Grid barrier state; one per concurrently running cooperative kernel.  The
+// launcher zeroes it before every launch.  `count` only grows during a launch:
+// barrier k of a grid of G CTAs is complete once count >= k G.
 struct GridBarrier {
   unsigned int count;
-  unsigned int gen;
+  unsigned int unused;
   unsigned int abort;
   unsigned int pad;
 };
@@ -34,39 +36,37 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
   return v;
 }
 
-__device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ unsigned int atom_add_release_u32(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
 }
 
-// All CTAs of a cooperative launch call this.  Returns false when the wait
-// ran out (or another CTA already gave up): the status word then carries
-// RQRCP_INFO_TIMEOUT and the caller must return without further barriers.
+// All CTAs of a cooperative launch call this.  Thread 0 arrives with one
+// release-ordered atomic add (its return value tells which barrier this is)
+// and polls the counter with acquire loads until the whole grid has arrived.
+// Returns false when the wait ran out (or another CTA already gave up): the
+// status word then carries RQRCP_INFO_TIMEOUT and the caller must return
+// without further barriers.
 __device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned int nblocks, int* status) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    unsigned int g = ld_acquire_u32(&bar->gen);
     __threadfence();
-    unsigned int arrived = atomicAdd(&bar->count, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      st_release_u32(&bar->gen, g + 1);
-    } else {
-      unsigned int polls = 0;
-      while (ld_acquire_u32(&bar->gen) == g) {
-        if (ld_acquire_u32(&bar->abort)) { ok = 0; break; }
-        if (++polls > kBarrierMaxPolls) {
-          atomicExch(&bar->abort, 1u);
-          atomicOr(status, RQRCP_INFO_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        if (polls > 64) __nanosleep(64);
+    const unsigned int old = atom_add_release_u32(&bar->count, 1u);
+    const unsigned int target = (old / nblocks + 1u) * nblocks;
+    unsigned int polls = 0;
+    while ((int)(ld_acquire_u32(&bar->count) - target) < 0) {
+      if (ld_acquire_u32(&bar->abort)) { ok = 0; break; }
+      if (++polls > kBarrierMaxPolls) {
+        atomicExch(&bar->abort, 1u);
+        atomicOr(status, RQRCP_INFO_TIMEOUT);
+        ok = 0;
+        break;
       }
+      if (polls > 256) __nanosleep(32);
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
@@ -99,6 +99,25 @@ __device__ __forceinline__ void house_scalars(double alpha, double xnorm, double
   }
   double h = hypot(alpha, xnorm);
   double bb = (alpha >= 0.0) ? -h : h;
+  *beta = bb;
+  *tau = (bb - alpha) / bb;
+  *scale = 1.0 / (alpha - bb);
+}
+
+// The same scalars from alpha and the squared tail norm sigma2 = ||x_1..||^2:
+// beta = -sign(alpha) sqrt(alpha^2 + sigma2) (one square root instead of a
+// square root and a scaled hypot; sigma2 is itself a sum of squares, so the
+// unscaled form adds no overflow that the caller has not already risked).
+__device__ __forceinline__ void house_scalars_sq(double alpha, double sigma2, double* beta,
+                                                 double* tau, double* scale) {
+  if (sigma2 == 0.0) {
+    *beta = alpha;
+    *tau = 0.0;
+    *scale = 0.0;
+    return;
+  }
+  const double h = sqrt(fma(alpha, alpha, sigma2));
+  const double bb = (alpha >= 0.0) ? -h : h;
   *beta = bb;
   *tau = (bb - alpha) / bb;
   *scale = 1.0 / (alpha - bb);

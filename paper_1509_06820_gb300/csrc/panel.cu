@@ -11,9 +11,14 @@
 //   beta = -sign(alpha) ||x||, tau = (beta - alpha)/beta, v = x/(alpha - beta),
 // and the same w_c = tau v^T a_c = tau (a_jc + (x^T a_c)_tail/(alpha - beta)),
 // update their rows, and compute the partial sums of the next column.
-// Finally the CTAs publish partial Gram matrices Y^T Y of their rows, CTA 0
-// adds them and builds T column by column:
-//   T(i,i) = tau_i,  T(0:i, i) = -tau_i T(0:i,0:i) (Y^T Y)(0:i, i).
+// Finally the CTAs publish partial Gram matrices Y^T Y of their rows and add
+// them in a fixed order.  T is the inverse of U = striu(Y^T Y) + diag(1/tau)
+// (the same T as the column recurrence T(i,i) = tau_i,
+// T(0:i, i) = -tau_i T(0:i,0:i) (Y^T Y)(0:i, i)), so its columns are
+// independent back-substitutions:
+//   x_j = tau_j,  x_r = -tau_r sum_{t=r+1..j} (Y^T Y)(r, t) x_t  (r < j),
+// which also holds with tau_r = 0 (a zero row and column); one warp sweeps
+// each column, the columns spread over the grid.
 #include "kernels.cuh"
 
 namespace rq {
@@ -72,16 +77,16 @@ __global__ void __launch_bounds__(NT, 1) panel_kernel(PanelArgs a) {
       double s = 0.0;
       if (c >= j) {
         // q = pp, pp + PARTS, ... in increasing order; loads issued in batches
-        // of 8 so that their L2 latencies overlap
-        for (int q0 = pp; q0 < G; q0 += 8 * PARTS) {
-          double v[8];
+        // of 20 so that their L2 latencies overlap
+        for (int q0 = pp; q0 < G; q0 += 20 * PARTS) {
+          double v[20];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
+          for (int u = 0; u < 20; ++u) {
             const int q = q0 + u * PARTS;
             v[u] = (q < G) ? __ldcg(part + (size_t)q * bJ + c) : 0.0;
           }
 #pragma unroll
-          for (int u = 0; u < 8; ++u) s += v[u];
+          for (int u = 0; u < 20; ++u) s += v[u];
         }
       }
       s_part[pp][c] = s;
@@ -98,7 +103,7 @@ __global__ void __launch_bounds__(NT, 1) panel_kernel(PanelArgs a) {
     __syncthreads();
     if (tid == 0) {
       double beta, tau, scale;
-      house_scalars(s_w[j], sqrt(s_tot[j]), &beta, &tau, &scale);
+      house_scalars_sq(s_w[j], s_tot[j], &beta, &tau, &scale);
       s_scal[0] = beta;
       s_scal[1] = tau;
       s_scal[2] = scale;
@@ -150,13 +155,15 @@ __global__ void __launch_bounds__(NT, 1) panel_kernel(PanelArgs a) {
   for (int e = tid; e < bJ * bJ; e += NT) {
     const int c1 = e % bJ, c2 = e / bJ;  // entry (c1, c2), c1 <= c2
     if (c1 > c2) continue;
+    // rows R >= c2 only (y2 is zero above its unit diagonal); the diagonal
+    // row of each column reads as 1
+    const int64_t r0 = imax64(0, (int64_t)c2 - r_lo);
     double s = 0.0;
-    for (int64_t r = 0; r < nrow; ++r) {
-      const int64_t R = r_lo + r;
-      if (R < c2) continue;
-      const double y2 = (R == c2) ? 1.0 : Ps[r + c2 * chunk];
-      const double y1 = (R == c1) ? 1.0 : Ps[r + c1 * chunk];
-      s = fma(y1, y2, s);
+    if (r0 < nrow && r_lo + r0 == c2) {
+      s = (c1 == c2) ? 1.0 : Ps[r0 + c1 * chunk];
+      for (int64_t r = r0 + 1; r < nrow; ++r) s = fma(Ps[r + c1 * chunk], Ps[r + c2 * chunk], s);
+    } else {
+      for (int64_t r = r0; r < nrow; ++r) s = fma(Ps[r + c1 * chunk], Ps[r + c2 * chunk], s);
     }
     gram[c1 + c2 * bJ] = s;
   }
@@ -197,38 +204,61 @@ __global__ void __launch_bounds__(NT, 1) panel_kernel(PanelArgs a) {
     }
   }
   if (!grid_barrier(a.bar, G, a.status)) return;
-  if (g != 0) return;
-  // CTA 0: the reduced Gram (upper triangle) into shared memory, then T
-  double* Gs = Ps;  // bJ x bJ
-  {
-    const double* gtot = part_base + (size_t)2 * G * bJ + (size_t)G * bJ * bJ;
-    for (int e = tid; e < bJ * bJ; e += NT) {
-      const int c1 = e % bJ, c2 = e / bJ;
-      Gs[e] = (c1 <= c2) ? __ldcg(gtot + e) : 0.0;
-    }
+  // ---- T by column back-substitution: column j on CTA j % G, warp j / G
+  const int warps_needed = (bJ + G - 1) / G;  // columns per CTA, rounded up
+  if (g >= bJ) return;
+  const double* gtot = part_base + (size_t)2 * G * bJ + (size_t)G * bJ * bJ;
+  // this CTA's largest column decides how much of the Gram it needs
+  int jmax = -1;
+  for (int j = g; j < bJ; j += G) jmax = j;
+  double* Gs = Ps;            // (jmax + 1) x (jmax + 1) upper part, ld bJ
+  double* taus = Ps + (size_t)bJ * bJ;  // bJ adjusted tau values
+  for (int e = tid; e < (jmax + 1) * bJ; e += NT) {
+    const int r = e % bJ, c = e / bJ;
+    if (r <= c) Gs[e] = __ldcg(gtot + e);
+  }
+  // every tau (CTA 0 writes the adjusted ones back in the mixed mode)
+  for (int r = tid; r < bJ; r += NT) {
+    double t = __ldcg(a.tau + r);
+    // mixed precision: tau_r = 2 / v_r^T v_r for the stored (rounded) v_r;
+    // zero stays zero
+    if (a.round_f32 && t != 0.0) t = 2.0 / __ldcg(gtot + r + (size_t)r * bJ);
+    taus[r] = t;
   }
   __syncthreads();
-  double* T = a.T;
-  for (int e = tid; e < bJ * bJ; e += NT) T[e] = 0.0;
-  __syncthreads();
-  if (a.round_f32) {
-    // tau_i = 2 / v_i^T v_i for the stored (rounded) v_i; zero stays zero
-    for (int i = tid; i < bJ; i += NT)
-      if (__ldcg(a.tau + i) != 0.0) a.tau[i] = 2.0 / Gs[i + i * bJ];
-    __syncthreads();
-  }
-  for (int i = 0; i < bJ; ++i) {
-    const double ti = __ldcg(a.tau + i);
-    // T(0:i, i) = -tau_i T(0:i, 0:i) G(0:i, i)
-    if (tid < i) {
-      double s = 0.0;
-      for (int t = tid; t < i; ++t) s = fma(T[tid + t * bJ], Gs[t + i * bJ], s);
-      s_w[tid] = -ti * s;
+  for (int wq = warp; wq < warps_needed; wq += nwarps) {
+    const int j = g + wq * G;
+    if (j < bJ) {
+      constexpr int RPL = MAXB / 32;  // rows per lane
+      double acc[RPL];
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) acc[q] = 0.0;
+      double xt = taus[j];
+      double* Tj = a.T + (size_t)j * bJ;
+      for (int r = j + 1 + lane; r < bJ; r += 32) Tj[r] = 0.0;
+      if (lane == 0) Tj[j] = xt;
+      for (int t = j; t >= 1; --t) {
+        // acc(r) += G(r, t) x_t for r < t, then x_{t-1} = -tau_{t-1} acc(t-1)
+        const double* gt = Gs + (size_t)t * bJ;
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+          const int r = lane + 32 * q;
+          if (r < t) acc[q] = fma(gt[r], xt, acc[q]);
+        }
+        const int rn = t - 1, owner = rn & 31, qn = rn >> 5;
+        double mine = 0.0;
+#pragma unroll
+        for (int q = 0; q < RPL; ++q)
+          if (q == qn) mine = acc[q];
+        const double val = -taus[rn] * mine;
+        xt = __shfl_sync(0xffffffffu, val, owner);
+        if (lane == owner) Tj[rn] = xt;
+      }
     }
+  }
+  if (a.round_f32 && g == 0) {
     __syncthreads();
-    if (tid < i) T[tid + i * bJ] = s_w[tid];
-    if (tid == 0) T[i + i * bJ] = ti;
-    __syncthreads();
+    for (int r = tid; r < bJ; r += NT) a.tau[r] = taus[r];
   }
 }
 
@@ -247,7 +277,7 @@ size_t panel_partial_doubles(int grid, int bJ) {
 
 static size_t panel_smem(int64_t chunk, int bJ) {
   size_t a = (size_t)chunk * bJ * 8;
-  size_t b = (size_t)bJ * bJ * 8;
+  size_t b = ((size_t)bJ * bJ + bJ) * 8;
   return a > b ? a : b;
 }
 

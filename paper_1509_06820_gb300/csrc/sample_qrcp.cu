@@ -42,8 +42,8 @@ __device__ __forceinline__ bool better(const Cand& a, const Cand& b) {
   return a.key > b.key || (a.key == b.key && a.pos < b.pos);
 }
 
-__device__ Cand block_argmax(Cand c, Cand* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Best candidate over the 32 lanes of a warp (all lanes get it).
+__device__ __forceinline__ Cand warp_argmax(Cand c) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     Cand d;
@@ -52,24 +52,7 @@ __device__ Cand block_argmax(Cand c, Cand* red) {
     d.who = __shfl_xor_sync(0xffffffffu, c.who, o);
     if (better(d, c)) c = d;
   }
-  if (lane == 0) red[warp] = c;
-  __syncthreads();
-  if (warp == 0) {
-    c = (lane < NT / 32) ? red[lane] : Cand{-3.0, LLONG_MAX, -1};
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      Cand d;
-      d.key = __shfl_xor_sync(0xffffffffu, c.key, o);
-      d.pos = __shfl_xor_sync(0xffffffffu, c.pos, o);
-      d.who = __shfl_xor_sync(0xffffffffu, c.who, o);
-      if (better(d, c)) c = d;
-    }
-    if (lane == 0) red[0] = c;
-  }
-  __syncthreads();
-  Cand r = red[0];
-  __syncthreads();
-  return r;
+  return c;
 }
 
 __global__ void __launch_bounds__(NT, 1) sample_qrcp_kernel(SampleQrcpArgs a) {
@@ -86,7 +69,7 @@ __global__ void __launch_bounds__(NT, 1) sample_qrcp_kernel(SampleQrcpArgs a) {
   long long* lpos = reinterpret_cast<long long*>(vn0 + chunk);  // chunk
   double* xv = reinterpret_cast<double*>(lpos + chunk);         // MAX_ELL (reflector v)
   int* done = reinterpret_cast<int*>(xv + MAX_ELL);             // chunk
-  __shared__ Cand red[NT / 32];
+  __shared__ Cand red[2];
   __shared__ double s_scal[4];
 
   const int tid = threadIdx.x;
@@ -120,49 +103,58 @@ __global__ void __launch_bounds__(NT, 1) sample_qrcp_kernel(SampleQrcpArgs a) {
   __syncthreads();
 
   for (int i = 0; i < a.steps; ++i) {
-    // ---- local candidate
-    Cand mine{-2.0, LLONG_MAX, -1};
-    for (int c = tid; c < ncol; c += NT) {
-      if (done[c]) continue;
-      Cand t{isnan(vn[c]) ? -1.0 : vn[c], lpos[c], c};
-      if (better(t, mine)) mine = t;
-    }
-    Cand best = block_argmax(mine, red);
-    const int my_pivot = best.who;  // local column index of this CTA's candidate
+    // ---- local candidate: warp 0 scans the owned columns
     double* cand = a.cand + (size_t)(i & 1) * G * 2;
     double* ccol = a.candcol + (size_t)(i & 1) * G * ell;
-    if (tid == 0) {
-      cand[2 * g] = best.key;
-      cand[2 * g + 1] = (double)best.pos;  // positions < 2^53: exact
+    if (tid < 32) {
+      Cand mine{-2.0, LLONG_MAX, -1};
+      for (int c = tid; c < ncol; c += 32) {
+        if (done[c]) continue;
+        Cand t{isnan(vn[c]) ? -1.0 : vn[c], lpos[c], c};
+        if (better(t, mine)) mine = t;
+      }
+      mine = warp_argmax(mine);
+      if (tid == 0) {
+        red[0] = mine;
+        cand[2 * g] = mine.key;
+        cand[2 * g + 1] = (double)mine.pos;  // positions < 2^53: exact
+      }
     }
+    __syncthreads();
+    const int my_pivot = red[0].who;  // local column index of this CTA's candidate
     if (my_pivot >= 0)
       for (int r = tid; r < ell; r += NT) ccol[(size_t)g * ell + r] = col[r + my_pivot * ell];
     if (!grid_barrier(a.bar, G, a.status)) return;
 
-    // ---- global winner (identical in every CTA)
-    Cand w{-3.0, LLONG_MAX, -1};
-    for (int q = tid; q < G; q += NT) {
-      Cand t{__ldcg(cand + 2 * q), (long long)__ldcg(cand + 2 * q + 1), q};
-      if (better(t, w)) w = t;
-    }
-    w = block_argmax(w, red);
-    const long long Lstar = w.pos;
-    // reflector from the winner's rows i..ell-1 (warp 0, fixed order)
-    for (int r = tid; r < ell; r += NT) xv[r] = (r >= i) ? __ldcg(ccol + (size_t)w.who * ell + r) : 0.0;
-    __syncthreads();
+    // ---- global winner (identical in every CTA): warp 0 scans the G
+    // candidates, then builds the reflector from the winner's rows i..ell-1
     if (tid < 32) {
+      Cand w{-3.0, LLONG_MAX, -1};
+      for (int q = tid; q < G; q += 32) {
+        Cand t{__ldcg(cand + 2 * q), (long long)__ldcg(cand + 2 * q + 1), q};
+        if (better(t, w)) w = t;
+      }
+      w = warp_argmax(w);
+      const double* wc = ccol + (size_t)w.who * ell;
       double s = 0.0;
-      for (int r = i + 1 + tid; r < ell; r += 32) s = fma(xv[r], xv[r], s);
+      for (int r = i + tid; r < ell; r += 32) {
+        const double x = __ldcg(wc + r);
+        xv[r] = x;
+        if (r > i) s = fma(x, x, s);
+      }
       s = warp_sum(s);
       if (tid == 0) {
         double beta, tau, scale;
-        house_scalars(xv[i], sqrt(s), &beta, &tau, &scale);
+        house_scalars_sq(xv[i], s, &beta, &tau, &scale);
         s_scal[0] = beta;
         s_scal[1] = tau;
         s_scal[2] = scale;
+        red[1] = w;
       }
     }
     __syncthreads();
+    const Cand w = red[1];
+    const long long Lstar = w.pos;
     const double beta = s_scal[0], tau = s_scal[1], scale = s_scal[2];
     for (int r = i + 1 + tid; r < ell; r += NT) xv[r] *= scale;
     if (tid == 0) xv[i] = 1.0;
@@ -184,32 +176,38 @@ __global__ void __launch_bounds__(NT, 1) sample_qrcp_kernel(SampleQrcpArgs a) {
       }
     }
     __syncthreads();
-    // ---- apply H = I - tau v v^T to the trailing columns, downdate norms;
-    // a column whose downdated norm lost too many digits is marked for an
-    // exact recompute, done in a second pass only when some column needs it
-    int need_any = 0;
-    for (int base = 0; base < ncol; base += GROUPS) {
-      const int c = base + grp;
-      const bool act = c < ncol && !done[c];
-      double* cc = col + (size_t)(act ? c : 0) * ell;
-      if (tau != 0.0) {
-        double s = 0.0;
-        if (act)
-          for (int r = i + lig; r < ell; r += LPC) s = fma(xv[r], cc[r], s);
-        s = group_sum<LPC>(s) * tau;
-        if (act)
-          for (int r = i + lig; r < ell; r += LPC) cc[r] = fma(-s, xv[r], cc[r]);
-      }
-      if (act && lig == 0 && vn[c] != 0.0) {
-        double rr = fabs(cc[i]) / vn[c];
-        double f = fmax(0.0, (1.0 - rr) * (1.0 + rr));
-        double q = vn[c] / vn0[c];
-        if (f * q * q <= TOL3Z) {
-          vn[c] = -1.0;  // recompute below
-          need_any = 1;
-        } else {
-          vn[c] *= sqrt(f);
+    // ---- apply H = I - tau v v^T to the trailing columns (LPC lanes per
+    // column, rounds of GROUPS columns keep the shuffles warp-uniform)
+    if (tau != 0.0) {
+      for (int base = 0; base < ncol; base += GROUPS) {
+        const int c = base + grp;
+        const bool act = c < ncol && !done[c];
+        if (__any_sync(0xffffffffu, act)) {
+          double* cc = col + (size_t)(act ? c : 0) * ell;
+          double s = 0.0;
+          if (act)
+            for (int r = i + lig; r < ell; r += LPC) s = fma(xv[r], cc[r], s);
+          s = group_sum<LPC>(s) * tau;
+          if (act)
+            for (int r = i + lig; r < ell; r += LPC) cc[r] = fma(-s, xv[r], cc[r]);
         }
+      }
+      __syncthreads();
+    }
+    // ---- downdate the norms, one thread per column; a column whose
+    // downdated norm lost too many digits is recomputed exactly from rows
+    // i+1.. (rare: a second pass only when some column needs it)
+    int need_any = 0;
+    for (int c = tid; c < ncol; c += NT) {
+      if (done[c] || vn[c] == 0.0) continue;
+      const double rr = fabs(col[i + (size_t)c * ell]) / vn[c];
+      const double f = fmax(0.0, (1.0 - rr) * (1.0 + rr));
+      const double q = vn[c] / vn0[c];
+      if (f * q * q <= TOL3Z) {
+        vn[c] = -1.0;  // recompute below
+        need_any = 1;
+      } else {
+        vn[c] *= sqrt(f);
       }
     }
     if (__syncthreads_or(need_any)) {
@@ -227,8 +225,8 @@ __global__ void __launch_bounds__(NT, 1) sample_qrcp_kernel(SampleQrcpArgs a) {
           vn0[c] = vn[c];
         }
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
 
   // every CTA finished loading before the first barrier: write S back in the
