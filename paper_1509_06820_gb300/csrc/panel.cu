@@ -26,7 +26,8 @@ namespace {
 
 constexpr int NT = 256;
 constexpr int MAXB = 128;
-constexpr int PARTS = 4;
+constexpr int PARTS = 8;   // threads per column in the partial-sum reduction
+constexpr int RB = 40;     // loads in flight per thread in that reduction
 
 __global__ void __launch_bounds__(NT, 1) panel_kernel(PanelArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -35,7 +36,8 @@ __global__ void __launch_bounds__(NT, 1) panel_kernel(PanelArgs a) {
   const int64_t chunk = (a.mJ + G - 1) / G;
   const int64_t r_lo = (int64_t)g * chunk;
   const int nrow = (int)imax64(0, imin64(a.mJ, r_lo + chunk) - r_lo);
-  double* Ps = reinterpret_cast<double*>(smem_raw);  // chunk x bJ, ld = chunk
+  const int64_t ldp = chunk | 1;  // odd: rows of one column in distinct banks
+  double* Ps = reinterpret_cast<double*>(smem_raw);  // chunk x bJ, ld = ldp
   __shared__ double s_tot[MAXB];
   __shared__ double s_w[MAXB];
   __shared__ double s_part[PARTS][MAXB];
@@ -45,7 +47,7 @@ __global__ void __launch_bounds__(NT, 1) panel_kernel(PanelArgs a) {
 
   for (int64_t e = tid; e < (int64_t)nrow * bJ; e += NT) {
     const int64_t r = e % nrow, c = e / nrow;
-    Ps[r + c * chunk] = a.P[(r_lo + r) + c * a.ld];
+    Ps[r + c * ldp] = a.P[(r_lo + r) + c * a.ld];
   }
   __syncthreads();
 
@@ -54,40 +56,52 @@ __global__ void __launch_bounds__(NT, 1) panel_kernel(PanelArgs a) {
   // partial dots of column j with columns j..bJ-1 over owned rows below row j
   auto publish = [&](int j) {
     double* part = part_base + (size_t)(j & 1) * G * bJ + (size_t)g * bJ;
-    const int64_t rstart = imax64(0, (int64_t)j + 1 - r_lo);  // local first row > j
-    for (int c = j + warp; c < bJ; c += nwarps) {
+    const int rstart = (int)imax64(0, (int64_t)j + 1 - r_lo);  // local first row > j
+    const int ncols = bJ - j;
+    // P lanes per column (a power of two within a warp), as many columns at
+    // once as fit in the block; the P partial sums meet by shuffles
+    int P = 32;
+    while (P > 1 && NT / P < ncols) P >>= 1;
+    const int cpr = NT / P;
+    const int p = tid % P;
+    for (int c0 = 0; c0 < ncols; c0 += cpr) {
+      const int c = j + c0 + tid / P;
       double s = 0.0;
-      for (int64_t r = rstart + lane; r < nrow; r += 32) s = fma(Ps[r + j * chunk], Ps[r + c * chunk], s);
-      s = warp_sum(s);
-      if (lane == 0) part[c] = s;
+      if (c < bJ) {
+        const double* xj = Ps + (size_t)j * ldp;
+        const double* xc = Ps + (size_t)c * ldp;
+        for (int r = rstart + p; r < nrow; r += P) s = fma(xj[r], xc[r], s);
+      }
+      for (int o = P >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (p == 0 && c < bJ) part[c] = s;
     }
     if (j >= r_lo && j < r_lo + nrow) {
       double* rowj = a.rowj + (size_t)(j & 1) * bJ;
-      for (int c = j + tid; c < bJ; c += NT) rowj[c] = Ps[(j - r_lo) + c * chunk];
+      for (int c = j + tid; c < bJ; c += NT) rowj[c] = Ps[(j - r_lo) + c * ldp];
     }
   };
 
   publish(0);
   for (int j = 0; j < bJ; ++j) {
     if (!grid_barrier(a.bar, G, a.status)) return;
-    // fixed-order reduction of the partial dots
+    // fixed-order reduction of the partial dots: PARTS threads per column,
+    // thread pp adds CTAs q = pp, pp + PARTS, ... in increasing order with up
+    // to RB loads in flight, then the PARTS sums are added in order
     const double* part = part_base + (size_t)(j & 1) * G * bJ;
-    for (int e = tid; e < PARTS * bJ; e += NT) {
-      const int c = e % bJ, pp = e / bJ;
+    const int ncols = bJ - j;
+    const int parts = imin64(PARTS, imax64(1, NT / ncols));
+    for (int e = tid; e < parts * ncols; e += NT) {
+      const int c = j + e % ncols, pp = e / ncols;
       double s = 0.0;
-      if (c >= j) {
-        // q = pp, pp + PARTS, ... in increasing order; loads issued in batches
-        // of 20 so that their L2 latencies overlap
-        for (int q0 = pp; q0 < G; q0 += 20 * PARTS) {
-          double v[20];
+      for (int q0 = pp; q0 < G; q0 += RB * parts) {
+        double v[RB];
 #pragma unroll
-          for (int u = 0; u < 20; ++u) {
-            const int q = q0 + u * PARTS;
-            v[u] = (q < G) ? __ldcg(part + (size_t)q * bJ + c) : 0.0;
-          }
-#pragma unroll
-          for (int u = 0; u < 20; ++u) s += v[u];
+        for (int u = 0; u < RB; ++u) {
+          const int q = q0 + u * parts;
+          v[u] = (q < G) ? __ldcg(part + (size_t)q * bJ + c) : 0.0;
         }
+#pragma unroll
+        for (int u = 0; u < RB; ++u) s += v[u];
       }
       s_part[pp][c] = s;
     }
@@ -95,8 +109,7 @@ __global__ void __launch_bounds__(NT, 1) panel_kernel(PanelArgs a) {
     const double* rowj = a.rowj + (size_t)(j & 1) * bJ;
     for (int c = j + tid; c < bJ; c += NT) {
       double s = 0.0;
-#pragma unroll
-      for (int pp = 0; pp < PARTS; ++pp) s += s_part[pp][c];
+      for (int pp = 0; pp < parts; ++pp) s += s_part[pp][c];
       s_tot[c] = s;
       s_w[c] = __ldcg(rowj + c);  // row j of the panel before this step
     }
@@ -117,21 +130,24 @@ __global__ void __launch_bounds__(NT, 1) panel_kernel(PanelArgs a) {
     const int64_t jl = (int64_t)j - r_lo;  // local index of row j (may be outside)
     const int64_t rstart = imax64(0, jl + 1);
     // scale column j into v, then a_rc -= v_r w_c on owned rows below j
-    for (int64_t r = rstart + tid; r < nrow; r += NT) Ps[r + j * chunk] *= scale;
+    for (int64_t r = rstart + tid; r < nrow; r += NT) Ps[r + j * ldp] *= scale;
     __syncthreads();
     if (tau != 0.0) {
+      // (row, column) pairs packed densely over the threads (32-bit indices)
       const int ncols = bJ - j - 1;
-      const int64_t rows = nrow - rstart;
-      for (int64_t e = tid; e < rows * ncols; e += NT) {
-        const int64_t r = rstart + e % rows;
-        const int c = j + 1 + (int)(e / rows);
-        Ps[r + c * chunk] = fma(-Ps[r + j * chunk], s_w[c], Ps[r + c * chunk]);
+      const int rows = nrow - (int)rstart;
+      const double* vj = Ps + (size_t)j * ldp;
+      for (int e = tid; e < rows * ncols; e += NT) {
+        const int cc = e / rows;
+        const int r = (int)rstart + (e - cc * rows);
+        const int c = j + 1 + cc;
+        Ps[r + (size_t)c * ldp] = fma(-vj[r], s_w[c], Ps[r + (size_t)c * ldp]);
       }
     }
     if (jl >= 0 && jl < nrow) {
       // row j: R entries
-      for (int c = j + 1 + tid; c < bJ; c += NT) Ps[jl + c * chunk] -= (tau != 0.0) ? s_w[c] : 0.0;
-      if (tid == 0) Ps[jl + j * chunk] = beta;
+      for (int c = j + 1 + tid; c < bJ; c += NT) Ps[jl + c * ldp] -= (tau != 0.0) ? s_w[c] : 0.0;
+      if (tid == 0) Ps[jl + j * ldp] = beta;
     }
     __syncthreads();
     if (j + 1 < bJ) publish(j + 1);
@@ -141,14 +157,14 @@ __global__ void __launch_bounds__(NT, 1) panel_kernel(PanelArgs a) {
   if (a.round_f32) {
     for (int64_t e = tid; e < (int64_t)nrow * bJ; e += NT) {
       const int64_t r = e % nrow, c = e / nrow;
-      if (r_lo + r > c) Ps[r + c * chunk] = (double)(float)Ps[r + c * chunk];
+      if (r_lo + r > c) Ps[r + c * ldp] = (double)(float)Ps[r + c * ldp];
     }
     __syncthreads();
   }
   // write the factored rows back
   for (int64_t e = tid; e < (int64_t)nrow * bJ; e += NT) {
     const int64_t r = e % nrow, c = e / nrow;
-    a.P[(r_lo + r) + c * a.ld] = Ps[r + c * chunk];
+    a.P[(r_lo + r) + c * a.ld] = Ps[r + c * ldp];
   }
   // partial Gram Y^T Y over owned rows (upper triangle, Y unit lower)
   double* gram = part_base + (size_t)2 * G * bJ + (size_t)g * bJ * bJ;
@@ -160,10 +176,10 @@ __global__ void __launch_bounds__(NT, 1) panel_kernel(PanelArgs a) {
     const int64_t r0 = imax64(0, (int64_t)c2 - r_lo);
     double s = 0.0;
     if (r0 < nrow && r_lo + r0 == c2) {
-      s = (c1 == c2) ? 1.0 : Ps[r0 + c1 * chunk];
-      for (int64_t r = r0 + 1; r < nrow; ++r) s = fma(Ps[r + c1 * chunk], Ps[r + c2 * chunk], s);
+      s = (c1 == c2) ? 1.0 : Ps[r0 + c1 * ldp];
+      for (int64_t r = r0 + 1; r < nrow; ++r) s = fma(Ps[r + c1 * ldp], Ps[r + c2 * ldp], s);
     } else {
-      for (int64_t r = r0; r < nrow; ++r) s = fma(Ps[r + c1 * chunk], Ps[r + c2 * chunk], s);
+      for (int64_t r = r0; r < nrow; ++r) s = fma(Ps[r + c1 * ldp], Ps[r + c2 * ldp], s);
     }
     gram[c1 + c2 * bJ] = s;
   }
@@ -276,16 +292,19 @@ size_t panel_partial_doubles(int grid, int bJ) {
 }
 
 static size_t panel_smem(int64_t chunk, int bJ) {
-  size_t a = (size_t)chunk * bJ * 8;
+  size_t a = (size_t)(chunk | 1) * bJ * 8;
   size_t b = ((size_t)bJ * bJ + bJ) * 8;
   return a > b ? a : b;
 }
+
+// dynamic shared memory limit: 227 KB per CTA less the kernel's static arrays
+constexpr size_t kPanelSmemLimit = 200 * 1024;
 
 bool panel_fits(int64_t mJ, int bJ, int num_sms) {
   if (bJ < 1 || bJ > MAXB) return false;
   const int G = panel_grid(mJ, bJ, num_sms);
   const int64_t chunk = (mJ + G - 1) / G;
-  return panel_smem(chunk, bJ) <= 216 * 1024;
+  return panel_smem(chunk, bJ) <= kPanelSmemLimit;
 }
 
 cudaError_t launch_panel(const PanelArgs& a, int num_sms, cudaStream_t st) {
@@ -293,11 +312,11 @@ cudaError_t launch_panel(const PanelArgs& a, int num_sms, cudaStream_t st) {
   const int G = panel_grid(a.mJ, a.bJ, num_sms);
   const int64_t chunk = (a.mJ + G - 1) / G;
   const size_t smem = panel_smem(chunk, a.bJ);
-  if (smem > 216 * 1024) return cudaErrorInvalidValue;
+  if (smem > kPanelSmemLimit) return cudaErrorInvalidValue;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         216 * 1024);
+                                         (int)kPanelSmemLimit);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }

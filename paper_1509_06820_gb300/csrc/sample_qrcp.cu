@@ -33,10 +33,18 @@ constexpr int MAX_ELL = 192;
 constexpr double TOL3Z = 1.4901161193847656e-08;  // sqrt(2^-52)
 
 struct Cand {
-  double key;    // norm; -1 for NaN, -2 when the CTA has no trailing column
+  long long key; // order-preserving integer image of the norm (see sort_key);
+                 // the norm -1 for NaN, -2 when the CTA has no trailing column
   long long pos; // logical position
   int who;       // CTA index or local column index
 };
+
+// Integer with the same order as the double d (also for negative d): the
+// comparisons of the argmax then run on the integer pipe instead of FP64.
+__device__ __forceinline__ long long sort_key(double d) {
+  const long long b = __double_as_longlong(d);
+  return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFLL);
+}
 
 __device__ __forceinline__ bool better(const Cand& a, const Cand& b) {
   return a.key > b.key || (a.key == b.key && a.pos < b.pos);
@@ -107,17 +115,17 @@ __global__ void __launch_bounds__(NT, 1) sample_qrcp_kernel(SampleQrcpArgs a) {
     double* cand = a.cand + (size_t)(i & 1) * G * 2;
     double* ccol = a.candcol + (size_t)(i & 1) * G * ell;
     if (tid < 32) {
-      Cand mine{-2.0, LLONG_MAX, -1};
+      Cand mine{sort_key(-2.0), LLONG_MAX, -1};
       for (int c = tid; c < ncol; c += 32) {
         if (done[c]) continue;
-        Cand t{isnan(vn[c]) ? -1.0 : vn[c], lpos[c], c};
+        Cand t{sort_key(isnan(vn[c]) ? -1.0 : vn[c]), lpos[c], c};
         if (better(t, mine)) mine = t;
       }
       mine = warp_argmax(mine);
       if (tid == 0) {
         red[0] = mine;
-        cand[2 * g] = mine.key;
-        cand[2 * g + 1] = (double)mine.pos;  // positions < 2^53: exact
+        cand[2 * g] = __longlong_as_double(mine.key);       // bit pattern
+        cand[2 * g + 1] = __longlong_as_double(mine.pos);
       }
     }
     __syncthreads();
@@ -129,12 +137,14 @@ __global__ void __launch_bounds__(NT, 1) sample_qrcp_kernel(SampleQrcpArgs a) {
     // ---- global winner (identical in every CTA): warp 0 scans the G
     // candidates, then builds the reflector from the winner's rows i..ell-1
     if (tid < 32) {
-      Cand w{-3.0, LLONG_MAX, -1};
+      Cand w{sort_key(-3.0), LLONG_MAX, -1};
       for (int q = tid; q < G; q += 32) {
-        Cand t{__ldcg(cand + 2 * q), (long long)__ldcg(cand + 2 * q + 1), q};
+        Cand t{__double_as_longlong(__ldcg(cand + 2 * q)),
+               __double_as_longlong(__ldcg(cand + 2 * q + 1)), q};
         if (better(t, w)) w = t;
       }
       w = warp_argmax(w);
+      // the winner's rows i..ell-1; each lane rescales the rows it loaded
       const double* wc = ccol + (size_t)w.who * ell;
       double s = 0.0;
       for (int r = i + tid; r < ell; r += 32) {
@@ -143,21 +153,22 @@ __global__ void __launch_bounds__(NT, 1) sample_qrcp_kernel(SampleQrcpArgs a) {
         if (r > i) s = fma(x, x, s);
       }
       s = warp_sum(s);
+      __syncwarp();
+      const double alpha = xv[i];
+      __syncwarp();  // every lane has read alpha before lane 0 overwrites it
+      double beta, tau, scale;
+      house_scalars_sq(alpha, s, &beta, &tau, &scale);
+      for (int r = i + tid; r < ell; r += 32) xv[r] = (r == i) ? 1.0 : xv[r] * scale;
       if (tid == 0) {
-        double beta, tau, scale;
-        house_scalars_sq(xv[i], s, &beta, &tau, &scale);
         s_scal[0] = beta;
         s_scal[1] = tau;
-        s_scal[2] = scale;
         red[1] = w;
       }
     }
     __syncthreads();
     const Cand w = red[1];
     const long long Lstar = w.pos;
-    const double beta = s_scal[0], tau = s_scal[1], scale = s_scal[2];
-    for (int r = i + 1 + tid; r < ell; r += NT) xv[r] *= scale;
-    if (tid == 0) xv[i] = 1.0;
+    const double beta = s_scal[0], tau = s_scal[1];
     if (g == 0 && tid == 0) a.swaps[i] = Lstar;
     // the trailing column at logical position i moves to Lstar (the pivot
     // itself sits at Lstar != i, so it is not matched here)

@@ -138,22 +138,32 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       : "memory");
 }
 
-// 8 columns of two accumulators (same lanes), then wait for both loads.
-__device__ __forceinline__ void tmem_ld8x2(uint32_t ta, uint32_t tb, float* a, float* b) {
-  uint32_t r[16];
+// 32 columns of two accumulators (same lanes), then one wait for both loads.
+__device__ __forceinline__ void tmem_ld32x2(uint32_t ta, uint32_t tb, float* a, float* b) {
+  uint32_t r[64];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%64];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,"
+      "%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%65];\n"
       "tcgen05.wait::ld.sync.aligned;"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]),
+        "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]),
+        "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]),
+        "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]),
+        "=r"(r[62]), "=r"(r[63])
       : "r"(ta), "r"(tb)
       : "memory");
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < 32; ++i) {
     a[i] = __uint_as_float(r[i]);
-    b[i] = __uint_as_float(r[8 + i]);
+    b[i] = __uint_as_float(r[32 + i]);
   }
 }
 
@@ -328,15 +338,17 @@ __global__ void __launch_bounds__(XNT, 1)
         }
       };
       cursor_unit(blockIdx.x);
+      // per ring slot: parity of its use count (bit st) and whether it was used
       int lst = 0;
-      uint32_t luse[XNST] = {};
+      uint32_t lpar = 0u, lused = 0u;
       auto issue_load = [&]() -> bool {
         if (lu >= g.units) return true;
-        if (!mbar_wait(&empty[lst], (luse[lst] & 1u) ^ 1u)) return false;
+        if (!mbar_wait(&empty[lst], ((lpar >> lst) & 1u) ^ 1u)) return false;
         mbar_expect_tx(&full[lst], STAGE_TX);
         tma_load_3d(stage_a(lst), &tmA, lkt * XBK, ltm * XBM, 0, &full[lst]);
         tma_load_3d(stage_b(lst), &tmB, lkt * XBK, ltn * XBN, 0, &full[lst]);
-        ++luse[lst];
+        lpar ^= 1u << lst;
+        lused |= 1u << lst;
         lst = (lst + 1 == XNST) ? 0 : lst + 1;
         if (++lkt >= lke) cursor_unit(lu + gridDim.x);
         return true;
@@ -344,7 +356,7 @@ __global__ void __launch_bounds__(XNT, 1)
       bool ok = true;
       for (int i = 0; i < XNST - 1 && ok; ++i) ok = issue_load();
       int st = 0, buf = 0;
-      uint32_t fuse[XNST] = {}, tuse[2] = {0u, 0u};
+      uint32_t fpar = 0u, tpar = 0u;  // parities of the full[] and tempty[] uses
       bool any = false;
       for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
         const int z = u / (g.tiles_m * g.tiles_n);
@@ -353,7 +365,7 @@ __global__ void __launch_bounds__(XNT, 1)
         for (int q = 0; q < nks; ++q) {
           const int sq = q & 3;
           if (sq == 0) {
-            if (!mbar_wait(&full[st], fuse[st] & 1u) || s_fail) {
+            if (!mbar_wait(&full[st], (fpar >> st) & 1u) || s_fail) {
               ok = false;
               break;
             }
@@ -362,7 +374,7 @@ __global__ void __launch_bounds__(XNT, 1)
           const bool cstart = (S == 3) ? (q % XCH == 0) : (q == 0);
           const bool cend = (S == 3) ? (q % XCH == XCH - 1) : (q == nks - 1);
           if (cstart) {
-            if (!mbar_wait(&tempty[buf], (tuse[buf] & 1u) ^ 1u) || s_fail) {
+            if (!mbar_wait(&tempty[buf], ((tpar >> buf) & 1u) ^ 1u) || s_fail) {
               ok = false;
               break;
             }
@@ -385,12 +397,12 @@ __global__ void __launch_bounds__(XNT, 1)
           any = true;
           if (cend) {
             mma_commit(&tfull[buf]);
-            ++tuse[buf];
+            tpar ^= 1u << buf;
             buf ^= 1;
           }
           if (sq == 3) {
             mma_commit(&empty[st]);
-            ++fuse[st];
+            fpar ^= 1u << st;
             st = (st + 1 == XNST) ? 0 : st + 1;
             if (!issue_load()) {
               ok = false;
@@ -403,7 +415,7 @@ __global__ void __launch_bounds__(XNT, 1)
         s_fail = 1;
         // wait (bounded) for the last copy issued on each slot
         for (int i = 0; i < XNST; ++i)
-          if (luse[i] > 0) mbar_wait(&full[i], (luse[i] - 1u) & 1u);
+          if ((lused >> i) & 1u) mbar_wait(&full[i], ((lpar >> i) & 1u) ^ 1u);
       }
       if (any) {
         // every MMA of this thread has completed once this commit arrives
@@ -418,7 +430,7 @@ __global__ void __launch_bounds__(XNT, 1)
     const uint32_t lane_base = tmem + ((uint32_t)(32 * quad) << 16);
     const int64_t MN = g.M * g.N;
     int buf = 0;
-    uint32_t tuse[2] = {0u, 0u};
+    uint32_t tpar = 0u;  // parity of the tfull[] uses
     bool ok = true;
     for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
       const int tm = u % g.tiles_m, rest = u / g.tiles_m;
@@ -430,7 +442,7 @@ __global__ void __launch_bounds__(XNT, 1)
 #pragma unroll
       for (int c = 0; c < XBN; ++c) hi[c] = cc[c] = 0.0f;
       for (int ch = 0; ch < nch; ++ch) {
-        if (!mbar_wait(&tfull[buf], tuse[buf] & 1u) || s_fail) {
+        if (!mbar_wait(&tfull[buf], (tpar >> buf) & 1u) || s_fail) {
           ok = false;
           break;
         }
@@ -438,11 +450,11 @@ __global__ void __launch_bounds__(XNT, 1)
         const uint32_t tb = lane_base + (uint32_t)(buf * NACC * XBN);
         if (S == 3) {
 #pragma unroll
-          for (int c0 = 0; c0 < XBN; c0 += 8) {
-            float v[8], w[8];
-            tmem_ld8x2(tb + c0, tb + XBN + c0, v, w);
+          for (int c0 = 0; c0 < XBN; c0 += 32) {
+            float v[32], w[32];
+            tmem_ld32x2(tb + c0, tb + XBN + c0, v, w);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
+            for (int e = 0; e < 32; ++e) {
               // Kahan step with the chunk's leading and correction parts
               const float y = (v[e] - cc[c0 + e]) + w[e];
               const float t = hi[c0 + e] + y;
@@ -462,7 +474,7 @@ __global__ void __launch_bounds__(XNT, 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[buf]);
-        ++tuse[buf];
+        tpar ^= 1u << buf;
         buf ^= 1;
       }
       if (!ok) break;
@@ -481,15 +493,24 @@ __global__ void __launch_bounds__(XNT, 1)
             ph += g.M;
           }
         } else {
+          // C read in batches of 16 independent loads, then written
           float* cp = g.C + r + c0 * g.ldc;
+          const int64_t ldc = g.ldc;
           const float alpha = g.alpha, beta = g.beta;
 #pragma unroll
-          for (int c = 0; c < XBN; ++c) {
-            if (c < nval) {
-              const float out = beta != 0.0f ? fmaf(alpha, hi[c], beta * *cp) : alpha * hi[c];
-              *cp = fmaf(-alpha, cc[c], out);
+          for (int cb = 0; cb < XBN; cb += 16) {
+            float cv[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+              cv[e] = (beta != 0.0f && cb + e < nval) ? __ldcs(cp + (cb + e) * ldc) : 0.0f;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const int c = cb + e;
+              if (c < nval) {
+                const float out = fmaf(alpha, hi[c], beta * cv[e]);
+                __stcs(cp + c * ldc, fmaf(-alpha, cc[c], out));
+              }
             }
-            cp += g.ldc;
           }
         }
       }
