@@ -76,8 +76,8 @@ int tc_launches(int64_t M, int64_t N, int64_t K, int num_sms, size_t partial_cap
 
 // ---- oz_gemm.cu: FP64-accurate GEMM on the BF16 tensor cores by exact
 // slicing.  C (M x N, FP64, ldc) = alpha * 2^(expA_i + expB_j) * (A_sl B_sl^T)
-// + beta * C, where A_sl (7 x M x Kp bf16) and B_sl (7 x N x Kp bf16) are the
-// slices written by launch_oz_slice (rows of op(A) and columns of op(B)).
+// + beta * C, where A_sl and B_sl are the slices written by launch_oz_slice
+// (rows of op(A) and columns of op(B), oz_slice_elems(rows, K) bf16 each).
 struct OzGemmArgs {
   int64_t M, N, Kp;
   const __nv_bfloat16* As;
@@ -88,14 +88,23 @@ struct OzGemmArgs {
   double* C;
   int64_t ldc;
   int* status;
+  float* partial;      // split-K sums (2 floats per element of C and split); may be null
+  size_t partial_cap;  // floats
+  int num_sms;
 };
 // Slices of the R rows of op(X) (K values each): kc -> row r is stored column
 // r (X[k + r ld]), else stored row r (X[r + k ld]); amode 1 reads X as a
-// unit-lower reflector block.  slices: 7 * R * Kp bf16, exps: R ints.
+// unit-lower reflector block.  slices: oz_slice_elems(R, K) bf16; exps: R ints,
+// the biased FP64 exponent field of each row's largest |x| (the row scale).
 cudaError_t launch_oz_slice(const double* X, int64_t ld, bool kc, int amode, int64_t R, int64_t K,
                             __nv_bfloat16* slices, int* exps, cudaStream_t st);
 cudaError_t launch_oz_gemm(const OzGemmArgs& g, cudaStream_t st);
 int64_t oz_kpad(int64_t K);
+size_t oz_slice_elems(int64_t rows, int64_t K);
+// kernel launches of one launch_oz_slice call
+int oz_slice_launches(bool kc, int64_t K);
+// kernel launches of one launch_oz_gemm call
+int oz_launches(int64_t M, int64_t N, int64_t Kp, int num_sms, size_t partial_cap);
 
 // ---- sample_qrcp.cu: partial QRCP (Alg. 1, b steps) on the l x nc sample.
 struct SampleQrcpArgs {

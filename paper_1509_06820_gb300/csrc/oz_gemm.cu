@@ -3,11 +3,14 @@
 // (W = T^T Y^T A2, A2 -= Y W) when the GPU's FP64 pipe (~1.25 TFLOP/s on a
 // GB300) is the bottleneck.
 //
-// Slicing (one pass per operand, oz_slice_kernel).  Row r of an operand
+// Slicing (launch_oz_slice, a memory-bound pass per operand).  Row r of an operand
 // (K values x_k) gets the power-of-two scale 2^e_r with max_k |x_k| < 2^e_r;
 // t = x 2^-e_r lies in (-1, 1) and is cut into S = 7 slices of 8 bits,
 //   t = sum_s y_s 2^{-8s} + (|rest| < 2^-56),  y_s integer in [-255, 255],
-// each slice value y_s 2^{-8s} exactly representable in BF16.
+// each slice value y_s 2^{-8s} exactly representable in BF16.  The slices are
+// stored in pairs: for pair q (slices 2q+1, 2q+2) and each 32-wide k chunk a
+// row holds 64 values [slice 2q+1, k 0..31 | slice 2q+2, k 0..31], so one
+// 128-byte swizzled shared-memory row feeds the MMA with two slices.
 //
 // Products.  C_ij = 2^{e_i + f_j} sum_{s,t} sum_k a_s(i,k) b_t(k,j).  The pairs
 // with s + t = d carry the common grid 2^{-8d}; with K <= 32 per accumulation
@@ -16,45 +19,68 @@
 // core's rounding (it truncates).  d = 2..6 get one accumulator each; d = 7, 8
 // share one (at most 2^-40 of the leading term, so even a truncating FP32 sum
 // of its 416 products errs below 2^-54); pairs with s + t > 8 are dropped
-// (below 2^-56).  28 BF16 MMAs per k-step.
+// (below 2^-56).  28 BF16 MMAs per 16-wide k step.
 //
-// Kernel (oz_gemm_kernel): one 128 x 64 output tile per CTA, 256 threads.
-// Per 64-wide k-stage the slices are copied (16-byte chunks) into the
-// 128-byte-swizzled K-major layout; for each 32-wide half of the stage,
-// thread 0 issues the 28 x 2 tcgen05.mma into the six tensor-memory
-// accumulators (6 x 64 columns), commits to an mbarrier, and the eight warps
-// (two per accumulator lane quadrant, one per 32-column half) drain the
-// accumulators into running double-FP32 sums (error-free TwoSum), so the
-// exactness bound never needs K > 32.  The epilogue forms
-// 2^{e_i + f_j} (hi + lo) in FP64 and writes C = alpha * that + beta * C.
+// Kernel (oz_gemm_kernel): persistent, one CTA per SM, 128 x 64 output tiles,
+// split-K units, 5 warps:
+//   warp 0      allocates tensor memory; one thread issues the TMA copies
+//               (per 32-k stage one 3-D box per operand: 64 values x rows x 4
+//               pairs) into a two-stage shared-memory ring, and the 56 MMAs
+//               of a stage into the six accumulators (6 x 64 tensor-memory
+//               columns);
+//   warps 1-8   drain: after each stage, warp w adds the six exact group sums
+//               of lanes 32 (w % 4).. (one output row per thread, 32 of the 64
+//               columns) into running double-FP32 sums (error-free TwoSum),
+//               smallest first; at the end of a unit it writes
+//               C = alpha 2^{e_i + f_j} (hi + lo) + beta C (or the split's hi
+//               and lo to the partial-sum buffer).  With alpha = +-1 and
+//               beta in {0, 1} the scaled hi and lo are built as FP64 bit
+//               fields with integer operations, so an output element costs
+//               two FP64 additions.
+// Every mbarrier wait is bounded; on timeout the status word gets
+// RQRCP_INFO_TIMEOUT, each role stops, in-flight copies and MMAs are waited
+// for (bounded) and the tensor memory is freed.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "kernels.cuh"
+#include "tcgen05.cuh"
 
 namespace rq {
 namespace {
 
+using namespace tc;
+
 constexpr int OZ_S = 7;        // slices per operand
+constexpr int OZ_PAIRS = 4;    // slice pairs per operand (the eighth slot is zero)
 constexpr int OZ_BITS = 8;     // bits per slice
 constexpr int OZ_NG = 6;       // accumulators: d = 2, 3, 4, 5, 6 and d >= 7
-constexpr int OZ_KH = 32;      // k per exact accumulation (one drain)
-constexpr int OZ_BM = 128;
-constexpr int OZ_BN = 64;
-constexpr int OZ_BK = 64;
-constexpr int OZ_NT = 256;  // warp w: accumulator lanes 32 (w % 4).., columns 32 (w / 4)..
-constexpr unsigned kOzPolls = 1u << 26;
+constexpr int OZ_BM = 128;     // tile rows (A role), UMMA M
+constexpr int OZ_BN = 64;      // tile columns (B role), UMMA N
+constexpr int OZ_BK = 32;      // k per stage (one exact accumulation)
+constexpr int OZ_KP = 64;      // K padding of the slice buffers
+constexpr int OZ_NST = 2;      // shared-memory ring stages
+constexpr int OZ_NT = 288;     // warp 0 TMA and MMA issue, warps 1..8 drain
+constexpr int OZ_CPT = 32;     // output columns per drain thread (two warps per lane quadrant)
+constexpr int OZ_PT_A = OZ_BM * 128;          // bytes of one A pair tile
+constexpr int OZ_PT_B = OZ_BN * 128;          // bytes of one B pair tile
+constexpr int OZ_STAGE_A = OZ_PAIRS * OZ_PT_A;
+constexpr int OZ_STAGE = OZ_PAIRS * (OZ_PT_A + OZ_PT_B);
+constexpr uint32_t OZ_IDESC = idesc_bf16_f32(OZ_BM, OZ_BN);
+constexpr uint32_t OZ_TCOLS = 512;  // power of two >= 6 x 64
 
-__device__ __forceinline__ uint32_t su32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
+// group of the diagonal d = s + t (s, t >= 1)
+__host__ __device__ constexpr int oz_group(int d) { return d - 2 < OZ_NG - 1 ? d - 2 : OZ_NG - 1; }
+
+int64_t rpad128(int64_t R) { return (R + OZ_BM - 1) / OZ_BM * OZ_BM; }
 
 // ---------------------------------------------------------------- slicing
 // Rows of op(X): KC -> element (r, k) at X[r * ld + k] (a stored column per
 // row); otherwise at X[r + k * ld].  amode 1: X is a unit-lower reflector
 // block stored in place (above the diagonal 0, diagonal 1; the diagonal is
-// the stored (row, col) with row == col).  Output: slices s = 0..6 at
-// out + s * R * Kp, row r at [r * Kp, r * Kp + Kp), K padded with zeros;
-// exps[r] = e_r.
+// the stored (row, col) with row == col).
 template <bool KC, int AMODE>
 __device__ __forceinline__ double oz_elem(const double* __restrict__ X, int64_t ld, int64_t r,
                                           int64_t k) {
@@ -68,304 +94,498 @@ __device__ __forceinline__ double oz_elem(const double* __restrict__ X, int64_t 
 
 // The slicing runs on integer bit fields only (the GPU's FP64 pipe is too
 // slow for a per-element pass): |x| = m 2^(E - 1075) with a 53-bit integer
-// m, T = |t| 2^56 = m 2^(E - 1075 + 56 - e) < 2^56, and slice s is the byte
-// (T >> (56 - 8s)) & 255 with the sign of x.
+// m, T = |t| 2^56 = m 2^(E - 1075 + 56 - e) < 2^56, and slice s (1-based) is
+// the byte (T >> (56 - 8s)) & 255 with the sign of x.
+// exps[r] holds F_r, the biased FP64 exponent field of max_k |x_rk| (0 when
+// the row is zero or subnormal); the scale is e_r = max(F_r, 1) - 1022, so
+// that max |x| < 2^e_r.
+__device__ __forceinline__ int oz_scale_exp(int field) { return (field > 1 ? field : 1) - 1022; }
+
+__device__ __forceinline__ int oz_field(double x) {
+  return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FFull);
+}
+
+// Output (Rp rows, Kp multiple of 64): pair q, row r, k chunk c (32 wide):
+// out[((q * Rp + r) * (Kp / 32) + c) * 64 + h * 32 + kk] = slice 2q + h + 1 at
+// k = 32 c + kk; rows r >= R and the eighth slot are zero.
 template <bool KC, int AMODE>
-__global__ void oz_slice_kernel(const double* __restrict__ X, int64_t ld, int64_t R, int64_t K,
-                                int64_t Kp, __nv_bfloat16* __restrict__ out, int* __restrict__ exps) {
-  // one warp per row
+__device__ __forceinline__ void oz_slice_one(const double* __restrict__ X, int64_t ld, int64_t R,
+                                             int64_t K, int64_t Rp, int64_t Kp, int64_t r,
+                                             int64_t k, int e, __nv_bfloat16* __restrict__ out) {
+  unsigned long long T = 0;
+  bool neg = false;
+  if (r < R && k < K) {
+    const unsigned long long b =
+        (unsigned long long)__double_as_longlong(oz_elem<KC, AMODE>(X, ld, r, k));
+    neg = (b >> 63) != 0;
+    const int E = (int)((b >> 52) & 0x7FF);
+    unsigned long long m = b & 0x000FFFFFFFFFFFFFull;
+    int Eu = E;
+    if (E != 0) m |= 0x0010000000000000ull;
+    else Eu = 1;
+    const int sh = Eu - 1075 + 56 - e;  // <= 3
+    if (sh >= 0) T = m << sh;
+    else if (sh > -64) T = m >> (-sh);
+  }
+  const size_t pstride = (size_t)Rp * Kp * 2;  // elements per pair plane
+  __nv_bfloat16* p = out + (size_t)r * (Kp / 32) * 64 + (k >> 5) * 64 + (k & 31);
+#pragma unroll
+  for (int s = 0; s < 2 * OZ_PAIRS; ++s) {
+    float v = 0.0f;
+    if (s < OZ_S) {
+      const float y = (float)(unsigned)((T >> (8 * (OZ_S - 1 - s))) & 0xFFull);
+      v = ldexpf(neg ? -y : y, -OZ_BITS * (s + 1));  // exact
+    }
+    p[(size_t)(s >> 1) * pstride + (s & 1) * 32] = __float2bfloat16_rn(v);
+  }
+}
+
+// Row-contiguous source (element (r, k) at X[r + k ld], small K): one warp per
+// row finds the maximum and slices the row.
+template <int AMODE>
+__global__ void oz_slice_rows(const double* __restrict__ X, int64_t ld, int64_t R, int64_t K,
+                              int64_t Rp, int64_t Kp, __nv_bfloat16* __restrict__ out,
+                              int* __restrict__ exps) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (r >= Rp) return;
+  int f = 0;
+  if (r < R)
+    for (int64_t k = lane; k < K; k += 32) f = max(f, oz_field(oz_elem<false, AMODE>(X, ld, r, k)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) f = max(f, __shfl_xor_sync(0xffffffffu, f, o));
+  if (lane == 0 && r < R) exps[r] = f;
+  const int e = oz_scale_exp(f);
+  for (int64_t k = lane; k < Kp; k += 32)
+    oz_slice_one<false, AMODE>(X, ld, R, K, Rp, Kp, r, k, e, out);
+}
+
+// Column-contiguous source (element (r, k) at X[r ld + k], K may be long):
+// pass 1 takes the maximum exponent field of each (row, 1024-wide k chunk)
+// into exps[r] (zeroed before) with an integer atomic maximum; pass 2 slices
+// each (row, k chunk) with the row's scale.  One warp per (row, chunk).
+constexpr int OZ_KCH = 1024;
+
+template <int AMODE>
+__global__ void oz_rowmax_cols(const double* __restrict__ X, int64_t ld, int64_t R, int64_t K,
+                               int* __restrict__ exps) {
   const int lane = threadIdx.x & 31;
   const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   if (r >= R) return;
-  unsigned long long mb = 0;  // max |x| as bits (monotone for non-negative doubles)
-  for (int64_t k = lane; k < K; k += 32) {
-    const unsigned long long b =
-        (unsigned long long)__double_as_longlong(oz_elem<KC, AMODE>(X, ld, r, k)) & 0x7FFFFFFFFFFFFFFFull;
-    mb = b > mb ? b : mb;
-  }
+  const int64_t k0 = (int64_t)blockIdx.y * OZ_KCH, k1 = imin64(K, k0 + OZ_KCH);
+  int f = 0;
+  for (int64_t k = k0 + lane; k < k1; k += 32) f = max(f, oz_field(oz_elem<true, AMODE>(X, ld, r, k)));
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long other = __shfl_xor_sync(0xffffffffu, mb, o);
-    mb = other > mb ? other : mb;
-  }
-  // e with max|x| < 2^e: biased exponent - 1022 (subnormals: -1022)
-  const int e = (mb == 0) ? 0 : (int)((mb >> 52) & 0x7FF) - 1022;
-  if (lane == 0) exps[r] = e;
-  for (int64_t k = lane; k < Kp; k += 32) {
-    unsigned long long T = 0;
-    bool neg = false;
-    if (k < K) {
-      const unsigned long long b = (unsigned long long)__double_as_longlong(oz_elem<KC, AMODE>(X, ld, r, k));
-      neg = (b >> 63) != 0;
-      const int E = (int)((b >> 52) & 0x7FF);
-      unsigned long long m = b & 0x000FFFFFFFFFFFFFull;
-      int Eu = E;
-      if (E != 0) m |= 0x0010000000000000ull;
-      else Eu = 1;
-      const int sh = Eu - 1075 + 56 - e;  // <= 3
-      if (sh >= 0) T = m << sh;
-      else if (sh > -64) T = m >> (-sh);
-    }
-#pragma unroll
-    for (int s = 0; s < OZ_S; ++s) {
-      const float y = (float)(unsigned)((T >> (8 * (OZ_S - 1 - s))) & 0xFFull);
-      const float v = ldexpf(neg ? -y : y, -OZ_BITS * (s + 1));  // exact
-      out[(int64_t)s * R * Kp + r * Kp + k] = __float2bfloat16_rn(v);
-    }
-  }
+  for (int o = 16; o > 0; o >>= 1) f = max(f, __shfl_xor_sync(0xffffffffu, f, o));
+  if (lane == 0 && f > 0) atomicMax(exps + r, f);
 }
 
-// ---------------------------------------------------------------- tcgen05
-__device__ __forceinline__ void oz_mbar_init(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bar)) : "memory");
+template <int AMODE>
+__global__ void oz_slice_cols(const double* __restrict__ X, int64_t ld, int64_t R, int64_t K,
+                              int64_t Rp, int64_t Kp, __nv_bfloat16* __restrict__ out,
+                              const int* __restrict__ exps) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (r >= Rp) return;
+  const int e = oz_scale_exp(r < R ? exps[r] : 0);
+  const int64_t k0 = (int64_t)blockIdx.y * OZ_KCH, k1 = imin64(Kp, k0 + OZ_KCH);
+  for (int64_t k = k0 + lane; k < k1; k += 32)
+    oz_slice_one<true, AMODE>(X, ld, R, K, Rp, Kp, r, k, e, out);
 }
 
-__device__ __forceinline__ bool oz_mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (unsigned i = 0; i < kOzPolls; ++i) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(su32(bar)), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if (i > 32) __nanosleep(32);
-  }
-  return false;
-}
+// ---------------------------------------------------------------- GEMM
+struct OzArgs {
+  int64_t M, N;
+  int KT;             // 32-k stages
+  int kt_per_split;
+  int tiles_m, tiles_n, units;
+  double alpha, beta;
+  double* C;
+  int64_t ldc;
+  const int* expA;
+  const int* expB;
+  float* part;        // splits > 1: hi at part[2z MN + r + c M], lo at part[(2z+1) MN + ...]
+  int* status;
+};
 
-__device__ __forceinline__ uint64_t oz_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-// kind::f16, FP32 accumulate, BF16 A and B, K-major, M = 128, N = 64
-constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
-                              ((uint32_t)(OZ_BM >> 4) << 24);
-
-__device__ __forceinline__ void oz_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(OZ_IDESC), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ void oz_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// error-free transformation: s + err = a + b exactly
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
   s = a + b;
   const float bb = s - a;
   err = (a - (s - bb)) + (b - bb);
 }
 
-// group of the diagonal d = s + t (s, t >= 1)
-__host__ __device__ constexpr int oz_group(int d) { return d - 2 < OZ_NG - 1 ? d - 2 : OZ_NG - 1; }
+// x 2^e as an FP64 value (sign flipped by neg = 0x80000000), built from the
+// FP32 bit fields with integer operations; exact.  FP32 subnormals and
+// results outside the normal FP64 range take the (rare) FP64 path.
+__device__ __forceinline__ double scaled_f64(float x, int e, uint32_t neg) {
+  const uint32_t b = __float_as_uint(x) ^ neg;
+  const uint32_t ex = (b >> 23) & 0xFFu;
+  if ((b & 0x7FFFFFFFu) == 0u) return 0.0;
+  const int e64 = (int)ex - 127 + 1023 + e;
+  if (ex == 0u || e64 <= 0 || e64 >= 2047) return ldexp((double)__uint_as_float(b), e);
+  const uint32_t hiw = (b & 0x80000000u) | ((uint32_t)e64 << 20) | ((b >> 3) & 0xFFFFFu);
+  const uint32_t low = (b & 7u) << 29;
+  return __hiloint2double((int)hiw, (int)low);
+}
 
-__global__ void __launch_bounds__(OZ_NT, 1) oz_gemm_kernel(OzGemmArgs g) {
+__device__ __forceinline__ double pow2(int e) {
+  return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52)
+                                   : ldexp(1.0, e);
+}
+
+__global__ void __launch_bounds__(OZ_NT, 1)
+    oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   OzArgs g) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  constexpr size_t A_SL = (size_t)OZ_BM * 128;  // one slice tile, 64 k x 2 bytes per row
-  constexpr size_t B_SL = (size_t)OZ_BN * 128;
-  unsigned char* As = smem;
-  unsigned char* Bs = smem + OZ_S * A_SL;
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t full[OZ_NST], empty[OZ_NST], tfull, tempty, done;
   __shared__ uint32_t s_tmem;
-  __shared__ int s_fail;
+  __shared__ volatile int s_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t i0 = (int64_t)blockIdx.x * OZ_BM, j0 = (int64_t)blockIdx.y * OZ_BN;
-  const int KT = (int)(g.Kp / OZ_BK);
-
   if (tid == 0) {
-    oz_mbar_init(&mbar);
+    for (int i = 0; i < OZ_NST; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(&tfull, 1);
+    mbar_init(&tempty, 8);
+    mbar_init(&done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     su32(&s_tmem)),
-                 "r"(512u)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  if (warp == 0) tmem_alloc(&s_tmem, OZ_TCOLS);
+  tc_fence_before();
   __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  tc_fence_after();
   const uint32_t tmem = s_tmem;
 
-  // running double-FP32 sums for this thread's row, 32 columns
-  constexpr int CPT = OZ_BN / 2;
-  const int quad = warp & 3, cbase = (warp >> 2) * CPT;
-  float hi[CPT], lo[CPT];
-#pragma unroll
-  for (int c = 0; c < CPT; ++c) hi[c] = lo[c] = 0.0f;
+  auto stage_a = [&](int st) { return smem + (size_t)st * OZ_STAGE; };
+  auto stage_b = [&](int st) { return smem + (size_t)st * OZ_STAGE + OZ_STAGE_A; };
 
-  for (int kt = 0; kt < KT; ++kt) {
-    // ---- copy the stage's slices into swizzled shared memory
-    const int64_t k0 = (int64_t)kt * OZ_BK;
-    for (int item = tid; item < OZ_S * OZ_BM * 8; item += OZ_NT) {
-      const int s = item / (OZ_BM * 8), rem = item % (OZ_BM * 8), r = rem >> 3, c = rem & 7;
-      const int64_t gr = i0 + r;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (gr < g.M)
-        v = *reinterpret_cast<const uint4*>(g.As + (int64_t)s * g.M * g.Kp + gr * g.Kp + k0 + 8 * c);
-      *reinterpret_cast<uint4*>(As + s * A_SL + r * 128 + ((c ^ (r & 7)) << 4)) = v;
+  if (warp == 0) {
+    // ------------------------------------------------ TMA + MMA issue
+    if (lane == 0) {
+      int lu = 0, lkt = 0, lke = 0, ltm = 0, ltn = 0;  // cursor of the next copy
+      auto cursor_unit = [&](int u) {
+        lu = u;
+        if (lu < g.units) {
+          ltm = lu % g.tiles_m;
+          const int rest = lu / g.tiles_m;
+          ltn = rest % g.tiles_n;
+          lkt = (rest / g.tiles_n) * g.kt_per_split;
+          lke = min(g.KT, lkt + g.kt_per_split);
+        }
+      };
+      cursor_unit(blockIdx.x);
+      int lst = 0;
+      uint32_t lpar = 0u, lused = 0u;
+      auto issue_load = [&]() -> bool {
+        if (lu >= g.units) return true;
+        if (!mbar_wait(&empty[lst], ((lpar >> lst) & 1u) ^ 1u)) return false;
+        mbar_expect_tx(&full[lst], OZ_STAGE);
+        tma_load_3d(stage_a(lst), &tmA, lkt * 64, ltm * OZ_BM, 0, &full[lst]);
+        tma_load_3d(stage_b(lst), &tmB, lkt * 64, ltn * OZ_BN, 0, &full[lst]);
+        lpar ^= 1u << lst;
+        lused |= 1u << lst;
+        lst = (lst + 1 == OZ_NST) ? 0 : lst + 1;
+        if (++lkt >= lke) cursor_unit(lu + gridDim.x);
+        return true;
+      };
+      bool ok = true;
+      for (int i = 0; i < OZ_NST - 1 && ok; ++i) ok = issue_load();
+      int st = 0;
+      uint32_t fpar = 0u, tpar = 0u;
+      bool any = false;
+      for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
+        const int z = u / (g.tiles_m * g.tiles_n);
+        const int kb = z * g.kt_per_split, ke = min(g.KT, kb + g.kt_per_split);
+        for (int kt = kb; kt < ke; ++kt) {
+          if (!mbar_wait(&full[st], (fpar >> st) & 1u) || s_fail) {
+            ok = false;
+            break;
+          }
+          // the accumulators are free once the drain of the previous stage
+          // has read them
+          if (!mbar_wait(&tempty, (tpar & 1u) ^ 1u) || s_fail) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(stage_a(st)), b0 = smem_u32(stage_b(st));
+          uint32_t started = 0;  // bit grp: accumulator grp written in this stage
+#pragma unroll
+          for (int d = OZ_S + 1; d >= 2; --d) {
+            const int grp = oz_group(d);
+#pragma unroll
+            for (int s = 1; s <= OZ_S; ++s) {
+              const int t = d - s;
+              if (t < 1 || t > OZ_S) continue;
+              // slice s (1-based) sits in pair (s-1)/2 at byte offset ((s-1)&1)*64
+              const uint32_t ao = (uint32_t)(((s - 1) >> 1) * OZ_PT_A + ((s - 1) & 1) * 64);
+              const uint32_t bo = (uint32_t)(((t - 1) >> 1) * OZ_PT_B + ((t - 1) & 1) * 64);
+#pragma unroll
+              for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+                const uint32_t acc = (started >> grp) & 1u;
+                mma_bf16(tmem + (uint32_t)(grp * OZ_BN), sw128_desc(a0 + ao + kk * 32),
+                         sw128_desc(b0 + bo + kk * 32), OZ_IDESC, acc);
+                started |= 1u << grp;
+              }
+            }
+          }
+          any = true;
+          mma_commit(&tfull);
+          tpar ^= 1u;
+          mma_commit(&empty[st]);
+          fpar ^= 1u << st;
+          st = (st + 1 == OZ_NST) ? 0 : st + 1;
+          if (!issue_load()) {
+            ok = false;
+            break;
+          }
+        }
+      }
+      if (!ok) {
+        s_fail = 1;
+        for (int i = 0; i < OZ_NST; ++i)
+          if ((lused >> i) & 1u) mbar_wait(&full[i], ((lpar >> i) & 1u) ^ 1u);
+      }
+      if (any) {
+        mma_commit(&done);
+        mbar_wait(&done, 0u);
+      }
     }
-    for (int item = tid; item < OZ_S * OZ_BN * 8; item += OZ_NT) {
-      const int s = item / (OZ_BN * 8), rem = item % (OZ_BN * 8), r = rem >> 3, c = rem & 7;
-      const int64_t gr = j0 + r;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (gr < g.N)
-        v = *reinterpret_cast<const uint4*>(g.Bs + (int64_t)s * g.N * g.Kp + gr * g.Kp + k0 + 8 * c);
-      *reinterpret_cast<uint4*>(Bs + s * B_SL + r * 128 + ((c ^ (r & 7)) << 4)) = v;
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    for (int half = 0; half < OZ_BK / OZ_KH; ++half) {
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = su32(As), b0 = su32(Bs);
-        uint32_t started = 0;  // bit g: accumulator g written in this half
+    __syncwarp();
+  } else {
+    // ------------------------------------------------ drain and epilogue
+    const int quad = warp & 3, half = (warp - 1) >> 2;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(half * OZ_CPT);
+    const int64_t MN = g.M * g.N;
+    uint32_t tpar = 0u;
+    bool ok = true;
+    for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
+      const int tm = u % g.tiles_m, rest = u / g.tiles_m;
+      const int tn = rest % g.tiles_n, z = rest / g.tiles_n;
+      const int kb = z * g.kt_per_split, ke = min(g.KT, kb + g.kt_per_split);
+      float hi[OZ_CPT], lo[OZ_CPT];
 #pragma unroll
-        for (int d = OZ_S + 1; d >= 2; --d) {
-          const int grp = oz_group(d);
+      for (int c = 0; c < OZ_CPT; ++c) hi[c] = lo[c] = 0.0f;
+      for (int kt = kb; kt < ke; ++kt) {
+        if (!mbar_wait(&tfull, tpar & 1u) || s_fail) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        // smallest groups first; each exact group sum goes into (hi, lo)
+#pragma unroll 1
+        for (int gp = OZ_NG - 1; gp >= 1; gp -= 2) {
+          float v[OZ_CPT], w[OZ_CPT];
+          tmem_ld32x2(lane_base + (uint32_t)(gp * OZ_BN), lane_base + (uint32_t)((gp - 1) * OZ_BN),
+                      v, w);
 #pragma unroll
-          for (int s = 1; s <= OZ_S; ++s) {
-            const int t = d - s;
-            if (t < 1 || t > OZ_S) continue;
+          for (int e = 0; e < OZ_CPT; ++e) {
+            float sm, err, sm2, err2;
+            two_sum(hi[e], v[e], sm, err);
+            two_sum(sm, w[e], sm2, err2);
+            hi[e] = sm2;
+            lo[e] += err + err2;
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty);
+        tpar ^= 1u;
+      }
+      if (!ok) break;
+      const int64_t r = (int64_t)tm * OZ_BM + 32 * quad + lane;
+      const int64_t c0 = (int64_t)tn * OZ_BN + half * OZ_CPT;
+      const int nval = (int)imin64(OZ_CPT, g.N - c0);
+      if (r < g.M && nval > 0) {
+        if (g.part != nullptr) {
+          float* ph = g.part + (int64_t)(2 * z) * MN + r + c0 * g.M;
 #pragma unroll
-            for (int kq = 0; kq < OZ_KH / 16; ++kq) {
-              const int kk = half * (OZ_KH / 16) + kq;
-              const uint32_t acc = (started >> grp) & 1u;
-              oz_mma(tmem + (uint32_t)(grp * OZ_BN),
-                     oz_desc(a0 + (uint32_t)((s - 1) * A_SL) + kk * 32),
-                     oz_desc(b0 + (uint32_t)((t - 1) * B_SL) + kk * 32), acc);
-              started |= 1u << grp;
+          for (int c = 0; c < OZ_CPT; ++c) {
+            if (c < nval) {
+              ph[0] = hi[c];
+              ph[MN] = lo[c];
+            }
+            ph += g.M;
+          }
+        } else {
+          const int ea = oz_scale_exp(g.expA[r]);
+          double* cp = g.C + r + c0 * g.ldc;
+          const int64_t ldc = g.ldc;
+          const double alpha = g.alpha, beta = g.beta;
+          const bool fast = (alpha == 1.0 || alpha == -1.0) && (beta == 0.0 || beta == 1.0);
+          const uint32_t neg = alpha < 0.0 ? 0x80000000u : 0u;
+#pragma unroll
+          for (int cb = 0; cb < OZ_CPT; cb += 16) {
+            double cv[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+              cv[e] = (beta != 0.0 && cb + e < nval) ? __ldcs(cp + (cb + e) * ldc) : 0.0;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const int c = cb + e;
+              if (c < nval) {
+                const int sc = ea + oz_scale_exp(__ldg(g.expB + c0 + c));
+                double out;
+                if (fast) {
+                  out = cv[e] + scaled_f64(hi[c], sc, neg);
+                  out = out + scaled_f64(lo[c], sc, neg);
+                } else {
+                  const double f = alpha * pow2(sc);
+                  out = fma(f, (double)hi[c], fma(f, (double)lo[c], beta * cv[e]));
+                }
+                __stcs(cp + c * ldc, out);
+              }
             }
           }
         }
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                su32(&mbar))
-            : "memory");
-        if (!oz_mbar_wait(&mbar, (uint32_t)((kt * (OZ_BK / OZ_KH) + half) & 1))) s_fail = 1;
       }
-      __syncthreads();
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (s_fail) break;
-      // ---- drain: add the exact group sums (smallest first) into the
-      // running double-FP32 sums of row 32 quad + lane, columns cbase..
-      const uint32_t lane_base = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)cbase;
-#pragma unroll
-      for (int c0 = 0; c0 < CPT; c0 += 16) {
-        float v[16], part_hi[16], part_lo[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) part_hi[e] = part_lo[e] = 0.0f;
-#pragma unroll
-        for (int grp = OZ_NG - 1; grp >= 0; --grp) {
-          oz_ld16(lane_base + (uint32_t)(grp * OZ_BN + c0), v);
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            float sm, err;
-            two_sum(part_hi[e], v[e], sm, err);
-            part_hi[e] = sm;
-            part_lo[e] += err;
-          }
-        }
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          float sm, err;
-          two_sum(hi[c0 + e], part_hi[e], sm, err);
-          hi[c0 + e] = sm;
-          lo[c0 + e] += err + part_lo[e];
-        }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();  // accumulators read before the next MMAs overwrite them
     }
-    if (s_fail) break;
+    if (!ok) s_fail = 1;
   }
 
-  if (s_fail) {
-    if (tid == 0) atomicOr(g.status, RQRCP_INFO_TIMEOUT);
-  } else {
-    const int64_t i = i0 + 32 * quad + lane;
-    if (i < g.M) {
-      const int ei = g.expA[i];
-#pragma unroll
-      for (int c = 0; c < CPT; ++c) {
-        const int64_t j = j0 + cbase + c;
-        if (j < g.N) {
-          const int sc = ei + g.expB[j];
-          const double x = ldexp((double)hi[c] + (double)lo[c], sc);
-          double* cp = g.C + i + j * g.ldc;
-          *cp = (g.beta != 0.0) ? fma(g.alpha, x, g.beta * *cp) : g.alpha * x;
-        }
-      }
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  if (tid == 0 && s_fail) atomicOr(g.status, RQRCP_INFO_TIMEOUT);
+  tc_fence_before();
   __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
-                 : "memory");
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, OZ_TCOLS);
+  }
+}
+
+// C = alpha 2^(e_i + f_j) sum_z (hi_z + lo_z) + beta C, the sum in FP64 in a
+// fixed order; splits = 0 gives C = beta C.
+__global__ void oz_reduce(const float* __restrict__ part, int splits, int64_t M, int64_t N,
+                          const int* __restrict__ expA, const int* __restrict__ expB, double alpha,
+                          double beta, double* __restrict__ C, int64_t ldc) {
+  const int64_t MN = M * N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < MN;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int z = 0; z < splits; ++z)
+      s += (double)part[(int64_t)(2 * z) * MN + e] + (double)part[(int64_t)(2 * z + 1) * MN + e];
+    const int64_t i = e % M, j = e / M;
+    double* cp = C + i + j * ldc;
+    const double v =
+        splits > 0 ? alpha * s * pow2(oz_scale_exp(expA[i]) + oz_scale_exp(expB[j])) : 0.0;
+    *cp = beta != 0.0 ? fma(beta, *cp, v) : v;
+  }
 }
 
 }  // namespace
 
-size_t oz_slice_bytes(int64_t rows, int64_t K) {
-  const int64_t Kp = (K + OZ_BK - 1) / OZ_BK * OZ_BK;
-  return (size_t)OZ_S * rows * Kp * 2 + (size_t)rows * 4 + 512;
-}
+int64_t oz_kpad(int64_t K) { return (K + OZ_KP - 1) / OZ_KP * OZ_KP; }
 
-int64_t oz_kpad(int64_t K) { return (K + OZ_BK - 1) / OZ_BK * OZ_BK; }
+size_t oz_slice_elems(int64_t rows, int64_t K) {
+  return (size_t)2 * OZ_PAIRS * rpad128(rows) * oz_kpad(K);
+}
 
 cudaError_t launch_oz_slice(const double* X, int64_t ld, bool kc, int amode, int64_t R, int64_t K,
                             __nv_bfloat16* slices, int* exps, cudaStream_t st) {
   if (R <= 0) return cudaSuccess;
-  const int64_t Kp = oz_kpad(K);
+  const int64_t Rp = rpad128(R), Kp = oz_kpad(K);
   const int warps = 8;
-  const unsigned grid = (unsigned)((R + warps - 1) / warps);
-  if (kc && amode == 1) oz_slice_kernel<true, 1><<<grid, 32 * warps, 0, st>>>(X, ld, R, K, Kp, slices, exps);
-  else if (kc) oz_slice_kernel<true, 0><<<grid, 32 * warps, 0, st>>>(X, ld, R, K, Kp, slices, exps);
-  else if (amode == 1) oz_slice_kernel<false, 1><<<grid, 32 * warps, 0, st>>>(X, ld, R, K, Kp, slices, exps);
-  else oz_slice_kernel<false, 0><<<grid, 32 * warps, 0, st>>>(X, ld, R, K, Kp, slices, exps);
+  const unsigned gx = (unsigned)((Rp + warps - 1) / warps);
+  if (!kc) {
+    if (amode == 1)
+      oz_slice_rows<1><<<gx, 32 * warps, 0, st>>>(X, ld, R, K, Rp, Kp, slices, exps);
+    else
+      oz_slice_rows<0><<<gx, 32 * warps, 0, st>>>(X, ld, R, K, Rp, Kp, slices, exps);
+    return cudaGetLastError();
+  }
+  cudaError_t e = cudaMemsetAsync(exps, 0, sizeof(int) * (size_t)R, st);
+  if (e != cudaSuccess) return e;
+  const dim3 g1((unsigned)((R + warps - 1) / warps), (unsigned)((K + OZ_KCH - 1) / OZ_KCH));
+  const dim3 g2(gx, (unsigned)((Kp + OZ_KCH - 1) / OZ_KCH));
+  if (K > 0) {
+    if (amode == 1)
+      oz_rowmax_cols<1><<<g1, 32 * warps, 0, st>>>(X, ld, R, K, exps);
+    else
+      oz_rowmax_cols<0><<<g1, 32 * warps, 0, st>>>(X, ld, R, K, exps);
+  }
+  if (amode == 1)
+    oz_slice_cols<1><<<g2, 32 * warps, 0, st>>>(X, ld, R, K, Rp, Kp, slices, exps);
+  else
+    oz_slice_cols<0><<<g2, 32 * warps, 0, st>>>(X, ld, R, K, Rp, Kp, slices, exps);
   return cudaGetLastError();
 }
 
-cudaError_t launch_oz_gemm(const OzGemmArgs& g, cudaStream_t st) {
-  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
-  const size_t smem = (size_t)OZ_S * ((size_t)OZ_BM + OZ_BN) * 128 + 1024;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
+int oz_slice_launches(bool kc, int64_t K) { return kc ? (K > 0 ? 2 : 1) : 1; }
+
+int oz_launches(int64_t M, int64_t N, int64_t Kp, int num_sms, size_t partial_cap) {
+  if (M <= 0 || N <= 0) return 0;
+  const int KT = (int)(Kp / OZ_BK);
+  if (KT == 0) return 1;
+  const int64_t tiles = (rpad128(M) / OZ_BM) * ((N + OZ_BN - 1) / OZ_BN);
+  int splits = 1;
+  if (partial_cap > 0 && tiles < num_sms && KT > 1) {
+    splits = (int)std::min<int64_t>((num_sms + tiles - 1) / tiles, KT);
+    while (splits > 1 && (size_t)2 * splits * M * N > partial_cap) --splits;
   }
-  dim3 grid((unsigned)((g.M + OZ_BM - 1) / OZ_BM), (unsigned)((g.N + OZ_BN - 1) / OZ_BN));
-  oz_gemm_kernel<<<grid, OZ_NT, smem, st>>>(g);
+  const int per = (KT + splits - 1) / splits;
+  splits = (KT + per - 1) / per;
+  return splits > 1 ? 2 : 1;
+}
+
+cudaError_t launch_oz_gemm(const OzGemmArgs& a, cudaStream_t st) {
+  if (a.M <= 0 || a.N <= 0) return cudaSuccess;
+  const int nsm = a.num_sms > 0 ? a.num_sms : 1;
+  const int KT = (int)(a.Kp / OZ_BK);
+  if (KT == 0) {
+    int64_t blocks = (a.M * a.N + 255) / 256;
+    if (blocks > (int64_t)nsm * 16) blocks = (int64_t)nsm * 16;
+    oz_reduce<<<(unsigned)blocks, 256, 0, st>>>(nullptr, 0, a.M, a.N, a.expA, a.expB, a.alpha,
+                                                a.beta, a.C, a.ldc);
+    return cudaGetLastError();
+  }
+  // both operands are stored with rows padded to 128 (see launch_oz_slice)
+  const int64_t RpA = rpad128(a.M), RpB = rpad128(a.N);
+  CUtensorMap ma, mb;
+  cudaError_t e = make_map_bf16_3d(&ma, a.As, (uint64_t)(2 * a.Kp), (uint64_t)RpA, OZ_PAIRS,
+                                   OZ_BM, OZ_PAIRS);
+  if (e != cudaSuccess) return e;
+  e = make_map_bf16_3d(&mb, a.Bs, (uint64_t)(2 * a.Kp), (uint64_t)RpB, OZ_PAIRS, OZ_BN, OZ_PAIRS);
+  if (e != cudaSuccess) return e;
+
+  OzArgs x{};
+  x.M = a.M;
+  x.N = a.N;
+  x.KT = KT;
+  x.tiles_m = (int)(RpA / OZ_BM);
+  x.tiles_n = (int)((a.N + OZ_BN - 1) / OZ_BN);
+  const int64_t tiles = (int64_t)x.tiles_m * x.tiles_n;
+  int splits = 1;
+  if (a.partial != nullptr && tiles < nsm && KT > 1) {
+    splits = (int)std::min<int64_t>((nsm + tiles - 1) / tiles, KT);
+    while (splits > 1 && (size_t)2 * splits * a.M * a.N > a.partial_cap) --splits;
+  }
+  x.kt_per_split = (KT + splits - 1) / splits;
+  splits = (KT + x.kt_per_split - 1) / x.kt_per_split;
+  x.units = (int)(tiles * splits);
+  x.alpha = a.alpha;
+  x.beta = a.beta;
+  x.C = a.C;
+  x.ldc = a.ldc;
+  x.expA = a.expA;
+  x.expB = a.expB;
+  x.part = splits > 1 ? a.partial : nullptr;
+  x.status = a.status;
+
+  const size_t smem = (size_t)OZ_NST * OZ_STAGE + 1024;
+  e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = (int)std::min<int64_t>(x.units, nsm);
+  oz_gemm_kernel<<<grid, OZ_NT, smem, st>>>(ma, mb, x);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || splits == 1) return e;
+  int64_t blocks = (a.M * a.N + 255) / 256;
+  if (blocks > (int64_t)nsm * 16) blocks = (int64_t)nsm * 16;
+  oz_reduce<<<(unsigned)blocks, 256, 0, st>>>(a.partial, splits, a.M, a.N, a.expA, a.expB, a.alpha,
+                                              a.beta, a.C, a.ldc);
   return cudaGetLastError();
 }
 

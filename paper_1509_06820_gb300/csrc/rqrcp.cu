@@ -182,9 +182,8 @@ Work carve(char op, int64_t m, int64_t n, int64_t k, int b, int p, int sms, char
     w.tslB = c.take<__nv_bfloat16>(w.tslcapB);
   } else if (op == 'X') {
     // slices of op(A) (m rows) and op(B)^T (n rows), K = k
-    const int64_t Kp = rq::oz_kpad(k);
-    w.slA = c.take<__nv_bfloat16>((size_t)7 * m * Kp);
-    w.slB = c.take<__nv_bfloat16>((size_t)7 * n * Kp);
+    w.slA = c.take<__nv_bfloat16>(rq::oz_slice_elems(m, k));
+    w.slB = c.take<__nv_bfloat16>(rq::oz_slice_elems(n, k));
     w.exA = c.take<int>(m);
     w.exB = c.take<int>(n);
   } else if (op == 'M') {
@@ -208,11 +207,9 @@ Work carve(char op, int64_t m, int64_t n, int64_t k, int b, int p, int sms, char
   }
   if (emul && (op == 'R' || op == 'Q')) {
     // slices of the trailing matrix A2^T (n rows of m) and of Y, W^T, and W^T itself
-    const int64_t Kp = rq::oz_kpad(m);
-    w.slA = c.take<__nv_bfloat16>((size_t)7 * n * Kp);
+    w.slA = c.take<__nv_bfloat16>(rq::oz_slice_elems(n, m));
     // Y sliced twice: b rows of m (as op(B) of Z^T), m rows of b (as op(A) of the update)
-    w.slB = c.take<__nv_bfloat16>(
-        (size_t)7 * std::max<int64_t>(bb * Kp, m * rq::oz_kpad(bb)));
+    w.slB = c.take<__nv_bfloat16>(std::max(rq::oz_slice_elems(bb, m), rq::oz_slice_elems(m, bb)));
     w.exA = c.take<int>(std::max(n, m));
     w.exB = c.take<int>(std::max(n, m));
   }
@@ -370,17 +367,23 @@ int trailing_update_emulated(Call& cl, const double* P, int64_t ld, int64_t mJ, 
   Work& w = cl.w;
   double* Zt = w.Z;  // n2 x bJ, ld n2
   double* Wt = w.W;  // n2 x bJ, ld n2
-  CKL(1, rq::launch_oz_slice(A2, ld, true, 0, n2, mJ, w.slA, w.exA, cl.st));
-  CKL(1, rq::launch_oz_slice(P, ld, true, 1, bJ, mJ, w.slB, w.exB, cl.st));
-  rq::OzGemmArgs z{n2, bJ, rq::oz_kpad(mJ), w.slA, w.exA, w.slB, w.exB, 1.0, 0.0, Zt, n2,
-                   cl.status};
-  CKL(1, rq::launch_oz_gemm(z, cl.st));
+  CKL(rq::oz_slice_launches(true, mJ),
+      rq::launch_oz_slice(A2, ld, true, 0, n2, mJ, w.slA, w.exA, cl.st));
+  CKL(rq::oz_slice_launches(true, mJ),
+      rq::launch_oz_slice(P, ld, true, 1, bJ, mJ, w.slB, w.exB, cl.st));
+  float* part = reinterpret_cast<float*>(w.skpart);
+  const size_t pcap = 2 * w.skcap;
+  rq::OzGemmArgs z{n2,   bJ,      rq::oz_kpad(mJ), w.slA,     w.exA, w.slB, w.exB, 1.0, 0.0,
+                   Zt,   n2,      cl.status,       part,      pcap,  cl.h->num_sms};
+  CKL(rq::oz_launches(n2, bJ, z.Kp, cl.h->num_sms, pcap), rq::launch_oz_gemm(z, cl.st));
   CK(gemm(cl, 'N', 'N', 0, n2, bJ, bJ, 1.0, Zt, n2, T, bJ, 0.0, Wt, n2));
-  CKL(1, rq::launch_oz_slice(P, ld, false, 1, mJ, bJ, w.slB, w.exB, cl.st));
-  CKL(1, rq::launch_oz_slice(Wt, n2, false, 0, n2, bJ, w.slA, w.exA, cl.st));
-  rq::OzGemmArgs u{mJ, n2, rq::oz_kpad(bJ), w.slB, w.exB, w.slA, w.exA, -1.0, 1.0, A2, ld,
-                   cl.status};
-  CKL(1, rq::launch_oz_gemm(u, cl.st));
+  CKL(rq::oz_slice_launches(false, bJ),
+      rq::launch_oz_slice(P, ld, false, 1, mJ, bJ, w.slB, w.exB, cl.st));
+  CKL(rq::oz_slice_launches(false, bJ),
+      rq::launch_oz_slice(Wt, n2, false, 0, n2, bJ, w.slA, w.exA, cl.st));
+  rq::OzGemmArgs u{mJ, n2, rq::oz_kpad(bJ), w.slB,  w.exB, w.slA,        w.exA, -1.0, 1.0,
+                   A2, ld, cl.status,       part,   pcap,  cl.h->num_sms};
+  CKL(rq::oz_launches(mJ, n2, u.Kp, cl.h->num_sms, pcap), rq::launch_oz_gemm(u, cl.st));
   return RQRCP_OK;
 }
 
@@ -1064,11 +1067,15 @@ int rqrcp_gemm_f64x(rqrcp_handle_t h, char transA, char transB, int64_t m, int64
   PhaseScope ps(h, PH_TRAIL, 2.0 * (double)m * (double)n * (double)k);
   // rows of op(A): stored columns when transposed; columns of op(B): stored
   // columns when not transposed
-  CKL(1, rq::launch_oz_slice(dA, lda, transA == 'T', 0, m, k, cl.w.slA, cl.w.exA, cl.st));
-  CKL(1, rq::launch_oz_slice(dB, ldb, transB == 'N', 0, n, k, cl.w.slB, cl.w.exB, cl.st));
-  rq::OzGemmArgs g{m, n, rq::oz_kpad(k), cl.w.slA, cl.w.exA, cl.w.slB, cl.w.exB, alpha, beta,
-                   dC, ldc, cl.status};
-  CKL(1, rq::launch_oz_gemm(g, cl.st));
+  CKL(rq::oz_slice_launches(transA == 'T', k),
+      rq::launch_oz_slice(dA, lda, transA == 'T', 0, m, k, cl.w.slA, cl.w.exA, cl.st));
+  CKL(rq::oz_slice_launches(transB == 'N', k),
+      rq::launch_oz_slice(dB, ldb, transB == 'N', 0, n, k, cl.w.slB, cl.w.exB, cl.st));
+  float* part = reinterpret_cast<float*>(cl.w.skpart);
+  const size_t pcap = 2 * cl.w.skcap;
+  rq::OzGemmArgs g{m,  n,   rq::oz_kpad(k), cl.w.slA, cl.w.exA, cl.w.slB,     cl.w.exB, alpha,
+                   beta, dC, ldc,           cl.status, part,    pcap,         cl.h->num_sms};
+  CKL(rq::oz_launches(m, n, g.Kp, cl.h->num_sms, pcap), rq::launch_oz_gemm(g, cl.st));
   return RQRCP_OK;
 }
 

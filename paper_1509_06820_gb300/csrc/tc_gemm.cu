@@ -38,12 +38,14 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
-#include <mutex>
 
 #include "kernels.cuh"
+#include "tcgen05.cuh"
 
 namespace rq {
 namespace {
+
+using namespace tc;
 
 constexpr int XBM = 128;          // tile rows (A role), UMMA M
 constexpr int XBN = 64;           // tile columns (B role), UMMA N
@@ -53,135 +55,7 @@ constexpr int XNT = 160;          // warp 0 TMA and MMA issue, warps 1..4 drain
 constexpr int XCH = 2;            // MMA k-steps per drained chunk (S = 3): 32 k
 constexpr int XTILE_A = XBM * 128;  // bytes of one A slice tile (128 rows x 64 k)
 constexpr int XTILE_B = XBN * 128;  // bytes of one B slice tile (64 rows x 64 k)
-constexpr unsigned kWaitPolls = 1u << 26;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-// Bounded wait for the phase with the given parity; false when it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (unsigned i = 0; i < kWaitPolls; ++i) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if (i > 64) __nanosleep(64);
-  }
-  return false;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (stride byte offset), descriptor version 1.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);  // start address
-  d |= (uint64_t)1 << 16;                     // leading byte offset (unused)
-  d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset
-  d |= (uint64_t)1 << 46;                     // version
-  d |= (uint64_t)2 << 61;                     // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B, both
-// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t XIDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(XBN >> 3) << 17) |
-                            ((uint32_t)(XBM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(XIDESC), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-// 32 columns of two accumulators (same lanes), then one wait for both loads.
-__device__ __forceinline__ void tmem_ld32x2(uint32_t ta, uint32_t tb, float* a, float* b) {
-  uint32_t r[64];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%64];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,"
-      "%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%65];\n"
-      "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
-        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]),
-        "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]),
-        "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]),
-        "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
-        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]),
-        "=r"(r[62]), "=r"(r[63])
-      : "r"(ta), "r"(tb)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    a[i] = __uint_as_float(r[i]);
-    b[i] = __uint_as_float(r[32 + i]);
-  }
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t ta, float* a) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15}, [%16];\n"
-      "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(ta)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) a[i] = __uint_as_float(r[i]);
-}
-
+constexpr uint32_t XIDESC = idesc_bf16_f32(XBM, XBN);
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&h);
@@ -305,13 +179,7 @@ __global__ void __launch_bounds__(XNT, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(&s_tmem)),
-                 "r"(TCOLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
+  if (warp == 0) tmem_alloc(&s_tmem, TCOLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -384,15 +252,15 @@ __global__ void __launch_bounds__(XNT, 1)
           const uint32_t a0 = smem_u32(stage_a(st)) + (uint32_t)sq * 32u;
           const uint32_t b0 = smem_u32(stage_b(st)) + (uint32_t)sq * 32u;
           const uint32_t d_big = tmem + (uint32_t)(buf * NACC * XBN);
-          mma_bf16(d_big, sw128_desc(a0), sw128_desc(b0), acc);  // x1 y1
+          mma_bf16(d_big, sw128_desc(a0), sw128_desc(b0), XIDESC, acc);  // x1 y1
           if (S == 3) {
             const uint32_t d_small = d_big + XBN;
             // correction products (s, t) with 2 < s + t <= 4
-            mma_bf16(d_small, sw128_desc(a0 + 2 * XTILE_A), sw128_desc(b0), acc);        // x3 y1
-            mma_bf16(d_small, sw128_desc(a0 + XTILE_A), sw128_desc(b0 + XTILE_B), 1u);   // x2 y2
-            mma_bf16(d_small, sw128_desc(a0), sw128_desc(b0 + 2 * XTILE_B), 1u);         // x1 y3
-            mma_bf16(d_small, sw128_desc(a0 + XTILE_A), sw128_desc(b0), 1u);             // x2 y1
-            mma_bf16(d_small, sw128_desc(a0), sw128_desc(b0 + XTILE_B), 1u);             // x1 y2
+            mma_bf16(d_small, sw128_desc(a0 + 2 * XTILE_A), sw128_desc(b0), XIDESC, acc);        // x3 y1
+            mma_bf16(d_small, sw128_desc(a0 + XTILE_A), sw128_desc(b0 + XTILE_B), XIDESC, 1u);   // x2 y2
+            mma_bf16(d_small, sw128_desc(a0), sw128_desc(b0 + 2 * XTILE_B), XIDESC, 1u);         // x1 y3
+            mma_bf16(d_small, sw128_desc(a0 + XTILE_A), sw128_desc(b0), XIDESC, 1u);             // x2 y1
+            mma_bf16(d_small, sw128_desc(a0), sw128_desc(b0 + XTILE_B), XIDESC, 1u);             // x1 y2
           }
           any = true;
           if (cend) {
@@ -523,8 +391,7 @@ __global__ void __launch_bounds__(XNT, 1)
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS)
-                 : "memory");
+    tmem_dealloc(tmem, TCOLS);
   }
 }
 
@@ -546,41 +413,13 @@ __global__ void tcx_reduce(const float* __restrict__ part, int splits, int64_t M
 }
 
 // ---------------------------------------------------------------- host side
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  });
-  return fn;
-}
-
 int64_t rpad(int64_t R, int tile) { return (R + tile - 1) / tile * tile; }
 int64_t kpad(int64_t K) { return (K + XBK - 1) / XBK * XBK; }
 
 // 3-D map over S slices of Rp rows x Kp k: box = 64 k x `rows` rows x S slices.
 cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t Rp, int64_t Kp, int S,
                      int rows) {
-  EncodeTiledFn fn = encode_fn();
-  if (fn == nullptr) return cudaErrorNotSupported;
-  const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)Rp, (cuuint64_t)S};
-  const cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Rp * Kp * 2};
-  const cuuint32_t box[3] = {(cuuint32_t)XBK, (cuuint32_t)rows, (cuuint32_t)S};
-  const cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(base), dims,
-                  strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+  return make_map_bf16_3d(map, base, (uint64_t)Kp, (uint64_t)Rp, (uint64_t)S, rows, S);
 }
 
 template <int S>
