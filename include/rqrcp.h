@@ -52,6 +52,7 @@ extern "C" {
 #define RQRCP_ERR_CUDA 1000
 #define RQRCP_ERR_ALLOC 1001
 #define RQRCP_ERR_UNSUPPORTED 1002
+#define RQRCP_ERR_BATCH 1003  /* a problem of trqrcp_batched failed its checks (see last_error) */
 
 #define RQRCP_INFO_NONFINITE 1  /* the sample held NaN/Inf: A is not finite */
 #define RQRCP_INFO_RESAMPLED 2  /* exactly singular R11: trailing sample re-drawn */
@@ -161,6 +162,51 @@ int trqrcp(rqrcp_handle_t handle, int64_t m, int64_t n, const double* dA, int64_
 int trqrcp_mixed(rqrcp_handle_t handle, int64_t m, int64_t n, const float* dA, int64_t lda,
                  int64_t k, int b, int p, uint64_t seed, int64_t* d_jpvt, double* d_tau,
                  float* dY, int64_t ldy, float* dR, int64_t ldr, double* d_rdiag);
+
+/*
+ * One problem of trqrcp_batched: the arguments of trqrcp_mixed.
+ */
+typedef struct rqrcp_problem {
+  int64_t m, n, k;
+  int b, p;
+  uint64_t seed;
+  const float* dA;
+  int64_t lda;
+  int64_t* d_jpvt;
+  double* d_tau;
+  float* dY;
+  int64_t ldy;
+  float* dR;
+  int64_t ldr;
+  double* d_rdiag;
+} rqrcp_problem;
+
+/*
+ * Many uneven-size mixed-precision TRQRCP problems (Alg. 6, as trqrcp_mixed;
+ * the served low-rank workload) in one call.  The paper factors one matrix
+ * at a time; this is the batched form of its truncated algorithm.
+ *   probs : host array of nprob problem descriptions (read during the call;
+ *           the device buffers they point to must not overlap)
+ *   lanes : 1..16 worker streams.  The problems are spread over the lanes
+ *           (longest first, by algorithmic flops); each lane has its own
+ *           scratch, re-sample flag and grid barrier, runs its problems in
+ *           order, and starts after, and is joined back to, the work already
+ *           enqueued on the handle's stream.  Results are those of
+ *           trqrcp_mixed on each problem alone.
+ * Every problem is checked before anything is enqueued: a failing problem
+ * returns RQRCP_ERR_BATCH (its index and status in rqrcp_last_error).  Lane
+ * scratch grows on demand (a device allocation, which is not allowed during
+ * stream capture): reserve it first with rqrcp_reserve_batched.  Device
+ * conditions of all problems are ORed into the handle's info word.
+ */
+int trqrcp_batched(rqrcp_handle_t handle, int nprob, const rqrcp_problem* probs, int lanes);
+
+/*
+ * Creates `lanes` worker lanes (1..16) and sizes each lane's scratch for
+ * problems up to m x n with rank k and block b, oversampling p.
+ */
+int rqrcp_reserve_batched(rqrcp_handle_t handle, int lanes, int64_t m, int64_t n, int64_t k,
+                          int b, int p);
 
 /*
  * Approximate truncated SVD -- Alg. 7 (TUXV) with j_max = 1:

@@ -21,6 +21,7 @@ RQRCP_OK = 0
 RQRCP_ERR_CUDA = 1000
 RQRCP_ERR_ALLOC = 1001
 RQRCP_ERR_UNSUPPORTED = 1002
+RQRCP_ERR_BATCH = 1003
 INFO_NONFINITE = 1
 INFO_RESAMPLED = 2
 INFO_TIMEOUT = 4
@@ -30,6 +31,15 @@ _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _I = ctypes.c_int
 _U64 = ctypes.c_uint64
+
+
+class Problem(ctypes.Structure):
+    """struct rqrcp_problem (include/rqrcp.h): one trqrcp_batched problem."""
+    _fields_ = [("m", _I64), ("n", _I64), ("k", _I64), ("b", _I), ("p", _I), ("seed", _U64),
+                ("dA", _P), ("lda", _I64), ("d_jpvt", _P), ("d_tau", _P), ("dY", _P),
+                ("ldy", _I64), ("dR", _P), ("ldr", _I64), ("d_rdiag", _P)]
+
+
 SIGNATURES = [
     ("rqrcp_create", _I, [ctypes.POINTER(_P), _P]),
     ("rqrcp_destroy", _I, [_P]),
@@ -46,6 +56,8 @@ SIGNATURES = [
     ("trqrcp", _I, [_P, _I64, _I64, _P, _I64, _I64, _I, _I, _U64, _P, _P, _P, _I64, _P, _I64]),
     ("trqrcp_mixed", _I, [_P, _I64, _I64, _P, _I64, _I64, _I, _I, _U64, _P, _P, _P, _I64, _P, _I64,
                           _P]),
+    ("trqrcp_batched", _I, [_P, _I, ctypes.POINTER(Problem), _I]),
+    ("rqrcp_reserve_batched", _I, [_P, _I, _I64, _I64, _I64, _I, _I]),
     ("tuxv", _I, [_P, _I64, _I64, _P, _I64, _I64, _I, _I, _U64, _P, _I64, _P, _I64, _P, _I64]),
     ("rqrcp_gaussian", _I, [_P, _U64, ctypes.c_uint32, _I64, _I64, _P, _I64]),
     ("rqrcp_sketch", _I, [_P, _I64, _I64, _P, _I64, _I, _U64, _P, _I64]),
@@ -110,6 +122,9 @@ class Handle:
     def reserve(self, op, m, n, k, b, p):
         _check(load().rqrcp_reserve(self.bind(), op.encode(), m, n, k, b, p), self.h)
 
+    def reserve_batched(self, lanes, m, n, k, b, p):
+        _check(load().rqrcp_reserve_batched(self.h, lanes, m, n, k, b, p), self.h)
+
     def set_fp64_emulation(self, on=True):
         """Run the FP64 trailing update on the BF16 tensor cores (exact slicing)."""
         _check(load().rqrcp_set_option(self.h, 1, 1 if on else 0), self.h)
@@ -157,7 +172,7 @@ def _check(code, h):
         return
     lib = load()
     msg = lib.rqrcp_status_string(code).decode()
-    if h is not None and code in (RQRCP_ERR_CUDA, RQRCP_ERR_ALLOC):
+    if h is not None and code in (RQRCP_ERR_CUDA, RQRCP_ERR_ALLOC, RQRCP_ERR_BATCH):
         msg += ": " + lib.rqrcp_last_error(h).decode()
     if code < 0:
         msg = f"argument {-code} invalid"
@@ -271,6 +286,36 @@ def trqrcp_mixed(A, k, b, p, seed, handle=None, out=None):
     _check(load().trqrcp_mixed(h.bind(), m, n, _ptr(A), _ld(A), k, b, p, seed, _ptr(jpvt),
                                _ptr(tau), _ptr(Y), _ld(Y), _ptr(R), _ld(R), _ptr(rdiag)), h.h)
     return jpvt, tau, Y, R, rdiag
+
+
+def trqrcp_batched(problems, lanes=8, handle=None, outs=None):
+    """Alg. 6 in mixed precision on many matrices in one call.  `problems` is a
+    list of (A, k, b, p, seed) with A a column-major float32 CUDA tensor;
+    returns one (jpvt, tau, Y, R, rdiag) tuple per problem, as trqrcp_mixed."""
+    if not problems:
+        return []
+    dev = problems[0][0].device
+    h = handle or default_handle(dev)
+    arr = (Problem * len(problems))()
+    results = []
+    for i, (A, k, b, p, seed) in enumerate(problems):
+        if A.device.type != "cuda" or A.dtype != torch.float32 or not _is_colmajor(A):
+            raise ValueError("A must be a column-major float32 CUDA tensor")
+        m, n = A.shape
+        if outs is not None:
+            out = outs[i]
+        else:
+            out = (torch.empty(n, dtype=torch.int64, device=A.device),
+                   torch.empty(k, dtype=torch.float64, device=A.device),
+                   empty_colmajor(m, k, A.device, torch.float32),
+                   empty_colmajor(k, n, A.device, torch.float32),
+                   torch.empty(k, dtype=torch.float64, device=A.device))
+        jpvt, tau, Y, R, rdiag = out
+        arr[i] = Problem(m, n, k, b, p, seed, _ptr(A), _ld(A), _ptr(jpvt), _ptr(tau), _ptr(Y),
+                         _ld(Y), _ptr(R), _ld(R), _ptr(rdiag))
+        results.append(out)
+    _check(load().trqrcp_batched(h.bind(), len(problems), arr, lanes), h.h)
+    return results
 
 
 def tuxv(A, k, b, p, seed, handle=None):

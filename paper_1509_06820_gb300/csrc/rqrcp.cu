@@ -31,6 +31,17 @@ struct rqrcp_handle_s {
   int64_t launch_total = 0;
   int cur_phase = 7;
   int fp64_emulation = 0;  // RQRCP_OPT_FP64_EMULATION
+  // worker lanes of trqrcp_batched: a stream, its scratch and its own
+  // re-sample flag and grid barrier each (the status word stays shared)
+  struct Lane {
+    cudaStream_t st = nullptr;
+    cudaEvent_t done = nullptr;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    int* state = nullptr;
+  };
+  std::vector<Lane> lanes;
+  cudaEvent_t fork = nullptr;
 };
 
 namespace {
@@ -476,6 +487,14 @@ int rqrcp_create(rqrcp_handle_t* handle, void* cuda_stream) {
 int rqrcp_destroy(rqrcp_handle_t h) {
   if (!h) return -1;
   cudaStreamSynchronize(h->stream);
+  for (auto& L : h->lanes) {
+    if (L.st) cudaStreamSynchronize(L.st);
+    if (L.ws) cudaFree(L.ws);
+    if (L.state) cudaFree(L.state);
+    if (L.done) cudaEventDestroy(L.done);
+    if (L.st) cudaStreamDestroy(L.st);
+  }
+  if (h->fork) cudaEventDestroy(h->fork);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   if (h->ws) cudaFree(h->ws);
   if (h->state) cudaFree(h->state);
@@ -535,6 +554,7 @@ const char* rqrcp_status_string(int code) {
     case RQRCP_ERR_CUDA: return "CUDA runtime error";
     case RQRCP_ERR_ALLOC: return "workspace allocation failed";
     case RQRCP_ERR_UNSUPPORTED: return "size outside the supported limits";
+    case RQRCP_ERR_BATCH: return "a problem of the batch failed its checks";
     case RQRCP_INFO_NONFINITE: return "non-finite input";
     case RQRCP_INFO_RESAMPLED: return "singular R11: sample re-drawn";
     case RQRCP_INFO_TIMEOUT: return "device wait timed out";
@@ -915,10 +935,15 @@ int rqrcp_factor_mixed(rqrcp_handle_t h, int64_t m, int64_t n, float* dA, int64_
   return RQRCP_OK;
 }
 
-int trqrcp_mixed(rqrcp_handle_t h, int64_t m, int64_t n, const float* dA, int64_t lda, int64_t k,
-                 int b, int p, uint64_t seed, int64_t* d_jpvt, double* d_tau, float* dY,
-                 int64_t ldy, float* dR, int64_t ldr, double* d_rdiag) {
-  if (!h) return -1;
+}  // extern "C"
+
+namespace {
+
+// Argument checks of trqrcp_mixed (0, -i for argument i, or
+// RQRCP_ERR_UNSUPPORTED); b is clamped to k.
+int check_trqrcp_mixed(int num_sms, int64_t m, int64_t n, const float* dA, int64_t lda, int64_t k,
+                       int& b, int p, const int64_t* d_jpvt, const double* d_tau, const float* dY,
+                       int64_t ldy, const float* dR, int64_t ldr, const double* d_rdiag) {
   if (m < 1) return -2;
   if (n < 1) return -3;
   if (!dA) return -4;
@@ -934,11 +959,17 @@ int trqrcp_mixed(rqrcp_handle_t h, int64_t m, int64_t n, const float* dA, int64_
   if (ldr < k) return -15;
   if (!d_rdiag) return -16;
   if (b > k) b = (int)k;
+  if (!sizes_fit(num_sms, m, n, b, b + p)) return RQRCP_ERR_UNSUPPORTED;
+  return RQRCP_OK;
+}
+
+// Alg. 6 in mixed precision on the call's stream and scratch (arguments
+// already checked, b <= k).
+int trqrcp_mixed_run(Call& cl, int64_t m, int64_t n, const float* dA, int64_t lda, int64_t k,
+                     int b, int p, uint64_t seed, int64_t* d_jpvt, double* d_tau, float* dY,
+                     int64_t ldy, float* dR, int64_t ldr, double* d_rdiag) {
   const int ell = b + p;
-  if (!sizes_fit(h->num_sms, m, n, b, ell)) return RQRCP_ERR_UNSUPPORTED;
-  Call cl;
-  int r = begin(h, 'V', m, n, k, b, p, &cl);
-  if (r) return r;
+  int r = RQRCP_OK;
   Work& w = cl.w;
   float* Ahat = w.Y32;
   float* Wt = w.W32;                                   // k x n, ld k
@@ -1016,6 +1047,161 @@ int trqrcp_mixed(rqrcp_handle_t h, int64_t m, int64_t n, const float* dA, int64_
     }
   }
   return RQRCP_OK;
+}
+
+
+}  // namespace
+
+extern "C" {
+
+int trqrcp_mixed(rqrcp_handle_t h, int64_t m, int64_t n, const float* dA, int64_t lda, int64_t k,
+                 int b, int p, uint64_t seed, int64_t* d_jpvt, double* d_tau, float* dY,
+                 int64_t ldy, float* dR, int64_t ldr, double* d_rdiag) {
+  if (!h) return -1;
+  int r = check_trqrcp_mixed(h->num_sms, m, n, dA, lda, k, b, p, d_jpvt, d_tau, dY, ldy, dR, ldr,
+                             d_rdiag);
+  if (r) return r;
+  Call cl;
+  r = begin(h, 'V', m, n, k, b, p, &cl);
+  if (r) return r;
+  return trqrcp_mixed_run(cl, m, n, dA, lda, k, b, p, seed, d_jpvt, d_tau, dY, ldy, dR, ldr,
+                          d_rdiag);
+}
+
+// ---------------------------------------------------------------- batched
+namespace {
+
+constexpr int kMaxLanes = 16;
+
+// Lanes 0..want-1 exist (stream, completion event, 256-byte state block).
+int ensure_lanes(rqrcp_handle_t h, int want) {
+  if ((int)h->lanes.size() >= want && h->fork) return RQRCP_OK;
+  cudaError_t e = cudaSuccess;
+  if (!h->fork) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
+  while (e == cudaSuccess && (int)h->lanes.size() < want) {
+    rqrcp_handle_s::Lane L;
+    e = cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&L.state, 256);
+    if (e == cudaSuccess) e = cudaMemset(L.state, 0, 256);
+    if (e != cudaSuccess) {
+      if (L.state) cudaFree(L.state);
+      if (L.done) cudaEventDestroy(L.done);
+      if (L.st) cudaStreamDestroy(L.st);
+      break;
+    }
+    h->lanes.push_back(L);
+  }
+  if (e != cudaSuccess) {
+    h->err = std::string("lanes: ") + cudaGetErrorString(e);
+    return RQRCP_ERR_ALLOC;
+  }
+  return RQRCP_OK;
+}
+
+int ensure_lane_ws(rqrcp_handle_t h, rqrcp_handle_s::Lane& L, size_t bytes) {
+  if (L.ws_bytes >= bytes) return RQRCP_OK;
+  cudaError_t e = cudaStreamSynchronize(L.st);
+  if (e == cudaSuccess && L.ws) e = cudaFree(L.ws);
+  L.ws = nullptr;
+  L.ws_bytes = 0;
+  if (e == cudaSuccess) e = cudaMalloc(&L.ws, bytes);
+  if (e != cudaSuccess) {
+    L.ws = nullptr;
+    h->err = std::string("lane workspace: ") + cudaGetErrorString(e);
+    return RQRCP_ERR_ALLOC;
+  }
+  L.ws_bytes = bytes;
+  return RQRCP_OK;
+}
+
+}  // namespace
+
+int rqrcp_reserve_batched(rqrcp_handle_t h, int lanes, int64_t m, int64_t n, int64_t k, int b,
+                          int p) {
+  if (!h) return -1;
+  if (lanes < 1 || lanes > kMaxLanes) return -2;
+  if (m < 1 || n < 1 || k < 1 || k > std::min(m, n) || b < 1 || p < 0) return -3;
+  if (b > k) b = (int)k;
+  int r = ensure_lanes(h, lanes);
+  if (r) return r;
+  const size_t bytes = carve('V', m, n, k, b, p, h->num_sms, nullptr).bytes;
+  for (int i = 0; i < lanes; ++i)
+    if ((r = ensure_lane_ws(h, h->lanes[i], bytes))) return r;
+  return RQRCP_OK;
+}
+
+int trqrcp_batched(rqrcp_handle_t h, int nprob, const rqrcp_problem* probs, int lanes) {
+  if (!h) return -1;
+  if (nprob < 0) return -2;
+  if (nprob > 0 && !probs) return -3;
+  if (lanes < 1 || lanes > kMaxLanes) return -4;
+  if (nprob == 0) return RQRCP_OK;
+  // every problem is checked before anything is enqueued
+  std::vector<int> bs(nprob);
+  for (int i = 0; i < nprob; ++i) {
+    const rqrcp_problem& q = probs[i];
+    int b = q.b;
+    const int r = check_trqrcp_mixed(h->num_sms, q.m, q.n, q.dA, q.lda, q.k, b, q.p, q.d_jpvt,
+                                     q.d_tau, q.dY, q.ldy, q.dR, q.ldr, q.d_rdiag);
+    if (r) {
+      h->err = "trqrcp_batched: problem " + std::to_string(i) + ": status " + std::to_string(r);
+      return RQRCP_ERR_BATCH;
+    }
+    bs[i] = b;
+  }
+  const int L = std::min(lanes, nprob);
+  int r = ensure_lanes(h, L);
+  if (r) return r;
+  // longest-processing-time-first assignment by algorithmic flops
+  std::vector<int> order(nprob);
+  for (int i = 0; i < nprob; ++i) order[i] = i;
+  auto work = [&](int i) {
+    const rqrcp_problem& q = probs[i];
+    return 2.0 * q.m * q.n * q.k + 2.0 * (bs[i] + q.p) * (double)q.m * q.n;
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return work(a) > work(c); });
+  std::vector<std::vector<int>> assign(L);
+  std::vector<double> load(L, 0.0);
+  std::vector<size_t> need(L, 0);
+  for (int i : order) {
+    const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    assign[l].push_back(i);
+    load[l] += work(i);
+    const rqrcp_problem& q = probs[i];
+    need[l] = std::max(need[l], carve('V', q.m, q.n, q.k, bs[i], q.p, h->num_sms, nullptr).bytes);
+  }
+  for (int l = 0; l < L; ++l)
+    if ((r = ensure_lane_ws(h, h->lanes[l], need[l]))) return r;
+  // fork from the handle's stream, run each lane's problems in order, join
+  const bool prof = h->prof;
+  h->prof = false;  // phase events are recorded on the handle's stream only
+  cudaError_t e = cudaEventRecord(h->fork, h->stream);
+  for (int l = 0; l < L && e == cudaSuccess && r == RQRCP_OK; ++l) {
+    rqrcp_handle_s::Lane& Ln = h->lanes[l];
+    e = cudaStreamWaitEvent(Ln.st, h->fork, 0);
+    for (size_t t = 0; t < assign[l].size() && e == cudaSuccess && r == RQRCP_OK; ++t) {
+      const int i = assign[l][t];
+      const rqrcp_problem& q = probs[i];
+      Call cl;
+      cl.h = h;
+      cl.w = carve('V', q.m, q.n, q.k, bs[i], q.p, h->num_sms, Ln.ws);
+      cl.st = Ln.st;
+      cl.status = h->state;  // shared: kernels OR their conditions into it
+      cl.flag = Ln.state + 1;
+      cl.bar = reinterpret_cast<rq::GridBarrier*>(reinterpret_cast<char*>(Ln.state) + 64);
+      r = trqrcp_mixed_run(cl, q.m, q.n, q.dA, q.lda, q.k, bs[i], q.p, q.seed, q.d_jpvt, q.d_tau,
+                           q.dY, q.ldy, q.dR, q.ldr, q.d_rdiag);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(Ln.done, Ln.st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, Ln.done, 0);
+  }
+  h->prof = prof;
+  if (e != cudaSuccess) {
+    h->err = std::string("trqrcp_batched: ") + cudaGetErrorString(e);
+    return RQRCP_ERR_CUDA;
+  }
+  return r;
 }
 
 int rqrcp_gemm_bf16x(rqrcp_handle_t h, char transA, char transB, int64_t m, int64_t n, int64_t k,

@@ -75,3 +75,80 @@ def test_poisson_run_reports_latency(lib):
     assert stats["requests"] > 50
     assert 0 < stats["p50_ms"] <= stats["p99_ms"]
     assert stats["throughput_rps"] > 0
+
+
+# uneven problems for the batched entry point: (m, n, k, b, p)
+BATCH = [(600, 900, 40, 32, 8), (1100, 700, 70, 64, 8), (300, 300, 16, 64, 8),
+         (900, 1200, 100, 128, 16), (512, 512, 32, 32, 8), (777, 1500, 64, 64, 16),
+         (150, 400, 20, 32, 8), (1200, 1000, 96, 64, 8), (420, 260, 50, 32, 16),
+         (1300, 1300, 128, 128, 16)]
+
+
+def _batch_inputs(seed0=0):
+    from paper_1509_06820_gb300 import colmajor
+    g = torch.Generator(device="cuda")
+    As = []
+    for i, (m, n, k, b, p) in enumerate(BATCH):
+        g.manual_seed(seed0 + i)
+        X = torch.randn((m, k), generator=g, device="cuda")
+        Yf = torch.randn((n, k), generator=g, device="cuda")
+        As.append(colmajor(X @ Yf.t()))
+    return As
+
+
+def test_trqrcp_batched_matches_individual(lib):
+    """trqrcp_batched over uneven problems on 4 lanes gives, bit for bit, what
+    trqrcp_mixed gives on each problem alone (same kernels, lanes only change
+    where a problem runs)."""
+    As = _batch_inputs()
+    probs = [(A, k, b, p, 11 + i) for i, (A, (m, n, k, b, p)) in enumerate(zip(As, BATCH))]
+    got = lib.trqrcp_batched(probs, lanes=4)
+    assert lib.sync_info() == 0
+    for (A, k, b, p, seed), out in zip(probs, got):
+        ref = lib.trqrcp_mixed(A, k, b, p, seed)
+        assert lib.sync_info() == 0
+        for x, y in zip(out, ref):
+            assert torch.equal(x, y)
+
+
+def test_trqrcp_batched_graph_replay(lib):
+    """A whole batch captured as one CUDA graph (fork to the lanes, join back)
+    replays on new data with the results of separate calls."""
+    h = lib.Handle()
+    h.reserve_batched(4, 1300, 1500, 128, 128, 16)
+    As = _batch_inputs(100)
+    bufs = [A.clone() for A in As]
+    probs = [(A, k, b, p, 5) for A, (m, n, k, b, p) in zip(bufs, BATCH)]
+    outs = lib.trqrcp_batched(probs, lanes=4, handle=h)  # eager run: sizes the lanes
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        lib.trqrcp_batched(probs, lanes=4, handle=h, outs=outs)
+    new = _batch_inputs(200)
+    for buf, A in zip(bufs, new):
+        buf.copy_(A)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert h.sync_info() == 0
+    for A, (m, n, k, b, p), out in zip(new, BATCH, outs):
+        ref = lib.trqrcp_mixed(A, k, b, p, 5)
+        for x, y in zip(out, ref):
+            assert torch.equal(x, y)
+
+
+def test_trqrcp_batched_rejects_before_launch(lib):
+    """One invalid problem (k > min(m, n)) fails the whole call with
+    RQRCP_ERR_BATCH before anything is enqueued."""
+    As = _batch_inputs()[:3]
+    ks = [16, 10**6, 16]
+    outs = [(torch.full((A.shape[1],), -7, dtype=torch.int64, device="cuda"),
+             torch.zeros(16, dtype=torch.float64, device="cuda"),
+             lib.empty_colmajor(A.shape[0], 16, "cuda", torch.float32),
+             lib.empty_colmajor(16, A.shape[1], "cuda", torch.float32),
+             torch.zeros(16, dtype=torch.float64, device="cuda")) for A in As]
+    probs = [(A, k, 16, 8, 1) for A, k in zip(As, ks)]
+    with pytest.raises(lib.RqrcpError, match="problem 1"):
+        lib.trqrcp_batched(probs, lanes=2, outs=outs)
+    torch.cuda.synchronize()
+    assert all(bool((o[0] == -7).all()) for o in outs)
