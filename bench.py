@@ -365,7 +365,57 @@ def serving_leg(args, dev):
     stats["autotune_s"] = tune_s
     stats["autotune_table"] = tuner.table
     stats["graphs_captured"] = sum(len(s.graphs) for s in srv.slots)
+    del srv
+    stats["batched"] = batched_leg(dev, tuner)
     return stats
+
+
+def batched_leg(dev, tuner, nprob=64, lanes=8, reps=5, seed=9):
+    """One static batch of served-size problems (m, n ~ U{256..4096},
+    k ~ U{16..128}, A = X Y^T in FP32, autotuned b/p) through trqrcp_batched
+    on `lanes` worker streams, captured as one CUDA graph and replayed."""
+    import numpy as np
+    import torch
+    import paper_1509_06820_gb300 as rq
+    from paper_1509_06820_gb300.serve import request_flops
+    rng = np.random.default_rng(seed)
+    specs = []
+    for _ in range(nprob):
+        m, n = int(rng.integers(256, 4097)), int(rng.integers(256, 4097))
+        k = int(min(rng.integers(16, 129), m, n))
+        b, p = tuner.choose(m, n, k)
+        specs.append((m, n, k, min(b, k), p))
+    g = torch.Generator(device=dev)
+    probs = []
+    for i, (m, n, k, b, p) in enumerate(specs):
+        g.manual_seed(1000 + i)
+        X = torch.randn((m, k), generator=g, device=dev)
+        Yf = torch.randn((n, k), generator=g, device=dev)
+        probs.append((rq.colmajor(X @ Yf.t()), k, b, p, 1000 + i))
+    h = rq.Handle(dev)
+    h.reserve_batched(lanes, max(s[0] for s in specs), max(s[1] for s in specs),
+                      max(s[2] for s in specs), max(s[3] for s in specs),
+                      max(s[4] for s in specs))
+    outs = rq.trqrcp_batched(probs, lanes=lanes, handle=h)
+    torch.cuda.synchronize(dev)
+    side = torch.cuda.Stream(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        rq.trqrcp_batched(probs, lanes=lanes, handle=h, outs=outs)
+    graph.replay()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    flops = sum(request_flops(m, n, k, b + p) for (m, n, k, b, p) in specs)
+    return {"problems": nprob, "lanes": lanes, "ms_per_batch": ms,
+            "problems_per_s": nprob / (ms / 1e3), "gflops": flops / (ms / 1e3) / 1e9,
+            "launch": "one CUDA graph per batch (fork to the lanes, join)",
+            "device_info": h.sync_info()}
 
 
 # ------------------------------------------------------------------ GPU leg
