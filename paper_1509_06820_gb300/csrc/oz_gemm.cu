@@ -13,12 +13,13 @@
 // 128-byte swizzled shared-memory row feeds the MMA with two slices.
 //
 // Products.  C_ij = 2^{e_i + f_j} sum_{s,t} sum_k a_s(i,k) b_t(k,j).  The pairs
-// with s + t = d carry the common grid 2^{-8d}; with K <= 32 per accumulation
-// their sum is an integer multiple of that grid below (d-1) 32 255^2 < 2^24
-// units for d <= 6, hence EXACT in an FP32 accumulator whatever the tensor
-// core's rounding (it truncates).  d = 2..6 get one accumulator each; d = 7, 8
-// share one (at most 2^-40 of the leading term, so even a truncating FP32 sum
-// of its 416 products errs below 2^-54); pairs with s + t > 8 are dropped
+// with s + t = d carry the common grid 2^{-8d}; with K <= 64 per accumulation
+// their sum is an integer multiple of that grid below (d-1) 64 255^2 < 2^24
+// units for d <= 5, hence EXACT in an FP32 accumulator whatever the tensor
+// core's rounding (it truncates).  d = 2..5 get one accumulator each; d = 6
+// gets one (its terms are below 2^-32 of the leading ones, so the truncation
+// of its 20 MMA additions per accumulation stays below 2^-42 of the leading
+// scale); d = 7, 8 share one (below 2^-40); pairs with s + t > 8 are dropped
 // (below 2^-56).  28 BF16 MMAs per 16-wide k step.
 //
 // Kernel (oz_gemm_kernel): persistent, one CTA per SM, 128 x 64 output tiles,
@@ -27,8 +28,8 @@
 //               (per 32-k stage one 3-D box per operand: 64 values x rows x 4
 //               pairs) into a two-stage shared-memory ring, and the 56 MMAs
 //               of a stage into the six accumulators (6 x 64 tensor-memory
-//               columns);
-//   warps 1-8   drain: after each stage, warp w adds the six exact group sums
+//               columns), which accumulate over two stages (64 k);
+//   warps 1-8   drain: after every two stages, warp w adds the six group sums
 //               of lanes 32 (w % 4).. (one output row per thread, 32 of the 64
 //               columns) into running double-FP32 sums (error-free TwoSum),
 //               smallest first; at the end of a unit it writes
@@ -59,7 +60,8 @@ constexpr int OZ_BITS = 8;     // bits per slice
 constexpr int OZ_NG = 6;       // accumulators: d = 2, 3, 4, 5, 6 and d >= 7
 constexpr int OZ_BM = 128;     // tile rows (A role), UMMA M
 constexpr int OZ_BN = 64;      // tile columns (B role), UMMA N
-constexpr int OZ_BK = 32;      // k per stage (one exact accumulation)
+constexpr int OZ_BK = 32;      // k per stage
+constexpr int OZ_DR = 2;       // stages per accumulation (drain every 64 k)
 constexpr int OZ_KP = 64;      // K padding of the slice buffers
 constexpr int OZ_NST = 2;      // shared-memory ring stages
 constexpr int OZ_NT = 288;     // warp 0 TMA and MMA issue, warps 1..8 drain
@@ -75,6 +77,24 @@ constexpr uint32_t OZ_TCOLS = 512;  // power of two >= 6 x 64
 __host__ __device__ constexpr int oz_group(int d) { return d - 2 < OZ_NG - 1 ? d - 2 : OZ_NG - 1; }
 
 int64_t rpad128(int64_t R) { return (R + OZ_BM - 1) / OZ_BM * OZ_BM; }
+
+// Split-K factor for `tiles` output tiles of KT stages on nsm persistent CTAs:
+// the smallest busiest-CTA stage count (rounds of units x stages per unit),
+// counting a split's partial-sum pass as two stages; at most `smax` splits.
+int pick_splits(int64_t tiles, int KT, int nsm, int smax) {
+  int best = 1;
+  int64_t best_cost = -1;
+  for (int sp = 1; sp <= smax && sp <= KT; ++sp) {
+    const int64_t rounds = (tiles * sp + nsm - 1) / nsm;
+    const int64_t per = (KT + sp - 1) / sp;
+    const int64_t cost = rounds * per + (sp > 1 ? 2 : 0);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = sp;
+    }
+  }
+  return best;
+}
 
 // ---------------------------------------------------------------- slicing
 // Rows of op(X): KC -> element (r, k) at X[r * ld + k] (a stored column per
@@ -109,11 +129,11 @@ __device__ __forceinline__ int oz_field(double x) {
 // out[((q * Rp + r) * (Kp / 32) + c) * 64 + h * 32 + kk] = slice 2q + h + 1 at
 // k = 32 c + kk; rows r >= R and the eighth slot are zero.
 template <bool KC, int AMODE>
-__device__ __forceinline__ void oz_slice_one(const double* __restrict__ X, int64_t ld, int64_t R,
-                                             int64_t K, int64_t Rp, int64_t Kp, int64_t r,
-                                             int64_t k, int e, __nv_bfloat16* __restrict__ out) {
+__device__ __forceinline__ unsigned long long oz_fixed(const double* __restrict__ X, int64_t ld,
+                                                       int64_t R, int64_t K, int64_t r, int64_t k,
+                                                       int e, bool& neg) {
   unsigned long long T = 0;
-  bool neg = false;
+  neg = false;
   if (r < R && k < K) {
     const unsigned long long b =
         (unsigned long long)__double_as_longlong(oz_elem<KC, AMODE>(X, ld, r, k));
@@ -127,16 +147,29 @@ __device__ __forceinline__ void oz_slice_one(const double* __restrict__ X, int64
     if (sh >= 0) T = m << sh;
     else if (sh > -64) T = m >> (-sh);
   }
+  return T;
+}
+
+__device__ __forceinline__ float oz_slice_val(unsigned long long T, bool neg, int s) {
+  const float y = (float)(unsigned)((T >> (8 * (OZ_S - 1 - s))) & 0xFFull);
+  return ldexpf(neg ? -y : y, -OZ_BITS * (s + 1));  // exact
+}
+
+// Slices of elements k and k + 1 (k even) of row r: one 4-byte store per
+// slice (the eighth slot of the last pair is never read and not written).
+template <bool KC, int AMODE>
+__device__ __forceinline__ void oz_slice_two(const double* __restrict__ X, int64_t ld, int64_t R,
+                                             int64_t K, int64_t Rp, int64_t Kp, int64_t r,
+                                             int64_t k, int e, __nv_bfloat16* __restrict__ out) {
+  bool n0, n1;
+  const unsigned long long T0 = oz_fixed<KC, AMODE>(X, ld, R, K, r, k, e, n0);
+  const unsigned long long T1 = oz_fixed<KC, AMODE>(X, ld, R, K, r, k + 1, e, n1);
   const size_t pstride = (size_t)Rp * Kp * 2;  // elements per pair plane
   __nv_bfloat16* p = out + (size_t)r * (Kp / 32) * 64 + (k >> 5) * 64 + (k & 31);
 #pragma unroll
-  for (int s = 0; s < 2 * OZ_PAIRS; ++s) {
-    float v = 0.0f;
-    if (s < OZ_S) {
-      const float y = (float)(unsigned)((T >> (8 * (OZ_S - 1 - s))) & 0xFFull);
-      v = ldexpf(neg ? -y : y, -OZ_BITS * (s + 1));  // exact
-    }
-    p[(size_t)(s >> 1) * pstride + (s & 1) * 32] = __float2bfloat16_rn(v);
+  for (int s = 0; s < OZ_S; ++s) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(oz_slice_val(T0, n0, s), oz_slice_val(T1, n1, s));
+    *reinterpret_cast<__nv_bfloat162*>(p + (size_t)(s >> 1) * pstride + (s & 1) * 32) = v;
   }
 }
 
@@ -156,8 +189,8 @@ __global__ void oz_slice_rows(const double* __restrict__ X, int64_t ld, int64_t 
   for (int o = 16; o > 0; o >>= 1) f = max(f, __shfl_xor_sync(0xffffffffu, f, o));
   if (lane == 0 && r < R) exps[r] = f;
   const int e = oz_scale_exp(f);
-  for (int64_t k = lane; k < Kp; k += 32)
-    oz_slice_one<false, AMODE>(X, ld, R, K, Rp, Kp, r, k, e, out);
+  for (int64_t k = 2 * lane; k < Kp; k += 64)
+    oz_slice_two<false, AMODE>(X, ld, R, K, Rp, Kp, r, k, e, out);
 }
 
 // Column-contiguous source (element (r, k) at X[r ld + k], K may be long):
@@ -189,8 +222,8 @@ __global__ void oz_slice_cols(const double* __restrict__ X, int64_t ld, int64_t 
   if (r >= Rp) return;
   const int e = oz_scale_exp(r < R ? exps[r] : 0);
   const int64_t k0 = (int64_t)blockIdx.y * OZ_KCH, k1 = imin64(Kp, k0 + OZ_KCH);
-  for (int64_t k = k0 + lane; k < k1; k += 32)
-    oz_slice_one<true, AMODE>(X, ld, R, K, Rp, Kp, r, k, e, out);
+  for (int64_t k = k0 + 2 * lane; k < k1; k += 64)
+    oz_slice_two<true, AMODE>(X, ld, R, K, Rp, Kp, r, k, e, out);
 }
 
 // ---------------------------------------------------------------- GEMM
@@ -301,20 +334,24 @@ __global__ void __launch_bounds__(OZ_NT, 1)
       for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
         const int z = u / (g.tiles_m * g.tiles_n);
         const int kb = z * g.kt_per_split, ke = min(g.KT, kb + g.kt_per_split);
+        uint32_t started = 0;  // bit grp: accumulator grp written in this accumulation
         for (int kt = kb; kt < ke; ++kt) {
+          const bool cstart = ((kt - kb) % OZ_DR) == 0;
+          const bool cend = ((kt - kb) % OZ_DR) == OZ_DR - 1 || kt == ke - 1;
           if (!mbar_wait(&full[st], (fpar >> st) & 1u) || s_fail) {
             ok = false;
             break;
           }
-          // the accumulators are free once the drain of the previous stage
-          // has read them
-          if (!mbar_wait(&tempty, (tpar & 1u) ^ 1u) || s_fail) {
-            ok = false;
-            break;
+          if (cstart) {
+            // the accumulators are free once the previous drain has read them
+            if (!mbar_wait(&tempty, (tpar & 1u) ^ 1u) || s_fail) {
+              ok = false;
+              break;
+            }
+            started = 0;
           }
           tc_fence_after();
           const uint32_t a0 = smem_u32(stage_a(st)), b0 = smem_u32(stage_b(st));
-          uint32_t started = 0;  // bit grp: accumulator grp written in this stage
 #pragma unroll
           for (int d = OZ_S + 1; d >= 2; --d) {
             const int grp = oz_group(d);
@@ -335,8 +372,10 @@ __global__ void __launch_bounds__(OZ_NT, 1)
             }
           }
           any = true;
-          mma_commit(&tfull);
-          tpar ^= 1u;
+          if (cend) {
+            mma_commit(&tfull);
+            tpar ^= 1u;
+          }
           mma_commit(&empty[st]);
           fpar ^= 1u << st;
           st = (st + 1 == OZ_NST) ? 0 : st + 1;
@@ -371,13 +410,13 @@ __global__ void __launch_bounds__(OZ_NT, 1)
       float hi[OZ_CPT], lo[OZ_CPT];
 #pragma unroll
       for (int c = 0; c < OZ_CPT; ++c) hi[c] = lo[c] = 0.0f;
-      for (int kt = kb; kt < ke; ++kt) {
+      for (int kt = kb; kt < ke; kt += OZ_DR) {
         if (!mbar_wait(&tfull, tpar & 1u) || s_fail) {
           ok = false;
           break;
         }
         tc_fence_after();
-        // smallest groups first; each exact group sum goes into (hi, lo)
+        // smallest groups first; each group sum goes into (hi, lo)
 #pragma unroll 1
         for (int gp = OZ_NG - 1; gp >= 1; gp -= 2) {
           float v[OZ_CPT], w[OZ_CPT];
@@ -418,13 +457,14 @@ __global__ void __launch_bounds__(OZ_NT, 1)
           const int64_t ldc = g.ldc;
           const double alpha = g.alpha, beta = g.beta;
           const bool fast = (alpha == 1.0 || alpha == -1.0) && (beta == 0.0 || beta == 1.0);
+          const bool use_c = beta != 0.0;
           const uint32_t neg = alpha < 0.0 ? 0x80000000u : 0u;
 #pragma unroll
           for (int cb = 0; cb < OZ_CPT; cb += 16) {
             double cv[16];
 #pragma unroll
             for (int e = 0; e < 16; ++e)
-              cv[e] = (beta != 0.0 && cb + e < nval) ? __ldcs(cp + (cb + e) * ldc) : 0.0;
+              cv[e] = (use_c && cb + e < nval) ? __ldcs(cp + (cb + e) * ldc) : 0.0;
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
               const int c = cb + e;
@@ -436,7 +476,7 @@ __global__ void __launch_bounds__(OZ_NT, 1)
                   out = out + scaled_f64(lo[c], sc, neg);
                 } else {
                   const double f = alpha * pow2(sc);
-                  out = fma(f, (double)hi[c], fma(f, (double)lo[c], beta * cv[e]));
+                  out = fma(f, (double)hi[c], fma(f, (double)lo[c], use_c ? beta * cv[e] : 0.0));
                 }
                 __stcs(cp + c * ldc, out);
               }
@@ -522,10 +562,9 @@ int oz_launches(int64_t M, int64_t N, int64_t Kp, int num_sms, size_t partial_ca
   if (KT == 0) return 1;
   const int64_t tiles = (rpad128(M) / OZ_BM) * ((N + OZ_BN - 1) / OZ_BN);
   int splits = 1;
-  if (partial_cap > 0 && tiles < num_sms && KT > 1) {
-    splits = (int)std::min<int64_t>((num_sms + tiles - 1) / tiles, KT);
-    while (splits > 1 && (size_t)2 * splits * M * N > partial_cap) --splits;
-  }
+  if (partial_cap > 0 && tiles < num_sms && KT > 1)
+    splits = pick_splits(tiles, KT, num_sms,
+                         (int)std::min<size_t>(64, partial_cap / (2 * (size_t)M * N)));
   const int per = (KT + splits - 1) / splits;
   splits = (KT + per - 1) / per;
   return splits > 1 ? 2 : 1;
@@ -559,10 +598,9 @@ cudaError_t launch_oz_gemm(const OzGemmArgs& a, cudaStream_t st) {
   x.tiles_n = (int)((a.N + OZ_BN - 1) / OZ_BN);
   const int64_t tiles = (int64_t)x.tiles_m * x.tiles_n;
   int splits = 1;
-  if (a.partial != nullptr && tiles < nsm && KT > 1) {
-    splits = (int)std::min<int64_t>((nsm + tiles - 1) / tiles, KT);
-    while (splits > 1 && (size_t)2 * splits * a.M * a.N > a.partial_cap) --splits;
-  }
+  if (a.partial != nullptr && tiles < nsm && KT > 1)
+    splits = pick_splits(tiles, KT, nsm,
+                         (int)std::min<size_t>(64, a.partial_cap / (2 * (size_t)a.M * a.N)));
   x.kt_per_split = (KT + splits - 1) / splits;
   splits = (KT + x.kt_per_split - 1) / x.kt_per_split;
   x.units = (int)(tiles * splits);

@@ -414,6 +414,24 @@ __global__ void tcx_reduce(const float* __restrict__ part, int splits, int64_t M
 
 // ---------------------------------------------------------------- host side
 int64_t rpad(int64_t R, int tile) { return (R + tile - 1) / tile * tile; }
+
+// Split-K factor for `tiles` output tiles of KT stages on nsm persistent CTAs:
+// the smallest busiest-CTA stage count (rounds of units x stages per unit),
+// counting a split's partial-sum pass as two stages; at most `smax` splits.
+int pick_splits(int64_t tiles, int KT, int nsm, int smax) {
+  int best = 1;
+  int64_t best_cost = -1;
+  for (int sp = 1; sp <= smax && sp <= KT; ++sp) {
+    const int64_t rounds = (tiles * sp + nsm - 1) / nsm;
+    const int64_t per = (KT + sp - 1) / sp;
+    const int64_t cost = rounds * per + (sp > 1 ? 2 : 0);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = sp;
+    }
+  }
+  return best;
+}
 int64_t kpad(int64_t K) { return (K + XBK - 1) / XBK * XBK; }
 
 // 3-D map over S slices of Rp rows x Kp k: box = 64 k x `rows` rows x S slices.
@@ -479,10 +497,9 @@ cudaError_t run(TcGemmArgs g, cudaStream_t st) {
   x.tiles_n = (int)(Rn / XBN);
   const int64_t tiles = (int64_t)x.tiles_m * x.tiles_n;
   int splits = 1;
-  if (g.partial != nullptr && tiles < nsm && KT > 1) {
-    splits = (int)std::min<int64_t>((nsm + tiles - 1) / tiles, KT);
-    while (splits > 1 && (size_t)2 * splits * g.M * g.N > g.partial_cap) --splits;
-  }
+  if (g.partial != nullptr && tiles < nsm && KT > 1)
+    splits = pick_splits(tiles, KT, nsm,
+                         (int)std::min<size_t>(64, g.partial_cap / (2 * (size_t)g.M * g.N)));
   x.kt_per_split = (KT + splits - 1) / splits;
   splits = (KT + x.kt_per_split - 1) / x.kt_per_split;
   x.units = (int)(tiles * splits);
@@ -520,10 +537,9 @@ int tc_launches(int64_t M, int64_t N, int64_t K, int num_sms, size_t partial_cap
   const int64_t tiles = (rpad(M, XBM) / XBM) * (rpad(N, XBN) / XBN);
   const int KT = (int)(kpad(K) / XBK);
   int splits = 1;
-  if (partial_cap > 0 && tiles < num_sms && KT > 1) {
-    splits = (int)std::min<int64_t>((num_sms + tiles - 1) / tiles, KT);
-    while (splits > 1 && (size_t)2 * splits * M * N > partial_cap) --splits;
-  }
+  if (partial_cap > 0 && tiles < num_sms && KT > 1)
+    splits = pick_splits(tiles, KT, num_sms,
+                         (int)std::min<size_t>(64, partial_cap / (2 * (size_t)M * N)));
   const int per = (KT + splits - 1) / splits;
   splits = (KT + per - 1) / per;
   return splits > 1 ? 4 : 3;
