@@ -16,6 +16,10 @@ namespace rq {
 // does nothing unless *gate != 0.
 cudaError_t launch_gaussian(uint64_t seed, uint32_t stream_id, int64_t rows, int64_t cols,
                             double* out, int64_t ld, const int* gate, cudaStream_t st);
+// The same rows x cols matrix stored transposed (element (i, r) at out[r + i ld],
+// ld >= cols).
+cudaError_t launch_gaussian_t(uint64_t seed, uint32_t stream_id, int64_t rows, int64_t cols,
+                              double* out, int64_t ld, cudaStream_t st);
 
 // ---- gemm_f64.cu: C = alpha op(A) op(B) + beta C (column-major FP64).
 // amode: how A is read -- 0 plain, 1 unit-lower-trapezoidal (entries above the

@@ -220,7 +220,9 @@ Work carve(char op, int64_t m, int64_t n, int64_t k, int b, int p, int sms, char
     // slices of the trailing matrix A2^T (n rows of m) and of Y, W^T, and W^T itself
     w.slA = c.take<__nv_bfloat16>(rq::oz_slice_elems(n, m));
     // Y sliced twice: b rows of m (as op(B) of Z^T), m rows of b (as op(A) of the update)
-    w.slB = c.take<__nv_bfloat16>(std::max(rq::oz_slice_elems(bb, m), rq::oz_slice_elems(m, bb)));
+    // (and the l x m Omega of the sketch)
+    w.slB = c.take<__nv_bfloat16>(std::max(rq::oz_slice_elems(std::max<int64_t>(bb, ell), m),
+                                           rq::oz_slice_elems(m, bb)));
     w.exA = c.take<int>(std::max(n, m));
     w.exB = c.take<int>(std::max(n, m));
   }
@@ -640,8 +642,23 @@ int rqrcp_factor(rqrcp_handle_t h, int64_t m, int64_t n, double* dA, int64_t lda
   // Alg. 4: Omega^[0] and the initial sample B^[0] = Omega^[0] A^[0]
   {
     PhaseScope ps(cl.h, PH_SKETCH, 2.0 * ell * (double)m * (double)n);
-    CKL(1, rq::launch_gaussian(seed, kOmegaStream, ell, m, w.omega, ell, nullptr, cl.st));
-    CK(gemm(cl, 'N', 'N', 0, ell, n, m, 1.0, w.omega, ell, dA, lda, 0.0, w.B, ell));
+    if (w.slA != nullptr) {
+      // FP64-accurate product on the tensor cores: Omega stored transposed so
+      // that its rows are contiguous for the slicing pass
+      CKL(1, rq::launch_gaussian_t(seed, kOmegaStream, ell, m, w.omega, m, cl.st));
+      CKL(rq::oz_slice_launches(true, m),
+          rq::launch_oz_slice(w.omega, m, true, 0, ell, m, w.slB, w.exB, cl.st));
+      CKL(rq::oz_slice_launches(true, m),
+          rq::launch_oz_slice(dA, lda, true, 0, n, m, w.slA, w.exA, cl.st));
+      float* part = reinterpret_cast<float*>(w.skpart);
+      const size_t pcap = 2 * w.skcap;
+      rq::OzGemmArgs sk{ell, n,  rq::oz_kpad(m), w.slB, w.exB, w.slA,         w.exA, 1.0, 0.0,
+                        w.B, ell, cl.status,     part,  pcap,  cl.h->num_sms};
+      CKL(rq::oz_launches(ell, n, sk.Kp, cl.h->num_sms, pcap), rq::launch_oz_gemm(sk, cl.st));
+    } else {
+      CKL(1, rq::launch_gaussian(seed, kOmegaStream, ell, m, w.omega, ell, nullptr, cl.st));
+      CK(gemm(cl, 'N', 'N', 0, ell, n, m, 1.0, w.omega, ell, dA, lda, 0.0, w.B, ell));
+    }
     CKL(1, rq::launch_iota(d_jpvt, n, cl.st));
   }
   int J = 0;
