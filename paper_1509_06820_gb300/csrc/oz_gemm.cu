@@ -23,13 +23,14 @@
 // (below 2^-56).  28 BF16 MMAs per 16-wide k step.
 //
 // Kernel (oz_gemm_kernel): persistent, one CTA per SM, 128 x 64 output tiles,
-// split-K units, 5 warps:
-//   warp 0      allocates tensor memory; one thread issues the TMA copies
-//               (per 32-k stage one 3-D box per operand: 64 values x rows x 4
-//               pairs) into a two-stage shared-memory ring, and the 56 MMAs
-//               of a stage into the six accumulators (6 x 64 tensor-memory
+// split-K units, 10 warps:
+//   warp 0      one thread issues the TMA copies (per 32-k stage one 3-D box
+//               per operand: 64 values x rows x 4 pairs) into a two-stage
+//               shared-memory ring, refilling a slot as soon as its MMAs end;
+//   warp 1      allocates tensor memory; one thread issues the 56 MMAs of a
+//               stage into the six accumulators (6 x 64 tensor-memory
 //               columns), which accumulate over two stages (64 k);
-//   warps 1-8   drain: after every two stages, warp w adds the six group sums
+//   warps 2-9   drain: after every two stages, warp w adds the six group sums
 //               of lanes 32 (w % 4).. (one output row per thread, 32 of the 64
 //               columns) into running double-FP32 sums (error-free TwoSum),
 //               smallest first; at the end of a unit it writes
@@ -64,7 +65,7 @@ constexpr int OZ_BK = 32;      // k per stage
 constexpr int OZ_DR = 2;       // stages per accumulation (drain every 64 k)
 constexpr int OZ_KP = 64;      // K padding of the slice buffers
 constexpr int OZ_NST = 2;      // shared-memory ring stages
-constexpr int OZ_NT = 288;     // warp 0 TMA and MMA issue, warps 1..8 drain
+constexpr int OZ_NT = 320;     // warp 0 TMA, warp 1 MMA issue, warps 2..9 drain
 constexpr int OZ_CPT = 32;     // output columns per drain thread (two warps per lane quadrant)
 constexpr int OZ_PT_A = OZ_BM * 128;          // bytes of one A pair tile
 constexpr int OZ_PT_B = OZ_BN * 128;          // bytes of one B pair tile
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(OZ_NT, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
   }
-  if (warp == 0) tmem_alloc(&s_tmem, OZ_TCOLS);
+  if (warp == 1) tmem_alloc(&s_tmem, OZ_TCOLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -298,39 +299,43 @@ __global__ void __launch_bounds__(OZ_NT, 1)
   auto stage_b = [&](int st) { return smem + (size_t)st * OZ_STAGE + OZ_STAGE_A; };
 
   if (warp == 0) {
-    // ------------------------------------------------ TMA + MMA issue
+    // ------------------------------------------------ TMA producer
+    // refills each ring slot as soon as the MMAs that read it have completed
     if (lane == 0) {
-      int lu = 0, lkt = 0, lke = 0, ltm = 0, ltn = 0;  // cursor of the next copy
-      auto cursor_unit = [&](int u) {
-        lu = u;
-        if (lu < g.units) {
-          ltm = lu % g.tiles_m;
-          const int rest = lu / g.tiles_m;
-          ltn = rest % g.tiles_n;
-          lkt = (rest / g.tiles_n) * g.kt_per_split;
-          lke = min(g.KT, lkt + g.kt_per_split);
-        }
-      };
-      cursor_unit(blockIdx.x);
       int lst = 0;
       uint32_t lpar = 0u, lused = 0u;
-      auto issue_load = [&]() -> bool {
-        if (lu >= g.units) return true;
-        if (!mbar_wait(&empty[lst], ((lpar >> lst) & 1u) ^ 1u)) return false;
-        mbar_expect_tx(&full[lst], OZ_STAGE);
-        tma_load_3d(stage_a(lst), &tmA, lkt * 64, ltm * OZ_BM, 0, &full[lst]);
-        tma_load_3d(stage_b(lst), &tmB, lkt * 64, ltn * OZ_BN, 0, &full[lst]);
-        lpar ^= 1u << lst;
-        lused |= 1u << lst;
-        lst = (lst + 1 == OZ_NST) ? 0 : lst + 1;
-        if (++lkt >= lke) cursor_unit(lu + gridDim.x);
-        return true;
-      };
       bool ok = true;
-      for (int i = 0; i < OZ_NST - 1 && ok; ++i) ok = issue_load();
+      for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
+        const int tm = u % g.tiles_m, rest = u / g.tiles_m;
+        const int tn = rest % g.tiles_n;
+        const int kb = (rest / g.tiles_n) * g.kt_per_split, ke = min(g.KT, kb + g.kt_per_split);
+        for (int kt = kb; kt < ke; ++kt) {
+          if (!mbar_wait(&empty[lst], ((lpar >> lst) & 1u) ^ 1u) || s_fail) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[lst], OZ_STAGE);
+          tma_load_3d(stage_a(lst), &tmA, kt * 64, tm * OZ_BM, 0, &full[lst]);
+          tma_load_3d(stage_b(lst), &tmB, kt * 64, tn * OZ_BN, 0, &full[lst]);
+          lpar ^= 1u << lst;
+          lused |= 1u << lst;
+          lst = (lst + 1 == OZ_NST) ? 0 : lst + 1;
+        }
+      }
+      if (!ok) {
+        s_fail = 1;
+        // wait (bounded) for the last copy issued on each slot
+        for (int i = 0; i < OZ_NST; ++i)
+          if ((lused >> i) & 1u) mbar_wait(&full[i], ((lpar >> i) & 1u) ^ 1u);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------------------------ MMA issue
+    if (lane == 0) {
       int st = 0;
       uint32_t fpar = 0u, tpar = 0u;
-      bool any = false;
+      bool ok = true, any = false;
       for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
         const int z = u / (g.tiles_m * g.tiles_n);
         const int kb = z * g.kt_per_split, ke = min(g.KT, kb + g.kt_per_split);
@@ -372,25 +377,18 @@ __global__ void __launch_bounds__(OZ_NT, 1)
             }
           }
           any = true;
+          mma_commit(&empty[st]);
+          fpar ^= 1u << st;
+          st = (st + 1 == OZ_NST) ? 0 : st + 1;
           if (cend) {
             mma_commit(&tfull);
             tpar ^= 1u;
           }
-          mma_commit(&empty[st]);
-          fpar ^= 1u << st;
-          st = (st + 1 == OZ_NST) ? 0 : st + 1;
-          if (!issue_load()) {
-            ok = false;
-            break;
-          }
         }
       }
-      if (!ok) {
-        s_fail = 1;
-        for (int i = 0; i < OZ_NST; ++i)
-          if ((lused >> i) & 1u) mbar_wait(&full[i], ((lpar >> i) & 1u) ^ 1u);
-      }
+      if (!ok) s_fail = 1;
       if (any) {
+        // every MMA of this thread has completed once this commit arrives
         mma_commit(&done);
         mbar_wait(&done, 0u);
       }
@@ -398,7 +396,7 @@ __global__ void __launch_bounds__(OZ_NT, 1)
     __syncwarp();
   } else {
     // ------------------------------------------------ drain and epilogue
-    const int quad = warp & 3, half = (warp - 1) >> 2;
+    const int quad = warp & 3, half = (warp - 2) >> 2;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(half * OZ_CPT);
     const int64_t MN = g.M * g.N;
     uint32_t tpar = 0u;
@@ -491,7 +489,7 @@ __global__ void __launch_bounds__(OZ_NT, 1)
   if (tid == 0 && s_fail) atomicOr(g.status, RQRCP_INFO_TIMEOUT);
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem, OZ_TCOLS);
   }

@@ -20,13 +20,14 @@
 // accumulated over the whole k range.
 //
 // Kernel (tcx_gemm_kernel): persistent, one CTA per SM, 128 x 64 output
-// tiles, split-K units; 5 warps with fixed roles:
-//   warp 0      allocates tensor memory; one thread issues the TMA copies
-//               (per 64-k stage one 3-D box per operand: 64 k x rows x S
-//               slices, 128-byte swizzle) into a three-stage shared-memory
-//               ring (mbarrier expect-tx), the tcgen05.mma (M = 128, N = 64,
-//               K = 16) and the tcgen05.commit;
-//   warps 1-4   drain: warp w reads accumulator lanes 32 (w % 4).. (one row
+// tiles, split-K units; 6 warps with fixed roles:
+//   warp 0      one thread issues the TMA copies (per 64-k stage one 3-D box
+//               per operand: 64 k x rows x S slices, 128-byte swizzle) into a
+//               three-stage shared-memory ring (mbarrier expect-tx), refilling
+//               a slot as soon as the MMAs that read it have completed;
+//   warp 1      allocates tensor memory; one thread issues the tcgen05.mma
+//               (M = 128, N = 64, K = 16) and the tcgen05.commit;
+//   warps 2-5   drain: warp w reads accumulator lanes 32 (w % 4).. (one row
 //               per thread, 64 columns), adds into the compensated sums and,
 //               at the end of a unit, writes C (or its split-K partial sums).
 // The accumulators are double-buffered in tensor memory (2 x 2 x 64
@@ -51,7 +52,7 @@ constexpr int XBM = 128;          // tile rows (A role), UMMA M
 constexpr int XBN = 64;           // tile columns (B role), UMMA N
 constexpr int XBK = 64;           // k per pipeline stage: one 128-byte swizzle row
 constexpr int XNST = 3;           // shared-memory ring stages
-constexpr int XNT = 160;          // warp 0 TMA and MMA issue, warps 1..4 drain
+constexpr int XNT = 192;          // warp 0 TMA, warp 1 MMA issue, warps 2..5 drain
 constexpr int XCH = 2;            // MMA k-steps per drained chunk (S = 3): 32 k
 constexpr int XTILE_A = XBM * 128;  // bytes of one A slice tile (128 rows x 64 k)
 constexpr int XTILE_B = XBN * 128;  // bytes of one B slice tile (64 rows x 64 k)
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(XNT, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
   }
-  if (warp == 0) tmem_alloc(&s_tmem, TCOLS);
+  if (warp == 1) tmem_alloc(&s_tmem, TCOLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -189,40 +190,41 @@ __global__ void __launch_bounds__(XNT, 1)
   auto stage_b = [&](int st) { return smem + (size_t)st * STAGE_TX + STAGE_A; };
 
   if (warp == 0) {
-    // ------------------------------------------------ TMA + MMA issue
-    // One thread walks the stages of its units in order.  It keeps XNST - 1
-    // copies ahead: after issuing the MMAs of stage i it refills the ring slot
-    // of stage i - 1 (once those MMAs have completed) with stage i + XNST - 1.
+    // ------------------------------------------------ TMA producer
+    // refills each ring slot as soon as the MMAs that read it have completed
     if (lane == 0) {
-      int lu = 0, lkt = 0, lke = 0, ltm = 0, ltn = 0;  // cursor of the next copy
-      auto cursor_unit = [&](int u) {
-        lu = u;
-        if (lu < g.units) {
-          ltm = lu % g.tiles_m;
-          const int rest = lu / g.tiles_m;
-          ltn = rest % g.tiles_n;
-          lkt = (rest / g.tiles_n) * g.kt_per_split;
-          lke = min(g.KT, lkt + g.kt_per_split);
-        }
-      };
-      cursor_unit(blockIdx.x);
-      // per ring slot: parity of its use count (bit st) and whether it was used
       int lst = 0;
-      uint32_t lpar = 0u, lused = 0u;
-      auto issue_load = [&]() -> bool {
-        if (lu >= g.units) return true;
-        if (!mbar_wait(&empty[lst], ((lpar >> lst) & 1u) ^ 1u)) return false;
-        mbar_expect_tx(&full[lst], STAGE_TX);
-        tma_load_3d(stage_a(lst), &tmA, lkt * XBK, ltm * XBM, 0, &full[lst]);
-        tma_load_3d(stage_b(lst), &tmB, lkt * XBK, ltn * XBN, 0, &full[lst]);
-        lpar ^= 1u << lst;
-        lused |= 1u << lst;
-        lst = (lst + 1 == XNST) ? 0 : lst + 1;
-        if (++lkt >= lke) cursor_unit(lu + gridDim.x);
-        return true;
-      };
+      uint32_t lpar = 0u, lused = 0u;  // per slot: parity of its uses, used at all
       bool ok = true;
-      for (int i = 0; i < XNST - 1 && ok; ++i) ok = issue_load();
+      for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
+        const int tm = u % g.tiles_m, rest = u / g.tiles_m;
+        const int tn = rest % g.tiles_n;
+        const int kb = (rest / g.tiles_n) * g.kt_per_split, ke = min(g.KT, kb + g.kt_per_split);
+        for (int kt = kb; kt < ke; ++kt) {
+          if (!mbar_wait(&empty[lst], ((lpar >> lst) & 1u) ^ 1u) || s_fail) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[lst], STAGE_TX);
+          tma_load_3d(stage_a(lst), &tmA, kt * XBK, tm * XBM, 0, &full[lst]);
+          tma_load_3d(stage_b(lst), &tmB, kt * XBK, tn * XBN, 0, &full[lst]);
+          lpar ^= 1u << lst;
+          lused |= 1u << lst;
+          lst = (lst + 1 == XNST) ? 0 : lst + 1;
+        }
+      }
+      if (!ok) {
+        s_fail = 1;
+        // wait (bounded) for the last copy issued on each slot
+        for (int i = 0; i < XNST; ++i)
+          if ((lused >> i) & 1u) mbar_wait(&full[i], ((lpar >> i) & 1u) ^ 1u);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------------------------ MMA issue
+    if (lane == 0) {
+      bool ok = true;
       int st = 0, buf = 0;
       uint32_t fpar = 0u, tpar = 0u;  // parities of the full[] and tempty[] uses
       bool any = false;
@@ -272,19 +274,10 @@ __global__ void __launch_bounds__(XNT, 1)
             mma_commit(&empty[st]);
             fpar ^= 1u << st;
             st = (st + 1 == XNST) ? 0 : st + 1;
-            if (!issue_load()) {
-              ok = false;
-              break;
-            }
           }
         }
       }
-      if (!ok) {
-        s_fail = 1;
-        // wait (bounded) for the last copy issued on each slot
-        for (int i = 0; i < XNST; ++i)
-          if ((lused >> i) & 1u) mbar_wait(&full[i], ((lpar >> i) & 1u) ^ 1u);
-      }
+      if (!ok) s_fail = 1;
       if (any) {
         // every MMA of this thread has completed once this commit arrives
         mma_commit(&done);
@@ -389,7 +382,7 @@ __global__ void __launch_bounds__(XNT, 1)
   if (tid == 0 && s_fail) atomicOr(g.status, RQRCP_INFO_TIMEOUT);
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem, TCOLS);
   }
