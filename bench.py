@@ -355,17 +355,26 @@ def serving_leg(args, dev):
     tuner = Tuner.tune([(1024, 1024, 64), (2048, 2048, 96), (4096, 4096, 128), (2048, 4096, 32)],
                        device=dev)
     tune_s = time.perf_counter() - t0
-    srv = Server.on_gpu(dev, slots=8, tuner=tuner)
+    # primary: slots that launch each request's kernels directly (no graph
+    # capture on the host's critical path)
+    srv = Server.on_gpu(dev, slots=8, tuner=tuner, use_graphs=False)
     stats = srv.run_poisson(rate=args.serve_rate, duration=args.serve_seconds, warmup=1.0, seed=7)
+    stats = {"mode": "eager launches per request", **stats}
     # the same server below saturation, for the service-time latency
     low = srv.run_poisson(rate=args.serve_rate / 5, duration=min(5.0, args.serve_seconds),
                           warmup=0.5, seed=8)
     stats["below_saturation"] = {k: low[k] for k in ("offered_rate", "requests", "throughput_rps",
                                                      "p50_ms", "p99_ms", "gflops")}
+    del srv
+    # the same stream with per-(slot, size bucket) CUDA graphs captured on first use
+    gsrv = Server.on_gpu(dev, slots=8, tuner=tuner)
+    gst = gsrv.run_poisson(rate=args.serve_rate, duration=args.serve_seconds, warmup=1.0, seed=7)
+    stats["graphs"] = {k: gst[k] for k in ("offered_rate", "requests", "throughput_rps", "p50_ms",
+                                           "p99_ms", "gflops")}
+    stats["graphs"]["graphs_captured"] = sum(len(s.graphs) for s in gsrv.slots)
+    del gsrv
     stats["autotune_s"] = tune_s
     stats["autotune_table"] = tuner.table
-    stats["graphs_captured"] = sum(len(s.graphs) for s in srv.slots)
-    del srv
     stats["batched"] = batched_leg(dev, tuner)
     return stats
 
@@ -499,9 +508,24 @@ def main():
     fp64_peak = bf16 * 1.25 / 2250.0      # nominal FP64 : BF16 dense ratio
     tr_ms, tr_fl, tr_launch = prof["trailing_update"]
     achieved = tr_fl / (tr_ms / 1e3) / 1e12 if tr_ms > 0 else None
+    # DRAM traffic of the trailing update: its algorithmic bytes (A2 read by
+    # Z = Y^T A2, read and written by A2 -= Y W) times the ratio of measured to
+    # algorithmic DRAM bytes of the same three kernels in an ncu capture on a
+    # 6144^2 factorization (837.8 MB / 890.2 MB); traffic grows with m_J n2 as
+    # the algorithmic bytes do.  Per launch, like `achieved`.
+    alg_bytes = 0.0
+    j0 = 0
+    while j0 < min(m, n):
+        bJ = min(b, min(m, n) - j0)
+        alg_bytes += 24.0 * (m - j0) * (n - j0 - bJ)
+        j0 += bJ
+    traffic = 0.941 * alg_bytes / max(tr_launch, 1)
     roofline = {"bound": "alu", "kernel": "trailing update (gemm_kernel FP64 FFMA)",
                 "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak if achieved else None, "traffic": None,
+                "frac": achieved / fp64_peak if achieved else None, "traffic": traffic,
+                "traffic_unit": "bytes per launch",
+                "traffic_source": "algorithmic bytes x 0.941 (ncu DRAM bytes / algorithmic bytes, "
+                                  "same kernels, 6144^2 factorization)",
                 "peak_source": "MEASURED_PEAKS bf16_tflops x 1.25/2250 (nominal FP64/BF16 ratio)",
                 "peak_nominal": 1.25,
                 "frac_nominal": achieved / 1.25 if achieved else None,

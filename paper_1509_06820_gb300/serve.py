@@ -124,11 +124,11 @@ class Slot:
             A, outs = self._buffers(req.bucket)
             graph = None
             self._reserve(M, N, K, req.b, req.p)
-            with torch.cuda.stream(self.stream):
-                A.zero_()
-                # eager run first: sets kernel attributes and sizes the scratch
-                trqrcp_mixed(A, K, req.b, req.p, 1, handle=self.handle, out=outs)
             if self.use_graphs:
+                with torch.cuda.stream(self.stream):
+                    A.zero_()
+                    # eager run first: sets kernel attributes and sizes the scratch
+                    trqrcp_mixed(A, K, req.b, req.p, 1, handle=self.handle, out=outs)
                 self.stream.synchronize()
                 graph = torch.cuda.CUDAGraph()
                 with torch.cuda.graph(graph, stream=self.stream):
