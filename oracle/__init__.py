@@ -18,7 +18,8 @@ Contents (paper sections in brackets):
 * ``householder`` -- Householder reflector, unblocked panel QR, compact-WY T
                      factor and block-reflector application [Sec. 2.1-2.2, Sec. 5.1].
 * ``rqrcp``       -- partial QRCP on the sample [Alg. 1, Sec. 5], RQRCP with the
-                     sample update formula [Alg. 4, Eq. (3)], the unpivoted
+                     sample update formula [Alg. 4, Eq. (3)], repeated-sampling
+                     RQRCP [Alg. 5], the unpivoted
                      blocked QR it reduces to [Table 3 note], TRQRCP [Alg. 6]
                      and TUXV [Alg. 7].
 
@@ -31,6 +32,7 @@ from . import philox, householder, rqrcp  # noqa: F401
 from .rqrcp import (  # noqa: F401
     sample_qrcp,
     rqrcp,
+    rsrqrcp,
     qr_blocked,
     trqrcp,
     tuxv,

@@ -167,8 +167,15 @@ def _resample(seed, J, ell, trailing):
 
 
 def rqrcp(A, b, p, seed=0, k=None, omega=None, replay_jpvt=None, tie_rtol=1e-8,
-          trace=None, ties=None):
+          trace=None, ties=None, resample_every_block=False, omega_fn=None):
     """Randomized QR with column pivoting, Alg. 4, on a copy of A.
+
+    resample_every_block: Alg. 5 (RSRQRCP) instead -- before every block after
+      the first, a fresh GIID sample of the trailing matrix (Philox stream
+      0x100 + J after block J) replaces the sample update of Eq. (3).
+    omega_fn: optional omega_fn(J, rows) -> l x rows matrix used for those
+      fresh samples instead of the Philox generator (J = 1, 2, ... counts the
+      finished blocks).
 
     Returns (F, jpvt, tau, info): F holds R on and above the diagonal and the
     reflectors below it (rows j0.., columns of each panel); jpvt[c] is the
@@ -221,7 +228,14 @@ def rqrcp(A, b, p, seed=0, k=None, omega=None, replay_jpvt=None, tie_rtol=1e-8,
         if j0 + bJ < k:
             R11 = F[j0:j0 + bJ, j0:j0 + bJ]
             R12 = F[j0:j0 + bJ, j0 + bJ:]
-            if np.any(np.diag(R11) == 0.0):
+            if resample_every_block:
+                # Alg. 5: a new GIID compression of the updated trailing matrix.
+                trailing = F[j0 + bJ:, j0 + bJ:]
+                if omega_fn is None:
+                    B = _resample(seed, J, ell, trailing)
+                else:
+                    B = np.asarray(omega_fn(J, trailing.shape[0]), dtype=np.float64) @ trailing
+            elif np.any(np.diag(R11) == 0.0):
                 info = 2
                 B = _resample(seed, J, ell, F[j0 + bJ:, j0 + bJ:])
             else:
@@ -232,6 +246,15 @@ def rqrcp(A, b, p, seed=0, k=None, omega=None, replay_jpvt=None, tie_rtol=1e-8,
                               Vb=Vb, taub=taub, Y=Y.copy(), T=T.copy(),
                               B_out=B.copy() if j0 + bJ < k else None))
     return F, jpvt, tau, info
+
+
+def rsrqrcp(A, b, p, seed=0, k=None, replay_jpvt=None, tie_rtol=1e-8, ties=None,
+            omega=None, omega_fn=None):
+    """Repeated-sampling RQRCP, Alg. 5: Alg. 4 with the sample of every block
+    formed anew from the trailing matrix, B^[J] = Omega^[J] A^[J] (Omega^[0]
+    as in Alg. 4, then Philox stream 0x100 + J).  Same returns as rqrcp."""
+    return rqrcp(A, b, p, seed=seed, k=k, omega=omega, replay_jpvt=replay_jpvt,
+                 tie_rtol=tie_rtol, ties=ties, resample_every_block=True, omega_fn=omega_fn)
 
 
 def qr_blocked(A, b):

@@ -11,6 +11,9 @@ What pins what:
 * sample update         -- Eq. (1)-(3): with Q_b and Q formed explicitly,
   W = Q_b^T Omega Q has W21 = 0 and the updated sample equals the explicit
   re-sample [W12; W22] A^[J] of the trailing matrix, block after block.
+* RSRQRCP (Alg. 5)      -- A P = Q R; with every sample drawn through
+  orthonormal columns the pivots and R are dgeqp3's; its first block is
+  Alg. 4's.
 * TRQRCP                -- equals RQRCP truncated to the same rank (Sec. 6:
   same pivots, reflectors and rows of R).
 * TUXV                  -- U, V orthonormal, X upper triangular, U X = A V and
@@ -251,3 +254,49 @@ def test_tuxv_properties():
     Qk = hh.form_q(Y, tt, k)
     e_tr = np.linalg.norm(A - Qk @ (Qk.T @ A))
     assert e_svd * (1 - 1e-10) <= e_tuxv <= e_tr * (1 + 1e-10)
+
+
+# ---------------------------------------------------------------- RSRQRCP (Alg. 5)
+@pytest.mark.parametrize("m,n,b,p", [(120, 100, 16, 8), (100, 120, 16, 8), (97, 97, 32, 8),
+                                     (200, 30, 64, 8)])
+def test_rsrqrcp_factorization(m, n, b, p):
+    """Alg. 5: A P = Q R with Q orthogonal and R upper triangular."""
+    A = synth.gaussian(m, n, seed=7)
+    F, jpvt, tau, info = oracle.rsrqrcp(A, b, p, seed=1)
+    assert info == 0
+    assert sorted(jpvt) == list(range(n))
+    Q = hh.form_q(F, tau, m)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(m), atol=1e-13)
+    assert np.linalg.norm(A[:, jpvt] - Q @ np.triu(F)) < 1e-14 * np.linalg.norm(A)
+
+
+@pytest.mark.parametrize("m,n,b", [(30, 24, 4), (40, 40, 8), (25, 60, 5), (60, 20, 7)])
+def test_rsrqrcp_exact_samples_reproduce_qrcp(m, n, b):
+    """With every sample drawn through orthonormal columns (l = m), each
+    block's sample norms are the true trailing column norms, so Alg. 5's pivots
+    and R are deterministic QRCP's (LAPACK dgeqp3 via scipy)."""
+    r = np.random.default_rng(m * n + 1)
+    A = r.standard_normal((m, n)) * (0.7 ** np.arange(n))[None, :]
+    A = A[:, r.permutation(n)]
+    Om, _ = np.linalg.qr(r.standard_normal((m, m)))
+
+    def omega_fn(J, rows):
+        Q, _ = np.linalg.qr(r.standard_normal((m, m)))
+        return Q[:, :rows]
+    F, jpvt, tau, info = oracle.rsrqrcp(A, b, 0, omega=Om, omega_fn=omega_fn)
+    Rs, piv = sla.qr(A, pivoting=True, mode="r")
+    k = min(m, n)
+    np.testing.assert_array_equal(jpvt[:k], piv[:k])
+    np.testing.assert_allclose(np.triu(F)[:k], Rs[:k], atol=1e-12 * np.abs(Rs).max())
+
+
+def test_rsrqrcp_first_block_equals_rqrcp():
+    """Alg. 4 and Alg. 5 share Omega^[0] and the first block, so the first b
+    pivots, reflectors and rows of R coincide; later blocks differ only
+    through the samples (both stay valid factorizations)."""
+    A = synth.gaussian(80, 70, seed=3)
+    F1, j1, t1, _ = oracle.rqrcp(A, 16, 8, seed=4)
+    F2, j2, t2, _ = oracle.rsrqrcp(A, 16, 8, seed=4)
+    np.testing.assert_array_equal(j1[:16], j2[:16])
+    np.testing.assert_allclose(t1[:16], t2[:16], atol=1e-14)
+    np.testing.assert_allclose(np.triu(F1)[:16, :16], np.triu(F2)[:16, :16], atol=1e-12)
