@@ -78,12 +78,17 @@ size_t rqrcp_workspace_bytes(char op, int64_t m, int64_t n, int64_t k, int b, in
  * not allocate, e.g. before stream capture). */
 int rqrcp_reserve(rqrcp_handle_t handle, char op, int64_t m, int64_t n, int64_t k, int b, int p);
 
-/* Handle options.  RQRCP_OPT_FP64_EMULATION (value 0/1, default 0): run the
- * two large products of the FP64 trailing update (rqrcp_factor, qr_factor;
- * blocks of b <= 64) on the BF16 tensor cores with the FP64-accurate slicing
- * of rqrcp_gemm_f64x instead of the FP64 pipe.  Its scratch adds 14 bytes
- * per element of A. */
+/* Handle options (value 0/1, default 0).
+ * RQRCP_OPT_FP64_EMULATION: run the sketch and the two large products of the
+ * FP64 trailing update (rqrcp_factor, qr_factor; blocks of b <= 64) on the
+ * BF16 tensor cores with the FP64-accurate slicing of rqrcp_gemm_f64x instead
+ * of the FP64 pipe.  Its scratch adds 16 bytes per element of A.
+ * RQRCP_OPT_RESAMPLE: rqrcp_factor runs Alg. 5 (RSRQRCP) -- before every block
+ * after the first, a fresh seeded GIID sample of the updated trailing matrix
+ * (Philox stream 0x100 + J after block J) replaces the sample update of
+ * Eq. (3); the paper's comparison for the cost of repeated sampling. */
 #define RQRCP_OPT_FP64_EMULATION 1
+#define RQRCP_OPT_RESAMPLE 2
 int rqrcp_set_option(rqrcp_handle_t handle, int option, int value);
 
 /* Wait for the handle's stream, then return the device status word in *info

@@ -22,6 +22,8 @@ RQRCP_ERR_CUDA = 1000
 RQRCP_ERR_ALLOC = 1001
 RQRCP_ERR_UNSUPPORTED = 1002
 RQRCP_ERR_BATCH = 1003
+OPT_FP64_EMULATION = 1
+OPT_RESAMPLE = 2
 INFO_NONFINITE = 1
 INFO_RESAMPLED = 2
 INFO_TIMEOUT = 4
@@ -127,7 +129,11 @@ class Handle:
 
     def set_fp64_emulation(self, on=True):
         """Run the FP64 trailing update on the BF16 tensor cores (exact slicing)."""
-        _check(load().rqrcp_set_option(self.h, 1, 1 if on else 0), self.h)
+        _check(load().rqrcp_set_option(self.h, OPT_FP64_EMULATION, 1 if on else 0), self.h)
+
+    def set_resample(self, on=True):
+        """rqrcp_factor runs Alg. 5 (a fresh sample every block) instead of Eq. (3)."""
+        _check(load().rqrcp_set_option(self.h, OPT_RESAMPLE, 1 if on else 0), self.h)
 
     def profile(self, enable=True):
         _check(load().rqrcp_profile(self.h, 1 if enable else 0), self.h)

@@ -31,6 +31,7 @@ struct rqrcp_handle_s {
   int64_t launch_total = 0;
   int cur_phase = 7;
   int fp64_emulation = 0;  // RQRCP_OPT_FP64_EMULATION
+  int resample = 0;        // RQRCP_OPT_RESAMPLE: Alg. 5 instead of Eq. (3)
   // worker lanes of trqrcp_batched: a stream, its scratch and its own
   // re-sample flag and grid barrier each (the status word stays shared)
   struct Lane {
@@ -532,6 +533,10 @@ int rqrcp_set_option(rqrcp_handle_t h, int option, int value) {
     h->fp64_emulation = value != 0;
     return RQRCP_OK;
   }
+  if (option == RQRCP_OPT_RESAMPLE) {
+    h->resample = value != 0;
+    return RQRCP_OK;
+  }
   return -2;
 }
 
@@ -676,7 +681,29 @@ int rqrcp_factor(rqrcp_handle_t h, int64_t m, int64_t n, double* dA, int64_t lda
     if ((r = panel_step(cl, P, lda, mJ, bJ, d_tau + j0, w.T))) return r;
     // R12 and the trailing matrix A^[J]
     if ((r = trailing_update(cl, P, lda, mJ, bJ, w.T, dA + j0 + (j0 + bJ) * lda, n2))) return r;
-    if (j0 + bJ < k) {
+    if (j0 + bJ < k && h->resample) {
+      // Alg. 5 (RSRQRCP): a fresh GIID sample of the updated trailing matrix
+      const int64_t mt = m - j0 - bJ;
+      double* Bnext = Bblk + (int64_t)bJ * ell;
+      const double* At = dA + (j0 + bJ) + (j0 + bJ) * lda;
+      PhaseScope ps(cl.h, PH_SUPD, 2.0 * ell * (double)mt * (double)n2);
+      if (w.slA != nullptr) {
+        CKL(1, rq::launch_gaussian_t(seed, kResampleStreamBase + J, ell, mt, w.omega, mt, cl.st));
+        CKL(rq::oz_slice_launches(true, mt),
+            rq::launch_oz_slice(w.omega, mt, true, 0, ell, mt, w.slB, w.exB, cl.st));
+        CKL(rq::oz_slice_launches(true, mt),
+            rq::launch_oz_slice(At, lda, true, 0, n2, mt, w.slA, w.exA, cl.st));
+        float* part = reinterpret_cast<float*>(w.skpart);
+        const size_t pcap = 2 * w.skcap;
+        rq::OzGemmArgs rs{ell,   n2,  rq::oz_kpad(mt), w.slB, w.exB, w.slA,         w.exA, 1.0,
+                          0.0,   Bnext, ell,           cl.status, part, pcap,        cl.h->num_sms};
+        CKL(rq::oz_launches(ell, n2, rs.Kp, cl.h->num_sms, pcap), rq::launch_oz_gemm(rs, cl.st));
+      } else {
+        CKL(1, rq::launch_gaussian(seed, kResampleStreamBase + J, ell, mt, w.omega, ell, nullptr,
+                                   cl.st));
+        CK(gemm(cl, 'N', 'N', 0, ell, n2, mt, 1.0, w.omega, ell, At, lda, 0.0, Bnext, ell));
+      }
+    } else if (j0 + bJ < k) {
       PhaseScope ps(cl.h, PH_SUPD, (double)bJ * bJ * bJ / 3.0 + 2.0 * bJ * bJ * (double)n2);
       // Eq. (3): B1 = S12 - S11 R11^{-1} R12, B2 = S22 (in place)
       CKL(1, rq::launch_w11(Bblk, ell, P, lda, bJ, w.W11, cl.flag, cl.status, cl.st));

@@ -62,16 +62,17 @@ def test_qr_matches_oracle(lib, m, n, b):
     assert np.linalg.norm(A - Q @ np.triu(F)) <= RTOL_REC * scale
 
 
-def _check_rqrcp(lib, A, b, p, seed, expect_info=0):
+def _check_rqrcp(lib, A, b, p, seed, expect_info=0, handle=None, resample=False):
     m, n = A.shape
     dA = to_dev(A)
-    jpvt, tau = lib.rqrcp_factor(dA, b, p, seed)
-    info = lib.sync_info()
+    jpvt, tau = lib.rqrcp_factor(dA, b, p, seed, handle=handle)
+    info = handle.sync_info() if handle is not None else lib.sync_info()
     assert info == expect_info
     F, jp, t = host(dA), host(jpvt), host(tau)
     assert sorted(jp.tolist()) == list(range(n))
     ties = []
-    Fo, jo, to, info_o = oracle.rqrcp(A, b, p, seed=seed, replay_jpvt=jp, ties=ties)
+    run = oracle.rsrqrcp if resample else oracle.rqrcp
+    Fo, jo, to, info_o = run(A, b, p, seed=seed, replay_jpvt=jp, ties=ties)
     assert info_o == expect_info
     np.testing.assert_array_equal(jo, jp)
     k = min(m, n)
@@ -120,6 +121,21 @@ def test_rqrcp_resample_path(lib):
     A = synth.gaussian(60, 40, seed=4)
     A[:, 12:] = 0.0
     _check_rqrcp(lib, A, 8, 4, 2, expect_info=2)
+
+
+@pytest.mark.parametrize("m,n,b,p,emul", [(1000, 1000, 32, 8, False), (300, 500, 64, 8, False),
+                                          (500, 300, 16, 4, False), (600, 600, 64, 8, True)])
+def test_rsrqrcp_matches_oracle(lib, m, n, b, p, emul):
+    """Alg. 5 (RQRCP_OPT_RESAMPLE): a fresh sample of the trailing matrix every
+    block; pivots, R and the reconstruction against the oracle's Alg. 5 at the
+    FP64 tolerances (also with the FP64-emulated products)."""
+    h = lib.Handle()
+    h.set_resample(True)
+    if emul:
+        h.set_fp64_emulation(True)
+    A = synth.gaussian(m, n, seed=m + n + b)
+    _, ties = _check_rqrcp(lib, A, b, p, 3, handle=h, resample=True)
+    assert len(ties) <= 2
 
 
 def test_rqrcp_nonfinite_flagged(lib):
