@@ -81,7 +81,7 @@ def parse():
     ap.add_argument("--only-emulated", action="store_true",
                     help="same as --legs emulated")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
-    ap.add_argument("--legs", default="qr,e2e,cpu,emulated,mixed,truncated,serving",
+    ap.add_argument("--legs", default="qr,e2e,cpu,emulated,rsrqrcp,mixed,truncated,serving",
                     help="comma-separated extra legs to run after the FP64 step")
     args = ap.parse_args()
     legs = set(x for x in args.legs.split(",") if x)
@@ -297,6 +297,43 @@ def emulated_leg(args, dev, A0, fp64_ms, qr_ms, stream):
     out["note"] = ("28 BF16 slice products per FP64 multiply-add, exact per-diagonal FP32 sums, "
                    "double-FP32 running sums; parity vs the FP64 oracle in tests")
     h.close()
+    del A
+    return out
+
+
+def rsrqrcp_leg(args, dev, A0, fp64_ms, emul_ms, stream):
+    """Alg. 5 (RSRQRCP: a fresh sample of the trailing matrix every block
+    instead of the sample update of Eq. 3) on the same matrix and (b, p):
+    the cost of repeated sampling, with the FP64 pipe and with the
+    FP64-emulated products."""
+    import torch
+    import paper_1509_06820_gb300 as rq
+    n, b, p = args.n, args.b, args.p
+    A = rq.empty_colmajor(n, n, dev)
+    out = {"workload": f"rsrqrcp_graded_{n}x{n}_b{b}_p{p}"}
+    for emul in (False, True):
+        h = rq.Handle(dev)
+        h.set_resample(True)
+        h.set_fp64_emulation(emul)
+        h.reserve("R", n, n, n, b, p)
+
+        def step():
+            A.copy_(A0)
+            rq.rqrcp_factor(A, b, p, 1, handle=h)
+        step()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        ref = emul_ms if emul else fp64_ms
+        out["emulated" if emul else "fp64"] = {
+            "ms_per_step": ms, "over_rqrcp_time": ms / ref if ref else None,
+            "device_info": h.sync_info()}
+        h.close()
+    out["paper_ratio_16k"] = 43.84 / 24.03
     del A
     return out
 
@@ -601,6 +638,9 @@ def main():
     if "emulated" in args.legs:
         extras["fp64_emulated"] = emulated_leg(args, dev, A0, ms, extras.get("qr_ms_per_step"),
                                                stream)
+    if "rsrqrcp" in args.legs:
+        em = extras.get("fp64_emulated", {}).get("rqrcp", {}).get("ms_per_step")
+        extras["rsrqrcp"] = rsrqrcp_leg(args, dev, A0, ms, em, stream)
     if "mixed" in args.legs:
         extras["mixed"] = mixed_leg(args, dev, ms, stream)
     if "truncated" in args.legs:
