@@ -346,11 +346,13 @@ def trqrcp(A, k, b, p, seed=0, omega=None, replay_jpvt=None, tie_rtol=1e-8, ties
     return jpvt, tau, Y, R, info
 
 
-def tuxv(A, k, b, p, seed=0, omega=None, replay_jpvt=None, tie_rtol=1e-8, ties=None):
-    """Approximate truncated SVD, Alg. 7 with j_max = 1.
+def tuxv(A, k, b, p, seed=0, omega=None, replay_jpvt=None, tie_rtol=1e-8, ties=None, jmax=1):
+    """Approximate truncated SVD, Alg. 7 (j_max LQ-QR iterations; the paper
+    sets j_max = 1).
 
     Returns (U, X, V, jpvt, info) with U (m x k) and V (n x k) having
-    orthonormal columns and X (k x k) upper triangular, A ~= U X V^T.
+    orthonormal columns and X (k x k) upper triangular after an odd number
+    of iterations and lower triangular after an even number, A ~= U X V^T.
     """
     A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
@@ -363,9 +365,22 @@ def tuxv(A, k, b, p, seed=0, omega=None, replay_jpvt=None, tie_rtol=1e-8, ties=N
     Zt = Z0.T.copy()
     tv = panel_qr(Zt)
     V = form_q(Zt, tv, k)
-    # Alg. 7: Z1 = A V(:, 1:k), then [U, X] = qr(Z1).
-    Z1 = A @ V
-    tu = panel_qr(Z1)
-    X = np.triu(Z1[:k, :k])
-    U = form_q(Z1, tu, k)
+    j = 1
+    while True:
+        # Alg. 7: Z^(j) = A V(:, 1:k), then [U, X] = qr(Z^(j)).
+        Z = A @ V
+        tu = panel_qr(Z)
+        X = np.triu(Z[:k, :k])
+        U = form_q(Z, tu, k)
+        if j == jmax:
+            break
+        # Alg. 7: Z^(j+1) = U(:, 1:k)^T A, LQ of it as the QR of its transpose.
+        Zt = U.T @ A
+        Zt = Zt.T.copy()
+        tv = panel_qr(Zt)
+        X = np.triu(Zt[:k, :k]).T
+        V = form_q(Zt, tv, k)
+        if j + 1 == jmax:
+            break
+        j += 2
     return U, X, V, jpvt, info

@@ -256,6 +256,62 @@ def test_tuxv_properties():
     assert e_svd * (1 - 1e-10) <= e_tuxv <= e_tr * (1 + 1e-10)
 
 
+@pytest.mark.parametrize("jmax", [1, 2, 3, 4])
+def test_tuxv_iterations_are_subspace_iteration(jmax):
+    """Alg. 7 with j_max iterations: span(V) after the i-th QR step is
+    (A^T A)^(i-1) applied to the row space of R P^T, span(U) after an LQ step
+    is A times the previous V.  Checked against projections built with
+    numpy's QR and pseudo-inverse, not the oracle's Householder routines."""
+    m, n, k = 110, 80, 10
+    A = synth.decaying_lowrank(m, n, rank=50, noise=1e-7)
+    U, X, V, jpvt, info = oracle.tuxv(A, k, 4, 4, seed=5, jmax=jmax)
+    np.testing.assert_allclose(U.T @ U, np.eye(k), atol=1e-13)
+    np.testing.assert_allclose(V.T @ V, np.eye(k), atol=1e-13)
+    if jmax % 2:
+        assert np.allclose(np.tril(X, -1), 0.0)
+        np.testing.assert_allclose(U @ X, A @ V, atol=1e-12)
+    else:
+        assert np.allclose(np.triu(X, 1), 0.0)
+        np.testing.assert_allclose(X @ V.T, U.T @ A, atol=1e-12)
+    jt, tt, Y, R, _ = oracle.trqrcp(A, k, 4, 4, seed=5)
+    Z0 = np.zeros((k, n))
+    Z0[:, jt] = R
+    W = np.linalg.qr(Z0.T)[0]              # row space of R P^T
+    for i in range(jmax):
+        if i % 2 == 0:
+            W = np.linalg.qr(A @ W)[0]     # column space, after a QR step
+        else:
+            W = np.linalg.qr(A.T @ W)[0]   # row space, after an LQ step
+    if jmax % 2:
+        # the last step was a QR step: U spans W
+        np.testing.assert_allclose(U @ U.T, W @ W.T, atol=1e-10)
+    else:
+        # the last step was an LQ step: V spans W
+        np.testing.assert_allclose(V @ V.T, W @ W.T, atol=1e-10)
+
+
+def test_tuxv_error_non_increasing_in_iterations():
+    """Each extra iteration of Alg. 7 projects onto a subspace at least as
+    good (Alg. 7's QR step gives A V V^T, its LQ step U U^T A with U spanning
+    A V), so ||A - U X V^T||_F never grows with j_max and stays above the
+    Eckart-Young bound; with a spectral gap it approaches that bound."""
+    m, n, k = 150, 120, 8
+    rng = np.random.default_rng(4)
+    Qa = np.linalg.qr(rng.standard_normal((m, n)))[0]
+    Qb = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    s = np.concatenate([np.geomspace(1.0, 0.5, k), 0.05 * np.geomspace(1.0, 0.1, n - k)])
+    A = (Qa * s) @ Qb.T
+    e_svd = np.sqrt(np.sum(s[k:] ** 2))
+    errs = []
+    for jmax in range(1, 7):
+        U, X, V, _, _ = oracle.tuxv(A, k, 4, 4, seed=2, jmax=jmax)
+        errs.append(np.linalg.norm(A - U @ X @ V.T))
+    for a, b in zip(errs, errs[1:]):
+        assert b <= a * (1 + 1e-12)
+    assert errs[0] >= e_svd * (1 - 1e-12)
+    assert errs[-1] <= e_svd * (1 + 1e-6)
+
+
 # ---------------------------------------------------------------- RSRQRCP (Alg. 5)
 @pytest.mark.parametrize("m,n,b,p", [(120, 100, 16, 8), (100, 120, 16, 8), (97, 97, 32, 8),
                                      (200, 30, 64, 8)])
