@@ -225,6 +225,20 @@ int tuxv(rqrcp_handle_t handle, int64_t m, int64_t n, const double* dA, int64_t 
          double* dV, int64_t ldv);
 
 /*
+ * Alg. 7 (TUXV) with jmax >= 1 iterations.  After V1 as in tuxv, odd
+ * iterations j compute Z = A V and [U, X] = qr(Z) (X upper triangular); even
+ * iterations compute Z = U^T A and its LQ factorization [X, V^T] = lq(Z),
+ * taken as the QR of Z^T = A^T U (X = R^T lower triangular).  The loop stops
+ * after iteration jmax, so X is upper triangular for odd jmax and lower for
+ * even jmax; A ~= U X V^T either way.  tuxv is tuxv_iter with jmax = 1.
+ * Arguments as in tuxv; jmax < 1 returns -9.  Every iteration is one m x n x k
+ * product with A and one k-column QR plus Q formation on the device.
+ */
+int tuxv_iter(rqrcp_handle_t handle, int64_t m, int64_t n, const double* dA, int64_t lda,
+              int64_t k, int b, int p, uint64_t seed, int jmax, double* dU, int64_t ldu,
+              double* dX, int64_t ldx, double* dV, int64_t ldv);
+
+/*
  * The Gaussian compression matrix of Alg. 4 (first steps): writes the
  * rows x cols block of the seeded GIID matrix for Philox stream `stream_id`
  * (1 = Omega) into dOut (column-major, ldo >= rows).

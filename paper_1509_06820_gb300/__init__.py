@@ -61,6 +61,8 @@ SIGNATURES = [
     ("trqrcp_batched", _I, [_P, _I, ctypes.POINTER(Problem), _I]),
     ("rqrcp_reserve_batched", _I, [_P, _I, _I64, _I64, _I64, _I, _I]),
     ("tuxv", _I, [_P, _I64, _I64, _P, _I64, _I64, _I, _I, _U64, _P, _I64, _P, _I64, _P, _I64]),
+    ("tuxv_iter", _I, [_P, _I64, _I64, _P, _I64, _I64, _I, _I, _U64, _I, _P, _I64, _P, _I64, _P,
+                       _I64]),
     ("rqrcp_gaussian", _I, [_P, _U64, ctypes.c_uint32, _I64, _I64, _P, _I64]),
     ("rqrcp_sketch", _I, [_P, _I64, _I64, _P, _I64, _I, _U64, _P, _I64]),
     ("rqrcp_gemm_bf16x", _I, [_P, ctypes.c_char, ctypes.c_char, _I64, _I64, _I64, ctypes.c_float,
@@ -324,16 +326,21 @@ def trqrcp_batched(problems, lanes=8, handle=None, outs=None):
     return results
 
 
-def tuxv(A, k, b, p, seed, handle=None):
-    """Alg. 7 with j_max = 1; returns (U (m x k), X (k x k), V (n x k))."""
+def tuxv(A, k, b, p, seed, handle=None, jmax=1):
+    """Alg. 7 with j_max iterations; returns (U (m x k), X (k x k), V (n x k)),
+    X upper triangular for odd j_max and lower for even j_max."""
     h = handle or default_handle(A.device)
     pa, lda = _cm(A, "A")
     m, n = A.shape
     U = empty_colmajor(m, k, A.device)
     X = empty_colmajor(k, k, A.device)
     V = empty_colmajor(n, k, A.device)
-    _check(load().tuxv(h.bind(), m, n, _P(pa), lda, k, b, p, seed, _ptr(U), _ld(U),
-                       _ptr(X), _ld(X), _ptr(V), _ld(V)), h.h)
+    if jmax == 1:
+        _check(load().tuxv(h.bind(), m, n, _P(pa), lda, k, b, p, seed, _ptr(U), _ld(U),
+                           _ptr(X), _ld(X), _ptr(V), _ld(V)), h.h)
+    else:
+        _check(load().tuxv_iter(h.bind(), m, n, _P(pa), lda, k, b, p, seed, jmax, _ptr(U),
+                                _ld(U), _ptr(X), _ld(X), _ptr(V), _ld(V)), h.h)
     return U, X, V
 
 

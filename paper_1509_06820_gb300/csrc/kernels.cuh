@@ -162,6 +162,10 @@ cudaError_t launch_scatter_transpose(const double* src, int64_t lds, int64_t row
 // zeros above, F below; R part (upper triangle, zeros below) into Rout.
 cudaError_t launch_split_qr(const double* F, int64_t ldf, int64_t rows, int64_t cols, int64_t yrow0,
                             double* Y, int64_t ldy, double* Rout, int64_t ldr, cudaStream_t st);
+// X = R^T (lower triangular, zeros above) for the upper triangle R of F's
+// leading cols x cols block
+cudaError_t launch_r_transposed(const double* F, int64_t ldf, int64_t cols, double* X,
+                                int64_t ldx, cudaStream_t st);
 
 // ---- panel.cu: Householder panel QR (unblocked, cooperative) of the
 // mJ x bJ panel P (ld), tau out, T (bJ x bJ, ld bJ) the compact-WY factor.

@@ -210,6 +210,18 @@ __global__ void split_qr_kernel(const double* __restrict__ F, int64_t ldf, int64
   }
 }
 
+// X = R^T for the upper triangle R of F's leading cols x cols block: the L of
+// an LQ factorization computed as the QR of the transpose (Alg. 7).
+__global__ void r_transposed_kernel(const double* __restrict__ F, int64_t ldf, int64_t cols,
+                                    double* __restrict__ X, int64_t ldx) {
+  const int64_t total = cols * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % cols, c = e / cols;
+    X[c + r * ldx] = (r <= c) ? F[r + c * ldf] : 0.0;
+  }
+}
+
 unsigned grid2(int64_t work) {
   int64_t b = (work + 255) / 256;
   if (b < 1) b = 1;
@@ -240,6 +252,13 @@ cudaError_t launch_split_qr(const double* F, int64_t ldf, int64_t rows, int64_t 
                             double* Y, int64_t ldy, double* Rout, int64_t ldr, cudaStream_t st) {
   if (rows <= 0 || cols <= 0) return cudaSuccess;
   split_qr_kernel<<<grid2(rows * cols), 256, 0, st>>>(F, ldf, rows, cols, yrow0, Y, ldy, Rout, ldr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_r_transposed(const double* F, int64_t ldf, int64_t cols, double* X,
+                                int64_t ldx, cudaStream_t st) {
+  if (cols <= 0) return cudaSuccess;
+  r_transposed_kernel<<<grid2(cols * cols), 256, 0, st>>>(F, ldf, cols, X, ldx);
   return cudaGetLastError();
 }
 

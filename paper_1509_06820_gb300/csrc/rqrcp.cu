@@ -853,9 +853,9 @@ int trqrcp(rqrcp_handle_t h, int64_t m, int64_t n, const double* dA, int64_t lda
   return trqrcp_core(cl, m, n, dA, lda, k, b, ell, seed, d_jpvt, d_tau, dY, ldy, dR, ldr);
 }
 
-int tuxv(rqrcp_handle_t h, int64_t m, int64_t n, const double* dA, int64_t lda, int64_t k, int b,
-         int p, uint64_t seed, double* dU, int64_t ldu, double* dX, int64_t ldx, double* dV,
-         int64_t ldv) {
+int tuxv_iter(rqrcp_handle_t h, int64_t m, int64_t n, const double* dA, int64_t lda, int64_t k,
+              int b, int p, uint64_t seed, int jmax, double* dU, int64_t ldu, double* dX,
+              int64_t ldx, double* dV, int64_t ldv) {
   if (!h) return -1;
   if (m < 1) return -2;
   if (n < 1) return -3;
@@ -864,6 +864,7 @@ int tuxv(rqrcp_handle_t h, int64_t m, int64_t n, const double* dA, int64_t lda, 
   if (k < 1 || k > std::min(m, n)) return -6;
   if (b < 1) return -7;
   if (p < 0) return -8;
+  if (jmax < 1) return -9;
   if (!dU) return -10;
   if (ldu < m) return -11;
   if (!dX) return -12;
@@ -892,19 +893,42 @@ int tuxv(rqrcp_handle_t h, int64_t m, int64_t n, const double* dA, int64_t lda, 
     CKL(1, rq::launch_copy2d(dV, ldv, w.F, n, n, k, cl.st));
   }
   if ((r = orgqr_core(cl, n, k, w.F, n, b, w.Tall, dV, ldv))) return r;
-  // Z1 = A V1, then [U, X] = qr(Z1)
-  {
-    PhaseScope ps(cl.h, PH_TRQ, 2.0 * (double)m * (double)n * (double)k);
-    CK(gemm(cl, 'N', 'N', 0, m, k, n, 1.0, dA, lda, dV, ldv, 0.0, dU, ldu));
+  for (int j = 1;; j += 2) {
+    // Alg. 7, odd j: Z = A V, then [U, X] = qr(Z) (X upper triangular)
+    {
+      PhaseScope ps(cl.h, PH_TRQ, 2.0 * (double)m * (double)n * (double)k);
+      CK(gemm(cl, 'N', 'N', 0, m, k, n, 1.0, dA, lda, dV, ldv, 0.0, dU, ldu));
+    }
+    if ((r = qr_core(cl, m, k, dU, ldu, b, w.tau2, w.Tall))) return r;
+    {
+      PhaseScope ps(cl.h, PH_OTHER, 0.0);
+      CKL(1, rq::launch_split_qr(dU, ldu, k, k, 0, nullptr, 0, dX, ldx, cl.st));
+      CKL(1, rq::launch_copy2d(dU, ldu, w.F, m, m, k, cl.st));
+    }
+    if ((r = orgqr_core(cl, m, k, w.F, m, b, w.Tall, dU, ldu))) return r;
+    if (j == jmax) break;
+    // Alg. 7, even j: Z = U^T A, then [X, V^T] = lq(Z) through the QR of
+    // Z^T = A^T U (X = R^T lower triangular)
+    {
+      PhaseScope ps(cl.h, PH_TRQ, 2.0 * (double)m * (double)n * (double)k);
+      CK(gemm(cl, 'T', 'N', 0, n, k, m, 1.0, dA, lda, dU, ldu, 0.0, dV, ldv));
+    }
+    if ((r = qr_core(cl, n, k, dV, ldv, b, w.tau2, w.Tall))) return r;
+    {
+      PhaseScope ps(cl.h, PH_OTHER, 0.0);
+      CKL(1, rq::launch_r_transposed(dV, ldv, k, dX, ldx, cl.st));
+      CKL(1, rq::launch_copy2d(dV, ldv, w.F, n, n, k, cl.st));
+    }
+    if ((r = orgqr_core(cl, n, k, w.F, n, b, w.Tall, dV, ldv))) return r;
+    if (j + 1 == jmax) break;
   }
-  if ((r = qr_core(cl, m, k, dU, ldu, b, w.tau2, w.Tall))) return r;
-  {
-    PhaseScope ps(cl.h, PH_OTHER, 0.0);
-    CKL(1, rq::launch_split_qr(dU, ldu, k, k, 0, nullptr, 0, dX, ldx, cl.st));
-    CKL(1, rq::launch_copy2d(dU, ldu, w.F, m, m, k, cl.st));
-  }
-  if ((r = orgqr_core(cl, m, k, w.F, m, b, w.Tall, dU, ldu))) return r;
   return RQRCP_OK;
+}
+
+int tuxv(rqrcp_handle_t h, int64_t m, int64_t n, const double* dA, int64_t lda, int64_t k, int b,
+         int p, uint64_t seed, double* dU, int64_t ldu, double* dX, int64_t ldx, double* dV,
+         int64_t ldv) {
+  return tuxv_iter(h, m, n, dA, lda, k, b, p, seed, 1, dU, ldu, dX, ldx, dV, ldv);
 }
 
 int rqrcp_factor_mixed(rqrcp_handle_t h, int64_t m, int64_t n, float* dA, int64_t lda, int b,

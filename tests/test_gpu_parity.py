@@ -205,6 +205,34 @@ def test_tuxv_matches_oracle(lib, m, n, k, b, p):
     np.testing.assert_allclose(np.abs(np.diag(Xg)), np.abs(np.diag(Xo)), rtol=1e-9)
 
 
+@pytest.mark.parametrize("m,n,k,b,jmax", [(400, 300, 24, 8, 2), (300, 400, 40, 16, 3),
+                                           (520, 260, 64, 32, 4), (257, 257, 17, 8, 5)])
+def test_tuxv_iter_matches_oracle(lib, m, n, k, b, jmax):
+    """Alg. 7 with j_max > 1: the same U X V^T as the oracle's iterations, X
+    lower triangular after an even number of iterations, upper after odd."""
+    A = synth.decaying_lowrank(m, n, rank=min(m, n) // 2, noise=1e-8)
+    U, X, V = lib.tuxv(to_dev(A), k, b, 8, 5, jmax=jmax)
+    assert lib.sync_info() == 0
+    Ug, Xg, Vg = host(U), host(X), host(V)
+    Uo, Xo, Vo, jo, info = oracle.tuxv(A, k, b, 8, seed=5, jmax=jmax)
+    if jmax % 2:
+        assert np.allclose(np.tril(Xg, -1), 0.0)
+    else:
+        assert np.allclose(np.triu(Xg, 1), 0.0)
+    np.testing.assert_allclose(Ug.T @ Ug, np.eye(k), atol=1e-13)
+    np.testing.assert_allclose(Vg.T @ Vg, np.eye(k), atol=1e-13)
+    approx_g = Ug @ Xg @ Vg.T
+    approx_o = Uo @ Xo @ Vo.T
+    assert np.linalg.norm(approx_g - approx_o) <= 1e-10 * np.linalg.norm(approx_o)
+    np.testing.assert_allclose(np.abs(np.diag(Xg)), np.abs(np.diag(Xo)), rtol=1e-9)
+
+
+def test_tuxv_iter_rejects_zero_iterations(lib):
+    A = to_dev(synth.gaussian(40, 30, seed=1))
+    with pytest.raises(lib.RqrcpError, match="argument 9"):
+        lib.tuxv(A, 4, 4, 4, 1, jmax=0)
+
+
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
 @pytest.mark.parametrize("m,n,k", [(128, 128, 64), (300, 200, 150), (64, 700, 1000), (129, 1, 7)])
 def test_tc_gemm_bf16x3(lib, ta, tb, m, n, k):
