@@ -57,6 +57,7 @@ extern "C" {
 #define RQRCP_INFO_NONFINITE 1  /* the sample held NaN/Inf: A is not finite */
 #define RQRCP_INFO_RESAMPLED 2  /* exactly singular R11: trailing sample re-drawn */
 #define RQRCP_INFO_TIMEOUT 4    /* a device-side wait gave up; results invalid */
+#define RQRCP_INFO_NOCONV 8     /* the Jacobi SVD of X hit its sweep limit (tuxv_svd) */
 
 typedef struct rqrcp_handle_s* rqrcp_handle_t;
 
@@ -231,12 +232,29 @@ int tuxv(rqrcp_handle_t handle, int64_t m, int64_t n, const double* dA, int64_t 
  * taken as the QR of Z^T = A^T U (X = R^T lower triangular).  The loop stops
  * after iteration jmax, so X is upper triangular for odd jmax and lower for
  * even jmax; A ~= U X V^T either way.  tuxv is tuxv_iter with jmax = 1.
- * Arguments as in tuxv; jmax < 1 returns -9.  Every iteration is one m x n x k
- * product with A and one k-column QR plus Q formation on the device.
+ * Arguments as in tuxv, with jmax (>= 1) the 10th.  Every iteration is one
+ * m x n x k product with A and one k-column QR plus Q formation on the device.
  */
 int tuxv_iter(rqrcp_handle_t handle, int64_t m, int64_t n, const double* dA, int64_t lda,
               int64_t k, int b, int p, uint64_t seed, int jmax, double* dU, int64_t ldu,
               double* dX, int64_t ldx, double* dV, int64_t ldv);
+
+/*
+ * Approximate truncated SVD: tuxv_iter followed by the SVD of the small
+ * connection matrix, X = Ux diag(sigma) Vs^T (Alg. 7 discussion: the diagonal
+ * of X approximates the leading singular values, its SVD does better).  The
+ * outputs are U Ux, sigma and V Vs, so A ~= U diag(sigma) V^T.
+ *   d_sigma : out, k doubles (device), descending, >= 0
+ *   dU, dV  : out as in tuxv (orthonormal columns; the column of U belonging
+ *             to an exactly zero singular value is 0)
+ * The SVD of X is one-sided Jacobi (column-pair rotations, parallel circle
+ * ordering, up to 40 sweeps; RQRCP_INFO_NOCONV in the info word if they run
+ * out).  Entries of X are assumed below 1e150 in magnitude (their squares are
+ * summed unscaled).
+ */
+int tuxv_svd(rqrcp_handle_t handle, int64_t m, int64_t n, const double* dA, int64_t lda,
+             int64_t k, int b, int p, uint64_t seed, int jmax, double* dU, int64_t ldu,
+             double* d_sigma, double* dV, int64_t ldv);
 
 /*
  * The Gaussian compression matrix of Alg. 4 (first steps): writes the

@@ -21,7 +21,8 @@ Contents (paper sections in brackets):
                      sample update formula [Alg. 4, Eq. (3)], repeated-sampling
                      RQRCP [Alg. 5], the unpivoted
                      blocked QR it reduces to [Table 3 note], TRQRCP [Alg. 6]
-                     and TUXV [Alg. 7].
+                     and TUXV [Alg. 7], with j_max iterations and the SVD of
+                     the connection matrix X.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` against a library routine, a closed form, a
@@ -36,6 +37,7 @@ from .rqrcp import (  # noqa: F401
     qr_blocked,
     trqrcp,
     tuxv,
+    tuxv_svd,
     PivotMismatch,
 )
 from .philox import philox4x32_10, gaussian_omega  # noqa: F401

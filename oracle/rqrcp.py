@@ -384,3 +384,16 @@ def tuxv(A, k, b, p, seed=0, omega=None, replay_jpvt=None, tie_rtol=1e-8, ties=N
             break
         j += 2
     return U, X, V, jpvt, info
+
+
+def tuxv_svd(A, k, b, p, seed=0, jmax=1, omega=None, replay_jpvt=None, tie_rtol=1e-8,
+             ties=None):
+    """Alg. 7 followed by the SVD of the k x k connection matrix X, which the
+    paper suggests for better singular value estimates than the diagonal of X:
+    X = Ux diag(sigma) Vs^T, returned as (U Ux, sigma, V Vs, jpvt, info) with
+    sigma descending, so that A ~= U diag(sigma) V^T.  The SVD of X is LAPACK's
+    (numpy), the plain definition of this step."""
+    U, X, V, jpvt, info = tuxv(A, k, b, p, seed=seed, omega=omega, replay_jpvt=replay_jpvt,
+                               tie_rtol=tie_rtol, ties=ties, jmax=jmax)
+    Ux, sigma, VsT = np.linalg.svd(X)
+    return U @ Ux, sigma, V @ VsT.T, jpvt, info

@@ -27,6 +27,7 @@ OPT_RESAMPLE = 2
 INFO_NONFINITE = 1
 INFO_RESAMPLED = 2
 INFO_TIMEOUT = 4
+INFO_NOCONV = 8
 
 # (name, restype, argtypes) of every symbol declared in include/rqrcp.h
 _P = ctypes.c_void_p
@@ -63,6 +64,7 @@ SIGNATURES = [
     ("tuxv", _I, [_P, _I64, _I64, _P, _I64, _I64, _I, _I, _U64, _P, _I64, _P, _I64, _P, _I64]),
     ("tuxv_iter", _I, [_P, _I64, _I64, _P, _I64, _I64, _I, _I, _U64, _I, _P, _I64, _P, _I64, _P,
                        _I64]),
+    ("tuxv_svd", _I, [_P, _I64, _I64, _P, _I64, _I64, _I, _I, _U64, _I, _P, _I64, _P, _P, _I64]),
     ("rqrcp_gaussian", _I, [_P, _U64, ctypes.c_uint32, _I64, _I64, _P, _I64]),
     ("rqrcp_sketch", _I, [_P, _I64, _I64, _P, _I64, _I, _U64, _P, _I64]),
     ("rqrcp_gemm_bf16x", _I, [_P, ctypes.c_char, ctypes.c_char, _I64, _I64, _I64, ctypes.c_float,
@@ -342,6 +344,20 @@ def tuxv(A, k, b, p, seed, handle=None, jmax=1):
         _check(load().tuxv_iter(h.bind(), m, n, _P(pa), lda, k, b, p, seed, jmax, _ptr(U),
                                 _ld(U), _ptr(X), _ld(X), _ptr(V), _ld(V)), h.h)
     return U, X, V
+
+
+def tuxv_svd(A, k, b, p, seed, handle=None, jmax=1):
+    """Alg. 7 with j_max iterations and the SVD of X; returns (U (m x k),
+    sigma (k, descending), V (n x k)) with A ~= U diag(sigma) V^T."""
+    h = handle or default_handle(A.device)
+    pa, lda = _cm(A, "A")
+    m, n = A.shape
+    U = empty_colmajor(m, k, A.device)
+    sigma = torch.empty(k, dtype=torch.float64, device=A.device)
+    V = empty_colmajor(n, k, A.device)
+    _check(load().tuxv_svd(h.bind(), m, n, _P(pa), lda, k, b, p, seed, jmax, _ptr(U), _ld(U),
+                           _ptr(sigma), _ptr(V), _ld(V)), h.h)
+    return U, sigma, V
 
 
 def gaussian(seed, stream_id, rows, cols, device="cuda", handle=None):

@@ -196,6 +196,29 @@ bool panel_fits(int64_t mJ, int bJ, int num_sms);
 cudaError_t launch_w11(const double* S, int ell, const double* R11, int64_t ldr, int bJ,
                        double* W11, int* flag, int* status, cudaStream_t st);
 
+// ---- svd_jacobi.cu: X = Ux diag(sigma) Vs^T for a k x k matrix X (one-sided
+// Jacobi, cooperative when the grid has more than one CTA).  Ux, Vs, G, Vx
+// are k x k with ld k; sigma descending.  A column of Ux whose singular value
+// is exactly 0 is left 0.  RQRCP_INFO_NOCONV is ORed into *status when the
+// sweeps run out before every pair is orthogonal.
+constexpr int kJacobiMaxSweeps = 40;
+struct JacobiArgs {
+  const double* X;
+  int64_t ldx;
+  int k;
+  double* G;       // scratch, the rotated copy of X
+  double* Vx;      // scratch, the accumulated rotations
+  double* Ux;      // out
+  double* Vs;      // out
+  double* sigma;   // out, k
+  double* sraw;    // scratch, k
+  int* rotated;    // scratch, kJacobiMaxSweeps ints
+  GridBarrier* bar;
+  int* status;
+};
+cudaError_t launch_jacobi_svd(const JacobiArgs& a, int num_sms, cudaStream_t st);
+int jacobi_grid(int k, int num_sms);
+
 // Q = first cols columns of the rows x rows identity
 cudaError_t launch_eye(double* Q, int64_t rows, int64_t cols, int64_t ld, cudaStream_t st);
 // Fill / copy helpers

@@ -86,6 +86,8 @@ struct Work {
   double* tau2 = nullptr;     // k
   double* Tall = nullptr;     // ceil(k/b) x b x b
   double* F = nullptr;        // max(m, n) x k copy of reflectors
+  double* svd = nullptr;      // 5 k x k + k: X, G, Vx, Ux, Vs and raw sigma
+  int* rotated = nullptr;     // Jacobi sweep flags
   // mixed precision (FP32 storage)
   float* omega32 = nullptr;   // l x m
   float* B32 = nullptr;       // l x n
@@ -162,6 +164,8 @@ Work carve(char op, int64_t m, int64_t n, int64_t k, int b, int p, int sms, char
     w.tau2 = c.take<double>(k);
     w.Tall = c.take<double>((size_t)((k + b - 1) / b) * bb * bb);
     w.F = c.take<double>((size_t)std::max(m, n) * k);
+    w.svd = c.take<double>((size_t)5 * k * k + k);
+    w.rotated = c.take<int>(rq::kJacobiMaxSweeps);
   } else if (op == 'Q') {
     w.Tall = nullptr;
   } else if (op == 'V') {
@@ -853,9 +857,9 @@ int trqrcp(rqrcp_handle_t h, int64_t m, int64_t n, const double* dA, int64_t lda
   return trqrcp_core(cl, m, n, dA, lda, k, b, ell, seed, d_jpvt, d_tau, dY, ldy, dR, ldr);
 }
 
-int tuxv_iter(rqrcp_handle_t h, int64_t m, int64_t n, const double* dA, int64_t lda, int64_t k,
-              int b, int p, uint64_t seed, int jmax, double* dU, int64_t ldu, double* dX,
-              int64_t ldx, double* dV, int64_t ldv) {
+// Arguments 1-8, shared by tuxv, tuxv_iter and tuxv_svd (same positions).
+int check_tuxv_head(rqrcp_handle_t h, int64_t m, int64_t n, const double* dA, int64_t lda,
+                    int64_t k, int b, int p) {
   if (!h) return -1;
   if (m < 1) return -2;
   if (n < 1) return -3;
@@ -864,21 +868,21 @@ int tuxv_iter(rqrcp_handle_t h, int64_t m, int64_t n, const double* dA, int64_t 
   if (k < 1 || k > std::min(m, n)) return -6;
   if (b < 1) return -7;
   if (p < 0) return -8;
-  if (jmax < 1) return -9;
-  if (!dU) return -10;
-  if (ldu < m) return -11;
-  if (!dX) return -12;
-  if (ldx < k) return -13;
-  if (!dV) return -14;
-  if (ldv < n) return -15;
+  return RQRCP_OK;
+}
+
+int check_tuxv_sizes(rqrcp_handle_t h, int64_t m, int64_t n, int64_t k, int b, int p) {
   if (b > k) b = (int)k;
-  const int ell = b + p;
-  if (!sizes_fit(h->num_sms, m, n, b, ell) || !rq::panel_fits(n, b, h->num_sms))
+  if (!sizes_fit(h->num_sms, m, n, b, b + p) || !rq::panel_fits(n, b, h->num_sms))
     return RQRCP_ERR_UNSUPPORTED;
-  Call cl;
-  int r = begin(h, 'U', m, n, k, b, p, &cl);
-  if (r) return r;
+  return RQRCP_OK;
+}
+
+int tuxv_core(Call& cl, int64_t m, int64_t n, const double* dA, int64_t lda, int64_t k, int b,
+              int ell, uint64_t seed, int jmax, double* dU, int64_t ldu, double* dX, int64_t ldx,
+              double* dV, int64_t ldv) {
   Work& w = cl.w;
+  int r;
   // Alg. 7: TRQRCP, then Z0 = R P^T
   if ((r = trqrcp_core(cl, m, n, dA, lda, k, b, ell, seed, w.jpvt, w.tau, w.Yk, m, w.Rk, k))) return r;
   // Z0^T (n x k) into V's storage: V(jpvt[c], :) = R(:, c)^T
@@ -925,10 +929,80 @@ int tuxv_iter(rqrcp_handle_t h, int64_t m, int64_t n, const double* dA, int64_t 
   return RQRCP_OK;
 }
 
+int tuxv_iter(rqrcp_handle_t h, int64_t m, int64_t n, const double* dA, int64_t lda, int64_t k,
+              int b, int p, uint64_t seed, int jmax, double* dU, int64_t ldu, double* dX,
+              int64_t ldx, double* dV, int64_t ldv) {
+  int r = check_tuxv_head(h, m, n, dA, lda, k, b, p);
+  if (r) return r;
+  if (jmax < 1) return -10;
+  if (!dU) return -11;
+  if (ldu < m) return -12;
+  if (!dX) return -13;
+  if (ldx < k) return -14;
+  if (!dV) return -15;
+  if (ldv < n) return -16;
+  if ((r = check_tuxv_sizes(h, m, n, k, b, p))) return r;
+  if (b > k) b = (int)k;
+  Call cl;
+  if ((r = begin(h, 'U', m, n, k, b, p, &cl))) return r;
+  return tuxv_core(cl, m, n, dA, lda, k, b, b + p, seed, jmax, dU, ldu, dX, ldx, dV, ldv);
+}
+
+int tuxv_svd(rqrcp_handle_t h, int64_t m, int64_t n, const double* dA, int64_t lda, int64_t k,
+             int b, int p, uint64_t seed, int jmax, double* dU, int64_t ldu, double* d_sigma,
+             double* dV, int64_t ldv) {
+  int r = check_tuxv_head(h, m, n, dA, lda, k, b, p);
+  if (r) return r;
+  if (jmax < 1) return -10;
+  if (!dU) return -11;
+  if (ldu < m) return -12;
+  if (!d_sigma) return -13;
+  if (!dV) return -14;
+  if (ldv < n) return -15;
+  if ((r = check_tuxv_sizes(h, m, n, k, b, p))) return r;
+  if (b > k) b = (int)k;
+  Call cl;
+  if ((r = begin(h, 'U', m, n, k, b, p, &cl))) return r;
+  Work& w = cl.w;
+  const int64_t kk = k * k;
+  double* X = w.svd;
+  double* Ux = w.svd + 3 * kk;
+  double* Vs = w.svd + 4 * kk;
+  if ((r = tuxv_core(cl, m, n, dA, lda, k, b, b + p, seed, jmax, dU, ldu, X, k, dV, ldv)))
+    return r;
+  // X = Ux diag(sigma) Vs^T, then U <- U Ux and V <- V Vs
+  {
+    PhaseScope ps(cl.h, PH_OTHER, 0.0);
+    rq::JacobiArgs ja{X,  k,       (int)k,         w.svd + kk, w.svd + 2 * kk, Ux,
+                      Vs, d_sigma, w.svd + 5 * kk, w.rotated,  cl.bar,         cl.status};
+    CKL(1, rq::launch_jacobi_svd(ja, cl.h->num_sms, cl.st));
+  }
+  {
+    PhaseScope ps(cl.h, PH_TRQ, 2.0 * (double)(m + n) * (double)k * (double)k);
+    CK(gemm(cl, 'N', 'N', 0, m, k, k, 1.0, dU, ldu, Ux, k, 0.0, w.F, m));
+    CKL(1, rq::launch_copy2d(w.F, m, dU, ldu, m, k, cl.st));
+    CK(gemm(cl, 'N', 'N', 0, n, k, k, 1.0, dV, ldv, Vs, k, 0.0, w.F, n));
+    CKL(1, rq::launch_copy2d(w.F, n, dV, ldv, n, k, cl.st));
+  }
+  return RQRCP_OK;
+}
+
 int tuxv(rqrcp_handle_t h, int64_t m, int64_t n, const double* dA, int64_t lda, int64_t k, int b,
          int p, uint64_t seed, double* dU, int64_t ldu, double* dX, int64_t ldx, double* dV,
          int64_t ldv) {
-  return tuxv_iter(h, m, n, dA, lda, k, b, p, seed, 1, dU, ldu, dX, ldx, dV, ldv);
+  int r = check_tuxv_head(h, m, n, dA, lda, k, b, p);
+  if (r) return r;
+  if (!dU) return -10;
+  if (ldu < m) return -11;
+  if (!dX) return -12;
+  if (ldx < k) return -13;
+  if (!dV) return -14;
+  if (ldv < n) return -15;
+  if ((r = check_tuxv_sizes(h, m, n, k, b, p))) return r;
+  if (b > k) b = (int)k;
+  Call cl;
+  if ((r = begin(h, 'U', m, n, k, b, p, &cl))) return r;
+  return tuxv_core(cl, m, n, dA, lda, k, b, b + p, seed, 1, dU, ldu, dX, ldx, dV, ldv);
 }
 
 int rqrcp_factor_mixed(rqrcp_handle_t h, int64_t m, int64_t n, float* dA, int64_t lda, int b,

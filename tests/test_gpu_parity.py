@@ -227,9 +227,46 @@ def test_tuxv_iter_matches_oracle(lib, m, n, k, b, jmax):
     np.testing.assert_allclose(np.abs(np.diag(Xg)), np.abs(np.diag(Xo)), rtol=1e-9)
 
 
+@pytest.mark.parametrize("m,n,k,b,jmax", [(300, 200, 1, 1, 1), (300, 200, 7, 4, 1),
+                                           (400, 300, 33, 16, 2), (600, 500, 160, 32, 3)])
+def test_tuxv_svd_matches_oracle(lib, m, n, k, b, jmax):
+    """Alg. 7 plus the SVD of X (one-sided Jacobi on the device, one CTA for
+    k <= 16, cooperative above): singular values and the approximation as
+    the oracle's (LAPACK SVD of its X), singular vectors up to sign where the
+    singular values are separated."""
+    A = synth.decaying_lowrank(m, n, rank=min(m, n) // 2, noise=1e-8)
+    U, sig, V = lib.tuxv_svd(to_dev(A), k, b, 8, 5, jmax=jmax)
+    assert lib.sync_info() == 0
+    Ug, sg, Vg = host(U), sig.cpu().numpy(), host(V)
+    Uo, so, Vo, _, _ = oracle.tuxv_svd(A, k, b, 8, seed=5, jmax=jmax)
+    assert np.all(np.diff(sg) <= 0)
+    assert np.abs(sg - so).max() <= 1e-10 * so[0]
+    np.testing.assert_allclose(Ug.T @ Ug, np.eye(k), atol=1e-12)
+    np.testing.assert_allclose(Vg.T @ Vg, np.eye(k), atol=1e-12)
+    approx_g = (Ug * sg) @ Vg.T
+    approx_o = (Uo * so) @ Vo.T
+    assert np.linalg.norm(approx_g - approx_o) <= 1e-10 * np.linalg.norm(approx_o)
+    gap = np.minimum(np.r_[np.inf, so[:-1] - so[1:]], np.r_[so[:-1] - so[1:], np.inf])
+    sep = gap > 1e-4 * so[0]
+    cu = np.abs(np.sum(Ug * Uo, axis=0))
+    cv = np.abs(np.sum(Vg * Vo, axis=0))
+    assert np.all(cu[sep] >= 1 - 1e-8) and np.all(cv[sep] >= 1 - 1e-8)
+
+
+def test_tuxv_svd_zero_matrix(lib):
+    """X = 0: every singular value 0 and, as documented, U's columns 0."""
+    A = torch.zeros((64, 48), dtype=torch.float64)
+    U, sig, V = lib.tuxv_svd(lib.colmajor(A.cuda()), 5, 4, 4, 1)
+    # R11 = 0 makes the sample update re-draw the trailing sample
+    assert lib.sync_info() & ~lib.INFO_RESAMPLED == 0
+    assert np.all(sig.cpu().numpy() == 0.0)
+    assert np.all(host(U) == 0.0)
+    np.testing.assert_allclose(host(V).T @ host(V), np.eye(5), atol=1e-15)
+
+
 def test_tuxv_iter_rejects_zero_iterations(lib):
     A = to_dev(synth.gaussian(40, 30, seed=1))
-    with pytest.raises(lib.RqrcpError, match="argument 9"):
+    with pytest.raises(lib.RqrcpError, match="argument 10"):
         lib.tuxv(A, 4, 4, 4, 1, jmax=0)
 
 

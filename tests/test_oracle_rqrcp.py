@@ -312,6 +312,30 @@ def test_tuxv_error_non_increasing_in_iterations():
     assert errs[-1] <= e_svd * (1 + 1e-6)
 
 
+@pytest.mark.parametrize("jmax", [1, 2, 3])
+def test_tuxv_svd_properties(jmax):
+    """The SVD of X leaves the approximation unchanged and its singular values
+    are those of the m x n approximation itself (brute-force SVD); they
+    interlace below those of A (the approximation is A projected on one side)."""
+    m, n, k = 90, 70, 9
+    A = synth.decaying_lowrank(m, n, rank=40, noise=1e-6)
+    U, X, V, _, _ = oracle.tuxv(A, k, 4, 4, seed=6, jmax=jmax)
+    Us, sig, Vs, _, _ = oracle.tuxv_svd(A, k, 4, 4, seed=6, jmax=jmax)
+    approx = U @ X @ V.T
+    np.testing.assert_allclose(Us @ np.diag(sig) @ Vs.T, approx, atol=1e-13)
+    np.testing.assert_allclose(Us.T @ Us, np.eye(k), atol=1e-13)
+    np.testing.assert_allclose(Vs.T @ Vs, np.eye(k), atol=1e-13)
+    assert np.all(np.diff(sig) <= 0) and sig[-1] >= 0
+    s_approx = np.linalg.svd(approx, compute_uv=False)
+    np.testing.assert_allclose(sig, s_approx[:k], rtol=1e-12, atol=1e-15)
+    s_A = np.linalg.svd(A, compute_uv=False)
+    assert np.all(sig <= s_A[:k] * (1 + 1e-12))
+    # |diag(X)| are estimates too; the SVD's are at least as large in sum
+    # of squares (both give ||X||_F^2) and dominate in the leading value
+    np.testing.assert_allclose(np.sum(sig ** 2), np.sum(X ** 2), rtol=1e-12)
+    assert sig[0] >= np.abs(np.diag(X)).max() * (1 - 1e-12)
+
+
 # ---------------------------------------------------------------- RSRQRCP (Alg. 5)
 @pytest.mark.parametrize("m,n,b,p", [(120, 100, 16, 8), (100, 120, 16, 8), (97, 97, 32, 8),
                                      (200, 30, 64, 8)])
