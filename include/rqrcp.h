@@ -72,7 +72,7 @@ int rqrcp_destroy(rqrcp_handle_t handle);
 int rqrcp_set_stream(rqrcp_handle_t handle, void* cuda_stream);
 
 /* Scratch bytes a call needs: op = 'R' (rqrcp_factor), 'Q' (qr_factor),
- * 'T' (trqrcp), 'U' (tuxv).  k is ignored for 'R' and 'Q'. */
+ * 'T' (trqrcp), 'U' (tuxv), 'P' (qrcp_factor).  k is ignored for 'R', 'Q' and 'P'. */
 size_t rqrcp_workspace_bytes(char op, int64_t m, int64_t n, int64_t k, int b, int p);
 
 /* Allocate the scratch for a later call now (so that the call itself does
@@ -213,6 +213,28 @@ int trqrcp_batched(rqrcp_handle_t handle, int nprob, const rqrcp_problem* probs,
  */
 int rqrcp_reserve_batched(rqrcp_handle_t handle, int lanes, int64_t m, int64_t n, int64_t k,
                           int b, int p);
+
+/*
+ * Deterministic QR with column pivoting, A P = Q R (Alg. 1's pivoting: the
+ * column of largest trailing norm at every step), computed with the level-3
+ * reflection blocking of Quintana-Orti et al. that the paper describes as the
+ * best deterministic scheme (Sec. 2, Alg. qrcp3).  The comparison point for
+ * rqrcp_factor: every pivot still needs one pass over the whole trailing
+ * matrix (the level-2 inner products y^T A), which the sample avoids.
+ *   dA     : in/out, m x n column-major, lda >= m; out: R on and above the
+ *            diagonal, reflectors below (LAPACK xGEQP3 layout)
+ *   b      : block size (clamped to [1, min(m, n)] and to 128)
+ *   d_jpvt : out, n int64 (device), original column index at each position
+ *   d_tau  : out, min(m, n) doubles (device)
+ * Norm downdates follow LAPACK xLAQP2/xLAQPS: a norm that lost too many digits
+ * is recomputed exactly (by ending the block there).  Ties between equal
+ * norms go to the lowest position.  Unlike the other calls, this one waits for
+ * the device once per block (the block length is read back), so it cannot be
+ * captured in a CUDA graph (RQRCP_ERR_UNSUPPORTED during capture).
+ * Errors: -i for argument i.
+ */
+int qrcp_factor(rqrcp_handle_t handle, int64_t m, int64_t n, double* dA, int64_t lda, int b,
+                int64_t* d_jpvt, double* d_tau);
 
 /*
  * Approximate truncated SVD -- Alg. 7 (TUXV) with j_max = 1:

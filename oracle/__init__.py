@@ -17,7 +17,8 @@ Contents (paper sections in brackets):
                      and the Gaussian compression matrix Omega [Sec. 3, Alg. 3 / Alg. 4].
 * ``householder`` -- Householder reflector, unblocked panel QR, compact-WY T
                      factor and block-reflector application [Sec. 2.1-2.2, Sec. 5.1].
-* ``rqrcp``       -- partial QRCP on the sample [Alg. 1, Sec. 5], RQRCP with the
+* ``rqrcp``       -- partial QRCP on the sample [Alg. 1, Sec. 5], the full
+                     deterministic QRCP it stands in for [Alg. 1], RQRCP with the
                      sample update formula [Alg. 4, Eq. (3)], repeated-sampling
                      RQRCP [Alg. 5], the unpivoted
                      blocked QR it reduces to [Table 3 note], TRQRCP [Alg. 6]
@@ -32,6 +33,7 @@ brute-force enumeration or a statistical law stated in the paper.
 from . import philox, householder, rqrcp  # noqa: F401
 from .rqrcp import (  # noqa: F401
     sample_qrcp,
+    qrcp,
     rqrcp,
     rsrqrcp,
     qr_blocked,

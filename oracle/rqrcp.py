@@ -141,6 +141,25 @@ def sample_qrcp(Bs, nsteps, ids=None, forced_ids=None, tie_rtol=1e-8, ties=None)
     return swaps, Vb, taub
 
 
+def qrcp(A, replay_jpvt=None, tie_rtol=1e-8, ties=None):
+    """Deterministic QR with column pivoting, A P = Q R (Alg. 1 run to
+    min(m, n) steps on A itself, with the xLAQP2 norm downdate and exact
+    recomputation).  Returns (F, jpvt, tau): F holds R on and above the
+    diagonal and the reflectors (unit leading entry implied) below it, the
+    LAPACK xGEQP3 layout; jpvt[i] is the original index of column i of A P.
+    replay_jpvt / tie_rtol / ties: as in ``sample_qrcp`` (follow another
+    implementation's choice where the norms tie within tie_rtol)."""
+    F = np.array(A, dtype=np.float64, copy=True)
+    m, n = F.shape
+    k = min(m, n)
+    ids = np.arange(n)
+    _, Vb, taub = sample_qrcp(F, k, ids=ids, forced_ids=replay_jpvt, tie_rtol=tie_rtol,
+                              ties=ties)
+    for i in range(k):
+        F[i + 1:, i] = Vb[i + 1:, i]
+    return F, ids, taub
+
+
 def _right_upper_solve(S11, R11):
     """W11 = S11 R11^{-1} for upper-triangular R11, column by column
     (W11[:, j] = (S11[:, j] - W11[:, :j] R11[:j, j]) / R11[j, j])."""

@@ -64,6 +64,7 @@ SIGNATURES = [
     ("tuxv", _I, [_P, _I64, _I64, _P, _I64, _I64, _I, _I, _U64, _P, _I64, _P, _I64, _P, _I64]),
     ("tuxv_iter", _I, [_P, _I64, _I64, _P, _I64, _I64, _I, _I, _U64, _I, _P, _I64, _P, _I64, _P,
                        _I64]),
+    ("qrcp_factor", _I, [_P, _I64, _I64, _P, _I64, _I, _P, _P]),
     ("tuxv_svd", _I, [_P, _I64, _I64, _P, _I64, _I64, _I, _I, _U64, _I, _P, _I64, _P, _P, _I64]),
     ("rqrcp_gaussian", _I, [_P, _U64, ctypes.c_uint32, _I64, _I64, _P, _I64]),
     ("rqrcp_sketch", _I, [_P, _I64, _I64, _P, _I64, _I, _U64, _P, _I64]),
@@ -263,6 +264,18 @@ def qr_factor(A, b, handle=None):
     tau = torch.empty(min(m, n), dtype=torch.float64, device=A.device)
     _check(load().qr_factor(h.bind(), m, n, _P(pa), lda, b, _ptr(tau)), h.h)
     return tau
+
+
+def qrcp_factor(A, b=64, handle=None):
+    """Deterministic QRCP (level-3 reflection blocking) in place; returns
+    (jpvt, tau).  Waits for the device once per block."""
+    h = handle or default_handle(A.device)
+    pa, lda = _cm(A, "A")
+    m, n = A.shape
+    jpvt = torch.empty(n, dtype=torch.int64, device=A.device)
+    tau = torch.empty(min(m, n), dtype=torch.float64, device=A.device)
+    _check(load().qrcp_factor(h.bind(), m, n, _P(pa), lda, b, _ptr(jpvt), _ptr(tau)), h.h)
+    return jpvt, tau
 
 
 def trqrcp(A, k, b, p, seed, handle=None):

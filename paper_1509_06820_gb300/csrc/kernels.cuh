@@ -219,6 +219,41 @@ struct JacobiArgs {
 cudaError_t launch_jacobi_svd(const JacobiArgs& a, int num_sms, cudaStream_t st);
 int jacobi_grid(int k, int num_sms);
 
+// ---- qrcp3.cu: deterministic QRCP with level-3 reflection blocking (the
+// paper's comparison method).  One cooperative launch factors up to bJ
+// columns starting at position i0 of the m x n matrix A (column-major, lda),
+// whose columns [i0, n) are up to date on rows >= i0.  Writes R rows, the
+// reflectors (LAPACK layout below the diagonal), tau, W(c, t) (n x kQrcp3MaxB
+// region used as n x bJ, ld n) and ctl[1] = the number of columns done (fewer
+// than bJ when a norm downdate lost too many digits).  The caller then applies
+// A(i0+nb:, i0+nb:) -= Y W^T.
+constexpr int kQrcp3MaxB = 128;
+constexpr int kQrcp3Chunks = 16;
+constexpr int64_t kQrcp3SmemRows = 24576;  // rows of the reflector staged in shared memory
+struct Qrcp3Args {
+  double* A;
+  int64_t lda;
+  int64_t m, n;
+  int64_t i0;
+  int bJ;
+  double* vn1;        // n, trailing column norms (downdated)
+  double* vn2;        // n, norms at their last exact computation
+  int* redo;          // n, nonzero: recompute the norm at the next block start
+  int64_t* jpvt;      // n, original column index at each position
+  double* tau;        // >= min(m, n)
+  double* W;          // n x bJ, ld n
+  double* ys;         // m, the current column before scaling
+  double* dots;       // kQrcp3Chunks x n partial inner products
+  long long* cand;    // 2 per CTA
+  double* npart;      // 1 per CTA
+  int* ctl;           // [0] stop flag, [1] columns done
+  GridBarrier* bar;
+  int* status;
+  int64_t smem_rows;  // set by the launcher
+};
+cudaError_t launch_qrcp3_block(const Qrcp3Args& a, int num_sms, cudaStream_t st);
+size_t qrcp3_smem_bytes(int64_t m);
+
 // Q = first cols columns of the rows x rows identity
 cudaError_t launch_eye(double* Q, int64_t rows, int64_t cols, int64_t ld, cudaStream_t st);
 // Fill / copy helpers

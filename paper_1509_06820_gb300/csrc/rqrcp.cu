@@ -88,6 +88,15 @@ struct Work {
   double* F = nullptr;        // max(m, n) x k copy of reflectors
   double* svd = nullptr;      // 5 k x k + k: X, G, Vx, Ux, Vs and raw sigma
   int* rotated = nullptr;     // Jacobi sweep flags
+  // deterministic QRCP (level-3 reflection blocking)
+  double* vn1 = nullptr;      // n
+  double* vn2 = nullptr;      // n
+  int* redo = nullptr;        // n
+  double* ys = nullptr;       // m
+  double* dots = nullptr;     // kQrcp3Chunks x n
+  long long* qcand = nullptr; // 2 per SM
+  double* npart = nullptr;    // 1 per SM
+  int* ctl = nullptr;         // 4
   // mixed precision (FP32 storage)
   float* omega32 = nullptr;   // l x m
   float* B32 = nullptr;       // l x n
@@ -130,7 +139,7 @@ Work carve(char op, int64_t m, int64_t n, int64_t k, int b, int p, int sms, char
   Carver c{base};
   const int64_t ell = b + p;
   const int64_t bb = b;
-  if (op != 'Q' && op != 'X') {
+  if (op != 'Q' && op != 'X' && op != 'P') {
     w.omega = c.take<double>((size_t)ell * m);
     w.B = c.take<double>((size_t)ell * n);
     w.swaps = c.take<int64_t>(bb);
@@ -150,6 +159,16 @@ Work carve(char op, int64_t m, int64_t n, int64_t k, int b, int p, int sms, char
   // split-K partial sums: up to ~20 splits of a b x max(n, k) product
   w.skcap = std::max((size_t)4 * sms * 4096, (size_t)20 * bb * (size_t)zc) + 4096;
   w.skpart = c.take<double>(w.skcap);
+  if (op == 'P') {
+    w.vn1 = c.take<double>(n);
+    w.vn2 = c.take<double>(n);
+    w.redo = c.take<int>(n);
+    w.ys = c.take<double>(m);
+    w.dots = c.take<double>((size_t)rq::kQrcp3Chunks * n);
+    w.qcand = c.take<long long>((size_t)2 * sms);
+    w.npart = c.take<double>(sms);
+    w.ctl = c.take<int>(4);
+  }
   if (op == 'T' || op == 'U') {
     w.Wt = c.take<double>((size_t)k * n);
     w.Ahat = c.take<double>((size_t)m * bb);
@@ -519,14 +538,14 @@ size_t rqrcp_workspace_bytes(char op, int64_t m, int64_t n, int64_t k, int b, in
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (op == 'R' || op == 'Q') k = std::min(m, n);
+  if (op == 'R' || op == 'Q' || op == 'P') k = std::min(m, n);
   if (b > k) b = (int)std::max<int64_t>(k, 1);
   return carve(op, m, n, k, b, p, sms, nullptr).bytes;
 }
 
 int rqrcp_reserve(rqrcp_handle_t h, char op, int64_t m, int64_t n, int64_t k, int b, int p) {
   if (!h) return -1;
-  if (op == 'R' || op == 'Q') k = std::min(m, n);
+  if (op == 'R' || op == 'Q' || op == 'P') k = std::min(m, n);
   if (b > k) b = (int)std::max<int64_t>(k, 1);
   return ensure(h, carve(op, m, n, k, b, p, h->num_sms, nullptr, h->fp64_emulation != 0).bytes);
 }
@@ -740,6 +759,62 @@ int qr_factor(rqrcp_handle_t h, int64_t m, int64_t n, double* dA, int64_t lda, i
   int r = begin(h, 'Q', m, n, k, b, 0, &cl);
   if (r) return r;
   return qr_core(cl, m, n, dA, lda, b, d_tau, nullptr);
+}
+
+int qrcp_factor(rqrcp_handle_t h, int64_t m, int64_t n, double* dA, int64_t lda, int b,
+                int64_t* d_jpvt, double* d_tau) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (n < 1) return -3;
+  if (!dA) return -4;
+  if (lda < m) return -5;
+  if (b < 1) return -6;
+  if (!d_jpvt) return -7;
+  if (!d_tau) return -8;
+  const int64_t k = std::min(m, n);
+  if (b > k) b = (int)k;
+  if (b > rq::kQrcp3MaxB) b = rq::kQrcp3MaxB;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    h->err = "qrcp_factor reads each block's length back on the host: not capturable";
+    return RQRCP_ERR_UNSUPPORTED;
+  }
+  Call cl;
+  int r = begin(h, 'P', m, n, k, b, 0, &cl);
+  if (r) return r;
+  Work& w = cl.w;
+  {
+    PhaseScope ps(cl.h, PH_OTHER, 0.0);
+    CKL(1, rq::launch_iota(d_jpvt, n, cl.st));
+    // every norm starts "to be recomputed": the first block computes them all
+    CK(cudaMemsetAsync(w.redo, 1, sizeof(int) * (size_t)n, cl.st));
+  }
+  int64_t i0 = 0;
+  while (i0 < k) {
+    const int bJ = (int)std::min<int64_t>(b, k - i0);
+    const int64_t mJ = m - i0, nJ = n - i0;
+    {
+      PhaseScope ps(cl.h, PH_PANEL, 4.0 * (double)mJ * (double)nJ * bJ);
+      rq::Qrcp3Args qa{dA,      lda,    m,     n,      i0,     bJ,       w.vn1,   w.vn2,
+                       w.redo,  d_jpvt, d_tau, w.W,    w.ys,   w.dots,   w.qcand, w.npart,
+                       w.ctl,   cl.bar, cl.status, 0};
+      CKL(1, rq::launch_qrcp3_block(qa, cl.h->num_sms, cl.st));
+    }
+    int ctl[2] = {0, 0};
+    CK(cudaMemcpyAsync(ctl, w.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, cl.st));
+    CK(cudaStreamSynchronize(cl.st));
+    const int nb = ctl[1];
+    if (nb < 1 || nb > bJ) break;  // a grid barrier gave up: RQRCP_INFO_TIMEOUT is set
+    const int64_t i1 = i0 + nb;
+    if (i1 < m && i1 < n) {
+      // the delayed block update A22 -= Y W^T
+      PhaseScope ps(cl.h, PH_TRAIL, 2.0 * (double)(m - i1) * (double)(n - i1) * nb);
+      CK(gemm(cl, 'N', 'T', 0, m - i1, n - i1, nb, -1.0, dA + i1 + i0 * lda, lda, w.W + i1, n,
+              1.0, dA + i1 + i1 * lda, lda));
+    }
+    i0 = i1;
+  }
+  return RQRCP_OK;
 }
 
 namespace {

@@ -75,6 +75,34 @@ def test_exact_sample_reproduces_qrcp(m, n, b):
     np.testing.assert_allclose(np.triu(F)[:k], Rs[:k], atol=1e-12 * np.abs(Rs).max())
 
 
+@pytest.mark.parametrize("m,n,graded", [(50, 40, False), (40, 70, False), (90, 30, False),
+                                         (120, 120, True), (80, 150, True)])
+def test_qrcp_equals_dgeqp3(m, n, graded):
+    """The deterministic QRCP oracle against LAPACK dgeqp3 (scipy): same pivots,
+    same R entry by entry (same reflector sign convention), A P = Q R.  The
+    graded cases (singular values 1 .. 1e-12) exercise the exact norm
+    recomputation after cancellation."""
+    r = np.random.default_rng(m + 3 * n)
+    if graded:
+        kk = min(m, n)
+        U = np.linalg.qr(r.standard_normal((m, kk)))[0]
+        V = np.linalg.qr(r.standard_normal((n, kk)))[0]
+        A = (U * np.logspace(0, -12, kk)) @ V.T
+    else:
+        A = r.standard_normal((m, n)) * (0.8 ** np.arange(n))[None, :]
+        A = A[:, r.permutation(n)]
+    F, jpvt, tau = oracle.qrcp(A)
+    Rs, piv = sla.qr(A, pivoting=True, mode="r")
+    k = min(m, n)
+    np.testing.assert_array_equal(jpvt[:k], piv[:k])
+    R = np.triu(F)[:k]
+    np.testing.assert_allclose(R, Rs[:k], atol=1e-12 * np.abs(Rs).max())
+    Q = hh.form_q(F, tau, m)
+    assert np.linalg.norm(A[:, jpvt] - Q[:, :k] @ R) <= 1e-14 * np.linalg.norm(A)
+    d = np.abs(np.diag(R))
+    assert np.all(d[1:] <= d[:-1] * (1 + 1e-12))
+
+
 def test_sample_qrcp_partial_equals_qrcp_on_sample():
     r = np.random.default_rng(9)
     B = r.standard_normal((12, 40)) * (0.8 ** np.arange(40))[None, :]
