@@ -81,7 +81,7 @@ def parse():
     ap.add_argument("--only-emulated", action="store_true",
                     help="same as --legs emulated")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
-    ap.add_argument("--legs", default="qr,e2e,cpu,emulated,rsrqrcp,mixed,truncated,serving",
+    ap.add_argument("--legs", default="qr,e2e,cpu,emulated,rsrqrcp,qrcp,mixed,truncated,serving",
                     help="comma-separated extra legs to run after the FP64 step")
     args = ap.parse_args()
     legs = set(x for x in args.legs.split(",") if x)
@@ -334,6 +334,51 @@ def rsrqrcp_leg(args, dev, A0, fp64_ms, emul_ms, stream):
             "device_info": h.sync_info()}
         h.close()
     out["paper_ratio_16k"] = 43.84 / 24.03
+    del A
+    return out
+
+
+def qrcp_leg(args, dev, A0, fp64_ms, stream):
+    """Deterministic QRCP with level-3 reflection blocking (the paper's
+    comparison method) on the same matrix: what the sample saves.  The
+    block kernels (one pass over the trailing matrix per pivot) and the
+    delayed block updates are timed separately with the handle's events."""
+    import torch
+    import paper_1509_06820_gb300 as rq
+    n, b = args.n, args.b
+    A = rq.empty_colmajor(n, n, dev)
+    h = rq.Handle(dev)
+    h.reserve("P", n, n, n, b, 0)
+    # warm-up on a small leading block (kernel attributes, handle scratch)
+    Aw = rq.colmajor(A0[:1024, :1024].clone())
+    rq.qrcp_factor(Aw, b, handle=h)
+    del Aw
+    A.copy_(A0)
+    torch.cuda.synchronize(dev)
+    h.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rq.qrcp_factor(A, b, handle=h)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    prof = h.profile_read()
+    h.profile(False)
+    # level-2 pass: column j reads rows j.. of the n - i0 - 1 other columns of
+    # its block and trailing matrix; summed as 8 (n - j)^2 bytes per pivot
+    l2_bytes = sum(8.0 * (n - j) * (n - j) for j in range(n))
+    blk_ms = prof["panel"][0]
+    out = {
+        "workload": f"qrcp_graded_{n}x{n}_b{b}",
+        "ms_per_step": ms, "gflops": 4.0 / 3.0 * n ** 3 / ms / 1e6,
+        "over_rqrcp_time": ms / fp64_ms if fp64_ms else None,
+        "block_kernels_ms": blk_ms, "block_launches": prof["panel"][2],
+        "level2_pass_gbs": l2_bytes / (blk_ms * 1e-3) / 1e9 if blk_ms else None,
+        "trailing_update_ms": prof["trailing_update"][0],
+        "device_info": h.sync_info(),
+        "paper_ratio_16k": 176.2 / 24.03,
+    }
+    h.close()
     del A
     return out
 
@@ -641,6 +686,8 @@ def main():
     if "rsrqrcp" in args.legs:
         em = extras.get("fp64_emulated", {}).get("rqrcp", {}).get("ms_per_step")
         extras["rsrqrcp"] = rsrqrcp_leg(args, dev, A0, ms, em, stream)
+    if "qrcp" in args.legs:
+        extras["qrcp"] = qrcp_leg(args, dev, A0, ms, stream)
     if "mixed" in args.legs:
         extras["mixed"] = mixed_leg(args, dev, ms, stream)
     if "truncated" in args.legs:
