@@ -81,7 +81,7 @@ def parse():
     ap.add_argument("--only-emulated", action="store_true",
                     help="same as --legs emulated")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
-    ap.add_argument("--legs", default="qr,e2e,cpu,emulated,rsrqrcp,qrcp,mixed,truncated,serving",
+    ap.add_argument("--legs", default="qr,e2e,cpu,emulated,rsrqrcp,qrcp,quality,mixed,truncated,serving",
                     help="comma-separated extra legs to run after the FP64 step")
     args = ap.parse_args()
     legs = set(x for x in args.legs.split(",") if x)
@@ -381,6 +381,95 @@ def qrcp_leg(args, dev, A0, fp64_ms, stream):
     h.close()
     del A
     return out
+
+
+def _quality_matrices(n, dev):
+    """Two seeded n x n test matrices for the error-vs-rank curves, with their
+    singular values: 'graded' (singular values 10^(-12 (i-1)/(n-1)), Haar
+    factors) and 'collinear_block' (n/2 columns of norm ~1 drawn from a 5-dim
+    subspace plus 1e-8 noise, then n/2 columns of a rank-n/2 matrix with
+    singular values 0.3 / i: presorting by norm takes every collinear column
+    first, which is where unpivoted QR fails to reveal rank)."""
+    import torch
+    import synth
+    g = torch.Generator(device="cpu").manual_seed(21)
+    out = {}
+    A = torch.from_numpy(synth.graded(n)).to(dev)
+    out["graded"] = A
+    h = n // 2
+    C = torch.randn(n, 5, generator=g, dtype=torch.float64) @ torch.randn(5, h, generator=g,
+                                                                          dtype=torch.float64)
+    C = C / C.norm(dim=0, keepdim=True) + 1e-8 * torch.randn(n, h, generator=g,
+                                                               dtype=torch.float64)
+    U = torch.linalg.qr(torch.randn(n, h, generator=g, dtype=torch.float64))[0]
+    V = torch.linalg.qr(torch.randn(h, h, generator=g, dtype=torch.float64))[0]
+    D = (U * (0.3 / torch.arange(1, h + 1, dtype=torch.float64))) @ V.T
+    out["collinear_block"] = torch.cat([C, D], dim=1).to(dev)
+    return out
+
+
+def quality_leg(args, dev):
+    """Error-vs-rank curves (relative Frobenius error of the rank-k
+    approximation) for QR after presorting the columns by norm, RQRCP,
+    RSRQRCP, deterministic QRCP, TUXV and the SVD, on synthetic stand-ins for
+    the paper's test matrices, plus the expected norm of the sample-selected
+    column (Fig. selectExpect) measured over seeds against its exact value."""
+    import numpy as np
+    import torch
+    import paper_1509_06820_gb300 as rq
+    n, b, p = 2000, 32, 8
+    ranks = [10, 50, 100, 200, 400, 800]
+    res = {"n": n, "b": b, "p": p, "ranks": ranks}
+
+    def tail_err(R, nrm):
+        r2 = (torch.triu(R[: min(R.shape)]) ** 2).sum(dim=1)
+        suf = torch.flip(torch.cumsum(torch.flip(r2, [0]), 0), [0])
+        return [float(torch.sqrt(suf[k]) / nrm) if k < len(suf) else 0.0 for k in ranks]
+
+    for name, A in _quality_matrices(n, dev).items():
+        nrm = torch.linalg.norm(A)
+        curves = {}
+        order = torch.argsort(A.norm(dim=0), descending=True)
+        F = rq.colmajor(A[:, order].clone())
+        rq.qr_factor(F, b)
+        curves["qr_presorted"] = tail_err(F, nrm)
+        for label, resample in (("rqrcp", False), ("rsrqrcp", True)):
+            h = rq.Handle(dev)
+            h.set_resample(resample)
+            F = rq.colmajor(A.clone())
+            rq.rqrcp_factor(F, b, p, 1, handle=h)
+            curves[label] = tail_err(F, nrm)
+            h.close()
+        F = rq.colmajor(A.clone())
+        rq.qrcp_factor(F, b)
+        curves["qrcp"] = tail_err(F, nrm)
+        tux = []
+        for k in ranks:
+            U, X, V = rq.tuxv(rq.colmajor(A.clone()), k, b, p, 1)
+            tux.append(float(torch.linalg.norm(A - U @ X @ V.T) / nrm))
+        curves["tuxv"] = tux
+        s = torch.linalg.svdvals(A)
+        suf = torch.sqrt(torch.flip(torch.cumsum(torch.flip(s ** 2, [0]), 0), [0]))
+        curves["svd"] = [float(suf[k] / nrm) for k in ranks]
+        res[name] = curves
+    # Fig. selectExpect: first sample pivot over seeds, orthogonal columns phi^j;
+    # exact values stored by tests/golden/gen_select_expectation.py
+    with open(os.path.join(ROOT, "tests", "golden", "select_expectation.json")) as f:
+        exact = {(c["phi"], c["ell"], c["n"]): c["exact"] for c in json.load(f)["cases"]}
+    sel = []
+    m, nc, trials = 96, 32, 2000
+    g = torch.Generator().manual_seed(17)
+    Q = torch.linalg.qr(torch.randn((m, nc), generator=g, dtype=torch.float64))[0]
+    for phi, ell in ((0.9, 8), (0.95, 8), (0.9, 16), (0.95, 16)):
+        A = rq.colmajor((Q * phi ** torch.arange(nc, dtype=torch.float64)).to(dev))
+        picks = [rq.sample_qrcp(rq.sketch(A, ell, seed), 1)[:1] for seed in range(1, trials + 1)]
+        vals = phi ** torch.cat(picks).double().cpu().numpy()
+        sel.append({"phi": phi, "ell": ell, "n": nc, "trials": trials,
+                    "measured": float(vals.mean()),
+                    "stderr": float(vals.std() / np.sqrt(trials)),
+                    "exact": exact[(phi, ell, nc)]})
+    res["select_expectation"] = sel
+    return res
 
 
 def truncated_leg(args, dev):
@@ -690,6 +779,8 @@ def main():
         extras["qrcp"] = qrcp_leg(args, dev, A0, ms, stream)
     if "mixed" in args.legs:
         extras["mixed"] = mixed_leg(args, dev, ms, stream)
+    if "quality" in args.legs and rank == 0:
+        extras["quality"] = quality_leg(args, dev)
     if "truncated" in args.legs:
         extras["truncated"] = truncated_leg(args, dev)
     if "serving" in args.legs and rank == 0:

@@ -25,12 +25,16 @@ Contents (paper sections in brackets):
                      and TUXV [Alg. 7], with j_max iterations and the SVD of
                      the connection matrix X.
 
+* ``selection``   -- the expected norm of the sample-selected column for
+                     orthogonal columns with geometric norms [Sec. 4, sample
+                     bias, Fig. selectExpect], by quadrature over chi variables.
+
 Parity status: every function here is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` against a library routine, a closed form, a
 brute-force enumeration or a statistical law stated in the paper.
 """
 
-from . import philox, householder, rqrcp  # noqa: F401
+from . import philox, householder, rqrcp, selection  # noqa: F401
 from .rqrcp import (  # noqa: F401
     sample_qrcp,
     qrcp,
