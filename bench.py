@@ -733,12 +733,9 @@ def main():
         torch.cuda.synchronize(dev)
 
         def estep():
-            # .t() views of contiguous buffers: one flat pinned copy each way
-            A.t().copy_(Ah.t(), non_blocking=True)
-            jp, tau = rq.rqrcp_factor(A, b, p, 1, handle=h)
-            Ah_out.t().copy_(A.t(), non_blocking=True)
-            jh.copy_(jp, non_blocking=True)
-            th.copy_(tau, non_blocking=True)
+            # the public host-buffer call: uploads in column chunks overlapped
+            # with the sketch, downloads finished columns behind the blocks
+            rq.rqrcp_factor_host(Ah, b, p, 1, dA=A, out=(Ah_out, jh, th), handle=h)
         estep()
         torch.cuda.synchronize(dev)
         barrier()

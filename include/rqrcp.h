@@ -119,6 +119,30 @@ int rqrcp_factor(rqrcp_handle_t handle, int64_t m, int64_t n, double* dA, int64_
                  int p, uint64_t seed, int64_t* d_jpvt, double* d_tau);
 
 /*
+ * rqrcp_factor for a matrix in host memory: the same factorization, with the
+ * host <-> device copies overlapped with the computation.  The matrix goes up
+ * in column chunks on a second stream of the handle, and each chunk's part of
+ * the sketch B = Omega A starts when the chunk has landed; after each group of
+ * blocks the columns that are final (those left of the current block: later
+ * blocks only touch and permute trailing columns) go back while the next
+ * blocks run.  The handle's stream completes only after every copy.
+ *   hA, ldha : in, host, m x n column-major, ldha >= m
+ *   dA, lda  : device work matrix, m x n, lda >= m; holds the factor on exit
+ *   b, p, seed : as in rqrcp_factor
+ *   hF, ldhf : out, host, m x n (ldhf >= m): R and the reflectors, as in dA;
+ *              may be hA itself (every upload precedes every download)
+ *   h_jpvt   : out, host, n int64;  h_tau : out, host, min(m, n) doubles
+ * Host buffers should be page-locked (cudaHostAlloc / cudaHostRegister) for
+ * the copies to overlap; pageable memory works but serialises them.  The
+ * first call (or a larger n) allocates the device pivots and tau.  Results
+ * are available after the handle's stream is synchronised.
+ * Errors: -i for argument i (hA is 4, hF 11).
+ */
+int rqrcp_factor_host(rqrcp_handle_t handle, int64_t m, int64_t n, const double* hA,
+                      int64_t ldha, double* dA, int64_t lda, int b, int p, uint64_t seed,
+                      double* hF, int64_t ldhf, int64_t* h_jpvt, double* h_tau);
+
+/*
  * Mixed-precision RQRCP (Alg. 4 with Eq. 3) on an FP32 matrix.
  * The sketch B = Omega A is a BF16 product with FP32 accumulation (it only
  * steers pivots); the trailing update W = T^T Y^T A2, A2 -= Y W runs as

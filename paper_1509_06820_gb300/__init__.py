@@ -64,6 +64,8 @@ SIGNATURES = [
     ("tuxv", _I, [_P, _I64, _I64, _P, _I64, _I64, _I, _I, _U64, _P, _I64, _P, _I64, _P, _I64]),
     ("tuxv_iter", _I, [_P, _I64, _I64, _P, _I64, _I64, _I, _I, _U64, _I, _P, _I64, _P, _I64, _P,
                        _I64]),
+    ("rqrcp_factor_host", _I, [_P, _I64, _I64, _P, _I64, _P, _I64, _I, _I, _U64, _P, _I64, _P,
+                               _P]),
     ("qrcp_factor", _I, [_P, _I64, _I64, _P, _I64, _I, _P, _P]),
     ("tuxv_svd", _I, [_P, _I64, _I64, _P, _I64, _I64, _I, _I, _U64, _I, _P, _I64, _P, _P, _I64]),
     ("rqrcp_gaussian", _I, [_P, _U64, ctypes.c_uint32, _I64, _I64, _P, _I64]),
@@ -264,6 +266,35 @@ def qr_factor(A, b, handle=None):
     tau = torch.empty(min(m, n), dtype=torch.float64, device=A.device)
     _check(load().qr_factor(h.bind(), m, n, _P(pa), lda, b, _ptr(tau)), h.h)
     return tau
+
+
+def rqrcp_factor_host(hA, b, p, seed, dA=None, out=None, handle=None):
+    """rqrcp_factor of a column-major float64 matrix in (preferably pinned)
+    host memory, copies overlapped with the factorization.  dA: device work
+    matrix (allocated if None).  out: (F_host, jpvt_host, tau_host) buffers
+    (allocated pinned if None; F may be hA).  Enqueued on the current stream;
+    returns (F, jpvt, tau, dA), valid once that stream is synchronised."""
+    if hA.device.type != "cpu" or hA.dtype != torch.float64 or not _is_colmajor(hA):
+        raise ValueError("hA must be a column-major float64 host tensor")
+    m, n = hA.shape
+    dev = torch.device("cuda", torch.cuda.current_device())
+    h = handle or default_handle(dev)
+    if dA is None:
+        dA = empty_colmajor(m, n, dev)
+    pd, lda = _cm(dA, "dA")
+    if out is None:
+        F = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+        jp = torch.empty(n, dtype=torch.int64, pin_memory=True)
+        tau = torch.empty(min(m, n), dtype=torch.float64, pin_memory=True)
+    else:
+        F, jp, tau = out
+    if F.device.type != "cpu" or not _is_colmajor(F) or jp.device.type != "cpu" \
+            or tau.device.type != "cpu":
+        raise ValueError("outputs must be host tensors (F column-major)")
+    _check(load().rqrcp_factor_host(h.bind(), m, n, _P(hA.data_ptr()), _ld(hA), _P(pd), lda, b, p,
+                                    seed, _P(F.data_ptr()), _ld(F), _P(jp.data_ptr()),
+                                    _P(tau.data_ptr())), h.h)
+    return F, jp, tau, dA
 
 
 def qrcp_factor(A, b=64, handle=None):

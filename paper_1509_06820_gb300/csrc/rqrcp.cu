@@ -43,6 +43,12 @@ struct rqrcp_handle_s {
   };
   std::vector<Lane> lanes;
   cudaEvent_t fork = nullptr;
+  // rqrcp_factor_host: copy stream, its events, device pivots and tau
+  cudaStream_t io_st = nullptr;
+  std::vector<cudaEvent_t> io_ev;
+  int64_t* io_jpvt = nullptr;
+  double* io_tau = nullptr;
+  int64_t io_cap = 0;
 };
 
 namespace {
@@ -522,6 +528,11 @@ int rqrcp_destroy(rqrcp_handle_t h) {
   }
   if (h->fork) cudaEventDestroy(h->fork);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  if (h->io_st) cudaStreamSynchronize(h->io_st);
+  for (cudaEvent_t e : h->io_ev) cudaEventDestroy(e);
+  if (h->io_st) cudaStreamDestroy(h->io_st);
+  if (h->io_jpvt) cudaFree(h->io_jpvt);
+  if (h->io_tau) cudaFree(h->io_tau);
   if (h->ws) cudaFree(h->ws);
   if (h->state) cudaFree(h->state);
   delete h;
@@ -648,28 +659,65 @@ int rqrcp_sample_qrcp(rqrcp_handle_t h, int ell, int64_t nc, int steps, double* 
   return RQRCP_OK;
 }
 
-int rqrcp_factor(rqrcp_handle_t h, int64_t m, int64_t n, double* dA, int64_t lda, int b, int p,
-                 uint64_t seed, int64_t* d_jpvt, double* d_tau) {
-  if (!h) return -1;
-  if (m < 1) return -2;
-  if (n < 1) return -3;
-  if (!dA) return -4;
-  if (lda < m) return -5;
-  if (b < 1) return -6;
-  if (p < 0) return -7;
-  if (!d_jpvt) return -9;
-  if (!d_tau) return -10;
+// Host buffers of rqrcp_factor_host and the copy stream that moves them while
+// the factorization runs on the handle's stream.
+struct HostIO {
+  const double* hA;
+  int64_t ldha;
+  double* hF;
+  int64_t ldhf;
+  int64_t* h_jpvt;
+  double* h_tau;
+  cudaStream_t cs;
+  cudaEvent_t* ev;
+  int nev;
+  int used;
+  int64_t chunk;    // columns per upload
+  int64_t group;    // columns per download
+  int64_t copied;   // columns [0, copied) downloaded (enqueued)
+  cudaEvent_t next() { return ev[used++ % nev]; }
+};
+
+// Enqueue on the copy stream, after everything enqueued so far on the compute
+// stream, the download of the final columns [io.copied, upto).
+cudaError_t io_download(Call& cl, HostIO& io, const double* dA, int64_t lda, int64_t m,
+                        int64_t upto) {
+  if (upto <= io.copied) return cudaSuccess;
+  cudaEvent_t e = io.next();
+  cudaError_t r = cudaEventRecord(e, cl.st);
+  if (r == cudaSuccess) r = cudaStreamWaitEvent(io.cs, e, 0);
+  if (r == cudaSuccess)
+    r = cudaMemcpy2DAsync(io.hF + io.copied * io.ldhf, io.ldhf * sizeof(double),
+                          dA + io.copied * lda, lda * sizeof(double), m * sizeof(double),
+                          upto - io.copied, cudaMemcpyDeviceToHost, io.cs);
+  io.copied = upto;
+  return r;
+}
+
+int rqrcp_factor_core(Call& cl, int64_t m, int64_t n, double* dA, int64_t lda, int b, int p,
+                      uint64_t seed, int64_t* d_jpvt, double* d_tau, HostIO* io) {
+  rqrcp_handle_t h = cl.h;
   const int64_t k = std::min(m, n);
-  if (b > k) b = (int)k;
   const int ell = b + p;
-  if (!sizes_fit(h->num_sms, m, n, b, ell)) return RQRCP_ERR_UNSUPPORTED;
-  Call cl;
-  int r = begin(h, 'R', m, n, k, b, p, &cl);
-  if (r) return r;
+  int r;
   Work& w = cl.w;
+  if (io != nullptr) {
+    // the copy stream starts after the work already on the compute stream
+    cudaEvent_t e = io->next();
+    CK(cudaEventRecord(e, cl.st));
+    CK(cudaStreamWaitEvent(io->cs, e, 0));
+  }
   // Alg. 4: Omega^[0] and the initial sample B^[0] = Omega^[0] A^[0]
   {
     PhaseScope ps(cl.h, PH_SKETCH, 2.0 * ell * (double)m * (double)n);
+    if (io != nullptr && w.slA != nullptr) {
+      // the sliced sketch needs all of A: upload first
+      CK(cudaMemcpy2DAsync(dA, lda * sizeof(double), io->hA, io->ldha * sizeof(double),
+                           m * sizeof(double), n, cudaMemcpyHostToDevice, io->cs));
+      cudaEvent_t e = io->next();
+      CK(cudaEventRecord(e, io->cs));
+      CK(cudaStreamWaitEvent(cl.st, e, 0));
+    }
     if (w.slA != nullptr) {
       // FP64-accurate product on the tensor cores: Omega stored transposed so
       // that its rows are contiguous for the slicing pass
@@ -683,6 +731,21 @@ int rqrcp_factor(rqrcp_handle_t h, int64_t m, int64_t n, double* dA, int64_t lda
       rq::OzGemmArgs sk{ell, n,  rq::oz_kpad(m), w.slB, w.exB, w.slA,         w.exA, 1.0, 0.0,
                         w.B, ell, cl.status,     part,  pcap,  cl.h->num_sms};
       CKL(rq::oz_launches(ell, n, sk.Kp, cl.h->num_sms, pcap), rq::launch_oz_gemm(sk, cl.st));
+    } else if (io != nullptr) {
+      // upload in column chunks; each chunk's share of the sketch starts as
+      // soon as it has landed
+      CKL(1, rq::launch_gaussian(seed, kOmegaStream, ell, m, w.omega, ell, nullptr, cl.st));
+      for (int64_t c0 = 0; c0 < n; c0 += io->chunk) {
+        const int64_t nc = std::min(io->chunk, n - c0);
+        CK(cudaMemcpy2DAsync(dA + c0 * lda, lda * sizeof(double), io->hA + c0 * io->ldha,
+                             io->ldha * sizeof(double), m * sizeof(double), nc,
+                             cudaMemcpyHostToDevice, io->cs));
+        cudaEvent_t e = io->next();
+        CK(cudaEventRecord(e, io->cs));
+        CK(cudaStreamWaitEvent(cl.st, e, 0));
+        CK(gemm(cl, 'N', 'N', 0, ell, nc, m, 1.0, w.omega, ell, dA + c0 * lda, lda, 0.0,
+                w.B + c0 * ell, ell));
+      }
     } else {
       CKL(1, rq::launch_gaussian(seed, kOmegaStream, ell, m, w.omega, ell, nullptr, cl.st));
       CK(gemm(cl, 'N', 'N', 0, ell, n, m, 1.0, w.omega, ell, dA, lda, 0.0, w.B, ell));
@@ -739,8 +802,99 @@ int rqrcp_factor(rqrcp_handle_t h, int64_t m, int64_t n, double* dA, int64_t lda
       CK(gemm(cl, 'N', 'N', 0, ell, n2, mt, 1.0, w.omega, ell, dA + (j0 + bJ) + (j0 + bJ) * lda,
               lda, 0.0, Bnext, ell, cl.flag, 1));
     }
+    // columns [0, j0 + bJ) are final (later blocks only touch and permute
+    // trailing columns); after the last block all n are
+    if (io != nullptr) {
+      const int64_t fin = (j0 + bJ >= k) ? n : j0 + bJ;
+      if (fin == n || fin - io->copied >= io->group) CK(io_download(cl, *io, dA, lda, m, fin));
+    }
+  }
+  if (io != nullptr) {
+    cudaEvent_t e = io->next();
+    CK(cudaEventRecord(e, cl.st));
+    CK(cudaStreamWaitEvent(io->cs, e, 0));
+    CK(cudaMemcpyAsync(io->h_jpvt, d_jpvt, n * sizeof(int64_t), cudaMemcpyDeviceToHost, io->cs));
+    CK(cudaMemcpyAsync(io->h_tau, d_tau, k * sizeof(double), cudaMemcpyDeviceToHost, io->cs));
+    // the compute stream completes only after the copies
+    e = io->next();
+    CK(cudaEventRecord(e, io->cs));
+    CK(cudaStreamWaitEvent(cl.st, e, 0));
   }
   return RQRCP_OK;
+}
+
+int rqrcp_factor(rqrcp_handle_t h, int64_t m, int64_t n, double* dA, int64_t lda, int b, int p,
+                 uint64_t seed, int64_t* d_jpvt, double* d_tau) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (n < 1) return -3;
+  if (!dA) return -4;
+  if (lda < m) return -5;
+  if (b < 1) return -6;
+  if (p < 0) return -7;
+  if (!d_jpvt) return -9;
+  if (!d_tau) return -10;
+  const int64_t k = std::min(m, n);
+  if (b > k) b = (int)k;
+  if (!sizes_fit(h->num_sms, m, n, b, b + p)) return RQRCP_ERR_UNSUPPORTED;
+  Call cl;
+  int r = begin(h, 'R', m, n, k, b, p, &cl);
+  if (r) return r;
+  return rqrcp_factor_core(cl, m, n, dA, lda, b, p, seed, d_jpvt, d_tau, nullptr);
+}
+
+int rqrcp_factor_host(rqrcp_handle_t h, int64_t m, int64_t n, const double* hA, int64_t ldha,
+                      double* dA, int64_t lda, int b, int p, uint64_t seed, double* hF,
+                      int64_t ldhf, int64_t* h_jpvt, double* h_tau) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (n < 1) return -3;
+  if (!hA) return -4;
+  if (ldha < m) return -5;
+  if (!dA) return -6;
+  if (lda < m) return -7;
+  if (b < 1) return -8;
+  if (p < 0) return -9;
+  if (!hF) return -11;
+  if (ldhf < m) return -12;
+  if (!h_jpvt) return -13;
+  if (!h_tau) return -14;
+  const int64_t k = std::min(m, n);
+  if (b > k) b = (int)k;
+  if (!sizes_fit(h->num_sms, m, n, b, b + p)) return RQRCP_ERR_UNSUPPORTED;
+  Call cl;
+  int r = begin(h, 'R', m, n, k, b, p, &cl);
+  if (r) return r;
+  cudaError_t e = cudaSuccess;
+  if (!h->io_st) e = cudaStreamCreateWithFlags(&h->io_st, cudaStreamNonBlocking);
+  while (e == cudaSuccess && h->io_ev.size() < 64) {
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) h->io_ev.push_back(ev);
+  }
+  if (e == cudaSuccess && h->io_cap < n) {
+    // device pivots and tau of the call (grown like the workspace)
+    e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->io_st);
+    if (h->io_jpvt) cudaFree(h->io_jpvt);
+    if (h->io_tau) cudaFree(h->io_tau);
+    h->io_jpvt = nullptr;
+    h->io_tau = nullptr;
+    h->io_cap = 0;
+    if (e == cudaSuccess) e = cudaMalloc(&h->io_jpvt, n * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&h->io_tau, n * sizeof(double));
+    if (e == cudaSuccess) h->io_cap = n;
+  }
+  if (e != cudaSuccess) {
+    h->err = std::string("rqrcp_factor_host: ") + cudaGetErrorString(e);
+    return RQRCP_ERR_CUDA;
+  }
+  HostIO io{hA, ldha, hF, ldhf, h_jpvt, h_tau, h->io_st, h->io_ev.data(), (int)h->io_ev.size(),
+            0, 0, 0, 0};
+  // 8 upload chunks; downloads every ~n/16 columns, in whole blocks
+  io.chunk = std::max<int64_t>(1, (n + 7) / 8);
+  io.group = std::max<int64_t>(b, (n + 15) / 16 / b * b);
+  return rqrcp_factor_core(cl, m, n, dA, lda, b, p, seed, h->io_jpvt, h->io_tau, &io);
 }
 
 int qr_factor(rqrcp_handle_t h, int64_t m, int64_t n, double* dA, int64_t lda, int b,

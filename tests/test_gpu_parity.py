@@ -483,3 +483,29 @@ def test_rqrcp_fp64_emulated_trailing(lib, m, n, b, p):
         assert np.linalg.norm(A[:, jp] - Q @ np.triu(F)) <= RTOL_REC * np.linalg.norm(A)
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("m,n,b,p,inplace,pinned", [(700, 500, 32, 8, False, True),
+                                                    (300, 900, 64, 8, True, True),
+                                                    (1000, 1000, 32, 8, False, False),
+                                                    (129, 17, 16, 4, True, False)])
+def test_rqrcp_factor_host_equals_device_call(lib, m, n, b, p, inplace, pinned):
+    """Host buffers, copies overlapped on the handle's copy stream: bit for bit
+    the device call's factor, pivots and tau (same kernels on the same data)."""
+    A = synth.gaussian(m, n, seed=m + 3 * n)
+    dref = to_dev(A)
+    jref, tref = lib.rqrcp_factor(dref, b, p, 7)
+    hA = torch.from_numpy(np.asfortranarray(A))
+    assert hA.stride() == (1, m)
+    if pinned:
+        hA = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t().copy_(hA)
+    out = None
+    if inplace:
+        out = (hA, torch.empty(n, dtype=torch.int64), torch.empty(min(m, n), dtype=torch.float64))
+    F, jp, tau, dA = lib.rqrcp_factor_host(hA, b, p, 7, out=out)
+    torch.cuda.synchronize()
+    assert lib.sync_info() == 0
+    assert torch.equal(jp, jref.cpu())
+    assert torch.equal(tau, tref.cpu())
+    assert torch.equal(F, dref.cpu())
+    assert torch.equal(dA.cpu(), dref.cpu())
