@@ -133,7 +133,10 @@ int rqrcp_factor(rqrcp_handle_t handle, int64_t m, int64_t n, double* dA, int64_
  *              may be hA itself (every upload precedes every download)
  *   h_jpvt   : out, host, n int64;  h_tau : out, host, min(m, n) doubles
  * Host buffers should be page-locked (cudaHostAlloc / cudaHostRegister) for
- * the copies to overlap; pageable memory works but serialises them.  The
+ * the copies to overlap; pageable memory works but serialises them.  hA and
+ * hF in page-locked memory are moved by a copy kernel reading or writing the
+ * mapped host memory (it keeps full speed where the first copy-engine transfer
+ * after seconds of computation does not); other memory by the copy engine.  The
  * first call (or a larger n) allocates the device pivots and tau.  Results
  * are available after the handle's stream is synchronised.
  * Errors: -i for argument i (hA is 4, hF 11).

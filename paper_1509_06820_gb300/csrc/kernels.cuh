@@ -162,6 +162,10 @@ cudaError_t launch_scatter_transpose(const double* src, int64_t lds, int64_t row
 // zeros above, F below; R part (upper triangle, zeros below) into Rout.
 cudaError_t launch_split_qr(const double* F, int64_t ldf, int64_t rows, int64_t cols, int64_t yrow0,
                             double* Y, int64_t ldy, double* Rout, int64_t ldr, cudaStream_t st);
+// dst(r, c) = src(r, c), rows x cols, one side page-locked host memory that is
+// mapped into the device address space (a copy made by the SMs)
+cudaError_t launch_copy_mapped(const double* src, int64_t lds, double* dst, int64_t ldd,
+                               int64_t rows, int64_t cols, cudaStream_t st);
 // X = R^T (lower triangular, zeros above) for the upper triangle R of F's
 // leading cols x cols block
 cudaError_t launch_r_transposed(const double* F, int64_t ldf, int64_t cols, double* X,

@@ -6,6 +6,9 @@
 // columns (all m rows, so completed rows of R move too) are gathered into
 // scratch and scattered back, 16-byte vectorised when the layout allows.
 // jpvt moves alongside.  The pivot list never leaves the device.
+#include <algorithm>
+#include <cstdint>
+
 #include "kernels.cuh"
 
 namespace rq {
@@ -222,6 +225,31 @@ __global__ void r_transposed_kernel(const double* __restrict__ F, int64_t ldf, i
   }
 }
 
+// dst(r, c) = src(r, c) for a rows x cols block where one side is page-locked
+// host memory mapped into the device address space: the SMs move the data
+// over the host link with 16-byte accesses when both sides allow them.
+__global__ void copy_mapped_kernel(const double* __restrict__ src, int64_t lds,
+                                   double* __restrict__ dst, int64_t ldd, int64_t rows,
+                                   int64_t cols, int vec) {
+  for (int64_t c = blockIdx.y; c < cols; c += gridDim.y) {
+    const double* s = src + c * lds;
+    double* d = dst + c * ldd;
+    if (vec) {
+      const int64_t r2 = rows / 2;
+      const double2* s2 = reinterpret_cast<const double2*>(s);
+      double2* d2 = reinterpret_cast<double2*>(d);
+      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < r2;
+           i += (int64_t)gridDim.x * blockDim.x)
+        d2[i] = s2[i];
+      if ((rows & 1) && blockIdx.x == 0 && threadIdx.x == 0) d[rows - 1] = s[rows - 1];
+    } else {
+      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
+           i += (int64_t)gridDim.x * blockDim.x)
+        d[i] = s[i];
+    }
+  }
+}
+
 unsigned grid2(int64_t work) {
   int64_t b = (work + 255) / 256;
   if (b < 1) b = 1;
@@ -252,6 +280,18 @@ cudaError_t launch_split_qr(const double* F, int64_t ldf, int64_t rows, int64_t 
                             double* Y, int64_t ldy, double* Rout, int64_t ldr, cudaStream_t st) {
   if (rows <= 0 || cols <= 0) return cudaSuccess;
   split_qr_kernel<<<grid2(rows * cols), 256, 0, st>>>(F, ldf, rows, cols, yrow0, Y, ldy, Rout, ldr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_mapped(const double* src, int64_t lds, double* dst, int64_t ldd,
+                               int64_t rows, int64_t cols, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0 &&
+                   (lds % 2) == 0 && (ldd % 2) == 0;
+  const int64_t per_col = (rows + 2 * 256 - 1) / (2 * 256);   // blocks covering a column once
+  dim3 grid((unsigned)std::min<int64_t>(std::max<int64_t>(per_col / 4, 1), 64),
+            (unsigned)std::min<int64_t>(cols, 65535));
+  copy_mapped_kernel<<<grid, 256, 0, st>>>(src, lds, dst, ldd, rows, cols, vec ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -666,6 +666,10 @@ struct HostIO {
   int64_t ldha;
   double* hF;
   int64_t ldhf;
+  // device-side addresses of hA / hF when they are page-locked and mapped
+  // (the copies are then made by a kernel), else nullptr (copy engine)
+  const double* mA;
+  double* mF;
   int64_t* h_jpvt;
   double* h_tau;
   cudaStream_t cs;
@@ -686,12 +690,28 @@ cudaError_t io_download(Call& cl, HostIO& io, const double* dA, int64_t lda, int
   cudaEvent_t e = io.next();
   cudaError_t r = cudaEventRecord(e, cl.st);
   if (r == cudaSuccess) r = cudaStreamWaitEvent(io.cs, e, 0);
-  if (r == cudaSuccess)
+  if (r == cudaSuccess && io.mF != nullptr) {
+    r = rq::launch_copy_mapped(dA + io.copied * lda, lda, io.mF + io.copied * io.ldhf, io.ldhf,
+                               m, upto - io.copied, io.cs);
+    if (r == cudaSuccess) count_launch(cl.h, 1);
+  } else if (r == cudaSuccess) {
     r = cudaMemcpy2DAsync(io.hF + io.copied * io.ldhf, io.ldhf * sizeof(double),
                           dA + io.copied * lda, lda * sizeof(double), m * sizeof(double),
                           upto - io.copied, cudaMemcpyDeviceToHost, io.cs);
+  }
   io.copied = upto;
   return r;
+}
+
+// Device-side address of page-locked, mapped host memory; nullptr for
+// pageable memory (or anything else).
+const void* mapped_host(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
 int rqrcp_factor_core(Call& cl, int64_t m, int64_t n, double* dA, int64_t lda, int b, int p,
@@ -712,8 +732,11 @@ int rqrcp_factor_core(Call& cl, int64_t m, int64_t n, double* dA, int64_t lda, i
     PhaseScope ps(cl.h, PH_SKETCH, 2.0 * ell * (double)m * (double)n);
     if (io != nullptr && w.slA != nullptr) {
       // the sliced sketch needs all of A: upload first
-      CK(cudaMemcpy2DAsync(dA, lda * sizeof(double), io->hA, io->ldha * sizeof(double),
-                           m * sizeof(double), n, cudaMemcpyHostToDevice, io->cs));
+      if (io->mA != nullptr)
+        CKL(1, rq::launch_copy_mapped(io->mA, io->ldha, dA, lda, m, n, io->cs));
+      else
+        CK(cudaMemcpy2DAsync(dA, lda * sizeof(double), io->hA, io->ldha * sizeof(double),
+                             m * sizeof(double), n, cudaMemcpyHostToDevice, io->cs));
       cudaEvent_t e = io->next();
       CK(cudaEventRecord(e, io->cs));
       CK(cudaStreamWaitEvent(cl.st, e, 0));
@@ -737,9 +760,13 @@ int rqrcp_factor_core(Call& cl, int64_t m, int64_t n, double* dA, int64_t lda, i
       CKL(1, rq::launch_gaussian(seed, kOmegaStream, ell, m, w.omega, ell, nullptr, cl.st));
       for (int64_t c0 = 0; c0 < n; c0 += io->chunk) {
         const int64_t nc = std::min(io->chunk, n - c0);
-        CK(cudaMemcpy2DAsync(dA + c0 * lda, lda * sizeof(double), io->hA + c0 * io->ldha,
-                             io->ldha * sizeof(double), m * sizeof(double), nc,
-                             cudaMemcpyHostToDevice, io->cs));
+        if (io->mA != nullptr)
+          CKL(1, rq::launch_copy_mapped(io->mA + c0 * io->ldha, io->ldha, dA + c0 * lda, lda, m,
+                                        nc, io->cs));
+        else
+          CK(cudaMemcpy2DAsync(dA + c0 * lda, lda * sizeof(double), io->hA + c0 * io->ldha,
+                               io->ldha * sizeof(double), m * sizeof(double), nc,
+                               cudaMemcpyHostToDevice, io->cs));
         cudaEvent_t e = io->next();
         CK(cudaEventRecord(e, io->cs));
         CK(cudaStreamWaitEvent(cl.st, e, 0));
@@ -889,8 +916,21 @@ int rqrcp_factor_host(rqrcp_handle_t h, int64_t m, int64_t n, const double* hA, 
     h->err = std::string("rqrcp_factor_host: ") + cudaGetErrorString(e);
     return RQRCP_ERR_CUDA;
   }
-  HostIO io{hA, ldha, hF, ldhf, h_jpvt, h_tau, h->io_st, h->io_ev.data(), (int)h->io_ev.size(),
-            0, 0, 0, 0};
+  HostIO io{hA,
+            ldha,
+            hF,
+            ldhf,
+            static_cast<const double*>(mapped_host(hA)),
+            static_cast<double*>(const_cast<void*>(mapped_host(hF))),
+            h_jpvt,
+            h_tau,
+            h->io_st,
+            h->io_ev.data(),
+            (int)h->io_ev.size(),
+            0,
+            0,
+            0,
+            0};
   // 8 upload chunks; downloads every ~n/16 columns, in whole blocks
   io.chunk = std::max<int64_t>(1, (n + 7) / 8);
   io.group = std::max<int64_t>(b, (n + 15) / 16 / b * b);
