@@ -83,6 +83,12 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--legs", default="qr,e2e,cpu,emulated,rsrqrcp,qrcp,quality,mixed,truncated,serving",
                     help="comma-separated extra legs to run after the FP64 step")
+    ap.add_argument("--case", choices=["panel", "gemm_bf16x", "gemm_f64x", "qrcp"], default=None,
+                    help="run one small kernel case (for profiling) instead of the benchmark")
+    ap.add_argument("--shape", default=None,
+                    help="--case gemm_*: transA,transB,M,N,K (e.g. T,N,128,8000,8192)")
+    ap.add_argument("--m", type=int, default=16384, help="--case panel: rows")
+    ap.add_argument("--reps", type=int, default=1, help="--case: timed repetitions")
     args = ap.parse_args()
     legs = set(x for x in args.legs.split(",") if x)
     if args.no_extras:
@@ -598,9 +604,96 @@ def batched_leg(dev, tuner, nprob=64, lanes=8, reps=5, seed=9):
             "device_info": h.sync_info()}
 
 
+# ------------------------------------------------------------------ kernel cases
+def run_case(args):
+    """One small kernel case for profiling (prints one JSON line):
+      panel       qr_factor of an m x 4b N(0,1) matrix (four b-column panels)
+      gemm_bf16x  C = -op(A) op(B) + C, split-BF16 x3 (FP32 operands)
+      gemm_f64x   the same in FP64 on the tensor cores (exact slices)
+      qrcp        qrcp_factor of an n x n N(0,1) matrix, block b
+    Two untimed runs precede the timed ones."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1509_06820_gb300 as rq
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    g = torch.Generator(device=dev).manual_seed(1)
+    h = rq.Handle(dev)
+    out = {"case": args.case}
+    if args.case in ("panel", "qrcp"):
+        if args.case == "panel":
+            m, n = args.m, 4 * args.b
+        else:
+            m = n = args.n
+        A0 = rq.colmajor(torch.randn((m, n), generator=g, device=dev, dtype=torch.float64))
+        A = rq.empty_colmajor(m, n, dev)
+
+        def call():
+            A.copy_(A0)
+            if args.case == "panel":
+                rq.qr_factor(A, args.b, handle=h)
+            else:
+                rq.qrcp_factor(A, args.b, handle=h)
+        out.update({"m": m, "n": n, "b": args.b})
+    else:
+        ta, tb, M, N, K = args.shape.split(",")
+        M, N, K = int(M), int(N), int(K)
+        dt = torch.float32 if args.case == "gemm_bf16x" else torch.float64
+
+        def colm(r, c):
+            return rq.colmajor(torch.randn((r, c), generator=g, device=dev, dtype=dt))
+        Am = colm(M, K) if ta == "N" else colm(K, M)
+        Bm = colm(K, N) if tb == "N" else colm(N, K)
+        C = colm(M, N)
+        fn = rq.gemm_bf16x if args.case == "gemm_bf16x" else rq.gemm_f64x
+
+        def call():
+            fn(Am, Bm, ta, tb, alpha=-1.0, beta=1.0, C=C, handle=h)
+        out.update({"transA": ta, "transB": tb, "M": M, "N": N, "K": K})
+    for _ in range(2):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h.profile(True)
+    e0.record()
+    for _ in range(args.reps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    out["ms_per_call"] = e0.elapsed_time(e1) / args.reps
+    out["phases_ms"] = {k: round(v[0] / args.reps, 4) for k, v in h.profile_read().items() if v[2]}
+    h.profile(False)
+    out["device_info"] = h.sync_info()
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ replicas
+def max_over_ranks(x, world, device):
+    """The largest of the ranks' values of x: the job's time is its slowest
+    replica's (no collective touches the data path; this one reduces a
+    timing)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(flops_per_rank, ms, world):
+    """Whole-job GFLOP/s: every replica factors its own matrix in the job's
+    time `ms` (the max over ranks)."""
+    return world * flops_per_rank / (ms / 1e3) / 1e9
+
+
 # ------------------------------------------------------------------ GPU leg
 def main():
     args = parse()
+    if args.case is not None:
+        run_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -661,12 +754,9 @@ def main():
     prof = h.profile_read()
     h.profile(False)
     info = h.sync_info()
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     fl = flops_geqrf(m, n)
-    value = world * fl / (ms / 1e3) / 1e9
+    value = job_rate(fl, ms, world)
     gpu_launches = sum(v[2] for v in prof.values())
 
     peaks = {}
@@ -747,11 +837,8 @@ def main():
         x1.record(stream)
         torch.cuda.synchronize(dev)
         e2e_ms = x0.elapsed_time(x1) / args.steps
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        extras["e2e"] = {"value": world * fl / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
+        e2e_ms = max_over_ranks(e2e_ms, world, dev)
+        extras["e2e"] = {"value": job_rate(fl, e2e_ms, world), "unit": UNIT,
                          "ms_per_step": e2e_ms, "h2d_bytes_per_step": m * n * 8,
                          "d2h_bytes_per_step": m * n * 8 + n * 8 + min(m, n) * 8}
         del Ah, Ah_out
