@@ -236,12 +236,27 @@ __global__ void __launch_bounds__(Q3NT, 1) qrcp3_block_kernel(Qrcp3Args a) {
       for (int u = 0; u < 8; ++u) acc[u] = 0.0;
       int64_t q = q0 + lane;
       const int64_t qs = q1 < staged ? q1 : staged;
-      for (; q + 7 * 32 < qs; q += 8 * 32) {
+      if (q + 7 * 32 < qs) {
+        // software-pipelined: the next 8 loads are in flight while the FP64
+        // pipe works through the current 8 products
         double x[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) x[u] = __ldcg(col + q + u * 32);
+        while (true) {
+          const int64_t qn = q + 8 * 32;
+          const bool more = qn + 7 * 32 < qs;
+          double xn[8];
+          if (more) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc[u] = fma(s_y[q + u * 32], x[u], acc[u]);
+            for (int u = 0; u < 8; ++u) xn[u] = __ldcg(col + qn + u * 32);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) acc[u] = fma(s_y[q + u * 32], x[u], acc[u]);
+          q = qn;
+          if (!more) break;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) x[u] = xn[u];
+        }
       }
       for (; q < qs; q += 32) acc[0] = fma(s_y[q], __ldcg(col + q), acc[0]);
       // rows beyond the staged part: y from global memory
