@@ -525,7 +525,8 @@ def truncated_leg(args, dev):
 
 def serving_leg(args, dev):
     """Served TRQRCP: Poisson arrivals, m, n ~ U{256..4096}, k ~ U{16..128},
-    A = X Y^T (FP32), continuous batching over 8 slots, autotuned b/p."""
+    A = X Y^T (FP32), continuous batching over 16 slots (each request's
+    launches capped at a quarter of the SMs), autotuned b/p."""
     from paper_1509_06820_gb300.serve import Server
     from paper_1509_06820_gb300.autotune import Tuner
     t0 = time.perf_counter()
@@ -534,7 +535,7 @@ def serving_leg(args, dev):
     tune_s = time.perf_counter() - t0
     # primary: slots that launch each request's kernels directly (no graph
     # capture on the host's critical path)
-    srv = Server.on_gpu(dev, slots=8, tuner=tuner, use_graphs=False)
+    srv = Server.on_gpu(dev, slots=16, tuner=tuner, use_graphs=False)
     stats = srv.run_poisson(rate=args.serve_rate, duration=args.serve_seconds, warmup=1.0, seed=7)
     stats = {"mode": "eager launches per request", **stats}
     # the same server below saturation, for the service-time latency
@@ -544,7 +545,7 @@ def serving_leg(args, dev):
                                                      "p50_ms", "p99_ms", "gflops")}
     del srv
     # the same stream with per-(slot, size bucket) CUDA graphs captured on first use
-    gsrv = Server.on_gpu(dev, slots=8, tuner=tuner)
+    gsrv = Server.on_gpu(dev, slots=16, tuner=tuner)
     gst = gsrv.run_poisson(rate=args.serve_rate, duration=args.serve_seconds, warmup=1.0, seed=7)
     stats["graphs"] = {k: gst[k] for k in ("offered_rate", "requests", "throughput_rps", "p50_ms",
                                            "p99_ms", "gflops")}
@@ -556,10 +557,12 @@ def serving_leg(args, dev):
     return stats
 
 
-def batched_leg(dev, tuner, nprob=64, lanes=8, reps=5, seed=9):
+def batched_leg(dev, tuner, nprob=64, lanes=16, reps=5, seed=9):
     """One static batch of served-size problems (m, n ~ U{256..4096},
     k ~ U{16..128}, A = X Y^T in FP32, autotuned b/p) through trqrcp_batched
-    on `lanes` worker streams, captured as one CUDA graph and replayed."""
+    on `lanes` worker streams (each launch capped at a quarter of the SMs so
+    that the lanes run side by side), captured as one CUDA graph and
+    replayed."""
     import numpy as np
     import torch
     import paper_1509_06820_gb300 as rq
@@ -579,6 +582,8 @@ def batched_leg(dev, tuner, nprob=64, lanes=8, reps=5, seed=9):
         Yf = torch.randn((n, k), generator=g, device=dev)
         probs.append((rq.colmajor(X @ Yf.t()), k, b, p, 1000 + i))
     h = rq.Handle(dev)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    h.set_max_sms(max(16, nsm // 4))
     h.reserve_batched(lanes, max(s[0] for s in specs), max(s[1] for s in specs),
                       max(s[2] for s in specs), max(s[3] for s in specs),
                       max(s[4] for s in specs))
@@ -598,7 +603,8 @@ def batched_leg(dev, tuner, nprob=64, lanes=8, reps=5, seed=9):
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / reps
     flops = sum(request_flops(m, n, k, b + p) for (m, n, k, b, p) in specs)
-    return {"problems": nprob, "lanes": lanes, "ms_per_batch": ms,
+    return {"problems": nprob, "lanes": lanes, "max_sms_per_launch": max(16, nsm // 4),
+            "ms_per_batch": ms,
             "problems_per_s": nprob / (ms / 1e3), "gflops": flops / (ms / 1e3) / 1e9,
             "launch": "one CUDA graph per batch (fork to the lanes, join)",
             "device_info": h.sync_info()}

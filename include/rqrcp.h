@@ -79,7 +79,7 @@ size_t rqrcp_workspace_bytes(char op, int64_t m, int64_t n, int64_t k, int b, in
  * not allocate, e.g. before stream capture). */
 int rqrcp_reserve(rqrcp_handle_t handle, char op, int64_t m, int64_t n, int64_t k, int b, int p);
 
-/* Handle options (value 0/1, default 0).
+/* Handle options (value 0/1, default 0, unless stated).
  * RQRCP_OPT_FP64_EMULATION: run the sketch and the two large products of the
  * FP64 trailing update (rqrcp_factor, qr_factor; blocks of b <= 64) on the
  * BF16 tensor cores with the FP64-accurate slicing of rqrcp_gemm_f64x instead
@@ -87,9 +87,16 @@ int rqrcp_reserve(rqrcp_handle_t handle, char op, int64_t m, int64_t n, int64_t 
  * RQRCP_OPT_RESAMPLE: rqrcp_factor runs Alg. 5 (RSRQRCP) -- before every block
  * after the first, a fresh seeded GIID sample of the updated trailing matrix
  * (Philox stream 0x100 + J after block J) replaces the sample update of
- * Eq. (3); the paper's comparison for the cost of repeated sampling. */
+ * Eq. (3); the paper's comparison for the cost of repeated sampling.
+ * RQRCP_OPT_MAX_SMS (value = a number of SMs, 0 = all, the default): every
+ * launch of the handle's calls uses at most that many CTAs per wave: grids of
+ * the cooperative kernels, the persistent tensor-core GEMMs and their split-K
+ * choice.  Calls of several handles on separate streams then share the GPU
+ * instead of each filling it (the serving slots use this).  Set it before
+ * rqrcp_reserve: the scratch size depends on it.  -3 for a negative value. */
 #define RQRCP_OPT_FP64_EMULATION 1
 #define RQRCP_OPT_RESAMPLE 2
+#define RQRCP_OPT_MAX_SMS 3
 int rqrcp_set_option(rqrcp_handle_t handle, int option, int value);
 
 /* Wait for the handle's stream, then return the device status word in *info

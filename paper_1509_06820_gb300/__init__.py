@@ -24,6 +24,7 @@ RQRCP_ERR_UNSUPPORTED = 1002
 RQRCP_ERR_BATCH = 1003
 OPT_FP64_EMULATION = 1
 OPT_RESAMPLE = 2
+OPT_MAX_SMS = 3
 INFO_NONFINITE = 1
 INFO_RESAMPLED = 2
 INFO_TIMEOUT = 4
@@ -137,6 +138,10 @@ class Handle:
     def set_fp64_emulation(self, on=True):
         """Run the FP64 trailing update on the BF16 tensor cores (exact slicing)."""
         _check(load().rqrcp_set_option(self.h, OPT_FP64_EMULATION, 1 if on else 0), self.h)
+
+    def set_max_sms(self, n):
+        """Cap the CTAs per wave of this handle's launches at n SMs (0: all)."""
+        _check(load().rqrcp_set_option(self.h, OPT_MAX_SMS, int(n)), self.h)
 
     def set_resample(self, on=True):
         """rqrcp_factor runs Alg. 5 (a fresh sample every block) instead of Eq. (3)."""

@@ -16,7 +16,8 @@
 struct rqrcp_handle_s {
   cudaStream_t stream = nullptr;
   int device = 0;
-  int num_sms = 1;
+  int num_sms = 1;       // SMs the handle's launches may use (RQRCP_OPT_MAX_SMS)
+  int dev_sms = 1;       // SMs of the device
   char* ws = nullptr;
   size_t ws_bytes = 0;
   int* state = nullptr;  // [0] status word, [1] re-sample flag; barrier at byte 64
@@ -505,6 +506,7 @@ int rqrcp_create(rqrcp_handle_t* handle, void* cuda_stream) {
   h->stream = static_cast<cudaStream_t>(cuda_stream);
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  h->dev_sms = h->num_sms;
   if (e == cudaSuccess) e = cudaMalloc(&h->state, 256);
   if (e == cudaSuccess) e = cudaMemset(h->state, 0, 256);
   if (e != cudaSuccess) {
@@ -569,6 +571,11 @@ int rqrcp_set_option(rqrcp_handle_t h, int option, int value) {
   }
   if (option == RQRCP_OPT_RESAMPLE) {
     h->resample = value != 0;
+    return RQRCP_OK;
+  }
+  if (option == RQRCP_OPT_MAX_SMS) {
+    if (value < 0) return -3;
+    h->num_sms = (value == 0 || value > h->dev_sms) ? h->dev_sms : value;
     return RQRCP_OK;
   }
   return -2;

@@ -16,7 +16,12 @@ sample, reflector and inner-product state on the device while it runs.
   the bucket, A zero-padded -- zero columns are never pivoted and zero rows
   leave the reflectors unchanged, and the Philox compression matrix is
   prefix-stable in m), later ones replay it.  With graphs off the calls are
-  enqueued eagerly.
+  enqueued eagerly at the request's exact size, into the request's own output
+  tensors.
+* Each slot's handle caps the SMs its launches spread over (by default a
+  quarter of the device's SMs), so requests of different slots run side
+  by side instead of each split-K product or cooperative kernel filling the
+  GPU.
 * Completion is polled with CUDA events; latency = completion - arrival.
 * b and p per size bucket come from the autotuner table (autotune.py).
 
@@ -65,15 +70,17 @@ def factors(req):
     return jpvt[keep][: req.n], tau, Y, R[:, keep], rdiag
 
 
-def make_input(req, out, stream):
+def make_input(req, out, stream, gen=None):
     """The request's matrix A = X Y^T (X: m x k, Y: n x k, N(0,1) from the
-    request's seed) written into the column-major FP32 view `out`."""
+    request's seed: one draw of (m + n) x k, X its first m rows) written into
+    the column-major FP32 view `out`.  gen: a CUDA generator to reseed (one
+    per slot saves creating one per request)."""
     with torch.cuda.stream(stream):
-        g = torch.Generator(device=out.device)
+        g = gen if gen is not None else torch.Generator(device=out.device)
         g.manual_seed(int(req.seed))
-        X = torch.randn((req.m, req.k), generator=g, device=out.device, dtype=torch.float32)
-        Y = torch.randn((req.n, req.k), generator=g, device=out.device, dtype=torch.float32)
-        out[: req.m, : req.n].t().copy_(Y @ X.t())
+        XY = torch.randn((req.m + req.n, req.k), generator=g, device=out.device,
+                         dtype=torch.float32)
+        out[: req.m, : req.n].t().copy_(XY[req.m:] @ XY[: req.m].t())
 
 
 class Slot:
@@ -84,11 +91,16 @@ class Slot:
     needs more, the slot's graphs are dropped before the scratch grows.
     """
 
-    def __init__(self, device, max_m, max_n, max_k, use_graphs, bp_choices=((128, 16), (64, 16))):
+    def __init__(self, device, max_m, max_n, max_k, use_graphs, bp_choices=((128, 16), (64, 16)),
+                 max_sms=0):
         self.device = device
         self.stream = torch.cuda.Stream(device)
         self.handle = Handle(device)
+        # cap the SMs one request's launches spread over, so that the slots'
+        # requests run side by side instead of each filling the GPU
+        self.handle.set_max_sms(max_sms)
         self.event = torch.cuda.Event()
+        self.gen = torch.Generator(device=device)
         self.req = None
         self.use_graphs = use_graphs
         self.graphs = {}  # (bucket, b, p) -> (graph, A view, outputs)
@@ -119,6 +131,9 @@ class Slot:
 
     def launch(self, req):
         M, N, K = req.bucket
+        if not self.use_graphs:
+            self._launch_eager(req)
+            return
         entry = self.graphs.get((req.bucket, req.b, req.p))
         if entry is None:
             A, outs = self._buffers(req.bucket)
@@ -138,20 +153,44 @@ class Slot:
         graph, A, outs = entry
         self.req = req
         req.slot = self
+        k, m = req.k, req.m
         with torch.cuda.stream(self.stream):
             if req.m < M or req.n < N:
                 A.zero_()
-            make_input(req, A, self.stream)
+            make_input(req, A, self.stream, self.gen)
             if graph is not None:
                 graph.replay()
             else:
                 trqrcp_mixed(A, K, req.b, req.p, 1, handle=self.handle, out=outs)
-            # the request keeps its own copy of the factors; the slot's
-            # buffers are reused by the next request
+            # the slot's buffers are reused by the next request: the request
+            # keeps its own copy of the factors
             jpvt, tau, Y, R, rdiag = outs
-            k, m = req.k, req.m
             req.result = (jpvt.clone(), tau[:k].clone(), Y[:m, :k].clone(), R[:k, :].clone(),
                           rdiag[:k].clone())
+            self.event.record(self.stream)
+
+    def _launch_eager(self, req):
+        """Eager launches at the request's own size (no bucket padding, which
+        only serves graph reuse), written straight into the request's own
+        output tensors (no copies)."""
+        M, N, K = req.bucket
+        self._reserve(M, N, K, req.b, req.p)
+        A = self.bufA[:M, :N]
+        self.req = req
+        req.slot = self
+        with torch.cuda.stream(self.stream):
+            if req.m < M or req.n < N:
+                A.zero_()
+            make_input(req, A, self.stream, self.gen)
+            own = (torch.empty(N, dtype=torch.int64, device=self.device),
+                   torch.empty(K, dtype=torch.float64, device=self.device),
+                   empty_colmajor(M, K, self.device, torch.float32),
+                   empty_colmajor(K, N, self.device, torch.float32),
+                   torch.empty(K, dtype=torch.float64, device=self.device))
+            trqrcp_mixed(A, K, req.b, req.p, 1, handle=self.handle, out=own)
+            jpvt, tau, Y, R, rdiag = own
+            k, m = req.k, req.m
+            req.result = (jpvt, tau[:k], Y[:m, :k], R[:k, :], rdiag[:k])
             self.event.record(self.stream)
 
     def done(self):
@@ -183,9 +222,18 @@ class Server:
 
     @classmethod
     def on_gpu(cls, device="cuda", slots=8, use_graphs=True, max_m=4096, max_n=4096, max_k=128,
-               **kw):
+               max_sms=None, **kw):
+        """max_sms: SMs per request's launches (None: a quarter of the
+        device's SMs, at least 16; 0: all)."""
         dev = torch.device(device)
-        return cls([Slot(dev, max_m, max_n, max_k, use_graphs) for _ in range(slots)], **kw)
+        # size buckets only serve graph reuse: eager slots solve exact sizes
+        kw.setdefault("bucket", 512 if use_graphs else 1)
+        kw.setdefault("kbucket", 32 if use_graphs else 1)
+        if max_sms is None:
+            nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+            max_sms = max(16, nsm // 4)
+        return cls([Slot(dev, max_m, max_n, max_k, use_graphs, max_sms=max_sms)
+                    for _ in range(slots)], **kw)
 
     # ---------------------------------------------------------------- sizing
     def plan(self, req):
