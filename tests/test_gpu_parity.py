@@ -509,3 +509,16 @@ def test_rqrcp_factor_host_equals_device_call(lib, m, n, b, p, inplace, pinned):
     assert torch.equal(tau, tref.cpu())
     assert torch.equal(F, dref.cpu())
     assert torch.equal(dA.cpu(), dref.cpu())
+
+
+def test_max_sms_cap_keeps_parity(lib):
+    """RQRCP_OPT_MAX_SMS: a handle whose launches use at most 20 SMs (smaller
+    cooperative grids, no split-K beyond 20 CTAs) still matches the oracle."""
+    h = lib.Handle()
+    h.set_max_sms(20)
+    A = synth.gaussian(700, 600, seed=12)
+    _check_rqrcp(lib, A, 32, 8, 1, handle=h)
+    with pytest.raises(lib.RqrcpError):
+        h.set_max_sms(-1)
+    h.set_max_sms(0)   # back to all SMs
+    _check_rqrcp(lib, A, 32, 8, 1, handle=h)
