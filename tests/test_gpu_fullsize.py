@@ -118,3 +118,28 @@ def test_fullsize_trqrcp_tuxv(lib):
     e_opt = (((sig[k:] ** 2).sum().item() + 1e-16 * m * n) / a2) ** 0.5
     assert e_tx <= e_tr * (1 + 1e-9)
     assert 0.99 * e_opt <= e_tx <= 1.05 * e_opt, (e_tx, e_opt)
+
+
+@pytest.mark.parametrize("option", ["fp64_emulation", "resample"])
+def test_fullsize_rqrcp_options(lib, option):
+    """The same 16384^2 graded factorization with the trailing update on the
+    tensor cores (exact slices) or with Alg. 5's fresh sample per block:
+    A P = Q R on sampled columns to the FP64 bound."""
+    n, b, p = 16384, 64, 8
+    dev = torch.device("cuda")
+    h = lib.Handle()
+    if option == "fp64_emulation":
+        h.set_fp64_emulation(True)
+    else:
+        h.set_resample(True)
+    A = synth.graded_device(n, dev)
+    dA = lib.colmajor(A.clone())
+    jpvt, tau = lib.rqrcp_factor(dA, b, p, 1, handle=h)
+    assert h.sync_info() == 0
+    assert torch.equal(torch.sort(jpvt).values, torch.arange(n, device=dev))
+    g = torch.Generator().manual_seed(4)
+    cols = torch.randperm(n, generator=g)[:16].to(dev)
+    rows = torch.arange(n, device=dev)[:, None]
+    X = _apply_q(dA, tau, dA[:, cols] * (rows <= cols[None, :]))
+    err = (A[:, jpvt[cols]] - X).norm(dim=0).max().item() / torch.linalg.norm(A).item()
+    assert err <= 1e-13, err
