@@ -83,7 +83,8 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--legs", default="qr,e2e,cpu,emulated,rsrqrcp,qrcp,quality,mixed,truncated,serving",
                     help="comma-separated extra legs to run after the FP64 step")
-    ap.add_argument("--case", choices=["panel", "gemm_bf16x", "gemm_f64x", "qrcp"], default=None,
+    ap.add_argument("--case", choices=["panel", "gemm_bf16x", "gemm_f64x", "qrcp", "sample"],
+                    default=None,
                     help="run one small kernel case (for profiling) instead of the benchmark")
     ap.add_argument("--shape", default=None,
                     help="--case gemm_*: transA,transB,M,N,K (e.g. T,N,128,8000,8192)")
@@ -617,6 +618,8 @@ def run_case(args):
       gemm_bf16x  C = -op(A) op(B) + C, split-BF16 x3 (FP32 operands)
       gemm_f64x   the same in FP64 on the tensor cores (exact slices)
       qrcp        qrcp_factor of an n x n N(0,1) matrix, block b
+      sample      the sample QRCP kernel alone: b pivots on a (b + p) x n
+                  N(0,1) sample
     Two untimed runs precede the timed ones."""
     import torch
     import __graft_entry__
@@ -627,7 +630,16 @@ def run_case(args):
     g = torch.Generator(device=dev).manual_seed(1)
     h = rq.Handle(dev)
     out = {"case": args.case}
-    if args.case in ("panel", "qrcp"):
+    if args.case == "sample":
+        ell, n = args.b + args.p, args.n
+        B0 = rq.colmajor(torch.randn((ell, n), generator=g, device=dev, dtype=torch.float64))
+        B = rq.empty_colmajor(ell, n, dev)
+
+        def call():
+            B.copy_(B0)
+            rq.sample_qrcp(B, args.b, handle=h)
+        out.update({"ell": ell, "n": n, "steps": args.b})
+    elif args.case in ("panel", "qrcp"):
         if args.case == "panel":
             m, n = args.m, 4 * args.b
         else:
