@@ -38,8 +38,8 @@ def _check_qrcp(lib, A, b, max_ties=2):
     assert np.linalg.norm(np.triu(F[:k]) - Ro) <= 1e-10 * np.linalg.norm(Ro)
     sig = np.abs(np.diag(Ro)) >= 1e-6 * abs(Ro[0, 0])
     assert np.abs(t - to)[sig].max() <= 1e-9
-    Q = hh.form_q(F, t, m)
-    assert np.linalg.norm(A[:, jp] - Q[:, :k] @ np.triu(F[:k])) <= 1e-13 * np.linalg.norm(A)
+    Q = hh.form_q(F, t, k)
+    assert np.linalg.norm(A[:, jp] - Q @ np.triu(F[:k])) <= 1e-13 * np.linalg.norm(A)
     return F, jp, t
 
 
