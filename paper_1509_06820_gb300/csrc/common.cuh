@@ -2,12 +2,28 @@
 // software grid barrier for cooperative launches, small reductions.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
 #include "../../include/rqrcp.h"
 
 namespace rq {
+
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current
+// device, once per device (the attribute belongs to the device, and several
+// host threads may launch): `done` keeps one bit per device ordinal < 64.
+template <typename Kernel>
+inline cudaError_t ensure_smem_attr(Kernel kernel, int bytes, std::atomic<uint64_t>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev < 64 ? (uint64_t{1} << dev) : 0;
+  if (bit != 0 && (done.load(std::memory_order_acquire) & bit) != 0) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit != 0) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
 
 // Device status word layout (one int in the handle's workspace):
 //   0                       -> ok

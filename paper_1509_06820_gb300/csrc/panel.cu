@@ -313,14 +313,10 @@ cudaError_t launch_panel(const PanelArgs& a, int num_sms, cudaStream_t st) {
   const int64_t chunk = (a.mJ + G - 1) / G;
   const size_t smem = panel_smem(chunk, a.bJ);
   if (smem > kPanelSmemLimit) return cudaErrorInvalidValue;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kPanelSmemLimit);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  cudaError_t e = cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), st);
+  static std::atomic<uint64_t> attr_done{0};
+  cudaError_t e = ensure_smem_attr(panel_kernel, (int)kPanelSmemLimit, attr_done);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), st);
   if (e != cudaSuccess) return e;
   PanelArgs args = a;
   void* params[] = {&args};

@@ -322,15 +322,11 @@ size_t qrcp3_smem_bytes(int64_t m) {
 
 cudaError_t launch_qrcp3_block(const Qrcp3Args& a, int num_sms, cudaStream_t st) {
   if (a.bJ < 1 || a.bJ > kQrcp3MaxB) return cudaErrorInvalidValue;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(qrcp3_block_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kQrcp3SmemRows * sizeof(double)));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  cudaError_t e = cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), st);
+  static std::atomic<uint64_t> attr_done{0};
+  cudaError_t e = ensure_smem_attr(qrcp3_block_kernel, (int)(kQrcp3SmemRows * sizeof(double)),
+                                   attr_done);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.ctl, 0, 2 * sizeof(int), st);
   if (e != cudaSuccess) return e;
   Qrcp3Args args = a;

@@ -274,15 +274,10 @@ cudaError_t launch_sample_qrcp(const SampleQrcpArgs& a, int num_sms, cudaStream_
   const int64_t chunk = (a.nc + G - 1) / G;
   const size_t smem = smem_bytes(a.ell, chunk);
   if (a.ell > MAX_ELL || smem > kSmemLimit) return cudaErrorInvalidValue;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(sample_qrcp_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmemLimit);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  cudaError_t e = cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), st);
+  static std::atomic<uint64_t> attr_done{0};
+  cudaError_t e = ensure_smem_attr(sample_qrcp_kernel, (int)kSmemLimit, attr_done);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), st);
   if (e != cudaSuccess) return e;
   SampleQrcpArgs args = a;
   void* params[] = {&args};

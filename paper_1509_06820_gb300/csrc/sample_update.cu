@@ -61,13 +61,10 @@ __global__ void w11_kernel(const double* __restrict__ S, int ell, const double* 
 cudaError_t launch_w11(const double* S, int ell, const double* R11, int64_t ldr, int bJ,
                        double* W11, int* flag, int* status, cudaStream_t st) {
   const size_t smem = ((size_t)bJ * bJ + (size_t)W11_ROWS * bJ) * sizeof(double);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(w11_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (128 * 128 + W11_ROWS * 128) * (int)sizeof(double));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<uint64_t> attr_done{0};
+  cudaError_t e = ensure_smem_attr(w11_kernel, (128 * 128 + W11_ROWS * 128) * (int)sizeof(double),
+                                   attr_done);
+  if (e != cudaSuccess) return e;
   const int grid = (bJ + W11_ROWS - 1) / W11_ROWS;
   w11_kernel<<<grid, 32 * W11_ROWS, smem, st>>>(S, ell, R11, ldr, bJ, W11, flag, status);
   return cudaGetLastError();
