@@ -83,7 +83,7 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--legs", default="qr,e2e,cpu,emulated,rsrqrcp,qrcp,quality,mixed,truncated,serving",
                     help="comma-separated extra legs to run after the FP64 step")
-    ap.add_argument("--case", choices=["panel", "gemm_bf16x", "gemm_f64x", "qrcp", "sample"],
+    ap.add_argument("--case", choices=["panel", "gemm_bf16x", "gemm_f64x", "qrcp", "sample", "mixed"],
                     default=None,
                     help="run one small kernel case (for profiling) instead of the benchmark")
     ap.add_argument("--shape", default=None,
@@ -206,6 +206,20 @@ def run_reference(args):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def measured_peaks():
+    """MEASURED_PEAKS.json as a dict ({} when absent)."""
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def fp64_peak_tflops(peaks):
+    """FP64 peak for a dtype without a measured figure: the measured BF16
+    burst rate times the nominal FP64 : BF16 ratio (1.25 : 2250)."""
+    return (peaks.get("bf16_tflops") or 1900.0) * 1.25 / 2250.0
 
 
 # ------------------------------------------------------------------ extra legs
@@ -504,7 +518,17 @@ def truncated_leg(args, dev):
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1) / steps
         fl = 2.0 * m * n * k + 2.0 * ell * m * n + extra
-        out[name] = {"ms": ms, "gflops": fl / (ms / 1e3) / 1e9, "flop_count": "2mnk + 2lmn (+2mnk)"}
+        # fewest HBM bytes: A read once by the sketch, once per block by
+        # Y2^T A (k / b blocks), and once more by Z1 = A V1 for TUXV
+        passes = 1 + k // b + (1 if extra else 0)
+        hbm_bytes = passes * 8.0 * m * n
+        peaks = measured_peaks()
+        out[name] = {"ms": ms, "gflops": fl / (ms / 1e3) / 1e9, "flop_count": "2mnk + 2lmn (+2mnk)",
+                     "roofline": {"fp64_frac": fl / (ms / 1e3) / 1e12 / fp64_peak_tflops(peaks),
+                                  "hbm_frac": hbm_bytes / (ms / 1e3) / 1e9
+                                  / (peaks.get("hbm_gbs") or 6800.0),
+                                  "hbm_min_bytes": hbm_bytes,
+                                  "peaks": "FP64 = measured BF16 x 1.25/2250; HBM measured copy"}}
     info = h.sync_info()
     U, X, V = res
     # ||A - U X V^T||_F^2 = ||A||^2 - 2 <U^T A V, X> + ||X||^2 (U, V orthonormal)
@@ -620,6 +644,8 @@ def run_case(args):
       qrcp        qrcp_factor of an n x n N(0,1) matrix, block b
       sample      the sample QRCP kernel alone: b pivots on a (b + p) x n
                   N(0,1) sample
+      mixed       rqrcp_factor_mixed of the n x n spiked FP32 matrix (the
+                  mixed-precision configuration), block b, oversampling p
     Two untimed runs precede the timed ones."""
     import torch
     import __graft_entry__
@@ -630,7 +656,17 @@ def run_case(args):
     g = torch.Generator(device=dev).manual_seed(1)
     h = rq.Handle(dev)
     out = {"case": args.case}
-    if args.case == "sample":
+    if args.case == "mixed":
+        import synth
+        n = args.n
+        A0 = rq.colmajor(synth.spiked_device(n, n, dev).float())
+        A = rq.empty_colmajor(n, n, dev, torch.float32)
+
+        def call():
+            A.t().copy_(A0.t())
+            rq.rqrcp_factor_mixed(A, args.b, args.p, 1, handle=h)
+        out.update({"n": n, "b": args.b, "p": args.p})
+    elif args.case == "sample":
         ell, n = args.b + args.p, args.n
         B0 = rq.colmajor(torch.randn((ell, n), generator=g, device=dev, dtype=torch.float64))
         B = rq.empty_colmajor(ell, n, dev)
@@ -777,14 +813,9 @@ def main():
     value = job_rate(fl, ms, world)
     gpu_launches = sum(v[2] for v in prof.values())
 
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
+    peaks = measured_peaks()
     # the FP64 path draws ~280 W, far from the power cap: the burst BF16 figure applies
-    bf16 = peaks.get("bf16_tflops") or 1900.0
-    fp64_peak = bf16 * 1.25 / 2250.0      # nominal FP64 : BF16 dense ratio
+    fp64_peak = fp64_peak_tflops(peaks)   # nominal FP64 : BF16 dense ratio
     tr_ms, tr_fl, tr_launch = prof["trailing_update"]
     achieved = tr_fl / (tr_ms / 1e3) / 1e12 if tr_ms > 0 else None
     # DRAM traffic of the trailing update: its algorithmic bytes (A2 read by
