@@ -716,7 +716,9 @@ def run_case(args):
     e1.record()
     torch.cuda.synchronize()
     out["ms_per_call"] = e0.elapsed_time(e1) / args.reps
-    out["phases_ms"] = {k: round(v[0] / args.reps, 4) for k, v in h.profile_read().items() if v[2]}
+    prof = h.profile_read()
+    out["phases_ms"] = {k: round(v[0] / args.reps, 4) for k, v in prof.items() if v[2]}
+    out["launches_per_call"] = sum(v[2] for v in prof.values()) // args.reps
     h.profile(False)
     out["device_info"] = h.sync_info()
     print(json.dumps(out), flush=True)

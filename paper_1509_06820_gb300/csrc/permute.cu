@@ -17,34 +17,61 @@ namespace {
 // map layout: map[0] = number of moves; moves at map[1 + 2t] (dest), map[2 + 2t] (src);
 // the jpvt staging buffer follows at map[1 + 8*steps].
 __global__ void compose_swaps(const int64_t* __restrict__ swaps, int steps, int64_t* map) {
-  // touched positions and the original position each holds, in shared memory
+  // touched positions and the original position each holds, in shared
+  // memory; one warp: the lanes search the touched list together
   __shared__ int64_t pos[256];
   __shared__ int64_t content[256];
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int ntouch = 0;
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  int ntouch = 0;  // identical in every lane
   for (int i = 0; i < steps; ++i) {
     const int64_t s = swaps[i];
     if (s == i) continue;
-    int ia = -1, ib = -1;
-    for (int t = 0; t < ntouch; ++t) {
-      if (pos[t] == i) ia = t;
-      if (pos[t] == s) ib = t;
+    int ia = -1, ib = -1;  // positions are unique in pos[]: at most one hit each
+    for (int t0 = 0; t0 < ntouch; t0 += 32) {
+      const int t = t0 + lane;
+      const int64_t p = t < ntouch ? pos[t] : -1;
+      const unsigned ma = __ballot_sync(0xffffffffu, t < ntouch && p == i);
+      const unsigned mb = __ballot_sync(0xffffffffu, t < ntouch && p == s);
+      if (ma != 0u) ia = t0 + __ffs(ma) - 1;
+      if (mb != 0u) ib = t0 + __ffs(mb) - 1;
     }
-    if (ia < 0) { pos[ntouch] = i; content[ntouch] = i; ia = ntouch++; }
-    if (ib < 0) { pos[ntouch] = s; content[ntouch] = s; ib = ntouch++; }
-    const int64_t tmp = content[ia];
-    content[ia] = content[ib];
-    content[ib] = tmp;
+    if (ia < 0) {
+      if (lane == 0) {
+        pos[ntouch] = i;
+        content[ntouch] = i;
+      }
+      ia = ntouch++;
+    }
+    if (ib < 0) {
+      if (lane == 0) {
+        pos[ntouch] = s;
+        content[ntouch] = s;
+      }
+      ib = ntouch++;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      const int64_t tmp = content[ia];
+      content[ia] = content[ib];
+      content[ib] = tmp;
+    }
+    __syncwarp();
   }
+  // moved entries, in the order they were first touched
   int nm = 0;
-  for (int t = 0; t < ntouch; ++t) {
-    if (content[t] != pos[t]) {
-      map[1 + 2 * nm] = pos[t];
-      map[2 + 2 * nm] = content[t];
-      ++nm;
+  for (int t0 = 0; t0 < ntouch; t0 += 32) {
+    const int t = t0 + lane;
+    const bool mv = t < ntouch && content[t] != pos[t];
+    const unsigned m = __ballot_sync(0xffffffffu, mv);
+    if (mv) {
+      const int k = nm + __popc(m & ((1u << lane) - 1u));
+      map[1 + 2 * k] = pos[t];
+      map[2 + 2 * k] = content[t];
     }
+    nm += __popc(m);
   }
-  map[0] = nm;
+  if (lane == 0) map[0] = nm;
 }
 
 // gather (dir = 0): buf[:, t] = A[:, col0 + src_t]; scatter (dir = 1):

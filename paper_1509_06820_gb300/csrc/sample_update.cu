@@ -12,26 +12,47 @@ namespace rq {
 namespace {
 
 constexpr int W11_ROWS = 8;  // rows of W11 per CTA, one warp each
+constexpr int W11_MAXQ = 4;  // columns per lane (b <= 128)
 
-// W11 = S11 R11^{-1}: CTA c owns rows 8c..8c+7 of W11; R11 (columns >= the
-// CTA's first row) is staged in shared memory; warp w computes row r of W11
-// left to right, W(r, j) = (S(r, j) - sum_{r <= t < j} W(r, t) R(t, j)) / R(j, j),
-// its lanes splitting the sum over t (fixed-order shuffle reduction).
+// W11 = S11 R11^{-1}: CTA c owns rows 8c..8c+7 of W11; R11's upper triangle
+// and the reciprocals of its diagonal are staged in shared memory; warp w
+// computes row r of W11 left to right by the right-looking recurrence
+//   W(r, j) = acc_j / R(j, j),  acc_c -= W(r, j) R(j, c) for c > j,
+// with acc_c = S(r, c) initially and lane l keeping acc_c for c = l (mod 32):
+// one shuffle, one multiply and a few FMAs per step, no reductions.
 __global__ void w11_kernel(const double* __restrict__ S, int ell, const double* __restrict__ R,
                            int64_t ldr, int bJ, double* __restrict__ W, int* flag, int* status) {
   extern __shared__ double sm[];
-  double* Rs = sm;                    // bJ x bJ, ld bJ
-  double* Wr = sm + bJ * bJ;          // W11_ROWS x bJ
+  double* Rs = sm;              // bJ x bJ, ld bJ, zeros below the diagonal
+  double* rinv = sm + bJ * bJ;  // bJ
   __shared__ int s_sing;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) s_sing = 0;
   __syncthreads();
-  for (int e = tid; e < bJ * bJ; e += blockDim.x) {
-    const int r = e % bJ, c = e / bJ;
-    Rs[e] = (r <= c) ? R[r + c * ldr] : 0.0;
+  // 8 independent loads in flight per thread
+  const int total = bJ * bJ;
+  for (int e0 = tid; e0 < total; e0 += (int)blockDim.x * 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      v[u] = 0.0;
+      if (e < total) {
+        const int r = e % bJ, c = e / bJ;
+        if (r <= c) v[u] = R[r + c * ldr];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      if (e < total) Rs[e] = v[u];
+    }
   }
-  for (int j = tid; j < bJ; j += blockDim.x)
-    if (R[j + j * ldr] == 0.0) s_sing = 1;
+  for (int j = tid; j < bJ; j += blockDim.x) {
+    const double d = R[j + j * ldr];
+    if (d == 0.0) s_sing = 1;
+    rinv[j] = 1.0 / d;
+  }
   __syncthreads();
   if (s_sing) {
     if (blockIdx.x == 0 && tid == 0) {
@@ -43,27 +64,38 @@ __global__ void w11_kernel(const double* __restrict__ S, int ell, const double* 
   if (blockIdx.x == 0 && tid == 0) *flag = 0;
   const int r = blockIdx.x * W11_ROWS + warp;
   if (r >= bJ) return;
-  double* wrow = Wr + warp * bJ;
-  for (int j = lane; j < bJ; j += 32) wrow[j] = 0.0;
-  __syncwarp();
-  for (int j = r; j < bJ; ++j) {
-    double s = 0.0;
-    for (int t = r + lane; t < j; t += 32) s = fma(wrow[t], Rs[t + j * bJ], s);
-    s = warp_sum(s);
-    if (lane == 0) wrow[j] = (S[r + (int64_t)j * ell] - s) / Rs[j + j * bJ];
-    __syncwarp();
+  double acc[W11_MAXQ];
+#pragma unroll
+  for (int q = 0; q < W11_MAXQ; ++q) {
+    const int c = lane + 32 * q;
+    acc[q] = (c >= r && c < bJ) ? S[r + (int64_t)c * ell] : 0.0;
   }
-  for (int j = lane; j < bJ; j += 32) W[r + j * bJ] = wrow[j];
+  for (int c = lane; c < r; c += 32) W[r + c * bJ] = 0.0;
+  for (int j = r; j < bJ; ++j) {
+    const int qj = j >> 5;  // warp-uniform
+    double aj = 0.0;
+#pragma unroll
+    for (int q = 0; q < W11_MAXQ; ++q)
+      if (q == qj) aj = acc[q];
+    const double wj = __shfl_sync(0xffffffffu, aj, j & 31) * rinv[j];
+    if (lane == (j & 31)) W[r + j * bJ] = wj;
+    const double* Rj = Rs + j;  // row j: R(j, c) at Rj[c * bJ]
+#pragma unroll
+    for (int q = 0; q < W11_MAXQ; ++q) {
+      const int c = lane + 32 * q;
+      if (c > j && c < bJ) acc[q] = fma(-wj, Rj[(size_t)c * bJ], acc[q]);
+    }
+  }
 }
 
 }  // namespace
 
 cudaError_t launch_w11(const double* S, int ell, const double* R11, int64_t ldr, int bJ,
                        double* W11, int* flag, int* status, cudaStream_t st) {
-  const size_t smem = ((size_t)bJ * bJ + (size_t)W11_ROWS * bJ) * sizeof(double);
+  if (bJ < 1 || bJ > 32 * W11_MAXQ) return cudaErrorInvalidValue;
+  const size_t smem = ((size_t)bJ * bJ + (size_t)bJ) * sizeof(double);
   static std::atomic<uint64_t> attr_done{0};
-  cudaError_t e = ensure_smem_attr(w11_kernel, (128 * 128 + W11_ROWS * 128) * (int)sizeof(double),
-                                   attr_done);
+  cudaError_t e = ensure_smem_attr(w11_kernel, (128 * 128 + 128) * (int)sizeof(double), attr_done);
   if (e != cudaSuccess) return e;
   const int grid = (bJ + W11_ROWS - 1) / W11_ROWS;
   w11_kernel<<<grid, 32 * W11_ROWS, smem, st>>>(S, ell, R11, ldr, bJ, W11, flag, status);
