@@ -71,8 +71,14 @@ int rqrcp_destroy(rqrcp_handle_t handle);
 /* Rebind the handle to another stream. */
 int rqrcp_set_stream(rqrcp_handle_t handle, void* cuda_stream);
 
-/* Scratch bytes a call needs: op = 'R' (rqrcp_factor), 'Q' (qr_factor),
- * 'T' (trqrcp), 'U' (tuxv), 'P' (qrcp_factor).  k is ignored for 'R', 'Q' and 'P'. */
+/* Scratch bytes a call needs: op = 'R' (rqrcp_factor, rqrcp_factor_host),
+ * 'Q' (qr_factor), 'T' (trqrcp), 'U' (tuxv, tuxv_iter, tuxv_svd),
+ * 'P' (qrcp_factor), 'M' (rqrcp_factor_mixed), 'V' (trqrcp_mixed),
+ * 'X' (rqrcp_gemm_f64x: m x n output, k the inner size), 'G'
+ * (rqrcp_gemm_bf16x), 'S' (rqrcp_sketch / rqrcp_sample_qrcp: m = l rows,
+ * n columns).  k is ignored for 'R', 'Q', 'M' and 'P'.  The size depends on
+ * the handle's options (RQRCP_OPT_FP64_EMULATION, RQRCP_OPT_MAX_SMS):
+ * rqrcp_reserve on the handle accounts for them. */
 size_t rqrcp_workspace_bytes(char op, int64_t m, int64_t n, int64_t k, int b, int p);
 
 /* Allocate the scratch for a later call now (so that the call itself does

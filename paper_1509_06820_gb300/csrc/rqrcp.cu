@@ -551,14 +551,14 @@ size_t rqrcp_workspace_bytes(char op, int64_t m, int64_t n, int64_t k, int b, in
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (op == 'R' || op == 'Q' || op == 'P') k = std::min(m, n);
+  if (op == 'R' || op == 'Q' || op == 'P' || op == 'M') k = std::min(m, n);
   if (b > k) b = (int)std::max<int64_t>(k, 1);
   return carve(op, m, n, k, b, p, sms, nullptr).bytes;
 }
 
 int rqrcp_reserve(rqrcp_handle_t h, char op, int64_t m, int64_t n, int64_t k, int b, int p) {
   if (!h) return -1;
-  if (op == 'R' || op == 'Q' || op == 'P') k = std::min(m, n);
+  if (op == 'R' || op == 'Q' || op == 'P' || op == 'M') k = std::min(m, n);
   if (b > k) b = (int)std::max<int64_t>(k, 1);
   return ensure(h, carve(op, m, n, k, b, p, h->num_sms, nullptr, h->fp64_emulation != 0).bytes);
 }
