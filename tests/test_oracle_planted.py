@@ -106,6 +106,19 @@ def test_selection_wrong_degrees_of_freedom_is_caught(monkeypatch):
     _fails(ts.test_two_columns_rayleigh_closed_form, 0.7)
 
 
+def test_truncation_law_upper_incomplete_gamma_is_caught(monkeypatch):
+    """The upper instead of the lower incomplete gamma function in the
+    truncated chi-squared expectation (Sec. 4)."""
+    real = selection.special
+
+    class _Special:
+        gammainc = staticmethod(real.gammaincc)
+        gamma = staticmethod(real.gamma)
+        gammaln = staticmethod(real.gammaln)
+    monkeypatch.setattr(selection, "special", _Special)
+    _fails(ts.test_truncated_chi2_expectation_is_the_integral, 8, 3.0)
+
+
 def test_unpatched_pins_pass():
     """The same pins pass on the oracle as written."""
     th.test_panel_qr_matches_lapack(40, 40)
@@ -114,6 +127,7 @@ def test_unpatched_pins_pass():
     tr.test_qr_blocked_matches_lapack(300, 200, 32)
     tr.test_qrcp_equals_dgeqp3(120, 120, True)
     ts.test_two_columns_rayleigh_closed_form(0.7)
+    ts.test_truncated_chi2_expectation_is_the_integral(8, 3.0)
     ctr, key, out = tp._kat()[0]
     tp.test_philox_known_answers(ctr, key, out)
     assert oracle.rqrcp is not None

@@ -59,3 +59,50 @@ def test_golden_file_matches_oracle():
     cases = json.load(open(path))["cases"]
     for c in cases[::7]:
         assert abs(selection.select_expectation(c["phi"], c["ell"], c["n"]) - c["exact"]) <= 1e-12
+
+
+# ---------------------------------------------------------------- Sec. 4, norm truncation
+@pytest.mark.parametrize("dof,tau", [(8, 3.0), (8, 20.0), (3, 0.5), (40, 30.0), (144, 60.0)])
+def test_truncated_chi2_expectation_is_the_integral(dof, tau):
+    """The paper's closed form for E(x) equals the mean of the truncated
+    density, integrated directly; the density has unit mass."""
+    from scipy import integrate
+    pdf = lambda x: selection.truncated_chi2_pdf(x, dof, tau)  # noqa: E731
+    mass = integrate.quad(pdf, 0.0, tau, limit=200)[0]
+    mean = integrate.quad(lambda x: x * pdf(x), 0.0, tau, limit=200)[0]
+    assert abs(mass - 1.0) <= 1e-9
+    assert abs(selection.truncated_chi2_expectation(dof, tau) - mean) <= 1e-8 * max(1.0, mean)
+
+
+def test_truncated_chi2_expectation_limits_and_monotone():
+    """Zero at tau = 0, increasing in tau, the untruncated mean (dof) for a
+    large cutoff (Sec. 4)."""
+    taus = np.linspace(0.01, 200.0, 60)
+    e = [selection.truncated_chi2_expectation(16, t) for t in taus]
+    assert selection.truncated_chi2_expectation(16, 0.0) == 0.0
+    # strictly increasing until it meets dof in floating point
+    assert all(b > a or b == 16.0 for a, b in zip(e, e[1:]))
+    # small cutoff: x is nearly uniform-weighted by x^(s-1) on [0, tau]:
+    # E -> dof tau / (dof + 2)
+    assert abs(selection.truncated_chi2_expectation(16, 1e-4) - 16e-4 / 18) <= 1e-8
+    assert abs(selection.truncated_chi2_expectation(16, 1e4) - 16.0) <= 1e-9
+    assert selection.truncated_chi2_expectation(16, 1e-4) <= 1e-4
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_trailing_sample_norms_respect_the_truncation_bound(seed):
+    """The premise of the Sec. 4 theorem: after j pivots of the sample QRCP,
+    every remaining column's squared trailing norm stays below
+    min_i (s_ii^2 - sum_{k=i}^{j-1} s_kc^2), because the i-th pivot was the
+    largest trailing norm at step i.  Checked on the oracle's sample QRCP."""
+    from oracle.rqrcp import sample_qrcp
+    rng = np.random.default_rng(seed)
+    ell, n, j = 24, 90, 12
+    B = rng.standard_normal((ell, n)) * rng.uniform(0.5, 2.0, n)[None, :]
+    S = B.copy()
+    sample_qrcp(S, j)
+    bounds, tail2 = selection.truncation_bounds(S, j)
+    scale = np.max(np.abs(np.diag(S[:j, :j]))) ** 2
+    assert np.all(tail2 <= bounds + 1e-12 * scale)
+    # the bound is a real cut: the slack of the column closest to it is small
+    assert np.min(bounds - tail2) <= 0.5 * scale
