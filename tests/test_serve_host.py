@@ -43,6 +43,16 @@ def make_server(nslots=2, budget=10, fp=lambda r: 4, **kw):
     return Server(slots, hbm_budget=budget, footprint_fn=fp, clock=Clock(), **kw), slots
 
 
+def test_unit_buckets_keep_exact_sizes():
+    """Eager slots solve each request at its own size: with buckets of 1 the
+    plan is the request itself (the graph mode rounds up for reuse)."""
+    srv, _ = make_server(bucket=1, kbucket=1)
+    r = srv.plan(Request(0, 300, 1000, 40))
+    assert r.bucket == (300, 1000, 40)
+    r = srv.plan(Request(1, 257, 129, 200))
+    assert r.bucket == (257, 129, 129)   # k capped at min(m, n)
+
+
 def test_bucketing_rounds_up_and_caps_k():
     srv, _ = make_server()
     r = srv.plan(Request(0, 300, 1000, 40))
