@@ -119,6 +119,17 @@ def test_truncation_law_upper_incomplete_gamma_is_caught(monkeypatch):
     _fails(ts.test_truncated_chi2_expectation_is_the_integral, 8, 3.0)
 
 
+def test_tuxv_misordered_basis_is_caught(monkeypatch):
+    """Q formed with its columns reversed: U and V stay orthonormal, but
+    U X = A V (and the triangular X) no longer hold (Alg. 7)."""
+    real = orq.form_q
+
+    def form_q_reversed(P, tau, ncols):
+        return real(P, tau, ncols)[:, ::-1].copy()
+    monkeypatch.setattr(orq, "form_q", form_q_reversed)
+    _fails(tr.test_tuxv_properties)
+
+
 def test_unpatched_pins_pass():
     """The same pins pass on the oracle as written."""
     th.test_panel_qr_matches_lapack(40, 40)
@@ -128,6 +139,7 @@ def test_unpatched_pins_pass():
     tr.test_qrcp_equals_dgeqp3(120, 120, True)
     ts.test_two_columns_rayleigh_closed_form(0.7)
     ts.test_truncated_chi2_expectation_is_the_integral(8, 3.0)
+    tr.test_tuxv_properties()
     ctr, key, out = tp._kat()[0]
     tp.test_philox_known_answers(ctr, key, out)
     assert oracle.rqrcp is not None
