@@ -130,6 +130,16 @@ def test_tuxv_misordered_basis_is_caught(monkeypatch):
     _fails(tr.test_tuxv_properties)
 
 
+def test_rsrqrcp_reused_compression_is_caught(monkeypatch):
+    """Alg. 5 that compresses every trailing matrix with the first block's
+    Omega instead of a fresh one: valid-looking samples, but not the fresh
+    compressions the algorithm defines."""
+    def not_fresh(seed, J, ell, trailing):
+        return orq.gaussian_block(seed, ell, trailing.shape[0], 1) @ trailing
+    monkeypatch.setattr(orq, "_resample", not_fresh)
+    _fails(tr.test_rsrqrcp_samples_are_fresh_compressions, 60, 50, 8, 4)
+
+
 def test_unpatched_pins_pass():
     """The same pins pass on the oracle as written."""
     th.test_panel_qr_matches_lapack(40, 40)
@@ -140,6 +150,7 @@ def test_unpatched_pins_pass():
     ts.test_two_columns_rayleigh_closed_form(0.7)
     ts.test_truncated_chi2_expectation_is_the_integral(8, 3.0)
     tr.test_tuxv_properties()
+    tr.test_rsrqrcp_samples_are_fresh_compressions(60, 50, 8, 4)
     ctr, key, out = tp._kat()[0]
     tp.test_philox_known_answers(ctr, key, out)
     assert oracle.rqrcp is not None

@@ -378,6 +378,28 @@ def test_rsrqrcp_factorization(m, n, b, p):
     assert np.linalg.norm(A[:, jpvt] - Q @ np.triu(F)) < 1e-14 * np.linalg.norm(A)
 
 
+@pytest.mark.parametrize("m,n,b,p", [(60, 50, 8, 4), (45, 70, 6, 6)])
+def test_rsrqrcp_samples_are_fresh_compressions(m, n, b, p):
+    """Alg. 5 by definition: after block J the next sample is Omega^[J] A^[J],
+    a fresh GIID block (Philox stream 0x100 + J) times the trailing matrix
+    updated by that block's reflectors, rebuilt here from explicit Q's."""
+    from oracle import philox as ph
+    A = synth.gaussian(m, n, seed=23)
+    trace = []
+    ell = b + p
+    oracle.rqrcp(A, b, p, seed=7, trace=trace, resample_every_block=True)
+    G = A.copy()
+    for J, blk in enumerate(trace[:-1], start=1):
+        j0, bJ = blk["j0"], blk["bJ"]
+        for i, c in enumerate(blk["swaps"]):
+            G[:, [j0 + i, j0 + c]] = G[:, [j0 + c, j0 + i]]
+        G[j0:, j0:] = _explicit_q(blk["Y"], blk["T"]).T @ G[j0:, j0:]
+        trailing = G[j0 + bJ:, j0 + bJ:]
+        om = ph.gaussian_block(7, ell, trailing.shape[0], 0x100 + J)
+        np.testing.assert_allclose(blk["B_out"], om @ trailing,
+                                   atol=1e-11 * np.abs(blk["B_out"]).max())
+
+
 @pytest.mark.parametrize("m,n,b", [(30, 24, 4), (40, 40, 8), (25, 60, 5), (60, 20, 7)])
 def test_rsrqrcp_exact_samples_reproduce_qrcp(m, n, b):
     """With every sample drawn through orthonormal columns (l = m), each
