@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--cpu-blocks", type=int, default=6,
                     help="blocks of the factorization in the oracle's bounded sample")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the QR baseline, e2e, cpu_baseline, mixed and serving legs")
+                    help="run the FP64 step only (no extra legs; same as --legs '')")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--only-emulated", action="store_true",
                     help="same as --legs emulated")
