@@ -83,7 +83,8 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--legs", default="qr,e2e,cpu,emulated,rsrqrcp,qrcp,quality,mixed,truncated,serving",
                     help="comma-separated extra legs to run after the FP64 step")
-    ap.add_argument("--case", choices=["panel", "gemm_bf16x", "gemm_f64x", "qrcp", "sample", "mixed"],
+    ap.add_argument("--case", choices=["panel", "gemm_bf16x", "gemm_f64x", "qrcp", "sample", "mixed",
+                                       "fp64peak"],
                     default=None,
                     help="run one small kernel case (for profiling) instead of the benchmark")
     ap.add_argument("--shape", default=None,
@@ -176,6 +177,13 @@ def host_matrix(n):
     return synth.graded(n)
 
 
+def workload_config(n, b, p, world=1):
+    """The `config` object of the JSON line; identical in both arms."""
+    return {"workload": f"rqrcp_graded_{n}x{n}_b{b}_p{p}", "m": n, "n": n, "b": b, "p": p,
+            "sigma": "10^(-12 (i-1)/(n-1))", "omega_seed": 1,
+            "l2": "inputs larger than L2 (2.1 GB matrix)", "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -192,17 +200,23 @@ def run_reference(args):
         secs.append(dt)
     value = statistics.mean(rates)
     full_s = flops_geqrf(n, n) / (value * 1e9)
-    sample = (f"first {max(1, args.cpu_blocks // 2)} blocks (b={b}) of the {n}x{n} factorization "
-              f"per step, rate scaled by algorithmic flops")
+    nb = max(1, args.cpu_blocks // 2)
+    sample = (f"first {nb} blocks (b={b}) of the {n}x{n} factorization per step "
+              f"({statistics.mean(secs):.2f} s measured per step), rate from their "
+              f"algorithmic flops")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * full_s,
+        "steps": args.steps, "warmup": args.warmup,
+        # a step is the bounded sample, timed; the whole factorization at the
+        # same rate is an extrapolation, reported under its own name
+        "ms_per_step": 1e3 * statistics.mean(secs),
+        "sample_blocks_per_step": nb,
+        "full_factorization_ms_extrapolated": 1e3 * full_s,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"rqrcp_graded_{n}x{n}_b{b}_p{p}", "m": n, "n": n, "b": b, "p": p,
-                   "l2": "inputs larger than L2"},
+        "config": workload_config(n, b, p, args.gpus),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "threads": "numpy BLAS default (all host cores)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -220,6 +234,29 @@ def fp64_peak_tflops(peaks):
     """FP64 peak for a dtype without a measured figure: the measured BF16
     burst rate times the nominal FP64 : BF16 ratio (1.25 : 2250)."""
     return (peaks.get("bf16_tflops") or 1900.0) * 1.25 / 2250.0
+
+
+def probe_peaks(dev, kinds=("fp64_fma", "fp64_dmma_m8n8k4", "fp64_dmma_m16n8k16"),
+                target_ms=60.0, reps=3):
+    """Measured arithmetic peaks of this GPU (rqrcp_peak_probe): per kind the
+    best TFLOP/s of `reps` launches of about `target_ms` each, with 4 CTAs of
+    256 threads per SM."""
+    import torch
+    import paper_1509_06820_gb300 as rq
+    grid = 4 * torch.cuda.get_device_properties(dev).multi_processor_count
+    out = {}
+    for kind in kinds:
+        iters = 64
+        ms, fl = rq.peak_probe(kind, iters, grid, dev)
+        for _ in range(3):   # scale the launch to about target_ms
+            iters = max(64, int(iters * target_ms / max(ms, 1e-3)))
+            ms, fl = rq.peak_probe(kind, iters, grid, dev)
+        best = 0.0
+        for _ in range(reps):
+            ms, fl = rq.peak_probe(kind, iters, grid, dev)
+            best = max(best, fl / (ms / 1e3) / 1e12)
+        out[kind] = {"tflops": best, "ms": ms, "iters": iters, "grid": grid}
+    return out
 
 
 # ------------------------------------------------------------------ extra legs
@@ -646,6 +683,8 @@ def run_case(args):
                   N(0,1) sample
       mixed       rqrcp_factor_mixed of the n x n spiked FP32 matrix (the
                   mixed-precision configuration), block b, oversampling p
+      fp64peak    the arithmetic-peak probes (FP64 FMA, FP64 DMMA m8n8k4 and
+                  m16n8k16, FP32 FMA) with the SM clock sampled meanwhile
     Two untimed runs precede the timed ones."""
     import torch
     import __graft_entry__
@@ -653,6 +692,20 @@ def run_case(args):
     import paper_1509_06820_gb300 as rq
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
+    if args.case == "fp64peak":
+        clocks = ClockSampler(0)
+        clocks.start()
+        time.sleep(0.3)
+        res = probe_peaks(dev, kinds=("fp64_fma", "fp64_dmma_m8n8k4", "fp64_dmma_m16n8k16",
+                                      "fp32_fma"), target_ms=200.0, reps=5)
+        clk = clocks.stop()
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = clk.get("sm_mhz") or 2070.0
+        for v in res.values():
+            v["flop_per_clk_per_sm"] = v["tflops"] * 1e12 / (sms * mhz * 1e6)
+        print(json.dumps({"case": "fp64peak", "sms": sms, "probes": res, "clocks": clk}),
+              flush=True)
+        return
     g = torch.Generator(device=dev).manual_seed(1)
     h = rq.Handle(dev)
     out = {"case": args.case}
@@ -722,6 +775,35 @@ def run_case(args):
     h.profile(False)
     out["device_info"] = h.sync_info()
     print(json.dumps(out), flush=True)
+
+
+def summary_of(line, extras):
+    """The metric's own comparisons in a few numbers (the last key of the line)."""
+    def r(x, nd=4):
+        return None if x is None else round(x, nd)
+    out = {"rqrcp_ms": r(line["ms_per_step"], 1), "rqrcp_gflops": r(line["value"], 1),
+           "qr_ms": r(extras.get("qr_ms_per_step"), 1),
+           "rqrcp_over_qr_time": r(extras.get("rqrcp_over_qr_time"))}
+    em = extras.get("fp64_emulated") or {}
+    if em:
+        out["fp64_emulated"] = {"rqrcp_ms": r(em.get("rqrcp", {}).get("ms_per_step"), 1),
+                                "qr_ms": r(em.get("qr", {}).get("ms_per_step"), 1),
+                                "rqrcp_over_qr_time": r(em.get("rqrcp_over_qr_time")),
+                                "speedup_vs_fp64": r(em.get("speedup_vs_fp64_pipe"), 2)}
+    mx = extras.get("mixed") or {}
+    if mx:
+        out["mixed"] = {"ms": r(mx.get("ms_per_step"), 1),
+                        "speedup_vs_fp64": r(mx.get("speedup_vs_f64"), 2),
+                        "recon_err": mx.get("recon_err_sampled_cols")}
+    sv = extras.get("serving") or {}
+    if sv:
+        out["serving"] = {"offered_rps": sv.get("offered_rate"),
+                          "rps": r(sv.get("throughput_rps"), 1), "p50_ms": r(sv.get("p50_ms"), 2),
+                          "p99_ms": r(sv.get("p99_ms"), 2)}
+    e2e = extras.get("e2e") or {}
+    if e2e:
+        out["e2e_gflops"] = r(e2e.get("value"), 1)
+    return out
 
 
 # ------------------------------------------------------------------ replicas
@@ -816,8 +898,13 @@ def main():
     gpu_launches = sum(v[2] for v in prof.values())
 
     peaks = measured_peaks()
-    # the FP64 path draws ~280 W, far from the power cap: the burst BF16 figure applies
-    fp64_peak = fp64_peak_tflops(peaks)   # nominal FP64 : BF16 dense ratio
+    # the FP64 rate of this GPU, measured now by the library's peak probes:
+    # FMA chains on the CUDA cores and DMMA (mma.sync) on the tensor cores;
+    # the roofline peak is the faster of the two
+    probes = probe_peaks(dev)
+    fp64_best = max(probes.values(), key=lambda v: v["tflops"])
+    fp64_peak = fp64_best["tflops"]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     tr_ms, tr_fl, tr_launch = prof["trailing_update"]
     achieved = tr_fl / (tr_ms / 1e3) / 1e12 if tr_ms > 0 else None
     # DRAM traffic of the trailing update: its algorithmic bytes (A2 read by
@@ -832,15 +919,26 @@ def main():
         alg_bytes += 24.0 * (m - j0) * (n - j0 - bJ)
         j0 += bJ
     traffic = 0.941 * alg_bytes / max(tr_launch, 1)
+    best_kind = max(probes, key=lambda k: probes[k]["tflops"])
+    # unit count x clock: the FP64 FMA lanes per SM that the probe implies,
+    # rounded, times the SMs and the SM clock sampled during the timed steps
+    mhz = clk.get("sm_mhz") or 2070.0
+    lanes = round(probes["fp64_fma"]["tflops"] * 1e12 / (2.0 * sms * mhz * 1e6))
+    derived = 2.0 * lanes * sms * mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "kernel": "trailing update (gemm_kernel FP64 FFMA)",
                 "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp64_peak if achieved else None, "traffic": traffic,
                 "traffic_unit": "bytes per launch",
                 "traffic_source": "algorithmic bytes x 0.941 (ncu DRAM bytes / algorithmic bytes, "
                                   "same kernels, 6144^2 factorization)",
-                "peak_source": "MEASURED_PEAKS bf16_tflops x 1.25/2250 (nominal FP64/BF16 ratio)",
+                "peak_source": f"measured in this run: rqrcp_peak_probe {best_kind} (best FP64 "
+                               f"rate of FMA chains, DMMA m8n8k4, DMMA m16n8k16)",
+                "peak_probes_tflops": {k: round(v["tflops"], 4) for k, v in probes.items()},
+                "peak_derived": derived,
+                "peak_derived_source": f"{lanes} FP64 FMA/clk/SM x 2 flop x {sms} SMs x "
+                                       f"{mhz:.0f} MHz (sampled)",
+                "frac_derived": achieved / derived if achieved and derived else None,
                 "peak_nominal": 1.25,
-                "frac_nominal": achieved / 1.25 if achieved else None,
                 "launch_ms_avg": tr_ms / max(tr_launch, 1)}
     phases = {k: {"ms": v[0], "gflop": v[1] / 1e9, "launches": v[2]} for k, v in prof.items()}
 
@@ -926,19 +1024,21 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"rqrcp_graded_{n}x{n}_b{b}_p{p}", "m": m, "n": n, "b": b,
-                       "p": p, "sigma": "10^(-12 (i-1)/(n-1))", "omega_seed": 1,
-                       "l2": "inputs larger than L2 (2.1 GB matrix)",
-                       "parallelism": f"replicas x{world}"},
+            "config": workload_config(n, b, p, world),
             "gpu_launches": gpu_launches,
             "device_info": info | info_warm,
-            "clocks": clk,
-            "roofline": roofline,
             "phases": phases,
         }
-        line.update({k: v for k, v in extras.items()})
-        line.setdefault("e2e", None)
-        line.setdefault("cpu_baseline", None)
+        # the long per-leg records first; the headline figures close the line
+        for k in ("truncated", "serving", "quality", "qrcp", "rsrqrcp", "fp64_emulated",
+                  "mixed"):
+            if k in extras:
+                line[k] = extras[k]
+        line["e2e"] = extras.get("e2e")
+        line["cpu_baseline"] = extras.get("cpu_baseline")
+        line["clocks"] = clk
+        line["roofline"] = roofline
+        line["summary"] = summary_of(line, extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -103,6 +103,14 @@ int rqrcp_reserve(rqrcp_handle_t handle, char op, int64_t m, int64_t n, int64_t 
 #define RQRCP_OPT_FP64_EMULATION 1
 #define RQRCP_OPT_RESAMPLE 2
 #define RQRCP_OPT_MAX_SMS 3
+/* RQRCP_OPT_TEST_BARRIER_TIMEOUT (test of the failure path only, value 0/1):
+ * while set, rqrcp_sample_qrcp on this handle launches its cooperative kernel
+ * with a grid barrier that waits for one CTA more than the grid has and gives
+ * up after a few milliseconds of polling.  The kernel then ORs
+ * RQRCP_INFO_TIMEOUT into the status word, writes no-exchange partners
+ * (d_swaps[i] = i) for the steps it did not take, leaves dB unchanged and
+ * returns; the handle stays usable.  No other call reads the option. */
+#define RQRCP_OPT_TEST_BARRIER_TIMEOUT 4
 int rqrcp_set_option(rqrcp_handle_t handle, int option, int value);
 
 /* Wait for the handle's stream, then return the device status word in *info
@@ -366,11 +374,14 @@ int rqrcp_sample_qrcp(rqrcp_handle_t handle, int ell, int64_t nc, int steps, dou
  * held by every GPU that loads the library until exit), so it needs no
  * handle and calls no cudaMalloc/cudaFree.
  *   ell, nc, steps, dB, ldb, d_swaps : as rqrcp_sample_qrcp (ell <= 192)
- *   d_info      : optional device int; RQRCP_INFO_* bits are ORed into it
- *                 (the caller clears it); NULL keeps the status internal
+ *   d_info      : device int, required; RQRCP_INFO_* bits are ORed into it
+ *                 (the caller clears it): RQRCP_INFO_NONFINITE for a sample
+ *                 holding NaN or Inf, RQRCP_INFO_TIMEOUT when a grid wait
+ *                 gave up (dB and d_swaps are then not a valid result)
  *   cuda_stream : the cudaStream_t to run on (NULL = legacy default stream)
- * Returns -i for an invalid argument i, RQRCP_ERR_UNSUPPORTED when the sample
- * does not fit the kernel's shared memory, RQRCP_ERR_CUDA on a CUDA error.
+ * Returns -i for an invalid argument i (-7 for a NULL d_info),
+ * RQRCP_ERR_UNSUPPORTED when the sample does not fit the kernel's shared
+ * memory, RQRCP_ERR_CUDA on a CUDA error.
  * The first call on a device looks up the array's device address; make it
  * before any stream capture.  All calls share the array: calls that overlap on
  * the GPU race, so order them (for example on one stream).
@@ -405,6 +416,22 @@ int rqrcp_gemm_f64x(rqrcp_handle_t handle, char transA, char transB, int64_t m, 
  * first nphase phases (<= 8), the device milliseconds, algorithmic FLOPs and
  * kernel launches since the last enable; any pointer may be NULL.
  */
+/*
+ * Arithmetic-peak probe (instrumentation, no counterpart in the paper): one
+ * launch of `grid` CTAs x 256 threads on `cuda_stream` that runs `iters`
+ * rounds of independent multiply-adds and writes one value per thread to
+ * d_sink (device, grid * 256 doubles; floats for kind 3).  *flops receives
+ * the launch's floating-point operation count, so that the caller's CUDA
+ * event time gives the rate:
+ *   kind 0  FP64 FMA on the CUDA cores (8 independent chains per thread)
+ *   kind 1  FP64 tensor-core mma.sync m8n8k4 (4 independent tiles per warp)
+ *   kind 2  FP64 tensor-core mma.sync m16n8k16 (2 independent tiles per warp)
+ *   kind 3  FP32 FMA on the CUDA cores
+ * Returns -i for an invalid argument i, RQRCP_ERR_CUDA for a launch error.
+ */
+int rqrcp_peak_probe(int kind, int64_t iters, int grid, void* d_sink, void* cuda_stream,
+                     double* flops);
+
 #define RQRCP_NPHASE 8
 int rqrcp_profile(rqrcp_handle_t handle, int enable);
 int rqrcp_profile_read(rqrcp_handle_t handle, int nphase, double* ms, double* flops,

@@ -25,6 +25,7 @@ RQRCP_ERR_BATCH = 1003
 OPT_FP64_EMULATION = 1
 OPT_RESAMPLE = 2
 OPT_MAX_SMS = 3
+OPT_TEST_BARRIER_TIMEOUT = 4
 INFO_NONFINITE = 1
 INFO_RESAMPLED = 2
 INFO_TIMEOUT = 4
@@ -77,6 +78,7 @@ SIGNATURES = [
                          _P, _I64, _P, _I64, ctypes.c_double, _P, _I64]),
     ("rqrcp_sample_qrcp", _I, [_P, _I, _I64, _I, _P, _I64, _P]),
     ("rqrcp_sample_qrcp_noalloc", _I, [_I, _I64, _I, _P, _I64, _P, _P, _P]),
+    ("rqrcp_peak_probe", _I, [_I, _I64, _I, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     ("rqrcp_profile", _I, [_P, _I]),
     ("rqrcp_profile_read", _I, [_P, _I, _P, _P, _P]),
 ]
@@ -134,6 +136,11 @@ class Handle:
 
     def reserve_batched(self, lanes, m, n, k, b, p):
         _check(load().rqrcp_reserve_batched(self.h, lanes, m, n, k, b, p), self.h)
+
+    def set_test_barrier_timeout(self, on=True):
+        """Test of the failure path only: rqrcp_sample_qrcp on this handle runs
+        with a grid barrier that cannot complete and gives up after a few ms."""
+        _check(load().rqrcp_set_option(self.h, OPT_TEST_BARRIER_TIMEOUT, 1 if on else 0), self.h)
 
     def set_fp64_emulation(self, on=True):
         """Run the FP64 trailing update on the BF16 tensor cores (exact slicing)."""
@@ -475,3 +482,25 @@ def gemm_f64x(A, B, transA="N", transB="N", alpha=1.0, beta=0.0, C=None, handle=
 
 def sync_info(device=None):
     return default_handle(device).sync_info()
+
+
+PEAK_KINDS = {"fp64_fma": 0, "fp64_dmma_m8n8k4": 1, "fp64_dmma_m16n8k16": 2, "fp32_fma": 3}
+
+
+def peak_probe(kind, iters, grid, device="cuda"):
+    """One launch of the arithmetic-peak probe `kind` (see PEAK_KINDS) on the
+    current stream; returns (CUDA-event milliseconds, flops of the launch)."""
+    dev = torch.device(device)
+    dt = torch.float32 if kind == "fp32_fma" else torch.float64
+    sink = torch.empty(grid * 256, dtype=dt, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    fl = ctypes.c_double(0.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rc = load().rqrcp_peak_probe(PEAK_KINDS[kind], iters, grid, _ptr(sink), _P(stream.cuda_stream),
+                                 ctypes.byref(fl))
+    e1.record(stream)
+    if rc != RQRCP_OK:
+        raise RqrcpError(f"rqrcp_peak_probe: {rc}")
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1), fl.value

@@ -45,6 +45,9 @@ struct GridBarrier {
 // Upper bound on the polls of one barrier wait.  A healthy barrier on a
 // GB300 completes in a few microseconds; this bound is ~1 s of polling.
 constexpr unsigned int kBarrierMaxPolls = 1u << 23;
+// Poll bound of the test-only phantom-CTA barrier (RQRCP_OPT_TEST_BARRIER_TIMEOUT):
+// a few milliseconds, so that a wait that cannot complete ends quickly.
+constexpr unsigned int kBarrierTestPolls = 1u << 14;
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
   unsigned int v;
@@ -63,8 +66,11 @@ __device__ __forceinline__ unsigned int atom_add_release_u32(unsigned int* p, un
 // and polls the counter with acquire loads until the whole grid has arrived.
 // Returns false when the wait ran out (or another CTA already gave up): the
 // status word then carries RQRCP_INFO_TIMEOUT and the caller must return
-// without further barriers.
-__device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned int nblocks, int* status) {
+// without further barriers.  `nblocks` is the number of arrivals that
+// complete a barrier (the grid size; more only in the test of the timeout
+// path) and `max_polls` bounds the wait of each CTA.
+__device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned int nblocks, int* status,
+                                             unsigned int max_polls = kBarrierMaxPolls) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -75,7 +81,7 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned int nblo
     unsigned int polls = 0;
     while ((int)(ld_acquire_u32(&bar->count) - target) < 0) {
       if (ld_acquire_u32(&bar->abort)) { ok = 0; break; }
-      if (++polls > kBarrierMaxPolls) {
+      if (++polls > max_polls) {
         atomicExch(&bar->abort, 1u);
         atomicOr(status, RQRCP_INFO_TIMEOUT);
         ok = 0;

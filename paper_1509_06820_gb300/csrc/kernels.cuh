@@ -122,6 +122,10 @@ struct SampleQrcpArgs {
   double* candcol;    // scratch: 2 * grid * l doubles
   GridBarrier* bar;
   int* status;
+  // test of the device-side timeout only: the grid barrier waits for this
+  // many extra CTAs that do not exist (with a poll bound of a few ms), so the
+  // first barrier runs out, RQRCP_INFO_TIMEOUT is set and every CTA returns
+  int phantom = 0;
 };
 cudaError_t launch_sample_qrcp(const SampleQrcpArgs& a, int num_sms, cudaStream_t st);
 bool sample_qrcp_fits(int ell, int64_t nc, int num_sms);

@@ -33,6 +33,7 @@ struct rqrcp_handle_s {
   int cur_phase = 7;
   int fp64_emulation = 0;  // RQRCP_OPT_FP64_EMULATION
   int resample = 0;        // RQRCP_OPT_RESAMPLE: Alg. 5 instead of Eq. (3)
+  int test_timeout = 0;    // RQRCP_OPT_TEST_BARRIER_TIMEOUT (rqrcp_sample_qrcp only)
   // worker lanes of trqrcp_batched: a stream, its scratch and its own
   // re-sample flag and grid barrier each (the status word stays shared)
   struct Lane {
@@ -573,6 +574,10 @@ int rqrcp_set_option(rqrcp_handle_t h, int option, int value) {
     h->resample = value != 0;
     return RQRCP_OK;
   }
+  if (option == RQRCP_OPT_TEST_BARRIER_TIMEOUT) {
+    h->test_timeout = value != 0;
+    return RQRCP_OK;
+  }
   if (option == RQRCP_OPT_MAX_SMS) {
     if (value < 0) return -3;
     h->num_sms = (value == 0 || value > h->dev_sms) ? h->dev_sms : value;
@@ -662,6 +667,7 @@ int rqrcp_sample_qrcp(rqrcp_handle_t h, int ell, int64_t nc, int steps, double* 
   PhaseScope ps(cl.h, PH_SAMPLE, fl);
   rq::SampleQrcpArgs a{dB, ldb, ell, nc, steps, d_swaps, cl.w.cand, cl.w.candcol, cl.bar,
                        cl.status};
+  a.phantom = h->test_timeout ? 1 : 0;
   CKL(1, rq::launch_sample_qrcp(a, cl.h->num_sms, cl.st));
   return RQRCP_OK;
 }

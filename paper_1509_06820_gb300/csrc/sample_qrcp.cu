@@ -132,7 +132,15 @@ __global__ void __launch_bounds__(NT, 1) sample_qrcp_kernel(SampleQrcpArgs a) {
     const int my_pivot = red[0].who;  // local column index of this CTA's candidate
     if (my_pivot >= 0)
       for (int r = tid; r < ell; r += NT) ccol[(size_t)g * ell + r] = col[r + my_pivot * ell];
-    if (!grid_barrier(a.bar, G, a.status)) return;
+    if (!grid_barrier(a.bar, G + a.phantom, a.status,
+                      a.phantom ? kBarrierTestPolls : kBarrierMaxPolls)) {
+      // the wait ran out (RQRCP_INFO_TIMEOUT is set): leave valid swap
+      // partners (no exchange) for the steps not taken, so that whatever
+      // consumes the list stays within its columns
+      if (g == 0)
+        for (int t = i + tid; t < a.steps; t += NT) a.swaps[t] = t;
+      return;
+    }
 
     // ---- global winner (identical in every CTA): warp 0 scans the G
     // candidates, then builds the reflector from the winner's rows i..ell-1
@@ -307,16 +315,18 @@ cudaError_t launch_sample_qrcp(const SampleQrcpArgs& a, int num_sms, cudaStream_
 //   cudaGetSymbolAddress (with that device current) and caches it.  Make that
 //   first call before any stream capture.
 // * Every call shares the array and it keeps the previous call's contents.
-//   Each call clears the words that must start at zero (the barrier, and the
-//   fallback status word when no info word is passed) on its stream before
-//   the launch.  Calls whose kernels overlap on the GPU race on the array:
-//   run them on one stream, or order them.
+//   Each call clears the words that must start at zero (the barrier) on its
+//   stream before the launch.  Calls whose kernels overlap on the GPU race on
+//   the array: run them on one stream, or order them.
+// * The caller's device status word is required: a timed-out wait or a
+//   non-finite sample leaves dB and the swaps unusable, and the status word
+//   is the only place that says so.
 namespace {
 
 constexpr int kNoAllocMaxGrid = 152;  // CTAs (one per SM, capped)
 constexpr int64_t kNoAllocCand = 2LL * kNoAllocMaxGrid * 2;
 constexpr int64_t kNoAllocCandCol = 2LL * kNoAllocMaxGrid * MAX_ELL;
-// candidates, candidate columns, then 8 doubles for the barrier and status
+// candidates, candidate columns, then 8 doubles for the barrier
 constexpr int64_t kNoAllocScratchDoubles = kNoAllocCand + kNoAllocCandCol + 8;
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
@@ -355,6 +365,7 @@ extern "C" int rqrcp_sample_qrcp_noalloc(int ell, int64_t nc, int steps, double*
   if (!dB) return -4;
   if (ldb < ell) return -5;
   if (!d_swaps) return -6;
+  if (!d_info) return -7;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -365,17 +376,7 @@ extern "C" int rqrcp_sample_qrcp_noalloc(int ell, int64_t nc, int steps, double*
   if (noalloc_scratch(&scratch) != cudaSuccess) return RQRCP_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   GridBarrier* bar = reinterpret_cast<GridBarrier*>(scratch + kNoAllocCand + kNoAllocCandCol);
-  int* status = d_info;
-  if (status == nullptr) {
-    // no caller word: keep the status in the array (cleared by every call)
-    status = reinterpret_cast<int*>(scratch + kNoAllocCand + kNoAllocCandCol + 4);
-    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return RQRCP_ERR_CUDA;
-  }
-  SampleQrcpArgs a{dB, ldb, ell, nc, steps, d_swaps, scratch, scratch + kNoAllocCand, bar, status};
+  SampleQrcpArgs a{dB, ldb, ell, nc, steps, d_swaps, scratch, scratch + kNoAllocCand, bar, d_info};
   // launch_sample_qrcp clears the barrier words before the cooperative launch
   return launch_sample_qrcp(a, sms, st) == cudaSuccess ? RQRCP_OK : RQRCP_ERR_CUDA;
 }
-
-namespace rq {
-
-}  // namespace rq

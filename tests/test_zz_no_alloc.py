@@ -53,6 +53,44 @@ def test_noalloc_matches_handle_entry_point(lib):
         assert (B_new - B_ref).abs().max().item() <= 1e-12 * scale
 
 
+def test_noalloc_matches_oracle(lib):
+    """One direct comparison with the oracle's Alg. 1 halted after `steps`
+    pivots (replaying the device's pivots through exact ties): the same swap
+    sequence and the same S = Q_b^T B P."""
+    from oracle.rqrcp import sample_qrcp
+    ell, nc, steps = 24, 300, 16
+    B = _sample(ell, nc, 7)
+    B_host = B.cpu().numpy().copy()
+    B_new = B.clone()
+    swaps, info = _noalloc(lib, B_new, steps)
+    assert info == 0
+    sw = swaps.cpu().numpy()
+    ids = np.arange(nc)
+    for i, s in enumerate(sw):
+        ids[[i, s]] = ids[[s, i]]
+    S = B_host.copy()
+    sw_o, _, _ = sample_qrcp(S, steps, ids=np.arange(nc), forced_ids=ids[:steps])
+    np.testing.assert_array_equal(sw, sw_o)
+    assert np.abs(B_new.cpu().numpy() - S).max() <= 1e-12 * np.abs(B_host).max()
+
+
+def test_noalloc_reports_nonfinite(lib):
+    """A NaN in the sample is reported through the caller's status word."""
+    B = _sample(16, 64, 3)
+    B[5, 17] = float("nan")
+    _, info = _noalloc(lib, B, 8)
+    assert info & lib.INFO_NONFINITE
+
+
+def test_noalloc_requires_info_word(lib):
+    raw = lib.load()
+    B = _sample(8, 16, 1)
+    swaps = torch.empty(8, dtype=torch.int64, device=B.device)
+    p = ctypes.c_void_p
+    assert raw.rqrcp_sample_qrcp_noalloc(8, 16, 8, p(B.data_ptr()), 8, p(swaps.data_ptr()),
+                                         None, None) == -7
+
+
 def test_noalloc_rejects_out_of_range(lib):
     raw = lib.load()
     B = _sample(8, 16, 1)
