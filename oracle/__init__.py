@@ -26,11 +26,11 @@ Contents (paper sections in brackets):
                      the connection matrix X.
 
 * ``selection``   -- the expected norm of the sample-selected column for
-                     orthogonal columns with geometric norms [Sec. 4, sample
+                     orthogonal columns with geometric norms [Sec. 3.2, sample
                      bias, Fig. selectExpect], by quadrature over chi variables;
                      the truncated chi-squared law of the trailing sample norms
                      after pivoting and the truncation bounds of a partial
-                     sample factorization [Sec. 4, norm truncation].
+                     sample factorization [Sec. 3.3, norm truncation].
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` against a library routine, a closed form, a

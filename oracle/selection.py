@@ -1,5 +1,5 @@
 """Selection quality of sample pivoting (the post-hoc selection bias of
-Sec. 4 and its Fig. selectExpect).
+Sec. 3.2 and its Fig. selectExpect).
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
@@ -18,7 +18,7 @@ import numpy as np
 from scipy import integrate, special, stats
 
 # (The norm-truncation section at the end covers the second form of sample
-# bias in Sec. 4: after pivoting, the trailing sample norms are truncated
+# bias in Sec. 3.3: after pivoting, the trailing sample norms are truncated
 # chi-squared variables.)
 
 
@@ -55,10 +55,10 @@ def select_expectation(phi, ell, n):
     return float(np.sum(p * phi ** np.arange(n)))
 
 
-# ---------------------------------------------------------------- Sec. 4, norm truncation
+# -------------------------------------------------------------- Sec. 3.3, norm truncation
 def truncated_chi2_pdf(x, dof, tau):
     """Density of the squared trailing sample norm ratio x after pivoting
-    (Sec. 4 theorem): the chi-squared density with `dof` degrees of freedom
+    (Sec. 3.3 theorem): the chi-squared density with `dof` degrees of freedom
     restricted to [0, tau] and renormalised."""
     x = np.asarray(x, dtype=np.float64)
     s = 0.5 * dof
@@ -84,7 +84,7 @@ def truncation_bounds(S, j):
     """For a sample after j pivots of partial QRCP (S = Q_b^T B P, upper
     triangular in its first j columns; Alg. 1), the bound each remaining
     column's squared trailing norm must respect: min over i < j of
-    s_ii^2 - sum_{k=i}^{j-1} s_{k,c}^2 (Sec. 4: the i-th pivot was the largest
+    s_ii^2 - sum_{k=i}^{j-1} s_{k,c}^2 (Sec. 3.3: the i-th pivot was the largest
     trailing norm at step i).  Returns (bounds, trailing norms squared) for
     the columns c >= j."""
     S = np.asarray(S, dtype=np.float64)

@@ -262,6 +262,49 @@ struct Qrcp3Args {
 cudaError_t launch_qrcp3_block(const Qrcp3Args& a, int num_sms, cudaStream_t st);
 size_t qrcp3_smem_bytes(int64_t m);
 
+// ---- batched.cu: persistent batched mixed-precision TRQRCP (Alg. 6) --
+// teams of G co-resident CTAs claim problems from a device table or from a
+// request ring in mapped host memory and run the whole algorithm on each.
+// Byte offsets of the per-team scratch areas.
+struct BatchLayout {
+  size_t ctl, omega, B, Wt, P64, T, T32, Z32, YY, W11, swaps, map, cbuf, jbuf, cand, candcol,
+      ppart, rowj, part;
+  int64_t part_elems;  // floats in `part`
+};
+// Largest problem a team's scratch must hold.
+struct BatchLimits {
+  int64_t m, n, k;
+  int b, ell;
+};
+// Request ring of the serving loop, in page-locked host memory mapped into
+// the device's address space.  Followed in memory by `cap` rqrcp_problem
+// slots, `cap` (rounded up to even) int info words and `cap` int64 done words
+// (ticket + 1 once the request is finished).  The host publishes a request
+// by writing its slot, then raising `tail` (release order).
+struct RequestRing {
+  long long tail;  // requests published
+  int stop;        // nonzero: teams exit once the ring is empty
+  int cap;         // slots
+  long long pad[6];
+};
+size_t request_ring_bytes(int cap);
+struct BatchLaunch {
+  const rqrcp_problem* table;  // device table (batch mode) or nullptr
+  int nprob;
+  RequestRing* ring;           // device address of the mapped ring (serving) or nullptr
+  unsigned long long* next;    // claim counter
+  int G, teams;
+  char* scratch;
+  size_t team_bytes;
+  BatchLayout L;
+  GridBarrier* bars;           // teams entries
+  int* status;
+  unsigned int idle_polls;     // serving: polls of an empty ring before a team exits
+};
+size_t batch_team_bytes(const BatchLimits& lim, int G, BatchLayout* L);
+bool batch_fits(int64_t m, int64_t n, int b, int ell, int G);
+cudaError_t launch_batch_trqrcp(const BatchLaunch& bl, cudaStream_t st);
+
 // Q = first cols columns of the rows x rows identity
 cudaError_t launch_eye(double* Q, int64_t rows, int64_t cols, int64_t ld, cudaStream_t st);
 // Fill / copy helpers

@@ -1,0 +1,275 @@
+// Householder panel QR with its compact-WY factor T as a device function
+// over a group of co-resident CTAs: the body of the cooperative panel kernel,
+// shared with the persistent batched kernel.  The algorithm and its data
+// layout are described in panel.cu.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace rq {
+namespace pn {
+
+constexpr int NT = 256;
+constexpr int MAXB = 128;
+constexpr int PARTS = 8;   // threads per column in the partial-sum reduction
+constexpr int RB = 40;     // loads in flight per thread in that reduction
+
+// The panel QR and T on CTA g of a group of G co-resident CTAs (the whole
+// grid of the standalone kernel, or one team of the persistent batched
+// kernel); smem_raw: panel_smem_bytes(chunk, bJ) bytes of dynamic shared memory.
+__device__ __forceinline__ void panel_body(const PanelArgs& a, int g, int G,
+                                           unsigned char* smem_raw) {
+  const int bJ = a.bJ;
+  const int64_t chunk = (a.mJ + G - 1) / G;
+  const int64_t r_lo = (int64_t)g * chunk;
+  const int nrow = (int)imax64(0, imin64(a.mJ, r_lo + chunk) - r_lo);
+  const int64_t ldp = chunk | 1;  // odd: rows of one column in distinct banks
+  double* Ps = reinterpret_cast<double*>(smem_raw);  // chunk x bJ, ld = ldp
+  __shared__ double s_tot[MAXB];
+  __shared__ double s_w[MAXB];
+  __shared__ double s_part[PARTS][MAXB];
+  __shared__ double s_scal[4];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = NT / 32;
+
+  for (int64_t e = tid; e < (int64_t)nrow * bJ; e += NT) {
+    const int64_t r = e % nrow, c = e / nrow;
+    Ps[r + c * ldp] = __ldcg(a.P + (r_lo + r) + c * a.ld);
+  }
+  __syncthreads();
+
+  // 2 x G x bJ (column dots), G x bJ x bJ (Gram partials), bJ x bJ (Gram)
+  double* part_base = a.partial;
+  // partial dots of column j with columns j..bJ-1 over owned rows below row j
+  auto publish = [&](int j) {
+    double* part = part_base + (size_t)(j & 1) * G * bJ + (size_t)g * bJ;
+    const int rstart = (int)imax64(0, (int64_t)j + 1 - r_lo);  // local first row > j
+    const int ncols = bJ - j;
+    // P lanes per column (a power of two within a warp), as many columns at
+    // once as fit in the block; the P partial sums meet by shuffles
+    int P = 32;
+    while (P > 1 && NT / P < ncols) P >>= 1;
+    const int cpr = NT / P;
+    const int p = tid % P;
+    for (int c0 = 0; c0 < ncols; c0 += cpr) {
+      const int c = j + c0 + tid / P;
+      double s = 0.0;
+      if (c < bJ) {
+        const double* xj = Ps + (size_t)j * ldp;
+        const double* xc = Ps + (size_t)c * ldp;
+        for (int r = rstart + p; r < nrow; r += P) s = fma(xj[r], xc[r], s);
+      }
+      for (int o = P >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (p == 0 && c < bJ) part[c] = s;
+    }
+    if (j >= r_lo && j < r_lo + nrow) {
+      double* rowj = a.rowj + (size_t)(j & 1) * bJ;
+      for (int c = j + tid; c < bJ; c += NT) rowj[c] = Ps[(j - r_lo) + c * ldp];
+    }
+  };
+
+  publish(0);
+  for (int j = 0; j < bJ; ++j) {
+    if (!grid_barrier(a.bar, G, a.status)) return;
+    // fixed-order reduction of the partial dots: PARTS threads per column,
+    // thread pp adds CTAs q = pp, pp + PARTS, ... in increasing order with up
+    // to RB loads in flight, then the PARTS sums are added in order
+    const double* part = part_base + (size_t)(j & 1) * G * bJ;
+    const int ncols = bJ - j;
+    const int parts = imin64(PARTS, imax64(1, NT / ncols));
+    for (int e = tid; e < parts * ncols; e += NT) {
+      const int c = j + e % ncols, pp = e / ncols;
+      double s = 0.0;
+      for (int q0 = pp; q0 < G; q0 += RB * parts) {
+        double v[RB];
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+          const int q = q0 + u * parts;
+          v[u] = (q < G) ? __ldcg(part + (size_t)q * bJ + c) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < RB; ++u) s += v[u];
+      }
+      s_part[pp][c] = s;
+    }
+    __syncthreads();
+    const double* rowj = a.rowj + (size_t)(j & 1) * bJ;
+    for (int c = j + tid; c < bJ; c += NT) {
+      double s = 0.0;
+      for (int pp = 0; pp < parts; ++pp) s += s_part[pp][c];
+      s_tot[c] = s;
+      s_w[c] = __ldcg(rowj + c);  // row j of the panel before this step
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double beta, tau, scale;
+      house_scalars_sq(s_w[j], s_tot[j], &beta, &tau, &scale);
+      s_scal[0] = beta;
+      s_scal[1] = tau;
+      s_scal[2] = scale;
+      if (g == 0) a.tau[j] = tau;
+    }
+    __syncthreads();
+    const double beta = s_scal[0], tau = s_scal[1], scale = s_scal[2];
+    // w_c = tau * v^T a_c for c > j (v_j = 1, v_r = scale x_r below)
+    for (int c = j + 1 + tid; c < bJ; c += NT) s_w[c] = tau * (s_w[c] + scale * s_tot[c]);
+    __syncthreads();
+    const int64_t jl = (int64_t)j - r_lo;  // local index of row j (may be outside)
+    const int64_t rstart = imax64(0, jl + 1);
+    // scale column j into v, then a_rc -= v_r w_c on owned rows below j
+    for (int64_t r = rstart + tid; r < nrow; r += NT) Ps[r + j * ldp] *= scale;
+    __syncthreads();
+    if (tau != 0.0) {
+      // (row, column) pairs packed densely over the threads (32-bit indices)
+      const int ncols = bJ - j - 1;
+      const int rows = nrow - (int)rstart;
+      const double* vj = Ps + (size_t)j * ldp;
+      for (int e = tid; e < rows * ncols; e += NT) {
+        const int cc = e / rows;
+        const int r = (int)rstart + (e - cc * rows);
+        const int c = j + 1 + cc;
+        Ps[r + (size_t)c * ldp] = fma(-vj[r], s_w[c], Ps[r + (size_t)c * ldp]);
+      }
+    }
+    if (jl >= 0 && jl < nrow) {
+      // row j: R entries
+      for (int c = j + 1 + tid; c < bJ; c += NT) Ps[jl + c * ldp] -= (tau != 0.0) ? s_w[c] : 0.0;
+      if (tid == 0) Ps[jl + j * ldp] = beta;
+    }
+    __syncthreads();
+    if (j + 1 < bJ) publish(j + 1);
+  }
+
+  // mixed precision: the stored reflectors are the FP32-rounded ones
+  if (a.round_f32) {
+    for (int64_t e = tid; e < (int64_t)nrow * bJ; e += NT) {
+      const int64_t r = e % nrow, c = e / nrow;
+      if (r_lo + r > c) Ps[r + c * ldp] = (double)(float)Ps[r + c * ldp];
+    }
+    __syncthreads();
+  }
+  // write the factored rows back
+  for (int64_t e = tid; e < (int64_t)nrow * bJ; e += NT) {
+    const int64_t r = e % nrow, c = e / nrow;
+    a.P[(r_lo + r) + c * a.ld] = Ps[r + c * ldp];
+  }
+  // partial Gram Y^T Y over owned rows (upper triangle, Y unit lower)
+  double* gram = part_base + (size_t)2 * G * bJ + (size_t)g * bJ * bJ;
+  for (int e = tid; e < bJ * bJ; e += NT) {
+    const int c1 = e % bJ, c2 = e / bJ;  // entry (c1, c2), c1 <= c2
+    if (c1 > c2) continue;
+    // rows R >= c2 only (y2 is zero above its unit diagonal); the diagonal
+    // row of each column reads as 1
+    const int64_t r0 = imax64(0, (int64_t)c2 - r_lo);
+    double s = 0.0;
+    if (r0 < nrow && r_lo + r0 == c2) {
+      s = (c1 == c2) ? 1.0 : Ps[r0 + c1 * ldp];
+      for (int64_t r = r0 + 1; r < nrow; ++r) s = fma(Ps[r + c1 * ldp], Ps[r + c2 * ldp], s);
+    } else {
+      for (int64_t r = r0; r < nrow; ++r) s = fma(Ps[r + c1 * ldp], Ps[r + c2 * ldp], s);
+    }
+    gram[c1 + c2 * bJ] = s;
+  }
+  if (!grid_barrier(a.bar, G, a.status)) return;
+  // every CTA adds the partials of the Gram entries e = g, g + G, ... over all
+  // CTAs q in increasing order (PP threads per entry, then a fixed-order
+  // combine), so the reduction is spread over the grid
+  {
+    const double* gp = part_base + (size_t)2 * G * bJ;
+    double* gtot = part_base + (size_t)2 * G * bJ + (size_t)G * bJ * bJ;
+    const int nent = (bJ * bJ - g + G - 1) / G;   // entries owned by this CTA
+    const int PP = nent >= NT ? 1 : (nent * 8 <= NT ? 8 : (nent * 4 <= NT ? 4 : (nent * 2 <= NT ? 2 : 1)));
+    __shared__ double s_g[NT];
+    for (int i0 = 0; i0 < nent; i0 += NT / PP) {
+      const int i = i0 + tid / PP, sub = tid % PP;
+      double s = 0.0;
+      if (i < nent) {
+        const int e = g + i * G;
+        for (int q0 = sub; q0 < G; q0 += 8 * PP) {
+          double v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u * PP;
+            v[u] = (q < G) ? __ldcg(gp + (size_t)q * bJ * bJ + e) : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) s += v[u];
+        }
+      }
+      s_g[tid] = s;
+      __syncthreads();
+      if (sub == 0 && i < nent) {
+        double t = 0.0;
+        for (int u = 0; u < PP; ++u) t += s_g[tid + u];
+        gtot[g + i * G] = t;
+      }
+      __syncthreads();
+    }
+  }
+  if (!grid_barrier(a.bar, G, a.status)) return;
+  // ---- T by column back-substitution: column j on CTA j % G, warp j / G
+  const int warps_needed = (bJ + G - 1) / G;  // columns per CTA, rounded up
+  if (g >= bJ) return;
+  const double* gtot = part_base + (size_t)2 * G * bJ + (size_t)G * bJ * bJ;
+  // this CTA's largest column decides how much of the Gram it needs
+  int jmax = -1;
+  for (int j = g; j < bJ; j += G) jmax = j;
+  double* Gs = Ps;            // (jmax + 1) x (jmax + 1) upper part, ld bJ
+  double* taus = Ps + (size_t)bJ * bJ;  // bJ adjusted tau values
+  for (int e = tid; e < (jmax + 1) * bJ; e += NT) {
+    const int r = e % bJ, c = e / bJ;
+    if (r <= c) Gs[e] = __ldcg(gtot + e);
+  }
+  // every tau (CTA 0 writes the adjusted ones back in the mixed mode)
+  for (int r = tid; r < bJ; r += NT) {
+    double t = __ldcg(a.tau + r);
+    // mixed precision: tau_r = 2 / v_r^T v_r for the stored (rounded) v_r;
+    // zero stays zero
+    if (a.round_f32 && t != 0.0) t = 2.0 / __ldcg(gtot + r + (size_t)r * bJ);
+    taus[r] = t;
+  }
+  __syncthreads();
+  for (int wq = warp; wq < warps_needed; wq += nwarps) {
+    const int j = g + wq * G;
+    if (j < bJ) {
+      constexpr int RPL = MAXB / 32;  // rows per lane
+      double acc[RPL];
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) acc[q] = 0.0;
+      double xt = taus[j];
+      double* Tj = a.T + (size_t)j * bJ;
+      for (int r = j + 1 + lane; r < bJ; r += 32) Tj[r] = 0.0;
+      if (lane == 0) Tj[j] = xt;
+      for (int t = j; t >= 1; --t) {
+        // acc(r) += G(r, t) x_t for r < t, then x_{t-1} = -tau_{t-1} acc(t-1)
+        const double* gt = Gs + (size_t)t * bJ;
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+          const int r = lane + 32 * q;
+          if (r < t) acc[q] = fma(gt[r], xt, acc[q]);
+        }
+        const int rn = t - 1, owner = rn & 31, qn = rn >> 5;
+        double mine = 0.0;
+#pragma unroll
+        for (int q = 0; q < RPL; ++q)
+          if (q == qn) mine = acc[q];
+        const double val = -taus[rn] * mine;
+        xt = __shfl_sync(0xffffffffu, val, owner);
+        if (lane == owner) Tj[rn] = xt;
+      }
+    }
+  }
+  if (a.round_f32 && g == 0) {
+    __syncthreads();
+    for (int r = tid; r < bJ; r += NT) a.tau[r] = taus[r];
+  }
+}
+
+__host__ __device__ inline size_t panel_smem_bytes(int64_t chunk, int bJ) {
+  size_t a = (size_t)(chunk | 1) * bJ * 8;
+  size_t b = ((size_t)bJ * bJ + bJ) * 8;
+  return a > b ? a : b;
+}
+
+}  // namespace pn
+}  // namespace rq

@@ -1,5 +1,5 @@
 """Writes select_expectation.json: the exact expected norm of the
-sample-selected column (Sec. 4, sample bias; Fig. selectExpect setting:
+sample-selected column (Sec. 3.2, sample bias; Fig. selectExpect setting:
 orthogonal columns with norms phi^j, j = 0..n-1, sample of l GIID rows),
 computed by the oracle's quadrature.  Run from the repository root:
     python tests/golden/gen_select_expectation.py

@@ -108,7 +108,7 @@ def test_selection_wrong_degrees_of_freedom_is_caught(monkeypatch):
 
 def test_truncation_law_upper_incomplete_gamma_is_caught(monkeypatch):
     """The upper instead of the lower incomplete gamma function in the
-    truncated chi-squared expectation (Sec. 4)."""
+    truncated chi-squared expectation (Sec. 3.3)."""
     real = selection.special
 
     class _Special:

@@ -1,4 +1,4 @@
-"""Pins of the selection-quality statistic (Sec. 4, post-hoc selection bias,
+"""Pins of the selection-quality statistic (Sec. 3.2, post-hoc selection bias,
 Fig. selectExpect): closed forms, limits, a Monte Carlo draw of the chi
 variables it integrates over, and the paper's stated worst case."""
 import numpy as np
@@ -61,7 +61,7 @@ def test_golden_file_matches_oracle():
         assert abs(selection.select_expectation(c["phi"], c["ell"], c["n"]) - c["exact"]) <= 1e-12
 
 
-# ---------------------------------------------------------------- Sec. 4, norm truncation
+# -------------------------------------------------------------- Sec. 3.3, norm truncation
 @pytest.mark.parametrize("dof,tau", [(8, 3.0), (8, 20.0), (3, 0.5), (40, 30.0), (144, 60.0)])
 def test_truncated_chi2_expectation_is_the_integral(dof, tau):
     """The paper's closed form for E(x) equals the mean of the truncated
@@ -76,7 +76,7 @@ def test_truncated_chi2_expectation_is_the_integral(dof, tau):
 
 def test_truncated_chi2_expectation_limits_and_monotone():
     """Zero at tau = 0, increasing in tau, the untruncated mean (dof) for a
-    large cutoff (Sec. 4)."""
+    large cutoff (Sec. 3.3)."""
     taus = np.linspace(0.01, 200.0, 60)
     e = [selection.truncated_chi2_expectation(16, t) for t in taus]
     assert selection.truncated_chi2_expectation(16, 0.0) == 0.0
@@ -91,7 +91,7 @@ def test_truncated_chi2_expectation_limits_and_monotone():
 
 @pytest.mark.parametrize("seed", range(6))
 def test_trailing_sample_norms_respect_the_truncation_bound(seed):
-    """The premise of the Sec. 4 theorem: after j pivots of the sample QRCP,
+    """The premise of the Sec. 3.3 theorem: after j pivots of the sample QRCP,
     every remaining column's squared trailing norm stays below
     min_i (s_ii^2 - sum_{k=i}^{j-1} s_kc^2), because the i-th pivot was the
     largest trailing norm at step i.  Checked on the oracle's sample QRCP."""
