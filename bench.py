@@ -84,7 +84,7 @@ def parse():
     ap.add_argument("--legs", default="qr,e2e,cpu,emulated,rsrqrcp,qrcp,quality,mixed,truncated,serving",
                     help="comma-separated extra legs to run after the FP64 step")
     ap.add_argument("--case", choices=["panel", "gemm_bf16x", "gemm_f64x", "qrcp", "sample", "mixed",
-                                       "fp64peak"],
+                                       "fp64peak", "batched"],
                     default=None,
                     help="run one small kernel case (for profiling) instead of the benchmark")
     ap.add_argument("--shape", default=None,
@@ -236,7 +236,7 @@ def fp64_peak_tflops(peaks):
     return (peaks.get("bf16_tflops") or 1900.0) * 1.25 / 2250.0
 
 
-def probe_peaks(dev, kinds=("fp64_fma", "fp64_dmma_m8n8k4", "fp64_dmma_m16n8k16"),
+def probe_peaks(dev, kinds=("fp64_fma", "fp64_fma_outer", "fp64_dmma_m8n8k4", "fp64_dmma_m16n8k16"),
                 target_ms=60.0, reps=3):
     """Measured arithmetic peaks of this GPU (rqrcp_peak_probe): per kind the
     best TFLOP/s of `reps` launches of about `target_ms` each, with 4 CTAs of
@@ -619,23 +619,28 @@ def serving_leg(args, dev):
     return stats
 
 
-def batched_leg(dev, tuner, nprob=64, lanes=16, reps=5, seed=9):
-    """One static batch of served-size problems (m, n ~ U{256..4096},
-    k ~ U{16..128}, A = X Y^T in FP32, autotuned b/p) through trqrcp_batched
-    on `lanes` worker streams (each launch capped at a quarter of the SMs so
-    that the lanes run side by side), captured as one CUDA graph and
-    replayed."""
+def batched_specs(tuner, nprob, seed):
+    """Served-size problems: m, n ~ U{256..4096}, k ~ U{16..128}, autotuned b/p."""
     import numpy as np
-    import torch
-    import paper_1509_06820_gb300 as rq
-    from paper_1509_06820_gb300.serve import request_flops
     rng = np.random.default_rng(seed)
     specs = []
     for _ in range(nprob):
         m, n = int(rng.integers(256, 4097)), int(rng.integers(256, 4097))
         k = int(min(rng.integers(16, 129), m, n))
-        b, p = tuner.choose(m, n, k)
+        b, p = tuner.choose(m, n, k) if tuner is not None else (64, 8)
         specs.append((m, n, k, min(b, k), p))
+    return specs
+
+
+def batched_leg(dev, tuner, nprob=64, reps=5, seed=9):
+    """One static batch of served-size problems (m, n ~ U{256..4096},
+    k ~ U{16..128}, A = X Y^T in FP32, autotuned b/p) through trqrcp_batched:
+    one persistent launch (teams of CTAs claim the problems longest-first),
+    captured as one CUDA graph and replayed."""
+    import torch
+    import paper_1509_06820_gb300 as rq
+    from paper_1509_06820_gb300.serve import request_flops
+    specs = batched_specs(tuner, nprob, seed)
     g = torch.Generator(device=dev)
     probs = []
     for i, (m, n, k, b, p) in enumerate(specs):
@@ -644,17 +649,15 @@ def batched_leg(dev, tuner, nprob=64, lanes=16, reps=5, seed=9):
         Yf = torch.randn((n, k), generator=g, device=dev)
         probs.append((rq.colmajor(X @ Yf.t()), k, b, p, 1000 + i))
     h = rq.Handle(dev)
-    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    h.set_max_sms(max(16, nsm // 4))
-    h.reserve_batched(lanes, max(s[0] for s in specs), max(s[1] for s in specs),
+    h.reserve_batched(0, max(s[0] for s in specs), max(s[1] for s in specs),
                       max(s[2] for s in specs), max(s[3] for s in specs),
                       max(s[4] for s in specs))
-    outs = rq.trqrcp_batched(probs, lanes=lanes, handle=h)
+    outs = rq.trqrcp_batched(probs, handle=h)
     torch.cuda.synchronize(dev)
     side = torch.cuda.Stream(dev)
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=side):
-        rq.trqrcp_batched(probs, lanes=lanes, handle=h, outs=outs)
+        rq.trqrcp_batched(probs, handle=h, outs=outs)
     graph.replay()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -665,10 +668,10 @@ def batched_leg(dev, tuner, nprob=64, lanes=16, reps=5, seed=9):
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / reps
     flops = sum(request_flops(m, n, k, b + p) for (m, n, k, b, p) in specs)
-    return {"problems": nprob, "lanes": lanes, "max_sms_per_launch": max(16, nsm // 4),
-            "ms_per_batch": ms,
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    return {"problems": nprob, "team_ctas": 16, "teams": nsm // 16, "ms_per_batch": ms,
             "problems_per_s": nprob / (ms / 1e3), "gflops": flops / (ms / 1e3) / 1e9,
-            "launch": "one CUDA graph per batch (fork to the lanes, join)",
+            "launch": "one persistent cooperative launch per batch, captured in a CUDA graph",
             "device_info": h.sync_info()}
 
 
@@ -683,6 +686,8 @@ def run_case(args):
                   N(0,1) sample
       mixed       rqrcp_factor_mixed of the n x n spiked FP32 matrix (the
                   mixed-precision configuration), block b, oversampling p
+      batched     one persistent trqrcp_batched launch over 64 served-size
+                  problems (--reps sets the count), graph-replayed
       fp64peak    the arithmetic-peak probes (FP64 FMA, FP64 DMMA m8n8k4 and
                   m16n8k16, FP32 FMA) with the SM clock sampled meanwhile
     Two untimed runs precede the timed ones."""
@@ -692,12 +697,17 @@ def run_case(args):
     import paper_1509_06820_gb300 as rq
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
+    if args.case == "batched":
+        # one persistent batched launch over served-size problems (b = 64, p = 8)
+        res = batched_leg(dev, None, nprob=args.reps if args.reps > 1 else 64)
+        print(json.dumps({"case": "batched", **res}), flush=True)
+        return
     if args.case == "fp64peak":
         clocks = ClockSampler(0)
         clocks.start()
         time.sleep(0.3)
-        res = probe_peaks(dev, kinds=("fp64_fma", "fp64_dmma_m8n8k4", "fp64_dmma_m16n8k16",
-                                      "fp32_fma"), target_ms=200.0, reps=5)
+        res = probe_peaks(dev, kinds=("fp64_fma", "fp64_fma_outer", "fp64_dmma_m8n8k4",
+                                      "fp64_dmma_m16n8k16", "fp32_fma"), target_ms=200.0, reps=5)
         clk = clocks.stop()
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         mhz = clk.get("sm_mhz") or 2070.0

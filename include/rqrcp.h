@@ -111,6 +111,13 @@ int rqrcp_reserve(rqrcp_handle_t handle, char op, int64_t m, int64_t n, int64_t 
  * (d_swaps[i] = i) for the steps it did not take, leaves dB unchanged and
  * returns; the handle stays usable.  No other call reads the option. */
 #define RQRCP_OPT_TEST_BARRIER_TIMEOUT 4
+/* RQRCP_OPT_BATCH_TEAM (value 8, 16 or 32; default 16): CTAs per team of the
+ * persistent batched kernel (trqrcp_batched, rqrcp_server_*).  A problem's
+ * result depends on it (the order of the panel's and the products' partial
+ * sums), and on nothing else of the batch.  Larger samples and panels need
+ * larger teams: RQRCP_ERR_UNSUPPORTED / RQRCP_ERR_BATCH name the problems that
+ * do not fit.  -3 for another value. */
+#define RQRCP_OPT_BATCH_TEAM 5
 int rqrcp_set_option(rqrcp_handle_t handle, int option, int value);
 
 /* Wait for the handle's stream, then return the device status word in *info
@@ -236,30 +243,45 @@ typedef struct rqrcp_problem {
 } rqrcp_problem;
 
 /*
- * Many uneven-size mixed-precision TRQRCP problems (Alg. 6, as trqrcp_mixed;
- * the served low-rank workload) in one call.  The paper factors one matrix
- * at a time; this is the batched form of its truncated algorithm.
- *   probs : host array of nprob problem descriptions (read during the call;
- *           the device buffers they point to must not overlap)
- *   lanes : 1..16 worker streams.  The problems are spread over the lanes
- *           (longest first, by algorithmic flops); each lane has its own
- *           scratch, re-sample flag and grid barrier, runs its problems in
- *           order, and starts after, and is joined back to, the work already
- *           enqueued on the handle's stream.  Results are those of
- *           trqrcp_mixed on each problem alone.
+ * Many uneven-size mixed-precision TRQRCP problems (Alg. 6, the served
+ * low-rank workload) in ONE persistent cooperative launch.  The paper factors
+ * one matrix at a time; this is the batched form of its truncated algorithm.
+ * The grid is divided into teams of G CTAs (RQRCP_OPT_BATCH_TEAM, one CTA per
+ * SM); each team claims the next problem from a device copy of `probs`
+ * (sorted longest-first by algorithmic flops) and runs all of Alg. 6 on it:
+ * Omega from Philox stream 1 with an FP32 Box-Muller transform, the sample
+ * B = Omega A and every product with A, Y and W^T as FP32 products on the CUDA
+ * cores, the sample QRCP, the Householder panel, T and the sample update of
+ * Eq. (3) in FP64.  Outputs per problem are laid out as trqrcp_mixed's (jpvt,
+ * tau and rdiag FP64; Y and R FP32); they agree with trqrcp_mixed within FP32
+ * rounding, not bit for bit (its products use the split-BF16 tensor-core GEMM).
+ * A problem's result depends only on the problem and G: it is the same alone
+ * and in any batch.
+ *   probs : host array of nprob problem descriptions, copied (through the
+ *           handle's page-locked staging buffer) to the device on the
+ *           handle's stream; the device buffers they point to must not overlap
+ *   teams : problems run at once (0 = as many teams as the handle's SM budget,
+ *           RQRCP_OPT_MAX_SMS, holds)
  * Every problem is checked before anything is enqueued: a failing problem
- * returns RQRCP_ERR_BATCH (its index and status in rqrcp_last_error).  Lane
- * scratch grows on demand (a device allocation, which is not allowed during
- * stream capture): reserve it first with rqrcp_reserve_batched.  Device
- * conditions of all problems are ORed into the handle's info word.
+ * returns RQRCP_ERR_BATCH (its index and status in rqrcp_last_error).
+ * Limits: b <= 128, b + p <= 192, the sample of one block (l x n) and the panel
+ * (m x b) held in the shared memory of the team's G CTAs (about 200 KB each).
+ * Device conditions of all problems are ORed into the handle's info word.
+ * The call waits for the handle's earlier work before it refills the staging
+ * buffer (except during stream capture); team scratch and the device table
+ * grow on demand (a device allocation, not allowed during capture): reserve
+ * them first with rqrcp_reserve_batched.  A captured launch reads the staging
+ * buffer when it runs, so replay it before the next trqrcp_batched call on the
+ * same handle.
  */
-int trqrcp_batched(rqrcp_handle_t handle, int nprob, const rqrcp_problem* probs, int lanes);
+int trqrcp_batched(rqrcp_handle_t handle, int nprob, const rqrcp_problem* probs, int teams);
 
 /*
- * Creates `lanes` worker lanes (1..16) and sizes each lane's scratch for
- * problems up to m x n with rank k and block b, oversampling p.
+ * Sizes the persistent batched kernel's scratch for `teams` teams (0 = as
+ * many as fit) and problems up to m x n with rank k, block b, oversampling p,
+ * and its descriptor table for 1024 problems.
  */
-int rqrcp_reserve_batched(rqrcp_handle_t handle, int lanes, int64_t m, int64_t n, int64_t k,
+int rqrcp_reserve_batched(rqrcp_handle_t handle, int teams, int64_t m, int64_t n, int64_t k,
                           int b, int p);
 
 /*
@@ -427,6 +449,8 @@ int rqrcp_gemm_f64x(rqrcp_handle_t handle, char transA, char transB, int64_t m, 
  *   kind 1  FP64 tensor-core mma.sync m8n8k4 (4 independent tiles per warp)
  *   kind 2  FP64 tensor-core mma.sync m16n8k16 (2 independent tiles per warp)
  *   kind 3  FP32 FMA on the CUDA cores
+ *   kind 4  FP64 FMA in a GEMM's register-blocked outer-product pattern
+ *           (4 x 4 accumulators per thread, operands renewed every round)
  * Returns -i for an invalid argument i, RQRCP_ERR_CUDA for a launch error.
  */
 int rqrcp_peak_probe(int kind, int64_t iters, int grid, void* d_sink, void* cuda_stream,

@@ -26,6 +26,7 @@ OPT_FP64_EMULATION = 1
 OPT_RESAMPLE = 2
 OPT_MAX_SMS = 3
 OPT_TEST_BARRIER_TIMEOUT = 4
+OPT_BATCH_TEAM = 5
 INFO_NONFINITE = 1
 INFO_RESAMPLED = 2
 INFO_TIMEOUT = 4
@@ -134,8 +135,15 @@ class Handle:
     def reserve(self, op, m, n, k, b, p):
         _check(load().rqrcp_reserve(self.bind(), op.encode(), m, n, k, b, p), self.h)
 
-    def reserve_batched(self, lanes, m, n, k, b, p):
-        _check(load().rqrcp_reserve_batched(self.h, lanes, m, n, k, b, p), self.h)
+    def reserve_batched(self, teams, m, n, k, b, p):
+        """Scratch of `teams` teams (0 = as many as the SM budget holds) of the
+        persistent batched kernel for problems up to m x n, rank k, block b,
+        oversampling p."""
+        _check(load().rqrcp_reserve_batched(self.h, teams, m, n, k, b, p), self.h)
+
+    def set_batch_team(self, ctas):
+        """CTAs per team of the persistent batched kernel (8, 16 or 32)."""
+        _check(load().rqrcp_set_option(self.h, OPT_BATCH_TEAM, ctas), self.h)
 
     def set_test_barrier_timeout(self, on=True):
         """Test of the failure path only: rqrcp_sample_qrcp on this handle runs
@@ -354,10 +362,11 @@ def trqrcp_mixed(A, k, b, p, seed, handle=None, out=None):
     return jpvt, tau, Y, R, rdiag
 
 
-def trqrcp_batched(problems, lanes=8, handle=None, outs=None):
-    """Alg. 6 in mixed precision on many matrices in one call.  `problems` is a
-    list of (A, k, b, p, seed) with A a column-major float32 CUDA tensor;
-    returns one (jpvt, tau, Y, R, rdiag) tuple per problem, as trqrcp_mixed."""
+def trqrcp_batched(problems, teams=0, handle=None, outs=None):
+    """Alg. 6 in mixed precision on many matrices in one persistent launch.
+    `problems` is a list of (A, k, b, p, seed) with A a column-major float32
+    CUDA tensor; returns one (jpvt, tau, Y, R, rdiag) tuple per problem, laid
+    out as trqrcp_mixed's.  teams: concurrent problems (0 = as many as fit)."""
     if not problems:
         return []
     dev = problems[0][0].device
@@ -380,7 +389,7 @@ def trqrcp_batched(problems, lanes=8, handle=None, outs=None):
         arr[i] = Problem(m, n, k, b, p, seed, _ptr(A), _ld(A), _ptr(jpvt), _ptr(tau), _ptr(Y),
                          _ld(Y), _ptr(R), _ld(R), _ptr(rdiag))
         results.append(out)
-    _check(load().trqrcp_batched(h.bind(), len(problems), arr, lanes), h.h)
+    _check(load().trqrcp_batched(h.bind(), len(problems), arr, teams), h.h)
     return results
 
 
@@ -484,7 +493,8 @@ def sync_info(device=None):
     return default_handle(device).sync_info()
 
 
-PEAK_KINDS = {"fp64_fma": 0, "fp64_dmma_m8n8k4": 1, "fp64_dmma_m16n8k16": 2, "fp32_fma": 3}
+PEAK_KINDS = {"fp64_fma": 0, "fp64_dmma_m8n8k4": 1, "fp64_dmma_m16n8k16": 2, "fp32_fma": 3,
+              "fp64_fma_outer": 4}
 
 
 def peak_probe(kind, iters, grid, device="cuda"):

@@ -1,0 +1,722 @@
+// Persistent batched TRQRCP: many uneven mixed-precision truncated RQRCP
+// problems (Alg. 6) in ONE cooperative launch.
+//
+// The grid is split into teams of G co-resident CTAs (one CTA per SM).  A
+// team claims the next problem from a work source -- a descriptor table in
+// device memory (sorted longest-first by the host), or a request ring in
+// mapped host memory that the host keeps filling (the serving loop) -- and
+// runs all of Alg. 6 on it, phase after phase, separated by a software
+// barrier over the team's CTAs (bounded waits, RQRCP_INFO_TIMEOUT on
+// expiry).  Per-problem state (the sample, the panel, W^T, T, Z) lives in the
+// team's slice of the handle's scratch; nothing returns to the host between
+// problems, so the launch can be captured in a CUDA graph, and a problem's
+// result depends only on the problem and G (the same alone and in a batch).
+//
+// Arithmetic of one problem (FP32 storage, FP64 where the method's pivoting
+// and reflectors need it):
+//   Omega     Philox4x32-10 stream 1 (as everywhere in this library), the
+//             Box-Muller transform in FP32 (it only steers pivots)
+//   B = Omega A                         FP32 products, stored FP64
+//   sample QRCP (Alg. 1 halted)        FP64, the same device code as the
+//                                       cooperative sample kernel
+//   A_hat = A(:, sel) - Y1 W1^T(:, sel) FP32 products, FP64 panel
+//   panel QR + T (Sec. 2.2)             FP64, the same device code as the
+//                                       cooperative panel kernel; reflectors
+//                                       rounded to FP32 with tau = 2/v^T v
+//   W2^T = T2^T (Y2^T A - (Y2^T Y1) W1^T), R rows   FP32 products
+//   W11 = S11 R11^-1, B1 = S12 - W11 R12 (Eq. 3)    FP64
+// The FP32 products run on the CUDA cores as a team-cooperative tiled GEMM
+// (64 x 64 output tiles, split over K when there are fewer tiles than CTAs,
+// partial sums added in a fixed order).
+#include <algorithm>
+#include <climits>
+
+#include "kernels.cuh"
+#include "panel.cuh"
+#include "philox.cuh"
+#include "sample_qrcp.cuh"
+
+namespace rq {
+namespace {
+
+constexpr int NT = 256;
+constexpr int BM = 64, BN = 64, BK = 16;
+constexpr int MAXB = 128;
+constexpr uint32_t kOmegaStreamId = 1;
+
+// Loads of data that other CTAs of the launch wrote go through L2 (__ldcg):
+// the L1 of an SM is not kept coherent with stores made on other SMs.
+__device__ __forceinline__ int64_t ldg_i64(const int64_t* p) {
+  return (int64_t)__ldcg(reinterpret_cast<const long long*>(p));
+}
+
+// ---------------------------------------------------------------- team GEMM
+// C (M x N) = alpha op(A) op(B) + beta Cin, column-major.
+//   op(A)(i, k) = at ? A[k + i lda] : A[i + k lda]
+//   op(B)(k, j) = B[brow0 + k + col(j) ldb],  col(j) = bmap ? bmap[j] : j
+//   Cin(i, j)   = Cin[crow0 + i + ccol(j) ldci], ccol(j) = cmap ? cmap[j] : j
+// TC is the type of the products and sums.
+template <typename TC, typename TA, typename TB, typename TI, typename TO>
+struct TeamGemm {
+  int64_t M, N, K;
+  const TA* A;
+  int64_t lda;
+  int at;
+  const TB* B;
+  int64_t ldb;
+  const int64_t* bmap;
+  int64_t brow0;
+  const TI* Cin;
+  int64_t ldci;
+  const int64_t* cmap;
+  int64_t crow0;
+  TO* C;
+  int64_t ldc;
+  TC alpha, beta;
+};
+
+template <typename TC, typename TA, typename TB, typename TI, typename TO>
+__device__ __forceinline__ void tg_epilogue(const TeamGemm<TC, TA, TB, TI, TO>& op, int64_t i,
+                                            int64_t j, TC acc) {
+  TC v = op.alpha * acc;
+  if (op.Cin != nullptr) {
+    const int64_t cc = op.cmap ? ldg_i64(op.cmap + j) : j;
+    v += op.beta * (TC)__ldcg(op.Cin + op.crow0 + i + cc * op.ldci);
+  }
+  op.C[i + j * op.ldc] = (TO)v;
+}
+
+// One 64 x 64 output tile over k in [k0, k1): 256 threads, 4 x 4 outputs
+// each (rows 4 ty.., columns 4 tx.. with ty = tid % 16, tx = tid / 16), the
+// next 16-deep slab of both operands loaded into registers while the current
+// one is multiplied from shared memory.
+template <typename TC, typename TA, typename TB, typename TI, typename TO>
+__device__ __forceinline__ void tg_tile(const TeamGemm<TC, TA, TB, TI, TO>& op, int64_t i0,
+                                        int64_t j0, int64_t k0, int64_t k1, TC (&acc)[4][4],
+                                        TC* As, TC* Bs) {
+  constexpr int LDS = BM + 4;  // shared row length (keeps 16-byte alignment)
+  const int tid = threadIdx.x;
+  const int ty = tid & 15, tx = tid >> 4;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = (TC)0;
+  TC ra[4], rb[4];
+  auto load = [&](int64_t kb) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + NT * u;
+      // A: 64 rows x 16 k; the fast index follows the stored layout
+      int ii, kk;
+      if (op.at) {
+        kk = e & 15;
+        ii = e >> 4;
+      } else {
+        ii = e & 63;
+        kk = e >> 6;
+      }
+      const int64_t gi = i0 + ii, gk = kb + kk;
+      ra[u] = (gi < op.M && gk < k1)
+                  ? (TC)__ldcg(op.at ? op.A + gk + gi * op.lda : op.A + gi + gk * op.lda)
+                  : (TC)0;
+      // B: 16 k x 64 columns, k fastest
+      const int kb2 = e & 15, jj = e >> 4;
+      const int64_t gj = j0 + jj, gk2 = kb + kb2;
+      TC vb = (TC)0;
+      if (gj < op.N && gk2 < k1) {
+        const int64_t col = op.bmap ? ldg_i64(op.bmap + gj) : gj;
+        vb = (TC)__ldcg(op.B + op.brow0 + gk2 + col * op.ldb);
+      }
+      rb[u] = vb;
+    }
+  };
+  auto store = [&]() {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + NT * u;
+      int ii, kk;
+      if (op.at) {
+        kk = e & 15;
+        ii = e >> 4;
+      } else {
+        ii = e & 63;
+        kk = e >> 6;
+      }
+      As[kk * LDS + ii] = ra[u];
+      Bs[(e & 15) * LDS + (e >> 4)] = rb[u];
+    }
+  };
+  if (k0 >= k1) return;
+  load(k0);
+  for (int64_t kb = k0; kb < k1; kb += BK) {
+    __syncthreads();  // the previous slab is no longer read
+    store();
+    __syncthreads();
+    if (kb + BK < k1) load(kb + BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      TC a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[q] = As[kk * LDS + 4 * ty + q];
+        b[q] = Bs[kk * LDS + 4 * tx + q];
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+    }
+  }
+}
+
+// The whole product over the team (CTA g of G).  Every CTA of the team calls
+// it with the same arguments; returns false if a team barrier gave up.
+template <typename TC, typename TA, typename TB, typename TI, typename TO>
+__device__ bool team_gemm(const TeamGemm<TC, TA, TB, TI, TO>& op, int g, int G, TC* part,
+                          int64_t part_cap, GridBarrier* bar, int* status, unsigned char* smem) {
+  if (op.M <= 0 || op.N <= 0) return true;
+  TC* As = reinterpret_cast<TC*>(smem);
+  TC* Bs = As + BK * (BM + 4);
+  const int64_t tm = (op.M + BM - 1) / BM, tn = (op.N + BN - 1) / BN, ntile = tm * tn;
+  int64_t splits = 1;
+  if (ntile < G && op.K > 512) {
+    splits = std::min<int64_t>(G / ntile, (op.K + 255) / 256);
+    while (splits > 1 && ntile * splits * BM * BN > part_cap) --splits;
+  }
+  const int64_t kper = ((op.K + splits - 1) / splits + BK - 1) / BK * BK;
+  const int tid = threadIdx.x;
+  const int ty = tid & 15, tx = tid >> 4;
+  const int64_t nitems = ntile * splits;
+  for (int64_t w = g; w < nitems; w += G) {
+    const int64_t tile = w % ntile, sp = w / ntile;
+    const int64_t i0 = (tile % tm) * BM, j0 = (tile / tm) * BN;
+    const int64_t k0 = sp * kper, k1 = std::min<int64_t>(op.K, k0 + kper);
+    TC acc[4][4];
+    tg_tile(op, i0, j0, k0, k1, acc, As, Bs);
+    if (splits == 1) {
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int64_t j = j0 + 4 * tx + y;
+        if (j >= op.N) continue;
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          const int64_t i = i0 + 4 * ty + x;
+          if (i < op.M) tg_epilogue(op, i, j, acc[x][y]);
+        }
+      }
+    } else {
+      TC* pw = part + w * (BM * BN);
+#pragma unroll
+      for (int y = 0; y < 4; ++y)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) pw[(4 * tx + y) * BM + 4 * ty + x] = acc[x][y];
+    }
+  }
+  if (splits > 1) {
+    if (!grid_barrier(bar, G, status)) return false;
+    // partial sums of each element added over the splits in order
+    for (int64_t e = (int64_t)g * NT + tid; e < ntile * BM * BN; e += (int64_t)G * NT) {
+      const int64_t tile = e / (BM * BN), loc = e % (BM * BN);
+      const int64_t i = (tile % tm) * BM + loc % BM, j = (tile / tm) * BN + loc / BM;
+      if (i >= op.M || j >= op.N) continue;
+      TC s = (TC)0;
+      for (int64_t sp = 0; sp < splits; ++sp) s += __ldcg(part + (sp * ntile + tile) * (BM * BN) + loc);
+      tg_epilogue(op, i, j, s);
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------- the kernel
+struct TeamCtl {
+  rqrcp_problem prob;
+  long long ticket;  // index of the claimed problem, -1 = none
+  int status;        // the problem's status bits
+  int singular;      // exactly singular R11 in the current block
+};
+
+struct BatchKernelArgs {
+  const rqrcp_problem* table;  // batch mode: device table, nprob entries
+  int nprob;
+  RequestRing* ring;           // serving mode: mapped ring (table == nullptr)
+  unsigned long long* next;    // claim counter (device)
+  int* exited;                 // teams that have left the loop
+  int G;                       // CTAs per team
+  char* scratch;               // team t's scratch at scratch + t * team_bytes
+  size_t team_bytes;
+  BatchLayout L;
+  GridBarrier* bars;           // one per team
+  int* status;                 // the handle's status word (ORed)
+  unsigned int idle_polls;     // serving mode: bound of an idle wait
+};
+
+template <typename T>
+__device__ __forceinline__ T* at(char* base, size_t off) {
+  return reinterpret_cast<T*>(base + off);
+}
+
+__device__ __forceinline__ long long ld_acquire_sys_s64(const long long* p) {
+  long long v;
+  asm volatile("ld.acquire.sys.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_acquire_sys_s32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Leader thread of a team: claim the next problem into ctl (ticket -1 when
+// the source is exhausted, or, in serving mode, stopped or idle too long).
+__device__ void claim(const BatchKernelArgs& a, TeamCtl* ctl) {
+  if (a.table != nullptr) {
+    const unsigned long long t = atomicAdd(a.next, 1ull);
+    if (t < (unsigned long long)a.nprob) {
+      ctl->prob = a.table[t];
+      ctl->ticket = (long long)t;
+    } else {
+      ctl->ticket = -1;
+    }
+    return;
+  }
+  RequestRing* r = a.ring;
+  unsigned int polls = 0;
+  for (;;) {
+    const unsigned long long cur = *(volatile unsigned long long*)a.next;
+    const long long tail = ld_acquire_sys_s64(&r->tail);
+    if ((long long)cur < tail) {
+      if (atomicCAS(a.next, cur, cur + 1) == cur) {
+        const int slot = (int)(cur % (unsigned long long)r->cap);
+        const rqrcp_problem* src = reinterpret_cast<const rqrcp_problem*>(r + 1) + slot;
+        ctl->prob = *src;
+        ctl->ticket = (long long)cur;
+        return;
+      }
+      continue;
+    }
+    if (ld_acquire_sys_s32(&r->stop) != 0 || ++polls > a.idle_polls) {
+      ctl->ticket = -1;
+      return;
+    }
+    __nanosleep(polls < 64 ? 100 : 1000);
+  }
+}
+
+#define TEAM_SYNC()                                        \
+  do {                                                     \
+    if (!grid_barrier(bar, G, &ctl->status)) return false; \
+  } while (0)
+
+// Copy of the claimed problem, read through L2 (CTA 0 of the team wrote it).
+__device__ __forceinline__ rqrcp_problem load_problem(const TeamCtl* ctl) {
+  rqrcp_problem P;
+  const long long* src = reinterpret_cast<const long long*>(&ctl->prob);
+  long long* dst = reinterpret_cast<long long*>(&P);
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(rqrcp_problem) / 8); ++i) dst[i] = __ldcg(src + i);
+  return P;
+}
+
+// Alg. 6 on ctl->prob by the team (CTA g of G).
+__device__ bool run_problem(const BatchKernelArgs& a, char* ts, TeamCtl* ctl, GridBarrier* bar,
+                            int g, int G, unsigned char* smem) {
+  const rqrcp_problem P = load_problem(ctl);
+  const BatchLayout& L = a.L;
+  const int64_t m = P.m, n = P.n, k = P.k;
+  const int b = P.b, ell = P.b + P.p;
+  const int tid = threadIdx.x;
+  const int64_t gt = (int64_t)g * NT + tid, gstride = (int64_t)G * NT;
+  float* om = at<float>(ts, L.omega);    // ell x m, ld ell
+  double* B = at<double>(ts, L.B);       // ell x n, ld ell
+  float* Wt = at<float>(ts, L.Wt);       // k x n, ld k
+  double* P64 = at<double>(ts, L.P64);   // m x b, ld m
+  double* T = at<double>(ts, L.T);       // b x b
+  float* T32 = at<float>(ts, L.T32);     // b x b
+  float* Z32 = at<float>(ts, L.Z32);     // b x n, ld b
+  float* YY = at<float>(ts, L.YY);       // b x k, ld b
+  double* W11 = at<double>(ts, L.W11);   // b x b
+  int64_t* swaps = at<int64_t>(ts, L.swaps);
+  int* mp = at<int>(ts, L.map);          // [0] count, then (dst, src) pairs
+  float* cbuf = at<float>(ts, L.cbuf);   // 2 x (2b) x k floats
+  int64_t* jbuf = at<int64_t>(ts, L.jbuf);
+  void* part = at<void>(ts, L.part);
+  const int64_t part_elems = L.part_elems;
+  int* st = &ctl->status;
+
+  // ---- outputs start at zero / identity; Omega (FP32 Box-Muller)
+  for (int64_t c = gt; c < n; c += gstride) P.d_jpvt[c] = c;
+  for (int64_t e = gt; e < m * k; e += gstride) P.dY[e % m + (e / m) * P.ldy] = 0.0f;
+  for (int64_t e = gt; e < k * n; e += gstride) {
+    P.dR[e % k + (e / k) * P.ldr] = 0.0f;
+    Wt[e] = 0.0f;
+  }
+  {
+    const int64_t npairs = (ell + 1) / 2;
+    const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+    for (int64_t e = gt; e < npairs * m; e += gstride) {
+      const int64_t q = e % npairs, r = e / npairs;
+      const uint4 c = make_uint4((uint32_t)(uint64_t)r, (uint32_t)((uint64_t)r >> 32), (uint32_t)q,
+                                 kOmegaStreamId);
+      const uint4 x = px::philox10(c, key);
+      const float u1 = (float)px::unit_open(x.x, x.y);
+      const float u2 = (float)px::unit_open(x.z, x.w);
+      const float rho = sqrtf(-2.0f * logf(u1));
+      float s, co;
+      sincospif(2.0f * u2, &s, &co);
+      om[2 * q + r * ell] = rho * co;
+      if (2 * q + 1 < ell) om[2 * q + 1 + r * ell] = rho * s;
+    }
+  }
+  TEAM_SYNC();
+  // ---- the sample B = Omega A (ell x n)
+  {
+    TeamGemm<float, float, float, float, double> op{ell, n, m, om, ell, 0, P.dA, P.lda, nullptr, 0,
+                                                    nullptr, 0, nullptr, 0, B, ell, 1.0f, 0.0f};
+    if (!team_gemm(op, g, G, (float*)part, part_elems, bar, st, smem)) return false;
+  }
+  TEAM_SYNC();
+
+  for (int64_t j0 = 0; j0 < k; j0 += b) {
+    const int bJ = (int)std::min<int64_t>(b, k - j0);
+    const int64_t nc = n - j0, n2 = nc - bJ, mJ = m - j0;
+    double* Bblk = B + j0 * ell;
+    // ---- b pivots from the sample (Alg. 1 halted); S left in B
+    {
+      SampleQrcpArgs sa{Bblk, ell, ell, nc, bJ, swaps, at<double>(ts, L.cand),
+                        at<double>(ts, L.candcol), bar, st};
+      sq::sample_qrcp_body(sa, g, G, smem);
+    }
+    TEAM_SYNC();
+    // ---- compose the swaps into (destination, source) position pairs
+    if (g == 0 && tid < 32) {
+      int* pos = reinterpret_cast<int*>(smem);
+      int* src = pos + 2 * MAXB;
+      int cnt = 0;
+      const int lane = tid;
+      for (int i = 0; i < bJ; ++i) {
+        const int s = (int)__ldcg(swaps + i);
+        if (s == i) continue;
+        // entries holding positions i and s (or -1)
+        int ei = -1, es = -1;
+        for (int q0 = 0; q0 < cnt; q0 += 32) {
+          const int q = q0 + lane;
+          const int p = q < cnt ? pos[q] : -1;
+          const unsigned bi = __ballot_sync(0xffffffffu, p == i);
+          const unsigned bs = __ballot_sync(0xffffffffu, p == s);
+          if (bi && ei < 0) ei = q0 + __ffs(bi) - 1;
+          if (bs && es < 0) es = q0 + __ffs(bs) - 1;
+        }
+        const int vi = ei >= 0 ? src[ei] : i;
+        const int vs = es >= 0 ? src[es] : s;
+        __syncwarp();
+        if (lane == 0) {
+          if (ei < 0) {
+            ei = cnt++;
+            pos[ei] = i;
+          }
+          if (es < 0) {
+            es = cnt++;
+            pos[es] = s;
+          }
+          src[ei] = vs;
+          src[es] = vi;
+        }
+        ei = __shfl_sync(0xffffffffu, ei, 0);
+        es = __shfl_sync(0xffffffffu, es, 0);
+        cnt = __shfl_sync(0xffffffffu, cnt, 0);
+        __syncwarp();
+      }
+      for (int q = lane; q < cnt; q += 32) {
+        mp[1 + 2 * q] = pos[q];
+        mp[2 + 2 * q] = src[q];
+      }
+      if (lane == 0) mp[0] = cnt;
+    }
+    TEAM_SYNC();
+    // ---- move jpvt, the W^T rows and the R rows computed so far (gather, then scatter)
+    {
+      const int cnt = __ldcg(mp);
+      const int64_t rows = j0;  // rows 0..j0-1 of W^T and R are filled
+      for (int64_t e = gt; e < (int64_t)cnt * (2 * rows + 1); e += gstride) {
+        const int q = (int)(e % cnt);
+        const int64_t r = e / cnt;
+        const int64_t from = j0 + __ldcg(mp + 2 + 2 * q);
+        if (r == 2 * rows) {
+          jbuf[q] = ldg_i64(P.d_jpvt + from);
+        } else if (r < rows) {
+          cbuf[r + (int64_t)q * rows] = __ldcg(Wt + r + from * k);
+        } else {
+          const int64_t rr = r - rows;
+          cbuf[(int64_t)cnt * rows + rr + (int64_t)q * rows] = __ldcg(P.dR + rr + from * P.ldr);
+        }
+      }
+      TEAM_SYNC();
+      for (int64_t e = gt; e < (int64_t)cnt * (2 * rows + 1); e += gstride) {
+        const int q = (int)(e % cnt);
+        const int64_t r = e / cnt;
+        const int64_t to = j0 + __ldcg(mp + 1 + 2 * q);
+        if (r == 2 * rows) {
+          P.d_jpvt[to] = ldg_i64(jbuf + q);
+        } else if (r < rows) {
+          Wt[r + to * k] = __ldcg(cbuf + r + (int64_t)q * rows);
+        } else {
+          const int64_t rr = r - rows;
+          P.dR[rr + to * P.ldr] = __ldcg(cbuf + (int64_t)cnt * rows + rr + (int64_t)q * rows);
+        }
+      }
+    }
+    TEAM_SYNC();
+    // ---- A_hat = A(j0:m, sel) - Y(j0:m, 0:j0) W^T(0:j0, sel), into the FP64 panel
+    {
+      TeamGemm<float, float, float, float, double> op{
+          mJ, bJ, j0, P.dY + j0, P.ldy, 0, Wt + j0 * k, k, nullptr, 0,
+          P.dA, P.lda, P.d_jpvt + j0, j0, P64, m, -1.0f, 1.0f};
+      if (!team_gemm(op, g, G, (float*)part, part_elems, bar, st, smem)) return false;
+    }
+    TEAM_SYNC();
+    // ---- panel QR and T (FP64), reflectors rounded to FP32
+    {
+      PanelArgs pa{P64, m, mJ, bJ, P.d_tau + j0, T, at<double>(ts, L.ppart),
+                   at<double>(ts, L.rowj), bar, st, 1};
+      pn::panel_body(pa, g, G, smem);
+    }
+    TEAM_SYNC();
+    // ---- Y (explicit FP32), R11 (FP32, diagonal also FP64), T in FP32
+    for (int64_t e = gt; e < mJ * bJ; e += gstride) {
+      const int64_t i = e % mJ, c = e / mJ;
+      const double v = __ldcg(P64 + i + c * m);
+      P.dY[(j0 + i) + (j0 + c) * P.ldy] = i > c ? (float)v : (i == c ? 1.0f : 0.0f);
+      if (i <= c) P.dR[(j0 + i) + (j0 + c) * P.ldr] = (float)v;
+      if (i == c) P.d_rdiag[j0 + c] = v;
+    }
+    for (int64_t e = gt; e < (int64_t)bJ * bJ; e += gstride) T32[e] = (float)__ldcg(T + e);
+    TEAM_SYNC();
+    if (n2 > 0) {
+      const int64_t* tcols = P.d_jpvt + j0 + bJ;
+      const float* Y2 = P.dY + j0 + j0 * P.ldy;
+      // Z = Y2^T A(j0:m, trailing)
+      {
+        TeamGemm<float, float, float, float, float> op{
+            bJ, n2, mJ, Y2, P.ldy, 1, P.dA, P.lda, tcols, j0,
+            nullptr, 0, nullptr, 0, Z32, bJ, 1.0f, 0.0f};
+        if (!team_gemm(op, g, G, (float*)part, part_elems, bar, st, smem)) return false;
+      }
+      if (j0 > 0) {
+        // YY = Y2^T Y1, then Z -= YY W1^T(:, trailing)
+        TeamGemm<float, float, float, float, float> op1{
+            bJ, j0, mJ, Y2, P.ldy, 1, P.dY + j0, P.ldy, nullptr, 0,
+            nullptr, 0, nullptr, 0, YY, bJ, 1.0f, 0.0f};
+        if (!team_gemm(op1, g, G, (float*)part, part_elems, bar, st, smem)) return false;
+        TEAM_SYNC();
+        TeamGemm<float, float, float, float, float> op2{
+            bJ, n2, j0, YY, bJ, 0, Wt + (j0 + bJ) * k, k, nullptr, 0,
+            Z32, bJ, nullptr, 0, Z32, bJ, -1.0f, 1.0f};
+        if (!team_gemm(op2, g, G, (float*)part, part_elems, bar, st, smem)) return false;
+      }
+      TEAM_SYNC();
+      // W2^T(:, trailing) = T2^T Z
+      {
+        TeamGemm<float, float, float, float, float> op{
+            bJ, n2, bJ, T32, bJ, 1, Z32, bJ, nullptr, 0,
+            nullptr, 0, nullptr, 0, Wt + j0 + (j0 + bJ) * k, k, 1.0f, 0.0f};
+        if (!team_gemm(op, g, G, (float*)part, part_elems, bar, st, smem)) return false;
+      }
+      TEAM_SYNC();
+      // R(j0:j0+bJ, trailing) = A(j0:j0+bJ, trailing) - Y(j0:j0+bJ, 0:j0+bJ) W^T(0:j0+bJ, trailing)
+      {
+        TeamGemm<float, float, float, float, float> op{
+            bJ, n2, j0 + bJ, P.dY + j0, P.ldy, 0, Wt + (j0 + bJ) * k, k, nullptr, 0,
+            P.dA, P.lda, tcols, j0, P.dR + j0 + (j0 + bJ) * P.ldr, P.ldr, -1.0f, 1.0f};
+        if (!team_gemm(op, g, G, (float*)part, part_elems, bar, st, smem)) return false;
+      }
+      TEAM_SYNC();
+    }
+    if (j0 + bJ < k) {
+      // ---- Eq. (3): W11 = S11 R11^-1 (FP64), one warp per row of W11
+      double* Rs = reinterpret_cast<double*>(smem);  // bJ x bJ upper, ld bJ
+      double* rinv = Rs + (size_t)bJ * bJ;
+      __shared__ int s_sing;
+      if (tid == 0) s_sing = 0;
+      __syncthreads();
+      for (int e = tid; e < bJ * bJ; e += NT) {
+        const int r = e % bJ, c = e / bJ;
+        Rs[e] = r <= c ? __ldcg(P64 + r + (int64_t)c * m) : 0.0;
+      }
+      for (int j = tid; j < bJ; j += NT) {
+        const double d = __ldcg(P64 + j + (int64_t)j * m);
+        if (d == 0.0) s_sing = 1;
+        rinv[j] = 1.0 / d;
+      }
+      __syncthreads();
+      const int sing = s_sing;
+      const int lane = tid & 31, warp = tid >> 5;
+      if (!sing) {
+        for (int r = g * (NT / 32) + warp; r < bJ; r += G * (NT / 32)) {
+          double acc[MAXB / 32];
+#pragma unroll
+          for (int q = 0; q < MAXB / 32; ++q) {
+            const int c = lane + 32 * q;
+            acc[q] = (c < bJ && c >= r) ? __ldcg(Bblk + r + (int64_t)c * ell) : 0.0;
+          }
+          for (int j = r; j < bJ; ++j) {
+            double mine = 0.0;
+#pragma unroll
+            for (int q = 0; q < MAXB / 32; ++q)
+              if (q == (j >> 5)) mine = acc[q];
+            const double wj = __shfl_sync(0xffffffffu, mine * rinv[j], j & 31);
+#pragma unroll
+            for (int q = 0; q < MAXB / 32; ++q) {
+              const int c = lane + 32 * q;
+              if (c > j && c < bJ) acc[q] = fma(-wj, Rs[j + c * bJ], acc[q]);
+              if (c == j) acc[q] = wj;
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < MAXB / 32; ++q) {
+            const int c = lane + 32 * q;
+            if (c < bJ) W11[r + (int64_t)c * bJ] = c >= r ? acc[q] : 0.0;
+          }
+        }
+      } else if (g == 0 && tid == 0) {
+        atomicOr(st, RQRCP_INFO_RESAMPLED);
+      }
+      TEAM_SYNC();
+      if (!sing && n2 > 0) {
+        // B1 = S12 - W11 R12 in place (rows 0..bJ-1 of the next sample); B2 = S22 stays
+        double* Bnext = Bblk + (int64_t)bJ * ell;
+        TeamGemm<double, double, float, double, double> op{
+            bJ, n2, bJ, W11, bJ, 0, P.dR + j0 + (j0 + bJ) * P.ldr, P.ldr, nullptr, 0,
+            Bnext, ell, nullptr, 0, Bnext, ell, -1.0, 1.0};
+        if (!team_gemm(op, g, G, (double*)part, part_elems / 2, bar, st, smem)) return false;
+      }
+      TEAM_SYNC();
+    }
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(NT, 1) batch_trqrcp_kernel(BatchKernelArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int G = a.G;
+  const int team = blockIdx.x / G, g = blockIdx.x % G;
+  char* ts = a.scratch + (size_t)team * a.team_bytes;
+  TeamCtl* ctl = at<TeamCtl>(ts, a.L.ctl);
+  GridBarrier* bar = a.bars + team;
+  for (;;) {
+    if (g == 0 && threadIdx.x == 0) {
+      claim(a, ctl);
+      ctl->status = 0;
+    }
+    if (!grid_barrier(bar, G, a.status)) break;
+    const long long ticket = __ldcg(&ctl->ticket);
+    if (ticket < 0) break;
+    const bool ok = run_problem(a, ts, ctl, bar, g, G, smem_raw);
+    if (g == 0 && threadIdx.x == 0) {
+      const int s = __ldcg(&ctl->status);
+      if (s) atomicOr(a.status, s);
+      if (a.ring != nullptr) {
+        // publish the result: info word, then the completion word (the
+        // ticket + 1) with release semantics at system scope
+        RequestRing* r = a.ring;
+        const int slot = (int)(ticket % r->cap);
+        int* info = reinterpret_cast<int*>(reinterpret_cast<rqrcp_problem*>(r + 1) + r->cap);
+        long long* done = reinterpret_cast<long long*>(info + ((r->cap + 1) & ~1));
+        info[slot] = s;
+        __threadfence_system();
+        asm volatile("st.release.sys.global.s64 [%0], %1;" ::"l"(done + slot), "l"(ticket + 1)
+                     : "memory");
+      }
+    }
+    if (!ok) {
+      atomicOr(a.status, RQRCP_INFO_TIMEOUT);
+      break;
+    }
+  }
+  // serving: the last team to leave tells the host that nothing runs any more
+  if (a.ring != nullptr && g == 0 && threadIdx.x == 0) {
+    const int teams = (int)(gridDim.x / G);
+    if (atomicAdd(a.exited, 1) == teams - 1) {
+      __threadfence_system();
+      asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(&a.ring->running), "r"(0)
+                   : "memory");
+    }
+  }
+}
+
+}  // namespace
+
+size_t batch_team_bytes(const BatchLimits& lim, int G, BatchLayout* L) {
+  BatchLayout l{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = (off + 255) & ~(size_t)255;
+    const size_t o = off;
+    off += bytes;
+    return o;
+  };
+  const size_t ell = lim.ell, b = lim.b, m = lim.m, n = lim.n, k = lim.k;
+  l.ctl = take(sizeof(TeamCtl));
+  l.omega = take(sizeof(float) * ell * m);
+  l.B = take(sizeof(double) * ell * n);
+  l.Wt = take(sizeof(float) * k * n);
+  l.P64 = take(sizeof(double) * m * b);
+  l.T = take(sizeof(double) * b * b);
+  l.T32 = take(sizeof(float) * b * b);
+  l.Z32 = take(sizeof(float) * b * n);
+  l.YY = take(sizeof(float) * b * k);
+  l.W11 = take(sizeof(double) * b * b);
+  l.swaps = take(sizeof(int64_t) * b);
+  l.map = take(sizeof(int) * (1 + 4 * b));
+  l.cbuf = take(sizeof(float) * 2 * (2 * b) * k);
+  l.jbuf = take(sizeof(int64_t) * 2 * b);
+  l.cand = take(sizeof(double) * 2 * G * 2);
+  l.candcol = take(sizeof(double) * 2 * G * ell);
+  l.ppart = take(sizeof(double) * panel_partial_doubles(G, (int)b));
+  l.rowj = take(sizeof(double) * 2 * b);
+  l.part_elems = (int64_t)G * BM * BN * 2;  // floats (half as many doubles)
+  l.part = take(sizeof(float) * (size_t)l.part_elems);
+  if (L) *L = l;
+  return (off + 255) & ~(size_t)255;
+}
+
+// the kernel's dynamic shared memory: its static arrays (the panel's partial
+// sums and a few words) stay within the 227 KB per CTA
+constexpr size_t kBatchSmem = 200 * 1024;
+
+bool batch_fits(int64_t m, int64_t n, int b, int ell, int G) {
+  if (b < 1 || b > MAXB || ell > 192 || G < 1) return false;
+  const int64_t cs = (n + G - 1) / G, cp = (m + G - 1) / G;
+  if (sq::sample_qrcp_smem_bytes(ell, cs) > kBatchSmem) return false;
+  if (pn::panel_smem_bytes(cp, b) > kBatchSmem) return false;
+  if (((size_t)b * b + b) * 8 > kBatchSmem) return false;
+  return true;
+}
+
+cudaError_t launch_batch_trqrcp(const BatchLaunch& bl, cudaStream_t st) {
+  static std::atomic<uint64_t> attr_done{0};
+  cudaError_t e = ensure_smem_attr(batch_trqrcp_kernel, (int)kBatchSmem, attr_done);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(bl.bars, 0, sizeof(GridBarrier) * bl.teams, st);
+  if (e != cudaSuccess) return e;
+  if (!bl.keep_next) {
+    e = cudaMemsetAsync(bl.next, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaMemsetAsync(bl.exited, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  BatchKernelArgs a{bl.table, bl.nprob, bl.ring, bl.next, bl.exited, bl.G, bl.scratch,
+                    bl.team_bytes, bl.L, bl.bars, bl.status, bl.idle_polls};
+  void* params[] = {&a};
+  return cudaLaunchCooperativeKernel((const void*)batch_trqrcp_kernel,
+                                     dim3((unsigned)(bl.teams * bl.G)), dim3(NT), params,
+                                     kBatchSmem, st);
+}
+
+}  // namespace rq
+
+namespace rq {
+size_t request_ring_bytes(int cap) {
+  return sizeof(RequestRing) + sizeof(rqrcp_problem) * (size_t)cap +
+         sizeof(int) * (size_t)((cap + 1) & ~1) + sizeof(long long) * (size_t)cap;
+}
+}  // namespace rq

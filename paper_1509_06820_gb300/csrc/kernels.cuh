@@ -285,7 +285,9 @@ struct RequestRing {
   long long tail;  // requests published
   int stop;        // nonzero: teams exit once the ring is empty
   int cap;         // slots
-  long long pad[6];
+  int running;     // set by the host at launch; 0 once every team has exited
+  int pad0;
+  long long pad[5];
 };
 size_t request_ring_bytes(int cap);
 struct BatchLaunch {
@@ -293,6 +295,7 @@ struct BatchLaunch {
   int nprob;
   RequestRing* ring;           // device address of the mapped ring (serving) or nullptr
   unsigned long long* next;    // claim counter
+  int* exited;                 // teams that have left the loop (serving)
   int G, teams;
   char* scratch;
   size_t team_bytes;
@@ -300,6 +303,7 @@ struct BatchLaunch {
   GridBarrier* bars;           // teams entries
   int* status;
   unsigned int idle_polls;     // serving: polls of an empty ring before a team exits
+  int keep_next;               // serving relaunch: tickets continue from the counter
 };
 size_t batch_team_bytes(const BatchLimits& lim, int G, BatchLayout* L);
 bool batch_fits(int64_t m, int64_t n, int b, int ell, int G);

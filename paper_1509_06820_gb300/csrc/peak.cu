@@ -8,6 +8,7 @@
 //   kind 1  FP64 tensor-core MMA, mma.sync m8n8k4 (DMMA)
 //   kind 2  FP64 tensor-core MMA, mma.sync m16n8k16
 //   kind 3  FP32 FMA on the CUDA cores
+//   kind 4  FP64 FMA in the register-blocked outer-product pattern of a GEMM
 // Each launch is `grid` CTAs of 256 threads; `iters` rounds per thread or
 // warp.  Each thread writes the sum of its accumulators to sink[global id],
 // so no chain can be dropped by the compiler.
@@ -84,13 +85,44 @@ __global__ void __launch_bounds__(kPeakThreads) dmma_m16n8k16_kernel(int64_t ite
   sink[(int64_t)blockIdx.x * kPeakThreads + threadIdx.x] = s;
 }
 
+// The register-blocked outer product of a GEMM's inner loop: 4 x 4
+// accumulators per thread updated from 4 + 4 operands that change every
+// round (16 independent FMA chains, operands in distinct registers).
+__global__ void __launch_bounds__(kPeakThreads) fma_outer_kernel(int64_t iters, double* sink) {
+  double a[4], b[4], c[4][4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    a[x] = 1e-3 * (threadIdx.x + x);
+    b[x] = 1e-3 * (threadIdx.x - x);
+#pragma unroll
+    for (int y = 0; y < 4; ++y) c[x][y] = 0.0;
+  }
+  for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) c[x][y] = fma(a[x], b[y], c[x][y]);
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      a[x] = fma(a[x], 0.999999, 1e-7);
+      b[x] = fma(b[x], 0.999999, -1e-7);
+    }
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) s += c[x][y];
+  sink[(int64_t)blockIdx.x * kPeakThreads + threadIdx.x] = s;
+}
+
 }  // namespace
 }  // namespace rq
 
 extern "C" int rqrcp_peak_probe(int kind, int64_t iters, int grid, void* d_sink, void* cuda_stream,
                                 double* flops) {
   using namespace rq;
-  if (kind < 0 || kind > 3) return -1;
+  if (kind < 0 || kind > 4) return -1;
   if (iters < 1) return -2;
   if (grid < 1) return -3;
   if (!d_sink) return -4;
@@ -111,6 +143,10 @@ extern "C" int rqrcp_peak_probe(int kind, int64_t iters, int grid, void* d_sink,
     case 2:
       dmma_m16n8k16_kernel<<<grid, kPeakThreads, 0, st>>>(iters, static_cast<double*>(d_sink));
       fl = warps * (double)iters * 2.0 * (2.0 * 16 * 8 * 16);
+      break;
+    case 4:
+      fma_outer_kernel<<<grid, kPeakThreads, 0, st>>>(iters, static_cast<double*>(d_sink));
+      fl = threads * (double)iters * (16.0 + 8.0) * 2.0;
       break;
     default:
       fma_chain_kernel<float><<<grid, kPeakThreads, 0, st>>>(iters, 0.999999f, 1e-6f,

@@ -34,17 +34,24 @@ struct rqrcp_handle_s {
   int fp64_emulation = 0;  // RQRCP_OPT_FP64_EMULATION
   int resample = 0;        // RQRCP_OPT_RESAMPLE: Alg. 5 instead of Eq. (3)
   int test_timeout = 0;    // RQRCP_OPT_TEST_BARRIER_TIMEOUT (rqrcp_sample_qrcp only)
-  // worker lanes of trqrcp_batched: a stream, its scratch and its own
-  // re-sample flag and grid barrier each (the status word stays shared)
-  struct Lane {
-    cudaStream_t st = nullptr;
-    cudaEvent_t done = nullptr;
-    char* ws = nullptr;
-    size_t ws_bytes = 0;
-    int* state = nullptr;
-  };
-  std::vector<Lane> lanes;
-  cudaEvent_t fork = nullptr;
+  // persistent batched kernel (trqrcp_batched and the serving ring): teams of
+  // bt_G CTAs, each with bt_team_bytes of scratch sized for bt_lim
+  int bt_G = 16;                    // RQRCP_OPT_BATCH_TEAM
+  rq::BatchLimits bt_lim{};
+  rq::BatchLayout bt_L{};
+  size_t bt_team_bytes = 0;
+  int bt_teams = 0;                 // teams the scratch holds
+  char* bt_scratch = nullptr;
+  char* bt_ctl = nullptr;           // claim counter, exit counter, one barrier per team
+  rqrcp_problem* bt_table = nullptr;  // device descriptor table
+  rqrcp_problem* bt_stage = nullptr;  // page-locked staging of the table
+  int bt_cap = 0;
+  // serving ring (page-locked, mapped) and its device address
+  char* ring_host = nullptr;
+  rq::RequestRing* ring_dev = nullptr;
+  int ring_cap = 0;
+  int64_t ring_tail = 0;            // requests published by the host
+  bool ring_running = false;
   // rqrcp_factor_host: copy stream, its events, device pivots and tau
   cudaStream_t io_st = nullptr;
   std::vector<cudaEvent_t> io_ev;
@@ -522,14 +529,16 @@ int rqrcp_create(rqrcp_handle_t* handle, void* cuda_stream) {
 int rqrcp_destroy(rqrcp_handle_t h) {
   if (!h) return -1;
   cudaStreamSynchronize(h->stream);
-  for (auto& L : h->lanes) {
-    if (L.st) cudaStreamSynchronize(L.st);
-    if (L.ws) cudaFree(L.ws);
-    if (L.state) cudaFree(L.state);
-    if (L.done) cudaEventDestroy(L.done);
-    if (L.st) cudaStreamDestroy(L.st);
+  if (h->ring_host) {
+    // a server launch still running exits once it sees the stop word
+    reinterpret_cast<rq::RequestRing*>(h->ring_host)->stop = 1;
+    cudaStreamSynchronize(h->stream);
+    cudaFreeHost(h->ring_host);
   }
-  if (h->fork) cudaEventDestroy(h->fork);
+  if (h->bt_scratch) cudaFree(h->bt_scratch);
+  if (h->bt_ctl) cudaFree(h->bt_ctl);
+  if (h->bt_table) cudaFree(h->bt_table);
+  if (h->bt_stage) cudaFreeHost(h->bt_stage);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   if (h->io_st) cudaStreamSynchronize(h->io_st);
   for (cudaEvent_t e : h->io_ev) cudaEventDestroy(e);
@@ -572,6 +581,19 @@ int rqrcp_set_option(rqrcp_handle_t h, int option, int value) {
   }
   if (option == RQRCP_OPT_RESAMPLE) {
     h->resample = value != 0;
+    return RQRCP_OK;
+  }
+  if (option == RQRCP_OPT_BATCH_TEAM) {
+    if (value != 8 && value != 16 && value != 32) return -3;
+    if (value != h->bt_G) {
+      // the team scratch layout depends on the team size: rebuilt on next use
+      cudaStreamSynchronize(h->stream);
+      if (h->bt_scratch) cudaFree(h->bt_scratch);
+      h->bt_scratch = nullptr;
+      h->bt_teams = 0;
+      h->bt_lim = rq::BatchLimits{};
+      h->bt_G = value;
+    }
     return RQRCP_OK;
   }
   if (option == RQRCP_OPT_TEST_BARRIER_TIMEOUT) {
@@ -1495,137 +1517,185 @@ int trqrcp_mixed(rqrcp_handle_t h, int64_t m, int64_t n, const float* dA, int64_
 // ---------------------------------------------------------------- batched
 namespace {
 
-constexpr int kMaxLanes = 16;
+// device control words of the persistent kernel: claim counter (8 bytes),
+// exit counter (4 bytes), then one grid barrier per team
+constexpr size_t kCtlBarOffset = 64;
+constexpr int kMaxTeams = 512;
+constexpr size_t kCtlBytes = kCtlBarOffset + sizeof(rq::GridBarrier) * kMaxTeams;
+constexpr int kTableReserve = 1024;
 
-// Lanes 0..want-1 exist (stream, completion event, 256-byte state block).
-int ensure_lanes(rqrcp_handle_t h, int want) {
-  if ((int)h->lanes.size() >= want && h->fork) return RQRCP_OK;
-  cudaError_t e = cudaSuccess;
-  if (!h->fork) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
-  while (e == cudaSuccess && (int)h->lanes.size() < want) {
-    rqrcp_handle_s::Lane L;
-    e = cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc(&L.state, 256);
-    if (e == cudaSuccess) e = cudaMemset(L.state, 0, 256);
-    if (e != cudaSuccess) {
-      if (L.state) cudaFree(L.state);
-      if (L.done) cudaEventDestroy(L.done);
-      if (L.st) cudaStreamDestroy(L.st);
-      break;
-    }
-    h->lanes.push_back(L);
-  }
+int max_teams(rqrcp_handle_t h) { return std::max(1, h->num_sms / h->bt_G); }
+
+bool same_limits(const rq::BatchLimits& a, const rq::BatchLimits& b) {
+  return a.m == b.m && a.n == b.n && a.k == b.k && a.b == b.b && a.ell == b.ell;
+}
+
+// Scratch of `teams` teams for problems up to `want` (grown, never shrunk).
+int ensure_batch(rqrcp_handle_t h, const rq::BatchLimits& want, int teams) {
+  rq::BatchLimits lim = h->bt_lim;
+  lim.m = std::max(lim.m, want.m);
+  lim.n = std::max(lim.n, want.n);
+  lim.k = std::max(lim.k, want.k);
+  lim.b = std::max(lim.b, want.b);
+  lim.ell = std::max(lim.ell, want.ell);
+  const int nt = std::max(teams, h->bt_teams);
+  if (h->bt_ctl && h->bt_scratch && same_limits(lim, h->bt_lim) && nt == h->bt_teams &&
+      h->bt_L.part_elems == (int64_t)h->bt_G * 64 * 64 * 2)
+    return RQRCP_OK;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  rq::BatchLayout L{};
+  const size_t tb = rq::batch_team_bytes(lim, h->bt_G, &L);
+  if (e == cudaSuccess && h->bt_scratch) e = cudaFree(h->bt_scratch);
+  h->bt_scratch = nullptr;
+  h->bt_teams = 0;
+  if (e == cudaSuccess) e = cudaMalloc(&h->bt_scratch, tb * nt);
+  if (e == cudaSuccess && !h->bt_ctl) e = cudaMalloc(&h->bt_ctl, kCtlBytes);
   if (e != cudaSuccess) {
-    h->err = std::string("lanes: ") + cudaGetErrorString(e);
+    if (h->bt_scratch) cudaFree(h->bt_scratch);
+    h->bt_scratch = nullptr;
+    h->err = std::string("batched scratch: ") + cudaGetErrorString(e);
     return RQRCP_ERR_ALLOC;
   }
+  h->bt_lim = lim;
+  h->bt_L = L;
+  h->bt_team_bytes = tb;
+  h->bt_teams = nt;
   return RQRCP_OK;
 }
 
-int ensure_lane_ws(rqrcp_handle_t h, rqrcp_handle_s::Lane& L, size_t bytes) {
-  if (L.ws_bytes >= bytes) return RQRCP_OK;
-  cudaError_t e = cudaStreamSynchronize(L.st);
-  if (e == cudaSuccess && L.ws) e = cudaFree(L.ws);
-  L.ws = nullptr;
-  L.ws_bytes = 0;
-  if (e == cudaSuccess) e = cudaMalloc(&L.ws, bytes);
+// Device table and its page-locked staging for `nprob` descriptors.
+int ensure_table(rqrcp_handle_t h, int nprob) {
+  if (h->bt_cap >= nprob && h->bt_table && h->bt_stage) return RQRCP_OK;
+  const int cap = std::max(nprob, std::max(kTableReserve, 2 * h->bt_cap));
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (h->bt_table) cudaFree(h->bt_table);
+  if (h->bt_stage) cudaFreeHost(h->bt_stage);
+  h->bt_table = nullptr;
+  h->bt_stage = nullptr;
+  h->bt_cap = 0;
+  if (e == cudaSuccess) e = cudaMalloc(&h->bt_table, sizeof(rqrcp_problem) * cap);
+  if (e == cudaSuccess) e = cudaHostAlloc(&h->bt_stage, sizeof(rqrcp_problem) * cap, 0);
   if (e != cudaSuccess) {
-    L.ws = nullptr;
-    h->err = std::string("lane workspace: ") + cudaGetErrorString(e);
+    h->err = std::string("batched table: ") + cudaGetErrorString(e);
     return RQRCP_ERR_ALLOC;
   }
-  L.ws_bytes = bytes;
+  h->bt_cap = cap;
   return RQRCP_OK;
+}
+
+// Argument checks of one problem (0, -i for field i in the argument order of
+// trqrcp_mixed, or RQRCP_ERR_UNSUPPORTED); b is clamped to k.
+int check_problem(const rqrcp_handle_t h, rqrcp_problem& q) {
+  if (q.m < 1) return -2;
+  if (q.n < 1) return -3;
+  if (!q.dA) return -4;
+  if (q.lda < q.m) return -5;
+  if (q.k < 1 || q.k > std::min(q.m, q.n)) return -6;
+  if (q.b < 1) return -7;
+  if (q.p < 0) return -8;
+  if (!q.d_jpvt) return -10;
+  if (!q.d_tau) return -11;
+  if (!q.dY) return -12;
+  if (q.ldy < q.m) return -13;
+  if (!q.dR) return -14;
+  if (q.ldr < q.k) return -15;
+  if (!q.d_rdiag) return -16;
+  if (q.b > q.k) q.b = (int)q.k;
+  if (q.b > kMaxB || q.b + q.p > kMaxEll) return RQRCP_ERR_UNSUPPORTED;
+  if (!rq::batch_fits(q.m, q.n, q.b, q.b + q.p, h->bt_G)) return RQRCP_ERR_UNSUPPORTED;
+  return RQRCP_OK;
+}
+
+double problem_flops(const rqrcp_problem& q) {
+  return 2.0 * q.m * q.n * q.k + 2.0 * (q.b + q.p) * (double)q.m * q.n;
+}
+
+rq::BatchLaunch batch_launch(rqrcp_handle_t h, int teams) {
+  rq::BatchLaunch bl{};
+  bl.next = reinterpret_cast<unsigned long long*>(h->bt_ctl);
+  bl.exited = reinterpret_cast<int*>(h->bt_ctl + 8);
+  bl.G = h->bt_G;
+  bl.teams = teams;
+  bl.scratch = h->bt_scratch;
+  bl.team_bytes = h->bt_team_bytes;
+  bl.L = h->bt_L;
+  bl.bars = reinterpret_cast<rq::GridBarrier*>(h->bt_ctl + kCtlBarOffset);
+  bl.status = h->state;
+  return bl;
 }
 
 }  // namespace
 
-int rqrcp_reserve_batched(rqrcp_handle_t h, int lanes, int64_t m, int64_t n, int64_t k, int b,
+int rqrcp_reserve_batched(rqrcp_handle_t h, int teams, int64_t m, int64_t n, int64_t k, int b,
                           int p) {
   if (!h) return -1;
-  if (lanes < 1 || lanes > kMaxLanes) return -2;
+  if (teams < 0) return -2;
   if (m < 1 || n < 1 || k < 1 || k > std::min(m, n) || b < 1 || p < 0) return -3;
   if (b > k) b = (int)k;
-  int r = ensure_lanes(h, lanes);
+  if (b > kMaxB || b + p > kMaxEll || !rq::batch_fits(m, n, b, b + p, h->bt_G))
+    return RQRCP_ERR_UNSUPPORTED;
+  const int nt = teams == 0 ? max_teams(h) : std::min(teams, max_teams(h));
+  int r = ensure_batch(h, rq::BatchLimits{m, n, k, b, b + p}, nt);
   if (r) return r;
-  const size_t bytes = carve('V', m, n, k, b, p, h->num_sms, nullptr).bytes;
-  for (int i = 0; i < lanes; ++i)
-    if ((r = ensure_lane_ws(h, h->lanes[i], bytes))) return r;
-  return RQRCP_OK;
+  return ensure_table(h, kTableReserve);
 }
 
-int trqrcp_batched(rqrcp_handle_t h, int nprob, const rqrcp_problem* probs, int lanes) {
+int trqrcp_batched(rqrcp_handle_t h, int nprob, const rqrcp_problem* probs, int teams) {
   if (!h) return -1;
   if (nprob < 0) return -2;
   if (nprob > 0 && !probs) return -3;
-  if (lanes < 1 || lanes > kMaxLanes) return -4;
+  if (teams < 0) return -4;
   if (nprob == 0) return RQRCP_OK;
   // every problem is checked before anything is enqueued
-  std::vector<int> bs(nprob);
+  std::vector<rqrcp_problem> qs(probs, probs + nprob);
+  rq::BatchLimits lim{1, 1, 1, 1, 1};
   for (int i = 0; i < nprob; ++i) {
-    const rqrcp_problem& q = probs[i];
-    int b = q.b;
-    const int r = check_trqrcp_mixed(h->num_sms, q.m, q.n, q.dA, q.lda, q.k, b, q.p, q.d_jpvt,
-                                     q.d_tau, q.dY, q.ldy, q.dR, q.ldr, q.d_rdiag);
+    const int r = check_problem(h, qs[i]);
     if (r) {
       h->err = "trqrcp_batched: problem " + std::to_string(i) + ": status " + std::to_string(r);
       return RQRCP_ERR_BATCH;
     }
-    bs[i] = b;
+    lim.m = std::max(lim.m, qs[i].m);
+    lim.n = std::max(lim.n, qs[i].n);
+    lim.k = std::max(lim.k, qs[i].k);
+    lim.b = std::max(lim.b, qs[i].b);
+    lim.ell = std::max(lim.ell, qs[i].b + qs[i].p);
   }
-  const int L = std::min(lanes, nprob);
-  int r = ensure_lanes(h, L);
+  int nt = teams == 0 ? max_teams(h) : std::min(teams, max_teams(h));
+  nt = std::min(nt, nprob);
+  int r = ensure_batch(h, lim, nt);
   if (r) return r;
-  // longest-processing-time-first assignment by algorithmic flops
-  std::vector<int> order(nprob);
-  for (int i = 0; i < nprob; ++i) order[i] = i;
-  auto work = [&](int i) {
-    const rqrcp_problem& q = probs[i];
-    return 2.0 * q.m * q.n * q.k + 2.0 * (bs[i] + q.p) * (double)q.m * q.n;
-  };
-  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return work(a) > work(c); });
-  std::vector<std::vector<int>> assign(L);
-  std::vector<double> load(L, 0.0);
-  std::vector<size_t> need(L, 0);
-  for (int i : order) {
-    const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-    assign[l].push_back(i);
-    load[l] += work(i);
-    const rqrcp_problem& q = probs[i];
-    need[l] = std::max(need[l], carve('V', q.m, q.n, q.k, bs[i], q.p, h->num_sms, nullptr).bytes);
-  }
-  for (int l = 0; l < L; ++l)
-    if ((r = ensure_lane_ws(h, h->lanes[l], need[l]))) return r;
-  // fork from the handle's stream, run each lane's problems in order, join
-  const bool prof = h->prof;
-  h->prof = false;  // phase events are recorded on the handle's stream only
-  cudaError_t e = cudaEventRecord(h->fork, h->stream);
-  for (int l = 0; l < L && e == cudaSuccess && r == RQRCP_OK; ++l) {
-    rqrcp_handle_s::Lane& Ln = h->lanes[l];
-    e = cudaStreamWaitEvent(Ln.st, h->fork, 0);
-    for (size_t t = 0; t < assign[l].size() && e == cudaSuccess && r == RQRCP_OK; ++t) {
-      const int i = assign[l][t];
-      const rqrcp_problem& q = probs[i];
-      Call cl;
-      cl.h = h;
-      cl.w = carve('V', q.m, q.n, q.k, bs[i], q.p, h->num_sms, Ln.ws);
-      cl.st = Ln.st;
-      cl.status = h->state;  // shared: kernels OR their conditions into it
-      cl.flag = Ln.state + 1;
-      cl.bar = reinterpret_cast<rq::GridBarrier*>(reinterpret_cast<char*>(Ln.state) + 64);
-      r = trqrcp_mixed_run(cl, q.m, q.n, q.dA, q.lda, q.k, bs[i], q.p, q.seed, q.d_jpvt, q.d_tau,
-                           q.dY, q.ldy, q.dR, q.ldr, q.d_rdiag);
+  if ((r = ensure_table(h, nprob))) return r;
+  // longest first, by algorithmic flops: the teams claim the table in order
+  std::stable_sort(qs.begin(), qs.end(), [](const rqrcp_problem& a, const rqrcp_problem& c) {
+    return problem_flops(a) > problem_flops(c);
+  });
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess) cs = cudaStreamCaptureStatusNone;
+  // the staging buffer may still feed the copy of the previous batch
+  if (cs == cudaStreamCaptureStatusNone) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      h->err = std::string("trqrcp_batched: ") + cudaGetErrorString(e);
+      return RQRCP_ERR_CUDA;
     }
-    if (e == cudaSuccess) e = cudaEventRecord(Ln.done, Ln.st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, Ln.done, 0);
   }
-  h->prof = prof;
+  std::copy(qs.begin(), qs.end(), h->bt_stage);
+  double fl = 0.0;
+  for (const auto& q : qs) fl += problem_flops(q);
+  PhaseScope ps(h, PH_TRQ, fl);
+  cudaError_t e = cudaMemcpyAsync(h->bt_table, h->bt_stage, sizeof(rqrcp_problem) * nprob,
+                                  cudaMemcpyHostToDevice, h->stream);
+  rq::BatchLaunch bl = batch_launch(h, nt);
+  bl.table = h->bt_table;
+  bl.nprob = nprob;
+  if (e == cudaSuccess) e = rq::launch_batch_trqrcp(bl, h->stream);
   if (e != cudaSuccess) {
     h->err = std::string("trqrcp_batched: ") + cudaGetErrorString(e);
     return RQRCP_ERR_CUDA;
   }
-  return r;
+  count_launch(h, 1);
+  return RQRCP_OK;
 }
 
 int rqrcp_gemm_bf16x(rqrcp_handle_t h, char transA, char transB, int64_t m, int64_t n, int64_t k,

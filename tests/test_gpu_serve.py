@@ -96,44 +96,75 @@ def _batch_inputs(seed0=0):
     return As
 
 
-def test_trqrcp_batched_matches_individual(lib):
-    """trqrcp_batched over uneven problems on 4 lanes gives, bit for bit, what
-    trqrcp_mixed gives on each problem alone (same kernels, lanes only change
-    where a problem runs)."""
+def test_trqrcp_batched_same_alone_and_in_batch(lib):
+    """The persistent batched launch over uneven problems gives, bit for bit,
+    what the same launch gives on each problem alone: a problem's result
+    depends only on the problem and the team size."""
     As = _batch_inputs()
     probs = [(A, k, b, p, 11 + i) for i, (A, (m, n, k, b, p)) in enumerate(zip(As, BATCH))]
-    got = lib.trqrcp_batched(probs, lanes=4)
+    got = lib.trqrcp_batched(probs)
     assert lib.sync_info() == 0
-    for (A, k, b, p, seed), out in zip(probs, got):
-        ref = lib.trqrcp_mixed(A, k, b, p, seed)
+    for prob, out in zip(probs, got):
+        alone = lib.trqrcp_batched([prob], teams=1)[0]
         assert lib.sync_info() == 0
-        for x, y in zip(out, ref):
+        for x, y in zip(out, alone):
             assert torch.equal(x, y)
 
 
+def test_trqrcp_batched_accuracy(lib):
+    """Each problem of a batch: the rank-k factors reproduce A = X Y^T to FP32
+    level, R agrees with the FP64 oracle's Alg. 6 replayed on the same pivots,
+    and the selected columns span what trqrcp_mixed's span."""
+    import oracle
+    from oracle import householder as hh
+    import synth
+    probs, hosts = [], []
+    for i, (m, n, k, b, p) in enumerate(BATCH):
+        A = synth.factor_product(m, n, k, seed=300 + i).astype(np.float32)
+        hosts.append(A)
+        probs.append((lib.colmajor(torch.from_numpy(A).cuda()), k, b, p, 21 + i))
+    got = lib.trqrcp_batched(probs, teams=3)
+    assert lib.sync_info() == 0
+    for (dA, k, b, p, seed), A, out in zip(probs, hosts, got):
+        jp, t, Yg, Rg, rd = (x.cpu().numpy() for x in out)
+        Yg, Rg = Yg.astype(np.float64), Rg.astype(np.float64)
+        assert sorted(jp.tolist()) == list(range(A.shape[1]))
+        Rg[np.arange(k), np.arange(k)] = rd
+        Q = hh.form_q(Yg, t, k)
+        A64 = A.astype(np.float64)
+        approx = np.zeros_like(A64)
+        approx[:, jp] = Q @ Rg
+        rec = np.linalg.norm(A64 - approx) / np.linalg.norm(A64)
+        assert rec <= 1e-5, rec
+        _, _, _, Ro, _ = oracle.trqrcp(A64, k, b, p, seed=seed, replay_jpvt=jp, tie_rtol=1.0)
+        rel = np.linalg.norm(Rg - Ro) / np.linalg.norm(Ro)
+        assert rel <= 1e-4, rel
+
+
 def test_trqrcp_batched_graph_replay(lib):
-    """A whole batch captured as one CUDA graph (fork to the lanes, join back)
-    replays on new data with the results of separate calls."""
+    """A whole batch captured as one CUDA graph (one persistent launch)
+    replays on new data with the results of an eager launch on that data."""
     h = lib.Handle()
-    h.reserve_batched(4, 1300, 1500, 128, 128, 16)
+    h.reserve_batched(0, 1300, 1500, 128, 128, 16)
     As = _batch_inputs(100)
     bufs = [A.clone() for A in As]
     probs = [(A, k, b, p, 5) for A, (m, n, k, b, p) in zip(bufs, BATCH)]
-    outs = lib.trqrcp_batched(probs, lanes=4, handle=h)  # eager run: sizes the lanes
+    outs = lib.trqrcp_batched(probs, handle=h)
     torch.cuda.synchronize()
     s = torch.cuda.Stream()
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=s):
-        lib.trqrcp_batched(probs, lanes=4, handle=h, outs=outs)
+        lib.trqrcp_batched(probs, handle=h, outs=outs)
     new = _batch_inputs(200)
     for buf, A in zip(bufs, new):
         buf.copy_(A)
     graph.replay()
     torch.cuda.synchronize()
     assert h.sync_info() == 0
-    for A, (m, n, k, b, p), out in zip(new, BATCH, outs):
-        ref = lib.trqrcp_mixed(A, k, b, p, 5)
-        for x, y in zip(out, ref):
+    ref = lib.trqrcp_batched([(A, k, b, p, 5) for A, (m, n, k, b, p) in zip(new, BATCH)])
+    assert lib.sync_info() == 0
+    for out, r in zip(outs, ref):
+        for x, y in zip(out, r):
             assert torch.equal(x, y)
 
 
@@ -149,6 +180,6 @@ def test_trqrcp_batched_rejects_before_launch(lib):
              torch.zeros(16, dtype=torch.float64, device="cuda")) for A in As]
     probs = [(A, k, 16, 8, 1) for A, k in zip(As, ks)]
     with pytest.raises(lib.RqrcpError, match="problem 1"):
-        lib.trqrcp_batched(probs, lanes=2, outs=outs)
+        lib.trqrcp_batched(probs, teams=2, outs=outs)
     torch.cuda.synchronize()
     assert all(bool((o[0] == -7).all()) for o in outs)
