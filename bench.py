@@ -627,9 +627,19 @@ def batched_specs(tuner, nprob, seed):
     for _ in range(nprob):
         m, n = int(rng.integers(256, 4097)), int(rng.integers(256, 4097))
         k = int(min(rng.integers(16, 129), m, n))
-        b, p = tuner.choose(m, n, k) if tuner is not None else (64, 8)
+        b, p = tuner.choose(m, n, k)
         specs.append((m, n, k, min(b, k), p))
     return specs
+
+
+class FixedBP:
+    """(b, p) for every problem (the kernel case's stand-in for the autotuner)."""
+
+    def __init__(self, b, p):
+        self.b, self.p = b, p
+
+    def choose(self, m, n, k):
+        return self.b, self.p
 
 
 def batched_leg(dev, tuner, nprob=64, reps=5, seed=9):
@@ -667,9 +677,15 @@ def batched_leg(dev, tuner, nprob=64, reps=5, seed=9):
     e1.record()
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / reps
+    # one eager launch with the kernel's phase timers on (team-milliseconds)
+    h.profile(True)
+    rq.trqrcp_batched(probs, handle=h, outs=outs)
+    team_ms = {k: round(v, 2) for k, v in h.batched_profile().items() if v > 0}
+    h.profile(False)
     flops = sum(request_flops(m, n, k, b + p) for (m, n, k, b, p) in specs)
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     return {"problems": nprob, "team_ctas": 16, "teams": nsm // 16, "ms_per_batch": ms,
+            "phase_team_ms": team_ms,
             "problems_per_s": nprob / (ms / 1e3), "gflops": flops / (ms / 1e3) / 1e9,
             "launch": "one persistent cooperative launch per batch, captured in a CUDA graph",
             "device_info": h.sync_info()}
@@ -687,7 +703,8 @@ def run_case(args):
       mixed       rqrcp_factor_mixed of the n x n spiked FP32 matrix (the
                   mixed-precision configuration), block b, oversampling p
       batched     one persistent trqrcp_batched launch over 64 served-size
-                  problems (--reps sets the count), graph-replayed
+                  problems (--reps sets the count, --b/--p the block and
+                  oversampling), graph-replayed, with its phase timers
       fp64peak    the arithmetic-peak probes (FP64 FMA, FP64 DMMA m8n8k4 and
                   m16n8k16, FP32 FMA) with the SM clock sampled meanwhile
     Two untimed runs precede the timed ones."""
@@ -699,7 +716,8 @@ def run_case(args):
     torch.cuda.set_device(dev)
     if args.case == "batched":
         # one persistent batched launch over served-size problems (b = 64, p = 8)
-        res = batched_leg(dev, None, nprob=args.reps if args.reps > 1 else 64)
+        res = batched_leg(dev, FixedBP(args.b, args.p), nprob=args.reps if args.reps > 1 else 64)
+        res.update({"b": args.b, "p": args.p})
         print(json.dumps({"case": "batched", **res}), flush=True)
         return
     if args.case == "fp64peak":

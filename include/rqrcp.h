@@ -461,6 +461,16 @@ int rqrcp_profile(rqrcp_handle_t handle, int enable);
 int rqrcp_profile_read(rqrcp_handle_t handle, int nphase, double* ms, double* flops,
                        int64_t* launches);
 
+/*
+ * Phase times of the persistent batched kernel (instrumentation): while
+ * profiling is enabled (rqrcp_profile), the leader CTA of every team adds the
+ * wall time of each phase of Alg. 6 to a device counter; this call
+ * synchronises the stream and writes, for the first nphase phases (<= 8, the
+ * phase numbers of rqrcp_profile; phase 7 includes waiting for a problem),
+ * the team-milliseconds summed over all teams since profiling was enabled.
+ */
+int rqrcp_batched_profile(rqrcp_handle_t handle, int nphase, double* team_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -81,6 +81,7 @@ SIGNATURES = [
     ("rqrcp_sample_qrcp_noalloc", _I, [_I, _I64, _I, _P, _I64, _P, _P, _P]),
     ("rqrcp_peak_probe", _I, [_I, _I64, _I, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     ("rqrcp_profile", _I, [_P, _I]),
+    ("rqrcp_batched_profile", _I, [_P, _I, _P]),
     ("rqrcp_profile_read", _I, [_P, _I, _P, _P, _P]),
 ]
 
@@ -175,6 +176,13 @@ class Handle:
         _check(load().rqrcp_profile_read(self.h, n, ctypes.cast(ms, _P), ctypes.cast(fl, _P),
                                          ctypes.cast(ln, _P)), self.h)
         return {p: (ms[i], fl[i], ln[i]) for i, p in enumerate(PHASES)}
+
+    def batched_profile(self):
+        """Team-milliseconds per phase of the persistent batched kernel since
+        profiling was enabled (summed over teams)."""
+        ms = (ctypes.c_double * len(PHASES))()
+        _check(load().rqrcp_batched_profile(self.h, len(PHASES), ms), self.h)
+        return {name: ms[i] for i, name in enumerate(PHASES)}
 
     def close(self):
         if getattr(self, "h", None):

@@ -40,7 +40,7 @@ namespace rq {
 namespace {
 
 constexpr int NT = 256;
-constexpr int BM = 64, BN = 64, BK = 16;
+constexpr int BM = 64, BN = 64, BK = 32;
 constexpr int MAXB = 128;
 constexpr uint32_t kOmegaStreamId = 1;
 
@@ -86,9 +86,27 @@ __device__ __forceinline__ void tg_epilogue(const TeamGemm<TC, TA, TB, TI, TO>& 
   op.C[i + j * op.ldc] = (TO)v;
 }
 
+// Four consecutive shared-memory values (16-byte aligned) in one or two
+// vector loads.
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x;
+  v[1] = t.y;
+  v[2] = t.z;
+  v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+  const double2 t0 = *reinterpret_cast<const double2*>(p);
+  const double2 t1 = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = t0.x;
+  v[1] = t0.y;
+  v[2] = t1.x;
+  v[3] = t1.y;
+}
+
 // One 64 x 64 output tile over k in [k0, k1): 256 threads, 4 x 4 outputs
 // each (rows 4 ty.., columns 4 tx.. with ty = tid % 16, tx = tid / 16), the
-// next 16-deep slab of both operands loaded into registers while the current
+// next 32-deep slab of both operands loaded into registers while the current
 // one is multiplied from shared memory.
 template <typename TC, typename TA, typename TB, typename TI, typename TO>
 __device__ __forceinline__ void tg_tile(const TeamGemm<TC, TA, TB, TI, TO>& op, int64_t i0,
@@ -101,26 +119,27 @@ __device__ __forceinline__ void tg_tile(const TeamGemm<TC, TA, TB, TI, TO>& op, 
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = (TC)0;
-  TC ra[4], rb[4];
+  constexpr int NL = BM * BK / NT;  // elements of each operand per thread and slab
+  TC ra[NL], rb[NL];
   auto load = [&](int64_t kb) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < NL; ++u) {
       const int e = tid + NT * u;
-      // A: 64 rows x 16 k; the fast index follows the stored layout
+      // A: 64 rows x BK k; the fast index follows the stored layout
       int ii, kk;
       if (op.at) {
-        kk = e & 15;
-        ii = e >> 4;
+        kk = e % BK;
+        ii = e / BK;
       } else {
-        ii = e & 63;
-        kk = e >> 6;
+        ii = e % BM;
+        kk = e / BM;
       }
       const int64_t gi = i0 + ii, gk = kb + kk;
       ra[u] = (gi < op.M && gk < k1)
                   ? (TC)__ldcg(op.at ? op.A + gk + gi * op.lda : op.A + gi + gk * op.lda)
                   : (TC)0;
-      // B: 16 k x 64 columns, k fastest
-      const int kb2 = e & 15, jj = e >> 4;
+      // B: BK k x 64 columns, k fastest
+      const int kb2 = e % BK, jj = e / BK;
       const int64_t gj = j0 + jj, gk2 = kb + kb2;
       TC vb = (TC)0;
       if (gj < op.N && gk2 < k1) {
@@ -132,18 +151,18 @@ __device__ __forceinline__ void tg_tile(const TeamGemm<TC, TA, TB, TI, TO>& op, 
   };
   auto store = [&]() {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < NL; ++u) {
       const int e = tid + NT * u;
       int ii, kk;
       if (op.at) {
-        kk = e & 15;
-        ii = e >> 4;
+        kk = e % BK;
+        ii = e / BK;
       } else {
-        ii = e & 63;
-        kk = e >> 6;
+        ii = e % BM;
+        kk = e / BM;
       }
       As[kk * LDS + ii] = ra[u];
-      Bs[(e & 15) * LDS + (e >> 4)] = rb[u];
+      Bs[(e % BK) * LDS + e / BK] = rb[u];
     }
   };
   if (k0 >= k1) return;
@@ -156,11 +175,8 @@ __device__ __forceinline__ void tg_tile(const TeamGemm<TC, TA, TB, TI, TO>& op, 
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       TC a[4], b[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        a[q] = As[kk * LDS + 4 * ty + q];
-        b[q] = Bs[kk * LDS + 4 * tx + q];
-      }
+      ld4(As + kk * LDS + 4 * ty, a);
+      ld4(Bs + kk * LDS + 4 * tx, b);
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -248,6 +264,7 @@ struct BatchKernelArgs {
   GridBarrier* bars;           // one per team
   int* status;                 // the handle's status word (ORed)
   unsigned int idle_polls;     // serving mode: bound of an idle wait
+  long long* trace;            // per team 8 phase times in ns (instrumentation), or null
 };
 
 template <typename T>
@@ -302,6 +319,30 @@ __device__ void claim(const BatchKernelArgs& a, TeamCtl* ctl) {
   }
 }
 
+__device__ __forceinline__ long long global_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Team wall time per phase (instrumentation): the team leader adds the time
+// since the previous mark to acc[phase]; acc is null on every other thread
+// and when tracing is off.  Phases follow the library's profile phases:
+// 0 Omega and sketch, 1 sample QRCP, 2 permutation, 3 panel, T and write-back,
+// 5 sample update, 6 products with A, Y and W^T, 7 other (outputs cleared,
+// waiting for a problem).
+struct Tracer {
+  long long* acc;
+  long long last;
+  __device__ void mark(int phase) {
+    if (acc != nullptr) {
+      const long long now = global_ns();
+      acc[phase] += now - last;
+      last = now;
+    }
+  }
+};
+
 #define TEAM_SYNC()                                        \
   do {                                                     \
     if (!grid_barrier(bar, G, &ctl->status)) return false; \
@@ -319,7 +360,7 @@ __device__ __forceinline__ rqrcp_problem load_problem(const TeamCtl* ctl) {
 
 // Alg. 6 on ctl->prob by the team (CTA g of G).
 __device__ bool run_problem(const BatchKernelArgs& a, char* ts, TeamCtl* ctl, GridBarrier* bar,
-                            int g, int G, unsigned char* smem) {
+                            int g, int G, unsigned char* smem, Tracer& tr) {
   const rqrcp_problem P = load_problem(ctl);
   const BatchLayout& L = a.L;
   const int64_t m = P.m, n = P.n, k = P.k;
@@ -368,6 +409,7 @@ __device__ bool run_problem(const BatchKernelArgs& a, char* ts, TeamCtl* ctl, Gr
     }
   }
   TEAM_SYNC();
+  tr.mark(7);
   // ---- the sample B = Omega A (ell x n)
   {
     TeamGemm<float, float, float, float, double> op{ell, n, m, om, ell, 0, P.dA, P.lda, nullptr, 0,
@@ -375,6 +417,7 @@ __device__ bool run_problem(const BatchKernelArgs& a, char* ts, TeamCtl* ctl, Gr
     if (!team_gemm(op, g, G, (float*)part, part_elems, bar, st, smem)) return false;
   }
   TEAM_SYNC();
+  tr.mark(0);
 
   for (int64_t j0 = 0; j0 < k; j0 += b) {
     const int bJ = (int)std::min<int64_t>(b, k - j0);
@@ -387,6 +430,7 @@ __device__ bool run_problem(const BatchKernelArgs& a, char* ts, TeamCtl* ctl, Gr
       sq::sample_qrcp_body(sa, g, G, smem);
     }
     TEAM_SYNC();
+    tr.mark(1);
     // ---- compose the swaps into (destination, source) position pairs
     if (g == 0 && tid < 32) {
       int* pos = reinterpret_cast<int*>(smem);
@@ -466,6 +510,7 @@ __device__ bool run_problem(const BatchKernelArgs& a, char* ts, TeamCtl* ctl, Gr
       }
     }
     TEAM_SYNC();
+    tr.mark(2);
     // ---- A_hat = A(j0:m, sel) - Y(j0:m, 0:j0) W^T(0:j0, sel), into the FP64 panel
     {
       TeamGemm<float, float, float, float, double> op{
@@ -474,6 +519,7 @@ __device__ bool run_problem(const BatchKernelArgs& a, char* ts, TeamCtl* ctl, Gr
       if (!team_gemm(op, g, G, (float*)part, part_elems, bar, st, smem)) return false;
     }
     TEAM_SYNC();
+    tr.mark(6);
     // ---- panel QR and T (FP64), reflectors rounded to FP32
     {
       PanelArgs pa{P64, m, mJ, bJ, P.d_tau + j0, T, at<double>(ts, L.ppart),
@@ -491,6 +537,7 @@ __device__ bool run_problem(const BatchKernelArgs& a, char* ts, TeamCtl* ctl, Gr
     }
     for (int64_t e = gt; e < (int64_t)bJ * bJ; e += gstride) T32[e] = (float)__ldcg(T + e);
     TEAM_SYNC();
+    tr.mark(3);
     if (n2 > 0) {
       const int64_t* tcols = P.d_jpvt + j0 + bJ;
       const float* Y2 = P.dY + j0 + j0 * P.ldy;
@@ -530,6 +577,7 @@ __device__ bool run_problem(const BatchKernelArgs& a, char* ts, TeamCtl* ctl, Gr
         if (!team_gemm(op, g, G, (float*)part, part_elems, bar, st, smem)) return false;
       }
       TEAM_SYNC();
+      tr.mark(6);
     }
     if (j0 + bJ < k) {
       // ---- Eq. (3): W11 = S11 R11^-1 (FP64), one warp per row of W11
@@ -590,6 +638,7 @@ __device__ bool run_problem(const BatchKernelArgs& a, char* ts, TeamCtl* ctl, Gr
         if (!team_gemm(op, g, G, (double*)part, part_elems / 2, bar, st, smem)) return false;
       }
       TEAM_SYNC();
+      tr.mark(5);
     }
   }
   return true;
@@ -602,15 +651,18 @@ __global__ void __launch_bounds__(NT, 1) batch_trqrcp_kernel(BatchKernelArgs a) 
   char* ts = a.scratch + (size_t)team * a.team_bytes;
   TeamCtl* ctl = at<TeamCtl>(ts, a.L.ctl);
   GridBarrier* bar = a.bars + team;
+  Tracer tr{(a.trace != nullptr && g == 0 && threadIdx.x == 0) ? a.trace + 8 * team : nullptr,
+            global_ns()};
   for (;;) {
     if (g == 0 && threadIdx.x == 0) {
       claim(a, ctl);
       ctl->status = 0;
     }
     if (!grid_barrier(bar, G, a.status)) break;
+    tr.mark(7);
     const long long ticket = __ldcg(&ctl->ticket);
     if (ticket < 0) break;
-    const bool ok = run_problem(a, ts, ctl, bar, g, G, smem_raw);
+    const bool ok = run_problem(a, ts, ctl, bar, g, G, smem_raw, tr);
     if (g == 0 && threadIdx.x == 0) {
       const int s = __ldcg(&ctl->status);
       if (s) atomicOr(a.status, s);
@@ -704,8 +756,9 @@ cudaError_t launch_batch_trqrcp(const BatchLaunch& bl, cudaStream_t st) {
   }
   e = cudaMemsetAsync(bl.exited, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  BatchKernelArgs a{bl.table, bl.nprob, bl.ring, bl.next, bl.exited, bl.G, bl.scratch,
-                    bl.team_bytes, bl.L, bl.bars, bl.status, bl.idle_polls};
+  BatchKernelArgs a{bl.table, bl.nprob, bl.ring, bl.next,   bl.exited,     bl.G,
+                    bl.scratch, bl.team_bytes, bl.L, bl.bars, bl.status, bl.idle_polls,
+                    bl.trace};
   void* params[] = {&a};
   return cudaLaunchCooperativeKernel((const void*)batch_trqrcp_kernel,
                                      dim3((unsigned)(bl.teams * bl.G)), dim3(NT), params,

@@ -304,6 +304,7 @@ struct BatchLaunch {
   int* status;
   unsigned int idle_polls;     // serving: polls of an empty ring before a team exits
   int keep_next;               // serving relaunch: tickets continue from the counter
+  long long* trace;            // 8 phase times (ns) per team, accumulated; null = off
 };
 size_t batch_team_bytes(const BatchLimits& lim, int G, BatchLayout* L);
 bool batch_fits(int64_t m, int64_t n, int b, int ell, int G);

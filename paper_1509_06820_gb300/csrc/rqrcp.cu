@@ -52,6 +52,7 @@ struct rqrcp_handle_s {
   int ring_cap = 0;
   int64_t ring_tail = 0;            // requests published by the host
   bool ring_running = false;
+  bool bt_trace_clear = true;       // the batched phase timers restart at the next launch
   // rqrcp_factor_host: copy stream, its events, device pivots and tau
   cudaStream_t io_st = nullptr;
   std::vector<cudaEvent_t> io_ev;
@@ -1521,7 +1522,9 @@ namespace {
 // exit counter (4 bytes), then one grid barrier per team
 constexpr size_t kCtlBarOffset = 64;
 constexpr int kMaxTeams = 512;
-constexpr size_t kCtlBytes = kCtlBarOffset + sizeof(rq::GridBarrier) * kMaxTeams;
+// per team 8 phase times (ns) of the instrumentation, after the barriers
+constexpr size_t kCtlTraceOffset = kCtlBarOffset + sizeof(rq::GridBarrier) * kMaxTeams;
+constexpr size_t kCtlBytes = kCtlTraceOffset + sizeof(long long) * 8 * kMaxTeams;
 constexpr int kTableReserve = 1024;
 
 int max_teams(rqrcp_handle_t h) { return std::max(1, h->num_sms / h->bt_G); }
@@ -1621,7 +1624,16 @@ rq::BatchLaunch batch_launch(rqrcp_handle_t h, int teams) {
   bl.L = h->bt_L;
   bl.bars = reinterpret_cast<rq::GridBarrier*>(h->bt_ctl + kCtlBarOffset);
   bl.status = h->state;
+  bl.trace = h->prof ? reinterpret_cast<long long*>(h->bt_ctl + kCtlTraceOffset) : nullptr;
   return bl;
+}
+
+// Clears the phase timers of the batched kernel when profiling was (re)enabled.
+cudaError_t batch_trace_prepare(rqrcp_handle_t h) {
+  if (!h->prof || !h->bt_trace_clear || !h->bt_ctl) return cudaSuccess;
+  h->bt_trace_clear = false;
+  return cudaMemsetAsync(h->bt_ctl + kCtlTraceOffset, 0, sizeof(long long) * 8 * kMaxTeams,
+                         h->stream);
 }
 
 }  // namespace
@@ -1684,8 +1696,10 @@ int trqrcp_batched(rqrcp_handle_t h, int nprob, const rqrcp_problem* probs, int 
   double fl = 0.0;
   for (const auto& q : qs) fl += problem_flops(q);
   PhaseScope ps(h, PH_TRQ, fl);
-  cudaError_t e = cudaMemcpyAsync(h->bt_table, h->bt_stage, sizeof(rqrcp_problem) * nprob,
-                                  cudaMemcpyHostToDevice, h->stream);
+  cudaError_t e = batch_trace_prepare(h);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->bt_table, h->bt_stage, sizeof(rqrcp_problem) * nprob,
+                        cudaMemcpyHostToDevice, h->stream);
   rq::BatchLaunch bl = batch_launch(h, nt);
   bl.table = h->bt_table;
   bl.nprob = nprob;
@@ -1767,6 +1781,7 @@ int rqrcp_profile(rqrcp_handle_t h, int enable) {
       h->flops[i] = 0.0;
       h->launches[i] = 0;
     }
+    h->bt_trace_clear = true;
   }
   h->prof = enable != 0;
   return RQRCP_OK;
@@ -1791,6 +1806,26 @@ int rqrcp_profile_read(rqrcp_handle_t h, int nphase, double* ms, double* flops, 
     if (flops) flops[i] = h->flops[i];
     if (launches) launches[i] = h->launches[i];
   }
+  return RQRCP_OK;
+}
+
+int rqrcp_batched_profile(rqrcp_handle_t h, int nphase, double* team_ms) {
+  if (!h) return -1;
+  if (nphase < 0 || nphase > RQRCP_NPHASE) return -2;
+  if (!team_ms && nphase > 0) return -3;
+  for (int i = 0; i < nphase; ++i) team_ms[i] = 0.0;
+  if (!h->bt_ctl || h->bt_teams == 0) return RQRCP_OK;
+  std::vector<long long> t((size_t)8 * h->bt_teams);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(t.data(), h->bt_ctl + kCtlTraceOffset, sizeof(long long) * t.size(),
+                   cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    h->err = std::string("batched_profile: ") + cudaGetErrorString(e);
+    return RQRCP_ERR_CUDA;
+  }
+  for (int tm = 0; tm < h->bt_teams; ++tm)
+    for (int i = 0; i < nphase; ++i) team_ms[i] += 1e-6 * (double)t[(size_t)8 * tm + i];
   return RQRCP_OK;
 }
 
