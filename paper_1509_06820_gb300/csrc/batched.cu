@@ -26,7 +26,8 @@
 //   W2^T = T2^T (Y2^T A - (Y2^T Y1) W1^T), R rows   FP32 products
 //   W11 = S11 R11^-1, B1 = S12 - W11 R12 (Eq. 3)    FP64
 // The FP32 products run on the CUDA cores as a team-cooperative tiled GEMM
-// (64 x 64 output tiles, split over K when there are fewer tiles than CTAs,
+// (4 x 8 outputs per thread, 64 x 128 tiles, or 32 x 256 / 16 x 512 for
+// products of few rows; split over K when there are fewer tiles than CTAs,
 // partial sums added in a fixed order).
 #include <algorithm>
 #include <climits>
@@ -40,7 +41,6 @@ namespace rq {
 namespace {
 
 constexpr int NT = 256;
-constexpr int BM = 64, BN = 64, BK = 32;
 constexpr int MAXB = 128;
 constexpr uint32_t kOmegaStreamId = 1;
 
@@ -104,115 +104,133 @@ __device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
   v[3] = t1.y;
 }
 
-// One 64 x 64 output tile over k in [k0, k1): 256 threads, 4 x 4 outputs
-// each (rows 4 ty.., columns 4 tx.. with ty = tid % 16, tx = tid / 16), the
-// next 32-deep slab of both operands loaded into registers while the current
-// one is multiplied from shared memory.
-template <typename TC, typename TA, typename TB, typename TI, typename TO>
+// Output tile shapes of the team GEMM, chosen by the row count M: every
+// thread computes 4 rows x 8 columns, 256 threads cover TM x TN =
+// (TM / 4 row groups) x (TN / 8 column groups), and TK-deep slabs of both
+// operands are staged in shared memory (rows padded by 4 to keep 16-byte
+// alignment).  Short products (M = the block's b_J rows) get wide tiles, so
+// that a partial last block does not pad its rows up to 64.
+template <int TM_, int TN_, int TK_>
+struct Tile {
+  static constexpr int TM = TM_, TN = TN_, TK = TK_;
+  static constexpr int RG = TM / 4;                  // row groups
+  static constexpr int LDA = TM + 4, LDB = TN + 4;   // shared row lengths
+  static constexpr int NLA = (TM * TK + NT - 1) / NT, NLB = TN * TK / NT;  // loads per thread
+  static_assert(RG * (TN / 8) == NT, "256 threads of 4 x 8 outputs");
+};
+using TileWide = Tile<16, 512, 8>;
+using TileMid = Tile<32, 256, 16>;
+using TileStd = Tile<64, 128, 16>;
+
+// One TM x TN output tile over k in [k0, k1), accumulated in acc (rows
+// 4 ty.., columns 8 tx.. with ty = tid % RG, tx = tid / RG); the next slab of
+// both operands is loaded into registers while the current one is multiplied
+// from shared memory.
+template <class TL, typename TC, typename TA, typename TB, typename TI, typename TO>
 __device__ __forceinline__ void tg_tile(const TeamGemm<TC, TA, TB, TI, TO>& op, int64_t i0,
-                                        int64_t j0, int64_t k0, int64_t k1, TC (&acc)[4][4],
+                                        int64_t j0, int64_t k0, int64_t k1, TC (&acc)[4][8],
                                         TC* As, TC* Bs) {
-  constexpr int LDS = BM + 4;  // shared row length (keeps 16-byte alignment)
   const int tid = threadIdx.x;
-  const int ty = tid & 15, tx = tid >> 4;
+  const int ty = tid % TL::RG, tx = tid / TL::RG;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = (TC)0;
-  constexpr int NL = BM * BK / NT;  // elements of each operand per thread and slab
-  TC ra[NL], rb[NL];
+    for (int b = 0; b < 8; ++b) acc[a][b] = (TC)0;
+  TC ra[TL::NLA], rb[TL::NLB];
   auto load = [&](int64_t kb) {
 #pragma unroll
-    for (int u = 0; u < NL; ++u) {
+    for (int u = 0; u < TL::NLA; ++u) {
       const int e = tid + NT * u;
-      // A: 64 rows x BK k; the fast index follows the stored layout
-      int ii, kk;
-      if (op.at) {
-        kk = e % BK;
-        ii = e / BK;
-      } else {
-        ii = e % BM;
-        kk = e / BM;
-      }
+      // the fast index follows the stored layout of A
+      const int ii = op.at ? e / TL::TK : e % TL::TM;
+      const int kk = op.at ? e % TL::TK : e / TL::TM;
       const int64_t gi = i0 + ii, gk = kb + kk;
-      ra[u] = (gi < op.M && gk < k1)
+      ra[u] = (e < TL::TM * TL::TK && gi < op.M && gk < k1)
                   ? (TC)__ldcg(op.at ? op.A + gk + gi * op.lda : op.A + gi + gk * op.lda)
                   : (TC)0;
-      // B: BK k x 64 columns, k fastest
-      const int kb2 = e % BK, jj = e / BK;
-      const int64_t gj = j0 + jj, gk2 = kb + kb2;
+    }
+#pragma unroll
+    for (int u = 0; u < TL::NLB; ++u) {
+      const int e = tid + NT * u;
+      const int kk = e % TL::TK, jj = e / TL::TK;  // k fastest
+      const int64_t gj = j0 + jj, gk = kb + kk;
       TC vb = (TC)0;
-      if (gj < op.N && gk2 < k1) {
+      if (gj < op.N && gk < k1) {
         const int64_t col = op.bmap ? ldg_i64(op.bmap + gj) : gj;
-        vb = (TC)__ldcg(op.B + op.brow0 + gk2 + col * op.ldb);
+        vb = (TC)__ldcg(op.B + op.brow0 + gk + col * op.ldb);
       }
       rb[u] = vb;
     }
   };
   auto store = [&]() {
 #pragma unroll
-    for (int u = 0; u < NL; ++u) {
+    for (int u = 0; u < TL::NLA; ++u) {
       const int e = tid + NT * u;
-      int ii, kk;
-      if (op.at) {
-        kk = e % BK;
-        ii = e / BK;
-      } else {
-        ii = e % BM;
-        kk = e / BM;
-      }
-      As[kk * LDS + ii] = ra[u];
-      Bs[(e % BK) * LDS + e / BK] = rb[u];
+      const int ii = op.at ? e / TL::TK : e % TL::TM;
+      const int kk = op.at ? e % TL::TK : e / TL::TM;
+      if (e < TL::TM * TL::TK) As[kk * TL::LDA + ii] = ra[u];
+    }
+#pragma unroll
+    for (int u = 0; u < TL::NLB; ++u) {
+      const int e = tid + NT * u;
+      Bs[(e % TL::TK) * TL::LDB + e / TL::TK] = rb[u];
     }
   };
   if (k0 >= k1) return;
   load(k0);
-  for (int64_t kb = k0; kb < k1; kb += BK) {
+  for (int64_t kb = k0; kb < k1; kb += TL::TK) {
     __syncthreads();  // the previous slab is no longer read
     store();
     __syncthreads();
-    if (kb + BK < k1) load(kb + BK);
+    if (kb + TL::TK < k1) load(kb + TL::TK);
 #pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      TC a[4], b[4];
-      ld4(As + kk * LDS + 4 * ty, a);
-      ld4(Bs + kk * LDS + 4 * tx, b);
+    for (int kk = 0; kk < TL::TK; ++kk) {
+      TC a[4], b0[4], b1[4];
+      ld4(As + kk * TL::LDA + 4 * ty, a);
+      ld4(Bs + kk * TL::LDB + 8 * tx, b0);
+      ld4(Bs + kk * TL::LDB + 8 * tx + 4, b1);
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+        for (int y = 0; y < 4; ++y) {
+          acc[x][y] = fma(a[x], b0[y], acc[x][y]);
+          acc[x][y + 4] = fma(a[x], b1[y], acc[x][y + 4]);
+        }
     }
   }
 }
 
-// The whole product over the team (CTA g of G).  Every CTA of the team calls
-// it with the same arguments; returns false if a team barrier gave up.
-template <typename TC, typename TA, typename TB, typename TI, typename TO>
-__device__ bool team_gemm(const TeamGemm<TC, TA, TB, TI, TO>& op, int g, int G, TC* part,
-                          int64_t part_cap, GridBarrier* bar, int* status, unsigned char* smem) {
-  if (op.M <= 0 || op.N <= 0) return true;
+// The whole product over the team (CTA g of G) with tile shape TL.  Tiles
+// (and, when there are fewer tiles than CTAs and K is long, K splits) are
+// dealt round-robin to the team's CTAs; split partial sums go to `part` and
+// are added over the splits in order after a team barrier.
+template <class TL, typename TC, typename TA, typename TB, typename TI, typename TO>
+__device__ bool team_gemm_t(const TeamGemm<TC, TA, TB, TI, TO>& op, int g, int G, TC* part,
+                            int64_t part_cap, GridBarrier* bar, int* status, unsigned char* smem) {
+  constexpr int TE = TL::TM * TL::TN;  // elements of a tile
   TC* As = reinterpret_cast<TC*>(smem);
-  TC* Bs = As + BK * (BM + 4);
-  const int64_t tm = (op.M + BM - 1) / BM, tn = (op.N + BN - 1) / BN, ntile = tm * tn;
+  TC* Bs = As + TL::TK * TL::LDA;
+  const int64_t tm = (op.M + TL::TM - 1) / TL::TM, tn = (op.N + TL::TN - 1) / TL::TN;
+  const int64_t ntile = tm * tn;
   int64_t splits = 1;
   if (ntile < G && op.K > 512) {
     splits = std::min<int64_t>(G / ntile, (op.K + 255) / 256);
-    while (splits > 1 && ntile * splits * BM * BN > part_cap) --splits;
+    while (splits > 1 && ntile * splits * TE > part_cap) --splits;
   }
-  const int64_t kper = ((op.K + splits - 1) / splits + BK - 1) / BK * BK;
+  const int64_t kper = ((op.K + splits - 1) / splits + TL::TK - 1) / TL::TK * TL::TK;
   const int tid = threadIdx.x;
-  const int ty = tid & 15, tx = tid >> 4;
+  const int ty = tid % TL::RG, tx = tid / TL::RG;
   const int64_t nitems = ntile * splits;
   for (int64_t w = g; w < nitems; w += G) {
     const int64_t tile = w % ntile, sp = w / ntile;
-    const int64_t i0 = (tile % tm) * BM, j0 = (tile / tm) * BN;
+    const int64_t i0 = (tile % tm) * TL::TM, j0 = (tile / tm) * TL::TN;
     const int64_t k0 = sp * kper, k1 = std::min<int64_t>(op.K, k0 + kper);
-    TC acc[4][4];
-    tg_tile(op, i0, j0, k0, k1, acc, As, Bs);
+    TC acc[4][8];
+    tg_tile<TL>(op, i0, j0, k0, k1, acc, As, Bs);
     if (splits == 1) {
 #pragma unroll
-      for (int y = 0; y < 4; ++y) {
-        const int64_t j = j0 + 4 * tx + y;
+      for (int y = 0; y < 8; ++y) {
+        const int64_t j = j0 + 8 * tx + y;
         if (j >= op.N) continue;
 #pragma unroll
         for (int x = 0; x < 4; ++x) {
@@ -221,26 +239,37 @@ __device__ bool team_gemm(const TeamGemm<TC, TA, TB, TI, TO>& op, int g, int G, 
         }
       }
     } else {
-      TC* pw = part + w * (BM * BN);
+      TC* pw = part + w * TE;
 #pragma unroll
-      for (int y = 0; y < 4; ++y)
+      for (int y = 0; y < 8; ++y)
 #pragma unroll
-        for (int x = 0; x < 4; ++x) pw[(4 * tx + y) * BM + 4 * ty + x] = acc[x][y];
+        for (int x = 0; x < 4; ++x) pw[(8 * tx + y) * TL::TM + 4 * ty + x] = acc[x][y];
     }
   }
   if (splits > 1) {
     if (!grid_barrier(bar, G, status)) return false;
-    // partial sums of each element added over the splits in order
-    for (int64_t e = (int64_t)g * NT + tid; e < ntile * BM * BN; e += (int64_t)G * NT) {
-      const int64_t tile = e / (BM * BN), loc = e % (BM * BN);
-      const int64_t i = (tile % tm) * BM + loc % BM, j = (tile / tm) * BN + loc / BM;
+    for (int64_t e = (int64_t)g * NT + tid; e < ntile * TE; e += (int64_t)G * NT) {
+      const int64_t tile = e / TE, loc = e % TE;
+      const int64_t i = (tile % tm) * TL::TM + loc % TL::TM;
+      const int64_t j = (tile / tm) * TL::TN + loc / TL::TM;
       if (i >= op.M || j >= op.N) continue;
       TC s = (TC)0;
-      for (int64_t sp = 0; sp < splits; ++sp) s += __ldcg(part + (sp * ntile + tile) * (BM * BN) + loc);
+      for (int64_t sp = 0; sp < splits; ++sp) s += __ldcg(part + (sp * ntile + tile) * TE + loc);
       tg_epilogue(op, i, j, s);
     }
   }
   return true;
+}
+
+// Every CTA of the team calls it with the same arguments; returns false if a
+// team barrier gave up.  The tile shape follows M (the same for every CTA).
+template <typename TC, typename TA, typename TB, typename TI, typename TO>
+__device__ bool team_gemm(const TeamGemm<TC, TA, TB, TI, TO>& op, int g, int G, TC* part,
+                          int64_t part_cap, GridBarrier* bar, int* status, unsigned char* smem) {
+  if (op.M <= 0 || op.N <= 0) return true;
+  if (op.M <= 16) return team_gemm_t<TileWide>(op, g, G, part, part_cap, bar, status, smem);
+  if (op.M <= 32) return team_gemm_t<TileMid>(op, g, G, part, part_cap, bar, status, smem);
+  return team_gemm_t<TileStd>(op, g, G, part, part_cap, bar, status, smem);
 }
 
 // ---------------------------------------------------------------- the kernel
@@ -725,7 +754,7 @@ size_t batch_team_bytes(const BatchLimits& lim, int G, BatchLayout* L) {
   l.candcol = take(sizeof(double) * 2 * G * ell);
   l.ppart = take(sizeof(double) * panel_partial_doubles(G, (int)b));
   l.rowj = take(sizeof(double) * 2 * b);
-  l.part_elems = (int64_t)G * BM * BN * 2;  // floats (half as many doubles)
+  l.part_elems = (int64_t)G * 8192 * 2;  // floats (half as many doubles): G tiles of 8192
   l.part = take(sizeof(float) * (size_t)l.part_elems);
   if (L) *L = l;
   return (off + 255) & ~(size_t)255;
