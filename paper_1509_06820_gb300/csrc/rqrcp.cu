@@ -1542,8 +1542,7 @@ int ensure_batch(rqrcp_handle_t h, const rq::BatchLimits& want, int teams) {
   lim.b = std::max(lim.b, want.b);
   lim.ell = std::max(lim.ell, want.ell);
   const int nt = std::max(teams, h->bt_teams);
-  if (h->bt_ctl && h->bt_scratch && same_limits(lim, h->bt_lim) && nt == h->bt_teams &&
-      h->bt_L.part_elems == (int64_t)h->bt_G * 64 * 64 * 2)
+  if (h->bt_ctl && h->bt_scratch && same_limits(lim, h->bt_lim) && nt == h->bt_teams)
     return RQRCP_OK;
   cudaError_t e = cudaStreamSynchronize(h->stream);
   rq::BatchLayout L{};
