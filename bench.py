@@ -91,6 +91,7 @@ def parse():
                     help="--case gemm_*: transA,transB,M,N,K (e.g. T,N,128,8000,8192)")
     ap.add_argument("--m", type=int, default=16384, help="--case panel: rows")
     ap.add_argument("--reps", type=int, default=1, help="--case: timed repetitions")
+    ap.add_argument("--team", type=int, default=16, help="--case batched: CTAs per team")
     args = ap.parse_args()
     legs = set(x for x in args.legs.split(",") if x)
     if args.no_extras:
@@ -642,7 +643,7 @@ class FixedBP:
         return self.b, self.p
 
 
-def batched_leg(dev, tuner, nprob=64, reps=5, seed=9):
+def batched_leg(dev, tuner, nprob=64, reps=5, seed=9, team=16):
     """One static batch of served-size problems (m, n ~ U{256..4096},
     k ~ U{16..128}, A = X Y^T in FP32, autotuned b/p) through trqrcp_batched:
     one persistent launch (teams of CTAs claim the problems longest-first),
@@ -659,6 +660,7 @@ def batched_leg(dev, tuner, nprob=64, reps=5, seed=9):
         Yf = torch.randn((n, k), generator=g, device=dev)
         probs.append((rq.colmajor(X @ Yf.t()), k, b, p, 1000 + i))
     h = rq.Handle(dev)
+    h.set_batch_team(team)
     h.reserve_batched(0, max(s[0] for s in specs), max(s[1] for s in specs),
                       max(s[2] for s in specs), max(s[3] for s in specs),
                       max(s[4] for s in specs))
@@ -684,7 +686,7 @@ def batched_leg(dev, tuner, nprob=64, reps=5, seed=9):
     h.profile(False)
     flops = sum(request_flops(m, n, k, b + p) for (m, n, k, b, p) in specs)
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    return {"problems": nprob, "team_ctas": 16, "teams": nsm // 16, "ms_per_batch": ms,
+    return {"problems": nprob, "team_ctas": team, "teams": nsm // team, "ms_per_batch": ms,
             "phase_team_ms": team_ms,
             "problems_per_s": nprob / (ms / 1e3), "gflops": flops / (ms / 1e3) / 1e9,
             "launch": "one persistent cooperative launch per batch, captured in a CUDA graph",
@@ -716,7 +718,8 @@ def run_case(args):
     torch.cuda.set_device(dev)
     if args.case == "batched":
         # one persistent batched launch over served-size problems (b = 64, p = 8)
-        res = batched_leg(dev, FixedBP(args.b, args.p), nprob=args.reps if args.reps > 1 else 64)
+        res = batched_leg(dev, FixedBP(args.b, args.p), nprob=args.reps if args.reps > 1 else 64,
+                          team=args.team)
         res.update({"b": args.b, "p": args.p})
         print(json.dumps({"case": "batched", **res}), flush=True)
         return

@@ -212,10 +212,21 @@ __device__ bool team_gemm_t(const TeamGemm<TC, TA, TB, TI, TO>& op, int g, int G
   TC* Bs = As + TL::TK * TL::LDA;
   const int64_t tm = (op.M + TL::TM - 1) / TL::TM, tn = (op.N + TL::TN - 1) / TL::TN;
   const int64_t ntile = tm * tn;
+  // K splits that balance the work items over the team: the makespan in
+  // tiles is ceil(ntile s / G) / s; each split keeps at least 128 of K and
+  // the partial tiles fit in `part`
   int64_t splits = 1;
-  if (ntile < G && op.K > 512) {
-    splits = std::min<int64_t>(G / ntile, (op.K + 255) / 256);
-    while (splits > 1 && ntile * splits * TE > part_cap) --splits;
+  {
+    double best = (double)((ntile + G - 1) / G);
+    const int64_t smax = std::min<int64_t>((int64_t)4 * G, op.K / 128);
+    for (int64_t sp = 2; sp <= smax; ++sp) {
+      if (ntile * sp * TE > part_cap) break;
+      const double cost = (double)((ntile * sp + G - 1) / G) / (double)sp;
+      if (cost < best - 1e-9) {
+        best = cost;
+        splits = sp;
+      }
+    }
   }
   const int64_t kper = ((op.K + splits - 1) / splits + TL::TK - 1) / TL::TK * TL::TK;
   const int tid = threadIdx.x;
@@ -267,9 +278,16 @@ template <typename TC, typename TA, typename TB, typename TI, typename TO>
 __device__ bool team_gemm(const TeamGemm<TC, TA, TB, TI, TO>& op, int g, int G, TC* part,
                           int64_t part_cap, GridBarrier* bar, int* status, unsigned char* smem) {
   if (op.M <= 0 || op.N <= 0) return true;
-  if (op.M <= 16) return team_gemm_t<TileWide>(op, g, G, part, part_cap, bar, status, smem);
-  if (op.M <= 32) return team_gemm_t<TileMid>(op, g, G, part, part_cap, bar, status, smem);
-  return team_gemm_t<TileStd>(op, g, G, part, part_cap, bar, status, smem);
+  // the tile shape with the least padded area (ties: the taller tile)
+  auto padded = [&](int64_t tm_, int64_t tn_) {
+    return ((op.M + tm_ - 1) / tm_) * tm_ * ((op.N + tn_ - 1) / tn_) * tn_;
+  };
+  const int64_t aw = padded(TileWide::TM, TileWide::TN), am = padded(TileMid::TM, TileMid::TN),
+                as = padded(TileStd::TM, TileStd::TN);
+  if (as <= am && as <= aw)
+    return team_gemm_t<TileStd>(op, g, G, part, part_cap, bar, status, smem);
+  if (am <= aw) return team_gemm_t<TileMid>(op, g, G, part, part_cap, bar, status, smem);
+  return team_gemm_t<TileWide>(op, g, G, part, part_cap, bar, status, smem);
 }
 
 // ---------------------------------------------------------------- the kernel
@@ -754,7 +772,7 @@ size_t batch_team_bytes(const BatchLimits& lim, int G, BatchLayout* L) {
   l.candcol = take(sizeof(double) * 2 * G * ell);
   l.ppart = take(sizeof(double) * panel_partial_doubles(G, (int)b));
   l.rowj = take(sizeof(double) * 2 * b);
-  l.part_elems = (int64_t)G * 8192 * 2;  // floats (half as many doubles): G tiles of 8192
+  l.part_elems = (int64_t)4 * G * 8192 * 2;  // floats (half as many doubles): 4G tiles of 8192
   l.part = take(sizeof(float) * (size_t)l.part_elems);
   if (L) *L = l;
   return (off + 255) & ~(size_t)255;
