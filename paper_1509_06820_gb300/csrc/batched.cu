@@ -129,13 +129,23 @@ using TileStd = Tile<64, 128, 16>;
 template <class TL, typename TC, typename TA, typename TB, typename TI, typename TO>
 __device__ __forceinline__ void tg_tile(const TeamGemm<TC, TA, TB, TI, TO>& op, int64_t i0,
                                         int64_t j0, int64_t k0, int64_t k1, TC (&acc)[4][8],
-                                        TC* As, TC* Bs) {
+                                        TC* As, TC* Bs, int64_t* Bcol) {
   const int tid = threadIdx.x;
   const int ty = tid % TL::RG, tx = tid / TL::RG;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 8; ++b) acc[a][b] = (TC)0;
+  // the stored column of each of the tile's TN columns of op(B), read once
+  // (a gather through bmap would otherwise put a dependent load in front of
+  // every operand load)
+  if (k0 < k1) {
+    __syncthreads();  // the previous tile no longer reads Bcol
+    for (int jj = tid; jj < TL::TN; jj += NT) {
+      const int64_t gj = j0 + jj;
+      Bcol[jj] = gj < op.N ? (op.bmap ? ldg_i64(op.bmap + gj) : gj) : 0;
+    }
+  }
   TC ra[TL::NLA], rb[TL::NLB];
   auto load = [&](int64_t kb) {
 #pragma unroll
@@ -155,10 +165,7 @@ __device__ __forceinline__ void tg_tile(const TeamGemm<TC, TA, TB, TI, TO>& op, 
       const int kk = e % TL::TK, jj = e / TL::TK;  // k fastest
       const int64_t gj = j0 + jj, gk = kb + kk;
       TC vb = (TC)0;
-      if (gj < op.N && gk < k1) {
-        const int64_t col = op.bmap ? ldg_i64(op.bmap + gj) : gj;
-        vb = (TC)__ldcg(op.B + op.brow0 + gk + col * op.ldb);
-      }
+      if (gj < op.N && gk < k1) vb = (TC)__ldcg(op.B + op.brow0 + gk + Bcol[jj] * op.ldb);
       rb[u] = vb;
     }
   };
@@ -177,6 +184,7 @@ __device__ __forceinline__ void tg_tile(const TeamGemm<TC, TA, TB, TI, TO>& op, 
     }
   };
   if (k0 >= k1) return;
+  __syncthreads();  // Bcol is complete
   load(k0);
   for (int64_t kb = k0; kb < k1; kb += TL::TK) {
     __syncthreads();  // the previous slab is no longer read
@@ -210,18 +218,23 @@ __device__ bool team_gemm_t(const TeamGemm<TC, TA, TB, TI, TO>& op, int g, int G
   constexpr int TE = TL::TM * TL::TN;  // elements of a tile
   TC* As = reinterpret_cast<TC*>(smem);
   TC* Bs = As + TL::TK * TL::LDA;
+  int64_t* Bcol = reinterpret_cast<int64_t*>(Bs + TL::TK * TL::LDB);
   const int64_t tm = (op.M + TL::TM - 1) / TL::TM, tn = (op.N + TL::TN - 1) / TL::TN;
   const int64_t ntile = tm * tn;
-  // K splits that balance the work items over the team: the makespan in
-  // tiles is ceil(ntile s / G) / s; each split keeps at least 128 of K and
-  // the partial tiles fit in `part`
+  // K splits that balance the work items over the team.  The makespan, in
+  // steps of k, is ceil(ntile s / G) (K / s + c [s > 1]): a split item also
+  // writes its partial tile and the reduction reads it back, which costs
+  // about as much as c = 128 steps of k (measured on GB300).  Each split keeps
+  // at least 128 of K and the partial tiles fit in `part`.
   int64_t splits = 1;
   {
-    double best = (double)((ntile + G - 1) / G);
+    constexpr double kPartialCost = 128.0;
+    double best = (double)((ntile + G - 1) / G) * (double)op.K;
     const int64_t smax = std::min<int64_t>((int64_t)4 * G, op.K / 128);
     for (int64_t sp = 2; sp <= smax; ++sp) {
       if (ntile * sp * TE > part_cap) break;
-      const double cost = (double)((ntile * sp + G - 1) / G) / (double)sp;
+      const double cost =
+          (double)((ntile * sp + G - 1) / G) * ((double)op.K / (double)sp + kPartialCost);
       if (cost < best - 1e-9) {
         best = cost;
         splits = sp;
@@ -237,7 +250,7 @@ __device__ bool team_gemm_t(const TeamGemm<TC, TA, TB, TI, TO>& op, int g, int G
     const int64_t i0 = (tile % tm) * TL::TM, j0 = (tile / tm) * TL::TN;
     const int64_t k0 = sp * kper, k1 = std::min<int64_t>(op.K, k0 + kper);
     TC acc[4][8];
-    tg_tile<TL>(op, i0, j0, k0, k1, acc, As, Bs);
+    tg_tile<TL>(op, i0, j0, k0, k1, acc, As, Bs, Bcol);
     if (splits == 1) {
 #pragma unroll
       for (int y = 0; y < 8; ++y) {
