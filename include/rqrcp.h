@@ -53,6 +53,7 @@ extern "C" {
 #define RQRCP_ERR_ALLOC 1001
 #define RQRCP_ERR_UNSUPPORTED 1002
 #define RQRCP_ERR_BATCH 1003  /* a problem of trqrcp_batched failed its checks (see last_error) */
+#define RQRCP_ERR_BUSY 1004   /* rqrcp_server_submit: the ring slot is still in use */
 
 #define RQRCP_INFO_NONFINITE 1  /* the sample held NaN/Inf: A is not finite */
 #define RQRCP_INFO_RESAMPLED 2  /* exactly singular R11: trailing sample re-drawn */
@@ -283,6 +284,50 @@ int trqrcp_batched(rqrcp_handle_t handle, int nprob, const rqrcp_problem* probs,
  */
 int rqrcp_reserve_batched(rqrcp_handle_t handle, int teams, int64_t m, int64_t n, int64_t k,
                           int b, int p);
+
+/*
+ * Serving loop on the persistent batched kernel (continuous batching; the
+ * paper has no serving layer).  rqrcp_server_start launches the kernel of
+ * trqrcp_batched on the handle's stream with a request ring in page-locked
+ * host memory mapped into the device's address space instead of a fixed
+ * table: its teams claim requests as the host publishes them, so requests
+ * that arrive while others run are admitted as soon as a team is free, and
+ * each request's result is the one trqrcp_batched gives it (the same alone
+ * and in any mix).  No graph capture or launch sits on a request's path.
+ *   capacity : ring slots (requests published but not yet finished)
+ *   teams    : concurrent requests (0 = as many as the handle's SM budget
+ *              holds; fewer leave SMs free for other work, e.g. producing the
+ *              inputs)
+ *   m, n, k, b, p : the largest request the server accepts (scratch sizes)
+ * The handle's stream is occupied until the server stops; the teams leave the
+ * kernel after about 0.2-0.5 s without requests, and rqrcp_server_submit or
+ * rqrcp_server_poll starts it again when needed.  Errors: -i for argument i,
+ * RQRCP_ERR_UNSUPPORTED if a server already runs on the handle.
+ */
+int rqrcp_server_start(rqrcp_handle_t handle, int capacity, int teams, int64_t m, int64_t n,
+                       int64_t k, int b, int p);
+
+/*
+ * Publishes one request (the fields of rqrcp_problem; device buffers that
+ * stay valid and untouched until the request is finished) and returns its
+ * ticket.  RQRCP_ERR_BUSY when the ring slot still holds an unfinished
+ * request (poll, then retry); RQRCP_ERR_UNSUPPORTED for a request larger than
+ * the server's sizes; -2 for an invalid request.
+ */
+int rqrcp_server_submit(rqrcp_handle_t handle, const rqrcp_problem* prob, int64_t* ticket);
+
+/*
+ * 1 when request `ticket` is finished (its outputs are in device memory and
+ * *info holds its RQRCP_INFO_* bits), 0 while it is not; -2 for an unknown or
+ * reused ticket.  Does not wait.
+ */
+int rqrcp_server_poll(rqrcp_handle_t handle, int64_t ticket, int* info);
+
+/*
+ * Asks the server to stop: its teams leave once the ring is empty.
+ * Synchronise the handle's stream to wait for them.
+ */
+int rqrcp_server_stop(rqrcp_handle_t handle);
 
 /*
  * Deterministic QR with column pivoting, A P = Q R (Alg. 1's pivoting: the

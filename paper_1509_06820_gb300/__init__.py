@@ -22,6 +22,7 @@ RQRCP_ERR_CUDA = 1000
 RQRCP_ERR_ALLOC = 1001
 RQRCP_ERR_UNSUPPORTED = 1002
 RQRCP_ERR_BATCH = 1003
+RQRCP_ERR_BUSY = 1004
 OPT_FP64_EMULATION = 1
 OPT_RESAMPLE = 2
 OPT_MAX_SMS = 3
@@ -79,6 +80,10 @@ SIGNATURES = [
                          _P, _I64, _P, _I64, ctypes.c_double, _P, _I64]),
     ("rqrcp_sample_qrcp", _I, [_P, _I, _I64, _I, _P, _I64, _P]),
     ("rqrcp_sample_qrcp_noalloc", _I, [_I, _I64, _I, _P, _I64, _P, _P, _P]),
+    ("rqrcp_server_start", _I, [_P, _I, _I, _I64, _I64, _I64, _I, _I]),
+    ("rqrcp_server_submit", _I, [_P, ctypes.POINTER(Problem), ctypes.POINTER(_I64)]),
+    ("rqrcp_server_poll", _I, [_P, _I64, ctypes.POINTER(_I)]),
+    ("rqrcp_server_stop", _I, [_P]),
     ("rqrcp_peak_probe", _I, [_I, _I64, _I, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     ("rqrcp_profile", _I, [_P, _I]),
     ("rqrcp_batched_profile", _I, [_P, _I, _P]),
@@ -370,6 +375,25 @@ def trqrcp_mixed(A, k, b, p, seed, handle=None, out=None):
     return jpvt, tau, Y, R, rdiag
 
 
+def problem_struct(A, k, b, p, seed, out):
+    """The rqrcp_problem of one TRQRCP request: A (column-major float32 CUDA
+    tensor), its rank, block, oversampling and seed, and its output tensors
+    (jpvt, tau, Y, R, rdiag) laid out as trqrcp_mixed's."""
+    m, n = A.shape
+    jpvt, tau, Y, R, rdiag = out
+    return Problem(m, n, k, b, p, seed, _ptr(A), _ld(A), _ptr(jpvt), _ptr(tau), _ptr(Y), _ld(Y),
+                   _ptr(R), _ld(R), _ptr(rdiag))
+
+
+def trqrcp_outputs(m, n, k, device):
+    """Output tensors (jpvt, tau, Y, R, rdiag) of a rank-k TRQRCP request."""
+    return (torch.empty(n, dtype=torch.int64, device=device),
+            torch.empty(k, dtype=torch.float64, device=device),
+            empty_colmajor(m, k, device, torch.float32),
+            empty_colmajor(k, n, device, torch.float32),
+            torch.empty(k, dtype=torch.float64, device=device))
+
+
 def trqrcp_batched(problems, teams=0, handle=None, outs=None):
     """Alg. 6 in mixed precision on many matrices in one persistent launch.
     `problems` is a list of (A, k, b, p, seed) with A a column-major float32
@@ -385,17 +409,8 @@ def trqrcp_batched(problems, teams=0, handle=None, outs=None):
         if A.device.type != "cuda" or A.dtype != torch.float32 or not _is_colmajor(A):
             raise ValueError("A must be a column-major float32 CUDA tensor")
         m, n = A.shape
-        if outs is not None:
-            out = outs[i]
-        else:
-            out = (torch.empty(n, dtype=torch.int64, device=A.device),
-                   torch.empty(k, dtype=torch.float64, device=A.device),
-                   empty_colmajor(m, k, A.device, torch.float32),
-                   empty_colmajor(k, n, A.device, torch.float32),
-                   torch.empty(k, dtype=torch.float64, device=A.device))
-        jpvt, tau, Y, R, rdiag = out
-        arr[i] = Problem(m, n, k, b, p, seed, _ptr(A), _ld(A), _ptr(jpvt), _ptr(tau), _ptr(Y),
-                         _ld(Y), _ptr(R), _ld(R), _ptr(rdiag))
+        out = outs[i] if outs is not None else trqrcp_outputs(m, n, k, A.device)
+        arr[i] = problem_struct(A, k, b, p, seed, out)
         results.append(out)
     _check(load().trqrcp_batched(h.bind(), len(problems), arr, teams), h.h)
     return results

@@ -113,14 +113,21 @@ __device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
 template <int TM_, int TN_, int TK_>
 struct Tile {
   static constexpr int TM = TM_, TN = TN_, TK = TK_;
-  static constexpr int RG = TM / 4;                  // row groups
+  static constexpr int RG = TM / 4, CG = TN / 8;     // row and column groups
+  static constexpr int ACTIVE = RG * CG;             // threads that compute
   static constexpr int LDA = TM + 4, LDB = TN + 4;   // shared row lengths
-  static constexpr int NLA = (TM * TK + NT - 1) / NT, NLB = TN * TK / NT;  // loads per thread
-  static_assert(RG * (TN / 8) == NT, "256 threads of 4 x 8 outputs");
+  static constexpr int NLA = (TM * TK + NT - 1) / NT, NLB = (TN * TK + NT - 1) / NT;
+  static_assert(ACTIVE <= NT && TM % 4 == 0 && TN % 8 == 0, "4 x 8 outputs per thread");
+  static_assert(LDA % 4 == 0 && LDB % 4 == 0, "16-byte aligned shared rows");
 };
 using TileWide = Tile<16, 512, 8>;
 using TileMid = Tile<32, 256, 16>;
 using TileStd = Tile<64, 128, 16>;
+// one tile over all rows of the sample B = Omega A (l <= 48, 80, 144 rows;
+// a few threads idle)
+using TileL48 = Tile<48, 160, 16>;
+using TileL80 = Tile<80, 96, 16>;
+using TileL144 = Tile<144, 56, 16>;
 
 // One TM x TN output tile over k in [k0, k1), accumulated in acc (rows
 // 4 ty.., columns 8 tx.. with ty = tid % RG, tx = tid / RG); the next slab of
@@ -165,7 +172,8 @@ __device__ __forceinline__ void tg_tile(const TeamGemm<TC, TA, TB, TI, TO>& op, 
       const int kk = e % TL::TK, jj = e / TL::TK;  // k fastest
       const int64_t gj = j0 + jj, gk = kb + kk;
       TC vb = (TC)0;
-      if (gj < op.N && gk < k1) vb = (TC)__ldcg(op.B + op.brow0 + gk + Bcol[jj] * op.ldb);
+      if (e < TL::TN * TL::TK && gj < op.N && gk < k1)
+        vb = (TC)__ldcg(op.B + op.brow0 + gk + Bcol[jj] * op.ldb);
       rb[u] = vb;
     }
   };
@@ -180,7 +188,7 @@ __device__ __forceinline__ void tg_tile(const TeamGemm<TC, TA, TB, TI, TO>& op, 
 #pragma unroll
     for (int u = 0; u < TL::NLB; ++u) {
       const int e = tid + NT * u;
-      Bs[(e % TL::TK) * TL::LDB + e / TL::TK] = rb[u];
+      if (e < TL::TN * TL::TK) Bs[(e % TL::TK) * TL::LDB + e / TL::TK] = rb[u];
     }
   };
   if (k0 >= k1) return;
@@ -191,6 +199,7 @@ __device__ __forceinline__ void tg_tile(const TeamGemm<TC, TA, TB, TI, TO>& op, 
     store();
     __syncthreads();
     if (kb + TL::TK < k1) load(kb + TL::TK);
+    if (TL::ACTIVE < NT && tid >= TL::ACTIVE) continue;
 #pragma unroll
     for (int kk = 0; kk < TL::TK; ++kk) {
       TC a[4], b0[4], b1[4];
@@ -251,6 +260,7 @@ __device__ bool team_gemm_t(const TeamGemm<TC, TA, TB, TI, TO>& op, int g, int G
     const int64_t k0 = sp * kper, k1 = std::min<int64_t>(op.K, k0 + kper);
     TC acc[4][8];
     tg_tile<TL>(op, i0, j0, k0, k1, acc, As, Bs, Bcol);
+    if (TL::ACTIVE < NT && tid >= TL::ACTIVE) continue;
     if (splits == 1) {
 #pragma unroll
       for (int y = 0; y < 8; ++y) {
@@ -283,6 +293,19 @@ __device__ bool team_gemm_t(const TeamGemm<TC, TA, TB, TI, TO>& op, int g, int G
     }
   }
   return true;
+}
+
+// The sample product B = Omega A (M = l rows): one tile spans every row, so
+// the matrix is read once.
+template <typename TC, typename TA, typename TB, typename TI, typename TO>
+__device__ bool team_gemm_rows(const TeamGemm<TC, TA, TB, TI, TO>& op, int g, int G, TC* part,
+                               int64_t part_cap, GridBarrier* bar, int* status,
+                               unsigned char* smem) {
+  if (op.M <= 0 || op.N <= 0) return true;
+  if (op.M <= 48) return team_gemm_t<TileL48>(op, g, G, part, part_cap, bar, status, smem);
+  if (op.M <= 80) return team_gemm_t<TileL80>(op, g, G, part, part_cap, bar, status, smem);
+  if (op.M <= 144) return team_gemm_t<TileL144>(op, g, G, part, part_cap, bar, status, smem);
+  return team_gemm_t<TileStd>(op, g, G, part, part_cap, bar, status, smem);
 }
 
 // Every CTA of the team calls it with the same arguments; returns false if a
@@ -474,7 +497,7 @@ __device__ bool run_problem(const BatchKernelArgs& a, char* ts, TeamCtl* ctl, Gr
   {
     TeamGemm<float, float, float, float, double> op{ell, n, m, om, ell, 0, P.dA, P.lda, nullptr, 0,
                                                     nullptr, 0, nullptr, 0, B, ell, 1.0f, 0.0f};
-    if (!team_gemm(op, g, G, (float*)part, part_elems, bar, st, smem)) return false;
+    if (!team_gemm_rows(op, g, G, (float*)part, part_elems, bar, st, smem)) return false;
   }
   TEAM_SYNC();
   tr.mark(0);

@@ -6,6 +6,7 @@
 // launch sequence depends only on (m, n, k, b, p), so a whole factorization
 // can be captured in a CUDA graph once its scratch is reserved.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -53,6 +54,7 @@ struct rqrcp_handle_s {
   int64_t ring_tail = 0;            // requests published by the host
   bool ring_running = false;
   bool bt_trace_clear = true;       // the batched phase timers restart at the next launch
+  int bt_server_teams = 0;          // teams of the serving launch
   // rqrcp_factor_host: copy stream, its events, device pivots and tau
   cudaStream_t io_st = nullptr;
   std::vector<cudaEvent_t> io_ev;
@@ -631,6 +633,7 @@ const char* rqrcp_status_string(int code) {
     case RQRCP_ERR_ALLOC: return "workspace allocation failed";
     case RQRCP_ERR_UNSUPPORTED: return "size outside the supported limits";
     case RQRCP_ERR_BATCH: return "a problem of the batch failed its checks";
+    case RQRCP_ERR_BUSY: return "the request ring is full: poll and retry";
     case RQRCP_INFO_NONFINITE: return "non-finite input";
     case RQRCP_INFO_RESAMPLED: return "singular R11: sample re-drawn";
     case RQRCP_INFO_TIMEOUT: return "device wait timed out";
@@ -1708,6 +1711,152 @@ int trqrcp_batched(rqrcp_handle_t h, int nprob, const rqrcp_problem* probs, int 
     return RQRCP_ERR_CUDA;
   }
   count_launch(h, 1);
+  return RQRCP_OK;
+}
+
+// ---------------------------------------------------------------- serving ring
+namespace {
+
+constexpr unsigned int kServerIdlePolls = 200000;  // ~0.2-0.5 s of an empty ring
+
+rq::RequestRing* ring_host(rqrcp_handle_t h) {
+  return reinterpret_cast<rq::RequestRing*>(h->ring_host);
+}
+rqrcp_problem* ring_slots(char* base) {
+  return reinterpret_cast<rqrcp_problem*>(base + sizeof(rq::RequestRing));
+}
+volatile int* ring_info(char* base, int cap) {
+  return reinterpret_cast<volatile int*>(ring_slots(base) + cap);
+}
+volatile long long* ring_done(char* base, int cap) {
+  return reinterpret_cast<volatile long long*>(ring_info(base, cap) + ((cap + 1) & ~1));
+}
+
+// (Re)launches the persistent kernel on the ring; tickets continue from the
+// device claim counter when `keep` is set.
+int server_launch(rqrcp_handle_t h, bool keep) {
+  rq::RequestRing* r = ring_host(h);
+  r->running = 1;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  rq::BatchLaunch bl = batch_launch(h, h->bt_server_teams);
+  bl.ring = h->ring_dev;
+  bl.idle_polls = kServerIdlePolls;
+  bl.keep_next = keep ? 1 : 0;
+  bl.trace = nullptr;
+  cudaError_t e = rq::launch_batch_trqrcp(bl, h->stream);
+  if (e != cudaSuccess) {
+    r->running = 0;
+    h->err = std::string("server launch: ") + cudaGetErrorString(e);
+    return RQRCP_ERR_CUDA;
+  }
+  count_launch(h, 1);
+  h->ring_running = true;
+  return RQRCP_OK;
+}
+
+}  // namespace
+
+int rqrcp_server_start(rqrcp_handle_t h, int capacity, int teams, int64_t m, int64_t n,
+                       int64_t k, int b, int p) {
+  if (!h) return -1;
+  if (capacity < 1 || capacity > (1 << 20)) return -2;
+  if (teams < 0) return -3;
+  if (h->ring_running) {
+    h->err = "server_start: a server is already running on this handle";
+    return RQRCP_ERR_UNSUPPORTED;
+  }
+  int r = rqrcp_reserve_batched(h, teams, m, n, k, b, p);
+  if (r) return r;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess && h->ring_cap != capacity) {
+    if (h->ring_host) cudaFreeHost(h->ring_host);
+    h->ring_host = nullptr;
+    h->ring_cap = 0;
+    e = cudaHostAlloc(&h->ring_host, rq::request_ring_bytes(capacity),
+                      cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e == cudaSuccess) h->ring_cap = capacity;
+  }
+  void* dptr = nullptr;
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&dptr, h->ring_host, 0);
+  if (e != cudaSuccess) {
+    h->err = std::string("server_start: ") + cudaGetErrorString(e);
+    return RQRCP_ERR_ALLOC;
+  }
+  std::memset(h->ring_host, 0, rq::request_ring_bytes(capacity));
+  rq::RequestRing* rg = ring_host(h);
+  rg->cap = capacity;
+  h->ring_dev = static_cast<rq::RequestRing*>(dptr);
+  h->ring_tail = 0;
+  h->bt_server_teams = teams == 0 ? h->bt_teams : std::min(teams, h->bt_teams);
+  return server_launch(h, false);
+}
+
+int rqrcp_server_submit(rqrcp_handle_t h, const rqrcp_problem* prob, int64_t* ticket) {
+  if (!h) return -1;
+  if (!prob) return -2;
+  if (!ticket) return -3;
+  if (!h->ring_running || !h->ring_host) {
+    h->err = "server_submit: no server running (rqrcp_server_start)";
+    return RQRCP_ERR_UNSUPPORTED;
+  }
+  rqrcp_problem q = *prob;
+  int r = check_problem(h, q);
+  if (r) return r < 0 ? -2 : r;
+  if (q.m > h->bt_lim.m || q.n > h->bt_lim.n || q.k > h->bt_lim.k || q.b > h->bt_lim.b ||
+      q.b + q.p > h->bt_lim.ell) {
+    h->err = "server_submit: problem larger than the sizes the server was started for";
+    return RQRCP_ERR_UNSUPPORTED;
+  }
+  rq::RequestRing* rg = ring_host(h);
+  const int cap = h->ring_cap;
+  const int64_t t = h->ring_tail;
+  const int slot = (int)(t % cap);
+  // the slot is free once the request that used it last is finished
+  if (t >= cap && ring_done(h->ring_host, cap)[slot] != (long long)(t - cap + 1)) return RQRCP_ERR_BUSY;
+  ring_slots(h->ring_host)[slot] = q;
+  ring_info(h->ring_host, cap)[slot] = 0;
+  std::atomic_thread_fence(std::memory_order_release);
+  reinterpret_cast<volatile long long*>(&rg->tail)[0] = (long long)(t + 1);
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  h->ring_tail = t + 1;
+  *ticket = t;
+  // every team may have left on an idle ring: start the kernel again
+  if (reinterpret_cast<volatile int*>(&rg->running)[0] == 0) {
+    r = server_launch(h, true);
+    if (r) return r;
+  }
+  return RQRCP_OK;
+}
+
+int rqrcp_server_poll(rqrcp_handle_t h, int64_t ticket, int* info) {
+  if (!h) return -1;
+  if (!h->ring_host || ticket < 0 || ticket >= h->ring_tail) return -2;
+  const int cap = h->ring_cap;
+  const int slot = (int)(ticket % cap);
+  const long long d = ring_done(h->ring_host, cap)[slot];
+  std::atomic_thread_fence(std::memory_order_acquire);
+  if (d == (long long)ticket + 1) {
+    if (info) *info = ring_info(h->ring_host, cap)[slot];
+    return 1;
+  }
+  if (d > (long long)ticket + 1) return -2;  // the slot has been reused since
+  rq::RequestRing* rg = ring_host(h);
+  if (h->ring_running && reinterpret_cast<volatile int*>(&rg->running)[0] == 0 &&
+      reinterpret_cast<volatile int*>(&rg->stop)[0] == 0) {
+    // the teams left while this request was being published: relaunch
+    const int r = server_launch(h, true);
+    if (r) return r;
+  }
+  return 0;
+}
+
+int rqrcp_server_stop(rqrcp_handle_t h) {
+  if (!h) return -1;
+  if (!h->ring_host || !h->ring_running) return RQRCP_OK;
+  rq::RequestRing* rg = ring_host(h);
+  reinterpret_cast<volatile int*>(&rg->stop)[0] = 1;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  h->ring_running = false;
   return RQRCP_OK;
 }
 

@@ -29,13 +29,14 @@ Only host-side scheduling lives here: every numerical step runs in the CUDA
 kernels behind the C ABI.
 """
 import collections
+import ctypes
 import math
 import time
 
 import numpy as np
 import torch
 
-from . import _ld, _ptr, empty_colmajor, Handle, trqrcp_mixed, load
+from . import _ld, _ptr, empty_colmajor, Handle, trqrcp_mixed, load, RQRCP_ERR_BUSY
 
 
 def request_flops(m, n, k, ell):
@@ -298,44 +299,214 @@ class Server:
                     k_range=(16, 128)):
         """Serve a Poisson stream at `rate` req/s for warmup + duration seconds;
         statistics cover requests that arrived after the warm-up."""
-        rng = np.random.default_rng(seed)
-        total = warmup + duration
-        t = 0.0
-        arrivals = []
-        rid = 0
-        while True:
-            t += rng.exponential(1.0 / rate)
-            if t > total:
-                break
-            m = int(rng.integers(size_range[0], size_range[1] + 1))
-            n = int(rng.integers(size_range[0], size_range[1] + 1))
-            k = int(rng.integers(k_range[0], k_range[1] + 1))
-            arrivals.append((t, Request(rid, m, n, min(k, m, n))))
-            rid += 1
+        return run_poisson(self, rate, duration, warmup, seed, size_range, k_range)
+
+
+def poisson_arrivals(rate, total, seed, size_range, k_range):
+    """(arrival time, Request) pairs of a Poisson stream over `total` seconds:
+    m, n uniform in size_range, k uniform in k_range (at most min(m, n))."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    arrivals = []
+    rid = 0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > total:
+            break
+        m = int(rng.integers(size_range[0], size_range[1] + 1))
+        n = int(rng.integers(size_range[0], size_range[1] + 1))
+        k = int(rng.integers(k_range[0], k_range[1] + 1))
+        arrivals.append((t, Request(rid, m, n, min(k, m, n))))
+        rid += 1
+    return arrivals
+
+
+def run_poisson(server, rate, duration, warmup=0.0, seed=7, size_range=(256, 4096),
+                k_range=(16, 128)):
+    """Drive `server` (submit / poll / pending / running / done) with a Poisson
+    stream; latency = completion seen by the host - arrival."""
+    arrivals = poisson_arrivals(rate, warmup + duration, seed, size_range, k_range)
+    server.done = []
+    t0 = time.perf_counter()
+    i = 0
+    def busy():
+        return bool(server.pending or server.running or getattr(server, "staged", None))
+
+    while i < len(arrivals) or busy():
+        now = time.perf_counter() - t0
+        while i < len(arrivals) and arrivals[i][0] <= now:
+            req = arrivals[i][1]
+            req.t_arrival = t0 + arrivals[i][0]
+            server.submit(req)
+            i += 1
+        server.poll()
+        if i < len(arrivals) and not busy():
+            wait = arrivals[i][0] - (time.perf_counter() - t0)
+            if wait > 50e-6:
+                time.sleep(min(wait, 200e-6))
+    t_end = time.perf_counter()
+    measured = [r for r in server.done if r.t_arrival - t0 >= warmup]
+    lat = np.array([r.t_done - r.t_arrival for r in measured]) * 1e3
+    span = max(r.t_done for r in measured) - min(r.t_arrival for r in measured)
+    flops = sum(request_flops(r.m, r.n, r.k, r.b + r.p) for r in measured)
+    return {
+        "requests": len(measured), "offered_rate": rate,
+        "throughput_rps": len(measured) / span, "gflops": flops / span / 1e9,
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+        "wall_s": t_end - t0, "slots": getattr(server, "nslots", len(getattr(server, "slots", []))),
+    }
+
+
+class RingServer:
+    """Continuous batching on the persistent kernel (rqrcp_server_*).
+
+    One long-running launch of the batched TRQRCP kernel serves every request:
+    its teams (groups of CTAs) claim requests from a ring in page-locked,
+    mapped host memory as the host publishes them, so no capture, graph
+    replay or per-request launch sits on a request's path.  The host side:
+
+    * admission: FIFO; a request is admitted when its HBM footprint (input and
+      outputs) fits the budget and the ring has a free slot;
+    * input: the request's matrix A = X Y^T is produced on a side stream by
+      SMs the teams leave free (`reserve_sms`); once it is ready the request
+      is published to the ring;
+    * completion: the ring's done word of the request (written by the team
+      with system-scope release) is polled; latency = completion - arrival.
+
+    Outputs are the request's own tensors (freed when it retires unless
+    `keep_results`); the kernel no longer touches them once the done word is
+    set, so they go back to the allocator without waiting on the server's
+    stream.
+    """
+
+    def __init__(self, device="cuda", team=16, teams=None, capacity=512, max_m=4096, max_n=4096,
+                 max_k=128, max_b=64, max_p=16, hbm_budget=16 << 30, tuner=None, reserve_sms=16,
+                 keep_results=False, clock=time.perf_counter):
+        from . import Problem  # noqa: F401  (the ring's descriptor type)
+        self.device = torch.device(device)
+        nsm = torch.cuda.get_device_properties(self.device).multi_processor_count
+        if teams is None:
+            teams = max(1, (nsm - reserve_sms) // team)
+        self.nslots = teams
+        self.team = team
+        self.capacity = capacity
+        self.limits = (max_m, max_n, max_k, max_b, max_p)
+        self.tuner = tuner
+        self.hbm_budget = hbm_budget
+        self.keep_results = keep_results
+        self.clock = clock
+        self.handle = Handle(self.device)
+        self.handle.set_batch_team(team)
+        self.stream = torch.cuda.Stream(self.device)      # the server's launch
+        self.in_stream = torch.cuda.Stream(self.device)   # request inputs
+        self.gen = torch.Generator(device=self.device)
+        self.handle.bind(self.stream)
+        from . import _check
+        _check(load().rqrcp_server_start(self.handle.h, capacity, teams, max_m, max_n, max_k,
+                                         max_b, max_p), self.handle.h)
+        self.pending = collections.deque()   # waiting for admission
+        self.staged = collections.deque()    # input being produced
+        self.running = []                    # published to the ring
         self.done = []
-        t0 = time.perf_counter()
-        i = 0
-        while i < len(arrivals) or self.pending or self.running:
-            now = time.perf_counter() - t0
-            while i < len(arrivals) and arrivals[i][0] <= now:
-                req = arrivals[i][1]
-                req.t_arrival = t0 + arrivals[i][0]
-                self.submit(req)
-                i += 1
+        self.in_flight_bytes = 0
+        self.max_in_flight = 0
+
+    def plan(self, req):
+        b, p = self.tuner.choose(req.m, req.n, req.k) if self.tuner else (min(req.k, 64), 8)
+        req.b, req.p = min(b, req.k), p
+        req.bucket = (req.m, req.n, req.k)
+        return req
+
+    @staticmethod
+    def footprint(req):
+        m, n, k = req.m, req.n, req.k
+        return m * n * 4 + n * 8 + k * 16 + (m * k + k * n) * 4
+
+    def submit(self, req):
+        self.pending.append(self.plan(req))
+
+    def _admit(self, req):
+        from . import trqrcp_outputs
+        with torch.cuda.stream(self.in_stream):
+            A = empty_colmajor(req.m, req.n, self.device, torch.float32)
+            out = trqrcp_outputs(req.m, req.n, req.k, self.device)
+            make_input(req, A, self.in_stream, self.gen)
+            ev = torch.cuda.Event()
+            ev.record(self.in_stream)
+        req.t_admit = self.clock()
+        req.slot = (A, out, ev, None)
+        self.in_flight_bytes += self.footprint(req)
+        self.staged.append(req)
+
+    def _publish(self, req):
+        from . import problem_struct
+        A, out, ev, _ = req.slot
+        prob = problem_struct(A, req.k, req.b, req.p, int(req.seed), out)
+        ticket = ctypes.c_int64(0)
+        rc = load().rqrcp_server_submit(self.handle.h, ctypes.byref(prob), ctypes.byref(ticket))
+        if rc == RQRCP_ERR_BUSY:
+            return False
+        if rc != 0:
+            raise RuntimeError(f"rqrcp_server_submit: {rc}")
+        req.slot = (A, out, ev, ticket.value)
+        return True
+
+    def poll(self):
+        info = ctypes.c_int(0)
+        still = []
+        for req in self.running:
+            rc = load().rqrcp_server_poll(self.handle.h, req.slot[3], ctypes.byref(info))
+            if rc < 0:
+                raise RuntimeError(f"rqrcp_server_poll: {rc}")
+            if rc == 1:
+                req.t_done = self.clock()
+                if info.value:
+                    raise RuntimeError(f"request {req.rid}: device status {info.value}")
+                A, out, _, _ = req.slot
+                jpvt, tau, Y, R, rdiag = out
+                req.result = (jpvt, tau, Y, R, rdiag) if self.keep_results else None
+                req.slot = None
+                self.in_flight_bytes -= self.footprint(req)
+                self.done.append(req)
+            else:
+                still.append(req)
+        self.running = still
+        while self.staged and self.staged[0].slot[2].query():
+            req = self.staged[0]
+            if not self._publish(req):
+                break
+            self.staged.popleft()
+            self.running.append(req)
+        while self.pending:
+            req = self.pending[0]
+            inflight = len(self.staged) + len(self.running)
+            if inflight >= self.capacity:
+                break
+            if self.in_flight_bytes + self.footprint(req) > self.hbm_budget and inflight:
+                break
+            self.pending.popleft()
+            self._admit(req)
+        self.max_in_flight = max(self.max_in_flight, len(self.running))
+
+    @property
+    def busy(self):
+        return bool(self.pending or self.staged or self.running)
+
+    def drain(self):
+        while self.busy:
             self.poll()
-            if i < len(arrivals) and not self.pending:
-                wait = arrivals[i][0] - (time.perf_counter() - t0)
-                if wait > 50e-6:
-                    time.sleep(min(wait, 200e-6))
-        t_end = time.perf_counter()
-        measured = [r for r in self.done if r.t_arrival - t0 >= warmup]
-        lat = np.array([r.t_done - r.t_arrival for r in measured]) * 1e3
-        span = max(r.t_done for r in measured) - min(r.t_arrival for r in measured)
-        flops = sum(request_flops(r.m, r.n, r.k, r.b + r.p) for r in measured)
-        return {
-            "requests": len(measured), "offered_rate": rate,
-            "throughput_rps": len(measured) / span, "gflops": flops / span / 1e9,
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
-            "wall_s": t_end - t0, "slots": len(self.slots),
-        }
+            if self.running:
+                time.sleep(20e-6)
+
+    def run_poisson(self, rate, duration, warmup=0.0, seed=7, size_range=(256, 4096),
+                    k_range=(16, 128)):
+        return run_poisson(self, rate, duration, warmup, seed, size_range, k_range)
+
+    def close(self):
+        """Stop the server's launch and wait for it."""
+        if self.handle is not None:
+            load().rqrcp_server_stop(self.handle.h)
+            self.stream.synchronize()
+            self.handle.close()
+            self.handle = None

@@ -183,3 +183,94 @@ def test_trqrcp_batched_rejects_before_launch(lib):
         lib.trqrcp_batched(probs, teams=2, outs=outs)
     torch.cuda.synchronize()
     assert all(bool((o[0] == -7).all()) for o in outs)
+
+
+# ---------------------------------------------------------------- ring server
+def _ring_run(srv, reqs, together):
+    if together:
+        for r in reqs:
+            srv.submit(r)
+        srv.drain()
+    else:
+        for r in reqs:
+            srv.submit(r)
+            srv.drain()
+    torch.cuda.synchronize()
+    return {r.rid: tuple(x.cpu().numpy() for x in r.result) for r in reqs}
+
+
+def test_ring_server_same_alone_and_in_mix(lib):
+    """Requests served through the mapped request ring of one persistent launch:
+    each result is bit for bit the same alone and in a concurrent mix, and the
+    same as trqrcp_batched gives on that matrix."""
+    from paper_1509_06820_gb300.serve import Request, RingServer, make_input
+    srv = RingServer(teams=4, capacity=16, keep_results=True)
+    try:
+        alone = _ring_run(srv, [Request(i, *s) for i, s in enumerate(SIZES)], together=False)
+        mixed = _ring_run(srv, [Request(i, *s) for i, s in enumerate(SIZES)], together=True)
+        assert srv.max_in_flight > 1
+    finally:
+        srv.close()
+    for i in range(len(SIZES)):
+        for x, y in zip(alone[i], mixed[i]):
+            np.testing.assert_array_equal(x, y)
+    # the batched entry point on the same inputs (same team size, b, p)
+    for i, (m, n, k) in enumerate(SIZES):
+        r = Request(i, m, n, k)
+        A = lib.empty_colmajor(m, n, "cuda", torch.float32)
+        make_input(r, A, torch.cuda.current_stream())
+        out = lib.trqrcp_batched([(A, k, min(k, 64), 8, i)])[0]
+        for x, y in zip(out, alone[i]):
+            np.testing.assert_array_equal(x.cpu().numpy(), y)
+
+
+def test_ring_server_factors_reconstruct(lib):
+    """The served rank-k factors reproduce A = X Y^T (rank k) to FP32 level."""
+    from oracle import householder as hh
+    from paper_1509_06820_gb300.serve import Request, RingServer, make_input
+    srv = RingServer(teams=2, capacity=8, keep_results=True)
+    try:
+        reqs = [Request(200 + i, *s) for i, s in enumerate(SIZES[:4])]
+        res = _ring_run(srv, reqs, together=True)
+    finally:
+        srv.close()
+    for r in reqs:
+        A = lib.empty_colmajor(r.m, r.n, "cuda", torch.float32)
+        make_input(r, A, torch.cuda.current_stream())
+        A64 = A.cpu().numpy().astype(np.float64)
+        jp, tau, Y, R, rd = res[r.rid]
+        k = r.k
+        R = R.astype(np.float64)
+        R[np.arange(k), np.arange(k)] = rd
+        Q = hh.form_q(Y.astype(np.float64), tau, k)
+        approx = np.zeros_like(A64)
+        approx[:, jp] = Q @ R
+        assert np.linalg.norm(A64 - approx) <= 1e-5 * np.linalg.norm(A64)
+
+
+def test_ring_server_restarts_after_idle(lib):
+    """The teams leave the kernel after an idle spell; the next request starts
+    it again and is served."""
+    import time
+    from paper_1509_06820_gb300.serve import Request, RingServer
+    srv = RingServer(teams=2, capacity=4, keep_results=True)
+    try:
+        first = _ring_run(srv, [Request(0, 300, 400, 20)], together=True)
+        time.sleep(1.5)  # longer than the kernel's idle bound
+        again = _ring_run(srv, [Request(0, 300, 400, 20)], together=True)
+    finally:
+        srv.close()
+    for x, y in zip(first[0], again[0]):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_ring_server_poisson(lib):
+    from paper_1509_06820_gb300.serve import RingServer
+    srv = RingServer(capacity=64)
+    try:
+        stats = srv.run_poisson(rate=500, duration=1.0, warmup=0.2, seed=3,
+                                size_range=(256, 1024), k_range=(16, 64))
+    finally:
+        srv.close()
+    assert stats["requests"] > 200
+    assert 0 < stats["p50_ms"] <= stats["p99_ms"]
