@@ -84,7 +84,7 @@ def parse():
     ap.add_argument("--legs", default="qr,e2e,cpu,emulated,rsrqrcp,qrcp,quality,mixed,truncated,serving",
                     help="comma-separated extra legs to run after the FP64 step")
     ap.add_argument("--case", choices=["panel", "gemm_bf16x", "gemm_f64x", "qrcp", "sample", "mixed",
-                                       "fp64peak", "batched"],
+                                       "fp64peak", "batched", "serve"],
                     default=None,
                     help="run one small kernel case (for profiling) instead of the benchmark")
     ap.add_argument("--shape", default=None,
@@ -586,6 +586,39 @@ def truncated_leg(args, dev):
     return out
 
 
+SERVE_BUCKETS = [(1024, 1024, 64), (2048, 2048, 96), (4096, 4096, 128), (2048, 4096, 32),
+                 (512, 512, 32)]
+
+
+def ring_serving(args, dev, team, tuner=None):
+    """The served TRQRCP workload on the persistent kernel's request ring:
+    Poisson arrivals at --serve-rate, then a rate below saturation."""
+    from paper_1509_06820_gb300.serve import RingServer
+    from paper_1509_06820_gb300.autotune import Tuner
+    t0 = time.perf_counter()
+    if tuner is None:
+        cands = [(16, 8), (32, 8), (64, 8)] if team >= 16 else [(16, 8), (32, 8)]
+        tuner = Tuner.tune_batched(SERVE_BUCKETS, device=dev, team=team, candidates=cands)
+    tune_s = time.perf_counter() - t0
+    bmax = max(v["b"] for v in tuner.table.values())
+    pmax = max(v["p"] for v in tuner.table.values())
+    srv = RingServer(dev, team=team, tuner=tuner, max_b=bmax, max_p=pmax, capacity=1024)
+    try:
+        stats = srv.run_poisson(rate=args.serve_rate, duration=args.serve_seconds, warmup=1.0,
+                                seed=7)
+        low = srv.run_poisson(rate=args.serve_rate / 5, duration=min(5.0, args.serve_seconds),
+                              warmup=0.5, seed=8)
+    finally:
+        srv.close()
+    stats = {"mode": "persistent kernel, mapped request ring", "team_ctas": team,
+             "teams": srv.nslots, **stats}
+    stats["below_saturation"] = {k: low[k] for k in ("offered_rate", "requests", "throughput_rps",
+                                                     "p50_ms", "p99_ms", "gflops")}
+    stats["autotune_s"] = tune_s
+    stats["autotune_table"] = tuner.table
+    return stats
+
+
 def serving_leg(args, dev):
     """Served TRQRCP: Poisson arrivals, m, n ~ U{256..4096}, k ~ U{16..128},
     A = X Y^T (FP32), continuous batching over 16 slots (each request's
@@ -716,6 +749,10 @@ def run_case(args):
     import paper_1509_06820_gb300 as rq
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
+    if args.case == "serve":
+        # the ring server alone at --serve-rate for --serve-seconds
+        print(json.dumps({"case": "serve", **ring_serving(args, dev, args.team)}), flush=True)
+        return
     if args.case == "batched":
         # one persistent batched launch over served-size problems (b = 64, p = 8)
         res = batched_leg(dev, FixedBP(args.b, args.p), nprob=args.reps if args.reps > 1 else 64,
