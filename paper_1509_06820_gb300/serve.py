@@ -46,8 +46,8 @@ def request_flops(m, n, k, ell):
 
 
 class Request:
-    __slots__ = ("rid", "m", "n", "k", "seed", "t_arrival", "t_admit", "t_done", "result",
-                 "bucket", "b", "p", "slot")
+    __slots__ = ("rid", "m", "n", "k", "seed", "t_arrival", "t_admit", "t_publish", "t_done",
+                 "result", "bucket", "b", "p", "slot")
 
     def __init__(self, rid, m, n, k, seed=None, t_arrival=0.0):
         self.rid = rid
@@ -55,6 +55,7 @@ class Request:
         self.seed = rid if seed is None else seed
         self.t_arrival = t_arrival
         self.t_admit = None
+        self.t_publish = None
         self.t_done = None
         self.result = None
         self.bucket = None
@@ -349,7 +350,20 @@ def run_poisson(server, rate, duration, warmup=0.0, seed=7, size_range=(256, 409
     lat = np.array([r.t_done - r.t_arrival for r in measured]) * 1e3
     span = max(r.t_done for r in measured) - min(r.t_arrival for r in measured)
     flops = sum(request_flops(r.m, r.n, r.k, r.b + r.p) for r in measured)
+    parts = {}
+    if measured and measured[0].t_publish is not None:
+        # where a request's latency goes: waiting for admission, its input
+        # being produced, and the device serving it after publication
+        def pct(xs):
+            xs = np.array(xs) * 1e3
+            return {"mean": float(xs.mean()), "p50": float(np.percentile(xs, 50)),
+                    "p99": float(np.percentile(xs, 99))}
+        parts = {"latency_parts_ms": {
+            "admission_wait": pct([r.t_admit - r.t_arrival for r in measured]),
+            "input": pct([r.t_publish - r.t_admit for r in measured]),
+            "service": pct([r.t_done - r.t_publish for r in measured])}}
     return {
+        **parts,
         "requests": len(measured), "offered_rate": rate,
         "throughput_rps": len(measured) / span, "gflops": flops / span / 1e9,
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
@@ -450,6 +464,7 @@ class RingServer:
         if rc != 0:
             raise RuntimeError(f"rqrcp_server_submit: {rc}")
         req.slot = (A, out, ev, ticket.value)
+        req.t_publish = self.clock()
         return True
 
     def poll(self):
