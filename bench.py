@@ -604,7 +604,7 @@ def ring_serving(args, dev, team, tuner=None):
     pmax = max(v["p"] for v in tuner.table.values())
     srv = RingServer(dev, team=team, tuner=tuner, max_b=bmax, max_p=pmax, capacity=1024)
     try:
-        stats = srv.run_poisson(rate=args.serve_rate, duration=args.serve_seconds, warmup=1.0,
+        stats = srv.run_poisson(rate=args.serve_rate, duration=args.serve_seconds, warmup=2.0,
                                 seed=7)
         low = srv.run_poisson(rate=args.serve_rate / 5, duration=min(5.0, args.serve_seconds),
                               warmup=0.5, seed=8)
@@ -621,35 +621,25 @@ def ring_serving(args, dev, team, tuner=None):
 
 def serving_leg(args, dev):
     """Served TRQRCP: Poisson arrivals, m, n ~ U{256..4096}, k ~ U{16..128},
-    A = X Y^T (FP32), continuous batching over 16 slots (each request's
-    launches capped at a quarter of the SMs), autotuned b/p."""
+    A = X Y^T (FP32).  Primary: the persistent kernel fed through the mapped
+    request ring (teams of 8 CTAs, SMs left free for the inputs), autotuned
+    b/p.  Beside it: the stream-slot server (16 slots, eager trqrcp_mixed
+    launches per request, each capped at a quarter of the SMs) on the same
+    stream, and one static batch through trqrcp_batched."""
     from paper_1509_06820_gb300.serve import Server
     from paper_1509_06820_gb300.autotune import Tuner
+    stats = ring_serving(args, dev, team=8)
     t0 = time.perf_counter()
-    tuner = Tuner.tune([(1024, 1024, 64), (2048, 2048, 96), (4096, 4096, 128), (2048, 4096, 32)],
-                       device=dev)
+    tuner = Tuner.tune(SERVE_BUCKETS[:4], device=dev)
     tune_s = time.perf_counter() - t0
-    # primary: slots that launch each request's kernels directly (no graph
-    # capture on the host's critical path)
     srv = Server.on_gpu(dev, slots=16, tuner=tuner, use_graphs=False)
-    stats = srv.run_poisson(rate=args.serve_rate, duration=args.serve_seconds, warmup=1.0, seed=7)
-    stats = {"mode": "eager launches per request", **stats}
-    # the same server below saturation, for the service-time latency
-    low = srv.run_poisson(rate=args.serve_rate / 5, duration=min(5.0, args.serve_seconds),
-                          warmup=0.5, seed=8)
-    stats["below_saturation"] = {k: low[k] for k in ("offered_rate", "requests", "throughput_rps",
-                                                     "p50_ms", "p99_ms", "gflops")}
+    sl = srv.run_poisson(rate=args.serve_rate, duration=args.serve_seconds, warmup=1.0, seed=7)
+    stats["stream_slots"] = {"mode": "16 stream slots, eager trqrcp_mixed per request",
+                             "autotune_s": tune_s,
+                             **{k: sl[k] for k in ("offered_rate", "requests", "throughput_rps",
+                                                   "p50_ms", "p99_ms", "gflops")}}
     del srv
-    # the same stream with per-(slot, size bucket) CUDA graphs captured on first use
-    gsrv = Server.on_gpu(dev, slots=16, tuner=tuner)
-    gst = gsrv.run_poisson(rate=args.serve_rate, duration=args.serve_seconds, warmup=1.0, seed=7)
-    stats["graphs"] = {k: gst[k] for k in ("offered_rate", "requests", "throughput_rps", "p50_ms",
-                                           "p99_ms", "gflops")}
-    stats["graphs"]["graphs_captured"] = sum(len(s.graphs) for s in gsrv.slots)
-    del gsrv
-    stats["autotune_s"] = tune_s
-    stats["autotune_table"] = tuner.table
-    stats["batched"] = batched_leg(dev, tuner)
+    stats["batched"] = batched_leg(dev, Tuner(stats["autotune_table"]), team=8)
     return stats
 
 
@@ -970,8 +960,6 @@ def main():
     # FMA chains on the CUDA cores and DMMA (mma.sync) on the tensor cores;
     # the roofline peak is the faster of the two
     probes = probe_peaks(dev)
-    fp64_best = max(probes.values(), key=lambda v: v["tflops"])
-    fp64_peak = fp64_best["tflops"]
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     tr_ms, tr_fl, tr_launch = prof["trailing_update"]
     achieved = tr_fl / (tr_ms / 1e3) / 1e12 if tr_ms > 0 else None
@@ -988,24 +976,25 @@ def main():
         j0 += bJ
     traffic = 0.941 * alg_bytes / max(tr_launch, 1)
     best_kind = max(probes, key=lambda k: probes[k]["tflops"])
-    # unit count x clock: the FP64 FMA lanes per SM that the probe implies,
-    # rounded, times the SMs and the SM clock sampled during the timed steps
+    best = probes[best_kind]["tflops"]
+    # the FP64 unit count of an SM: the best probe (FMA chains, a GEMM's
+    # outer-product pattern, DMMA m8n8k4 and m16n8k16, all within a few % of
+    # one another) divided by SMs x clock x 2 flop, rounded to whole units;
+    # peak = units x 2 flop x SMs x the SM clock sampled during the timed steps
     mhz = clk.get("sm_mhz") or 2070.0
-    lanes = round(probes["fp64_fma"]["tflops"] * 1e12 / (2.0 * sms * mhz * 1e6))
-    derived = 2.0 * lanes * sms * mhz * 1e6 / 1e12
+    units = max(1, round(best * 1e12 / (2.0 * sms * mhz * 1e6)))
+    peak = 2.0 * units * sms * mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "kernel": "trailing update (gemm_kernel FP64 FFMA)",
-                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak if achieved else None, "traffic": traffic,
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "traffic_unit": "bytes per launch",
                 "traffic_source": "algorithmic bytes x 0.941 (ncu DRAM bytes / algorithmic bytes, "
                                   "same kernels, 6144^2 factorization)",
-                "peak_source": f"measured in this run: rqrcp_peak_probe {best_kind} (best FP64 "
-                               f"rate of FMA chains, DMMA m8n8k4, DMMA m16n8k16)",
+                "peak_source": f"FP64 unit count x clock: {units} FP64 FMA/clk/SM (from the "
+                               f"best of this run's probes, {best_kind} {best:.3f} TFLOP/s) x 2 "
+                               f"flop x {sms} SMs x {mhz:.0f} MHz (sampled)",
                 "peak_probes_tflops": {k: round(v["tflops"], 4) for k, v in probes.items()},
-                "peak_derived": derived,
-                "peak_derived_source": f"{lanes} FP64 FMA/clk/SM x 2 flop x {sms} SMs x "
-                                       f"{mhz:.0f} MHz (sampled)",
-                "frac_derived": achieved / derived if achieved and derived else None,
+                "frac_of_best_probe": achieved / best if achieved else None,
                 "peak_nominal": 1.25,
                 "launch_ms_avg": tr_ms / max(tr_launch, 1)}
     phases = {k: {"ms": v[0], "gflop": v[1] / 1e9, "launches": v[2]} for k, v in prof.items()}
