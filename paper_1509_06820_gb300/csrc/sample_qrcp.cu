@@ -3,20 +3,14 @@
 //
 // One cooperative launch per block of pivots.  CTA g owns a contiguous range
 // of sample columns and keeps them in shared memory for the whole launch;
-// columns never move between CTAs.  Each pivot step costs one exchange:
-//   1. every CTA finds its best trailing column (a block argmax), publishes
-//      that column's values and its key (order-preserving image of the norm),
-//      then, with a release store, its logical position stamped with the step;
-//   2. warp 0 of every CTA polls (bounded) the G stamped words until all carry
-//      this step -- the exchange doubles as the grid-wide synchronisation, so
-//      no counter is shared by all CTAs -- and every CTA picks the same winner
-//      (largest norm, lowest logical position on a tie), builds the same
-//      Householder reflector from the published column, records the swap,
-//      applies the reflector to its trailing columns (8 lanes per column,
-//      shuffle reductions) and downdates their norms.
-// Publication slots are double-buffered by step parity: a CTA that sees every
-// stamp of step i knows every CTA has finished reading step i - 1's slots.
-// The stamps are cleared at launch behind one grid barrier.
+// columns never move between CTAs.  Each pivot step costs one grid barrier:
+//   1. every CTA publishes its best trailing column (norm, logical position)
+//      and that column's values;
+//   2. after the barrier every CTA picks the same winner (largest norm, lowest
+//      logical position on a tie), builds the same Householder reflector from
+//      the published column, records the swap in its own bookkeeping, applies
+//      the reflector to its trailing columns (8 lanes per column, shuffle
+//      reductions), downdates their norms and computes its next candidate.
 // Swaps are tracked as logical positions; at the end every column is written
 // back to B at its final logical position, so B holds S = [S11 S12; 0 S22]
 // in the permuted order and `swaps` the partner position of each step.
@@ -61,7 +55,7 @@ cudaError_t launch_sample_qrcp(const SampleQrcpArgs& a, int num_sms, cudaStream_
   const int G = sample_grid(a.nc, num_sms);
   const int64_t chunk = (a.nc + G - 1) / G;
   const size_t smem = smem_bytes(a.ell, chunk);
-  if (a.ell > MAX_ELL || smem > kSmemLimit || G > 32 * kMaxQ) return cudaErrorInvalidValue;
+  if (a.ell > MAX_ELL || smem > kSmemLimit) return cudaErrorInvalidValue;
   static std::atomic<uint64_t> attr_done{0};
   cudaError_t e = ensure_smem_attr(sample_qrcp_kernel, (int)kSmemLimit, attr_done);
   if (e != cudaSuccess) return e;

@@ -18,22 +18,6 @@ constexpr int GROUPS = NT / LPC;       // columns processed concurrently
 constexpr int MAX_ELL = 192;
 constexpr double TOL3Z = 1.4901161193847656e-08;  // sqrt(2^-52)
 
-// Publication word of a CTA's candidate: logical position << kStampBits |
-// (step + 1); positions stay below 2^43.  kNoPos marks "no trailing column".
-constexpr int kStampBits = 20;
-constexpr unsigned long long kStampMask = (1ull << kStampBits) - 1;
-constexpr long long kNoPos = (1ll << 43) - 1;
-constexpr int kMaxQ = 8;  // candidates per lane of the winner search: G <= 256 CTAs
-
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
 struct Cand {
   long long key; // order-preserving integer image of the norm (see sort_key);
                  // the norm -1 for NaN, -2 when the CTA has no trailing column
@@ -82,7 +66,6 @@ __device__ __forceinline__ void sample_qrcp_body(const SampleQrcpArgs& a, int g,
   double* xv = reinterpret_cast<double*>(lpos + chunk);         // MAX_ELL (reflector v)
   int* done = reinterpret_cast<int*>(xv + MAX_ELL);             // chunk
   __shared__ Cand red[2];
-  __shared__ Cand wred[NT / 32];
   __shared__ double s_scal[4];
 
   const int tid = threadIdx.x;
@@ -113,126 +96,32 @@ __device__ __forceinline__ void sample_qrcp_body(const SampleQrcpArgs& a, int g,
       vn0[c] = nv;
     }
   }
-  // the step stamps of this CTA's two publication slots start invalid, and
-  // nobody reads a slot before every CTA has cleared its own (stale words of
-  // an earlier launch on the same scratch could otherwise carry a valid stamp)
-  if (tid == 0) {
-    reinterpret_cast<unsigned long long*>(a.cand)[2 * g + 1] = 0ull;
-    reinterpret_cast<unsigned long long*>(a.cand)[(size_t)2 * G + 2 * g + 1] = 0ull;
-  }
-  __shared__ int s_fail;
-  if (tid == 0) s_fail = 0;
-  if (!grid_barrier(a.bar, G, a.status)) {
-    if (g == 0)
-      for (int t = tid; t < a.steps; t += NT) a.swaps[t] = t;
-    return;
-  }
+  __syncthreads();
 
   for (int i = 0; i < a.steps; ++i) {
-    // ---- local candidate: every thread scans its columns, then a block argmax
+    // ---- local candidate: warp 0 scans the owned columns
     double* cand = a.cand + (size_t)(i & 1) * G * 2;
     double* ccol = a.candcol + (size_t)(i & 1) * G * ell;
-    {
-      Cand mine{sort_key(-2.0), kNoPos, -1};
-      for (int c = tid; c < ncol; c += NT) {
+    if (tid < 32) {
+      Cand mine{sort_key(-2.0), LLONG_MAX, -1};
+      for (int c = tid; c < ncol; c += 32) {
         if (done[c]) continue;
         Cand t{sort_key(isnan(vn[c]) ? -1.0 : vn[c]), lpos[c], c};
         if (better(t, mine)) mine = t;
       }
       mine = warp_argmax(mine);
-      if ((tid & 31) == 0) wred[tid >> 5] = mine;
-      __syncthreads();
-      if (tid < 32) {
-        Cand t = tid < NT / 32 ? wred[tid] : Cand{sort_key(-2.0), kNoPos, -1};
-        t = warp_argmax(t);
-        if (tid == 0) red[0] = t;
+      if (tid == 0) {
+        red[0] = mine;
+        cand[2 * g] = __longlong_as_double(mine.key);       // bit pattern
+        cand[2 * g + 1] = __longlong_as_double(mine.pos);
       }
-      __syncthreads();
     }
+    __syncthreads();
     const int my_pivot = red[0].who;  // local column index of this CTA's candidate
     if (my_pivot >= 0)
       for (int r = tid; r < ell; r += NT) ccol[(size_t)g * ell + r] = col[r + my_pivot * ell];
-    __syncthreads();
-    // ---- publish: the candidate's key, then its position stamped with the
-    // step (release: the column above is visible to whoever sees the stamp)
-    const unsigned long long stamp = (unsigned long long)(i + 1) & kStampMask;
-    if (tid == 0) {
-      __threadfence();
-      reinterpret_cast<long long*>(cand)[2 * g] = red[0].key;
-      st_release_u64(reinterpret_cast<unsigned long long*>(cand) + 2 * g + 1,
-                     ((unsigned long long)red[0].pos << kStampBits) | stamp);
-    }
-
-    // ---- global winner (identical in every CTA): warp 0 waits (bounded) for
-    // every CTA's stamp of this step, takes the best candidate, then builds the
-    // reflector from the winner's rows i..ell-1
-    if (tid < 32) {
-      unsigned long long wq[kMaxQ];
-      const unsigned int limit = a.phantom ? kBarrierTestPolls : kBarrierMaxPolls;
-      unsigned int polls = 0;
-      bool ok = true;
-      for (;;) {
-        bool ready = true;
-#pragma unroll
-        for (int u = 0; u < kMaxQ; ++u) {
-          const int q = tid + 32 * u;
-          if (q < G) {
-            wq[u] = ld_acquire_u64(reinterpret_cast<const unsigned long long*>(cand) + 2 * q + 1);
-            if ((wq[u] & kStampMask) != stamp) ready = false;
-          }
-        }
-        // test of the timeout path: a CTA that never publishes
-        if (a.phantom) ready = false;
-        if (__all_sync(0xffffffffu, ready)) break;
-        const bool gave_up = __any_sync(0xffffffffu, ld_acquire_u32(&a.bar->abort) != 0u);
-        if (gave_up || ++polls > limit) {
-          if (tid == 0 && !gave_up) {
-            atomicExch(&a.bar->abort, 1u);
-            atomicOr(a.status, RQRCP_INFO_TIMEOUT);
-          }
-          ok = false;
-          break;
-        }
-        if (polls > 256) __nanosleep(32);
-      }
-      if (!ok) {
-        if (tid == 0) s_fail = 1;
-      } else {
-        Cand w{sort_key(-3.0), kNoPos, -1};
-#pragma unroll
-        for (int u = 0; u < kMaxQ; ++u) {
-          const int q = tid + 32 * u;
-          if (q < G) {
-            const Cand t{__ldcg(reinterpret_cast<const long long*>(cand) + 2 * q),
-                         (long long)(wq[u] >> kStampBits), q};
-            if (better(t, w)) w = t;
-          }
-        }
-        w = warp_argmax(w);
-        // the winner's rows i..ell-1; each lane rescales the rows it loaded
-        const double* wc = ccol + (size_t)w.who * ell;
-        double s = 0.0;
-        for (int r = i + tid; r < ell; r += 32) {
-          const double x = __ldcg(wc + r);
-          xv[r] = x;
-          if (r > i) s = fma(x, x, s);
-        }
-        s = warp_sum(s);
-        __syncwarp();
-        const double alpha = xv[i];
-        __syncwarp();  // every lane has read alpha before lane 0 overwrites it
-        double beta, tau, scale;
-        house_scalars_sq(alpha, s, &beta, &tau, &scale);
-        for (int r = i + tid; r < ell; r += 32) xv[r] = (r == i) ? 1.0 : xv[r] * scale;
-        if (tid == 0) {
-          s_scal[0] = beta;
-          s_scal[1] = tau;
-          red[1] = w;
-        }
-      }
-    }
-    __syncthreads();
-    if (s_fail) {
+    if (!grid_barrier(a.bar, G + a.phantom, a.status,
+                      a.phantom ? kBarrierTestPolls : kBarrierMaxPolls)) {
       // the wait ran out (RQRCP_INFO_TIMEOUT is set): leave valid swap
       // partners (no exchange) for the steps not taken, so that whatever
       // consumes the list stays within its columns
@@ -240,6 +129,39 @@ __device__ __forceinline__ void sample_qrcp_body(const SampleQrcpArgs& a, int g,
         for (int t = i + tid; t < a.steps; t += NT) a.swaps[t] = t;
       return;
     }
+
+    // ---- global winner (identical in every CTA): warp 0 scans the G
+    // candidates, then builds the reflector from the winner's rows i..ell-1
+    if (tid < 32) {
+      Cand w{sort_key(-3.0), LLONG_MAX, -1};
+      for (int q = tid; q < G; q += 32) {
+        Cand t{__double_as_longlong(__ldcg(cand + 2 * q)),
+               __double_as_longlong(__ldcg(cand + 2 * q + 1)), q};
+        if (better(t, w)) w = t;
+      }
+      w = warp_argmax(w);
+      // the winner's rows i..ell-1; each lane rescales the rows it loaded
+      const double* wc = ccol + (size_t)w.who * ell;
+      double s = 0.0;
+      for (int r = i + tid; r < ell; r += 32) {
+        const double x = __ldcg(wc + r);
+        xv[r] = x;
+        if (r > i) s = fma(x, x, s);
+      }
+      s = warp_sum(s);
+      __syncwarp();
+      const double alpha = xv[i];
+      __syncwarp();  // every lane has read alpha before lane 0 overwrites it
+      double beta, tau, scale;
+      house_scalars_sq(alpha, s, &beta, &tau, &scale);
+      for (int r = i + tid; r < ell; r += 32) xv[r] = (r == i) ? 1.0 : xv[r] * scale;
+      if (tid == 0) {
+        s_scal[0] = beta;
+        s_scal[1] = tau;
+        red[1] = w;
+      }
+    }
+    __syncthreads();
     const Cand w = red[1];
     const long long Lstar = w.pos;
     const double beta = s_scal[0], tau = s_scal[1];
