@@ -119,17 +119,17 @@ __device__ __forceinline__ void panel_body(const PanelArgs& a, int g, int G,
     // scale column j into v, then a_rc -= v_r w_c on owned rows below j
     for (int64_t r = rstart + tid; r < nrow; r += NT) Ps[r + j * ldp] *= scale;
     __syncthreads();
-    const double* vj = Ps + (size_t)j * ldp;
-    const int64_t j1l = (int64_t)(j + 1) - r_lo;  // local index of row j + 1
-    if (tau != 0.0 && j + 1 < bJ) {
-      // column j + 1 on the owned rows below j, and row j + 1 (if owned) on
-      // the other trailing columns: what the partial dots of column j + 1 read
-      const double w1 = s_w[j + 1];
-      double* x1 = Ps + (size_t)(j + 1) * ldp;
-      for (int64_t r = rstart + tid; r < nrow; r += NT) x1[r] = fma(-vj[r], w1, x1[r]);
-      if (j1l >= rstart && j1l < nrow)
-        for (int c = j + 2 + tid; c < bJ; c += NT)
-          Ps[j1l + (size_t)c * ldp] = fma(-vj[j1l], s_w[c], Ps[j1l + (size_t)c * ldp]);
+    if (tau != 0.0) {
+      // (row, column) pairs packed densely over the threads (32-bit indices)
+      const int ncols = bJ - j - 1;
+      const int rows = nrow - (int)rstart;
+      const double* vj = Ps + (size_t)j * ldp;
+      for (int e = tid; e < rows * ncols; e += NT) {
+        const int cc = e / rows;
+        const int r = (int)rstart + (e - cc * rows);
+        const int c = j + 1 + cc;
+        Ps[r + (size_t)c * ldp] = fma(-vj[r], s_w[c], Ps[r + (size_t)c * ldp]);
+      }
     }
     if (jl >= 0 && jl < nrow) {
       // row j: R entries
@@ -137,44 +137,7 @@ __device__ __forceinline__ void panel_body(const PanelArgs& a, int g, int G,
       if (tid == 0) Ps[jl + j * ldp] = beta;
     }
     __syncthreads();
-    if (j + 1 < bJ) {
-      // the update of the remaining columns on the rows below j + 1, fused
-      // with the partial dots of column j + 1 that the next step publishes
-      // (the same lanes, rows and order as publish(j + 1): one pass over
-      // shared memory instead of two)
-      const int jn = j + 1;
-      double* part = part_base + (size_t)(jn & 1) * G * bJ + (size_t)g * bJ;
-      const int rs1 = (int)imax64(0, (int64_t)jn + 1 - r_lo);  // local first row > j + 1
-      const int ncols = bJ - jn;
-      int P = 32;
-      while (P > 1 && NT / P < ncols) P >>= 1;
-      const int cpr = NT / P;
-      const int p = tid % P;
-      const double* xj = Ps + (size_t)jn * ldp;
-      for (int c0 = 0; c0 < ncols; c0 += cpr) {
-        const int c = jn + c0 + tid / P;
-        double s = 0.0;
-        if (c < bJ) {
-          double* xc = Ps + (size_t)c * ldp;
-          if (c == jn || tau == 0.0) {
-            for (int r = rs1 + p; r < nrow; r += P) s = fma(xj[r], xc[r], s);
-          } else {
-            const double wc = s_w[c];
-            for (int r = rs1 + p; r < nrow; r += P) {
-              const double v = fma(-vj[r], wc, xc[r]);
-              xc[r] = v;
-              s = fma(xj[r], v, s);
-            }
-          }
-        }
-        for (int o = P >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (p == 0 && c < bJ) part[c] = s;
-      }
-      if (j1l >= 0 && j1l < nrow) {
-        double* rowj = a.rowj + (size_t)(jn & 1) * bJ;
-        for (int c = jn + tid; c < bJ; c += NT) rowj[c] = Ps[j1l + (size_t)c * ldp];
-      }
-    }
+    if (j + 1 < bJ) publish(j + 1);
   }
 
   // mixed precision: the stored reflectors are the FP32-rounded ones
