@@ -274,3 +274,50 @@ def test_ring_server_poisson(lib):
         srv.close()
     assert stats["requests"] > 200
     assert 0 < stats["p50_ms"] <= stats["p99_ms"]
+
+
+EDGE = [(1, 1, 1, 1, 0), (5, 3, 3, 8, 2), (300, 40, 40, 16, 4), (40, 300, 40, 32, 0),
+        (257, 129, 100, 32, 8), (64, 64, 64, 64, 8), (1000, 17, 17, 128, 16)]
+
+
+def test_trqrcp_batched_edge_shapes(lib):
+    """Degenerate and ragged problems in one batch (1 x 1, b > k clamped,
+    k = n so the last block has no trailing columns, p = 0, m < n, a ragged
+    last block): the first k selected columns are reproduced by Q R, R agrees
+    with the FP64 oracle's Alg. 6 replayed on the device's pivots, and the
+    trailing columns of R are Q_k^T A P."""
+    import oracle
+    from oracle import householder as hh
+    import synth
+    probs, hosts = [], []
+    for i, (m, n, k, b, p) in enumerate(EDGE):
+        A = synth.gaussian(m, n, seed=40 + i).astype(np.float32)
+        hosts.append(A)
+        probs.append((lib.colmajor(torch.from_numpy(A).cuda()), k, b, p, 3 + i))
+    got = lib.trqrcp_batched(probs, teams=2)
+    assert lib.sync_info() == 0
+    for (dA, k, b, p, seed), A, out in zip(probs, hosts, got):
+        jp, t, Yg, Rg, rd = (x.cpu().numpy() for x in out)
+        A64 = A.astype(np.float64)
+        m, n = A64.shape
+        assert sorted(jp.tolist()) == list(range(n))
+        Rg = Rg.astype(np.float64)
+        Rg[np.arange(k), np.arange(k)] = rd
+        Q = hh.form_q(Yg.astype(np.float64), t, k)
+        sel = A64[:, jp[:k]]
+        assert np.linalg.norm(sel - Q @ Rg[:, :k]) <= 1e-5 * np.linalg.norm(sel)
+        if k < n:
+            rest = Q.T @ A64[:, jp[k:]]
+            assert np.linalg.norm(Rg[:, k:] - rest) <= 1e-5 * np.linalg.norm(A64)
+        _, _, _, Ro, _ = oracle.trqrcp(A64, k, min(b, k), p, seed=seed, replay_jpvt=jp,
+                                       tie_rtol=1.0)
+        assert np.linalg.norm(Rg - Ro) <= 1e-4 * max(np.linalg.norm(Ro), 1e-30)
+
+
+def test_trqrcp_batched_rejects_oversize_sample(lib):
+    """A problem whose sample does not fit the team's shared memory fails the
+    whole call before launch, naming the problem."""
+    A = lib.colmajor(torch.randn(600, 4096, device="cuda"))
+    ok = lib.colmajor(torch.randn(300, 300, device="cuda"))
+    with pytest.raises(lib.RqrcpError, match="problem 1"):
+        lib.trqrcp_batched([(ok, 16, 16, 8, 1), (A, 128, 128, 64, 1)])
