@@ -92,6 +92,8 @@ def parse():
     ap.add_argument("--m", type=int, default=16384, help="--case panel: rows")
     ap.add_argument("--reps", type=int, default=1, help="--case: timed repetitions")
     ap.add_argument("--team", type=int, default=16, help="--case batched: CTAs per team")
+    ap.add_argument("--max-sms", type=int, default=0,
+                    help="--case: cap on the CTAs per wave of the handle's launches (0: all)")
     args = ap.parse_args()
     legs = set(x for x in args.legs.split(",") if x)
     if args.no_extras:
@@ -766,7 +768,9 @@ def run_case(args):
         return
     g = torch.Generator(device=dev).manual_seed(1)
     h = rq.Handle(dev)
-    out = {"case": args.case}
+    if args.max_sms:
+        h.set_max_sms(args.max_sms)
+    out = {"case": args.case, "max_sms": args.max_sms}
     if args.case == "mixed":
         import synth
         n = args.n
