@@ -91,7 +91,8 @@ def parse():
                     help="--case gemm_*: transA,transB,M,N,K (e.g. T,N,128,8000,8192)")
     ap.add_argument("--m", type=int, default=16384, help="--case panel: rows")
     ap.add_argument("--reps", type=int, default=1, help="--case: timed repetitions")
-    ap.add_argument("--team", type=int, default=16, help="--case batched: CTAs per team")
+    ap.add_argument("--team", type=int, default=16,
+                    help="--case batched / serve: CTAs per team (serve: 0 = autotuned)")
     ap.add_argument("--max-sms", type=int, default=0,
                     help="--case: cap on the CTAs per wave of the handle's launches (0: all)")
     args = ap.parse_args()
@@ -592,13 +593,36 @@ SERVE_BUCKETS = [(1024, 1024, 64), (2048, 2048, 96), (4096, 4096, 128), (2048, 4
                  (512, 512, 32)]
 
 
-def ring_serving(args, dev, team, tuner=None):
+def tune_serving(dev, teams=(8, 16), reserve_sms=16, nprob=48):
+    """Autotuning of the persistent kernel for the served workload: for each
+    team size (CTAs per team, the launch's tile shape) the (b, p) table per
+    size bucket, then the team size whose teams serve a batch of served-size
+    problems fastest with the SMs a server leaves free for inputs."""
+    import torch
+    from paper_1509_06820_gb300.autotune import Tuner
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    best, tried = None, {}
+    for team in teams:
+        cands = [(16, 8), (32, 8), (64, 8)] if team >= 16 else [(16, 8), (32, 8)]
+        tuner = Tuner.tune_batched(SERVE_BUCKETS, device=dev, team=team, candidates=cands)
+        nteams = max(1, (nsm - reserve_sms) // team)
+        res = batched_leg(dev, tuner, nprob=nprob, reps=3, seed=11, team=team, teams=nteams)
+        tried[team] = round(res["problems_per_s"], 1)
+        if best is None or res["problems_per_s"] > best[2]:
+            best = (team, tuner, res["problems_per_s"])
+    return best[0], best[1], tried
+
+
+def ring_serving(args, dev, team=None, tuner=None):
     """The served TRQRCP workload on the persistent kernel's request ring:
     Poisson arrivals at --serve-rate, then a rate below saturation."""
     from paper_1509_06820_gb300.serve import RingServer
     from paper_1509_06820_gb300.autotune import Tuner
     t0 = time.perf_counter()
-    if tuner is None:
+    tried = None
+    if team is None:
+        team, tuner, tried = tune_serving(dev)
+    elif tuner is None:
         cands = [(16, 8), (32, 8), (64, 8)] if team >= 16 else [(16, 8), (32, 8)]
         tuner = Tuner.tune_batched(SERVE_BUCKETS, device=dev, team=team, candidates=cands)
     tune_s = time.perf_counter() - t0
@@ -614,6 +638,8 @@ def ring_serving(args, dev, team, tuner=None):
         srv.close()
     stats = {"mode": "persistent kernel, mapped request ring", "team_ctas": team,
              "teams": srv.nslots, **stats}
+    if tried is not None:
+        stats["autotune_team_problems_per_s"] = tried
     stats["below_saturation"] = {k: low[k] for k in ("offered_rate", "requests", "throughput_rps",
                                                      "p50_ms", "p99_ms", "gflops")}
     stats["autotune_s"] = tune_s
@@ -630,7 +656,7 @@ def serving_leg(args, dev):
     stream, and one static batch through trqrcp_batched."""
     from paper_1509_06820_gb300.serve import Server
     from paper_1509_06820_gb300.autotune import Tuner
-    stats = ring_serving(args, dev, team=8)
+    stats = ring_serving(args, dev)
     t0 = time.perf_counter()
     tuner = Tuner.tune(SERVE_BUCKETS[:4], device=dev)
     tune_s = time.perf_counter() - t0
@@ -641,7 +667,7 @@ def serving_leg(args, dev):
                              **{k: sl[k] for k in ("offered_rate", "requests", "throughput_rps",
                                                    "p50_ms", "p99_ms", "gflops")}}
     del srv
-    stats["batched"] = batched_leg(dev, Tuner(stats["autotune_table"]), team=8)
+    stats["batched"] = batched_leg(dev, Tuner(stats["autotune_table"]), team=stats["team_ctas"])
     return stats
 
 
@@ -668,7 +694,7 @@ class FixedBP:
         return self.b, self.p
 
 
-def batched_leg(dev, tuner, nprob=64, reps=5, seed=9, team=16):
+def batched_leg(dev, tuner, nprob=64, reps=5, seed=9, team=16, teams=0):
     """One static batch of served-size problems (m, n ~ U{256..4096},
     k ~ U{16..128}, A = X Y^T in FP32, autotuned b/p) through trqrcp_batched:
     one persistent launch (teams of CTAs claim the problems longest-first),
@@ -689,12 +715,12 @@ def batched_leg(dev, tuner, nprob=64, reps=5, seed=9, team=16):
     h.reserve_batched(0, max(s[0] for s in specs), max(s[1] for s in specs),
                       max(s[2] for s in specs), max(s[3] for s in specs),
                       max(s[4] for s in specs))
-    outs = rq.trqrcp_batched(probs, handle=h)
+    outs = rq.trqrcp_batched(probs, teams=teams, handle=h)
     torch.cuda.synchronize(dev)
     side = torch.cuda.Stream(dev)
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=side):
-        rq.trqrcp_batched(probs, handle=h, outs=outs)
+        rq.trqrcp_batched(probs, teams=teams, handle=h, outs=outs)
     graph.replay()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -706,12 +732,12 @@ def batched_leg(dev, tuner, nprob=64, reps=5, seed=9, team=16):
     ms = e0.elapsed_time(e1) / reps
     # one eager launch with the kernel's phase timers on (team-milliseconds)
     h.profile(True)
-    rq.trqrcp_batched(probs, handle=h, outs=outs)
+    rq.trqrcp_batched(probs, teams=teams, handle=h, outs=outs)
     team_ms = {k: round(v, 2) for k, v in h.batched_profile().items() if v > 0}
     h.profile(False)
     flops = sum(request_flops(m, n, k, b + p) for (m, n, k, b, p) in specs)
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    return {"problems": nprob, "team_ctas": team, "teams": nsm // team, "ms_per_batch": ms,
+    return {"problems": nprob, "team_ctas": team, "teams": teams or nsm // team, "ms_per_batch": ms,
             "phase_team_ms": team_ms,
             "problems_per_s": nprob / (ms / 1e3), "gflops": flops / (ms / 1e3) / 1e9,
             "launch": "one persistent cooperative launch per batch, captured in a CUDA graph",
@@ -743,7 +769,8 @@ def run_case(args):
     torch.cuda.set_device(dev)
     if args.case == "serve":
         # the ring server alone at --serve-rate for --serve-seconds
-        print(json.dumps({"case": "serve", **ring_serving(args, dev, args.team)}), flush=True)
+        team = args.team if args.team > 0 else None
+        print(json.dumps({"case": "serve", **ring_serving(args, dev, team)}), flush=True)
         return
     if args.case == "batched":
         # one persistent batched launch over served-size problems (b = 64, p = 8)
