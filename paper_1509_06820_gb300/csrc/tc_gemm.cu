@@ -19,19 +19,23 @@
 // S = 1 (the sketch B = Omega A, which only steers pivots) is one product
 // accumulated over the whole k range.
 //
-// Kernel (tcx_gemm_kernel): persistent, one CTA per SM, 128 x 64 output
-// tiles, split-K units; 6 warps with fixed roles:
+// Kernel (tcx_gemm_kernel): persistent, one CTA per SM, 128 x 128 output
+// tiles, split-K units; 10 warps with fixed roles:
 //   warp 0      one thread issues the TMA copies (per 64-k stage one 3-D box
-//               per operand: 64 k x rows x S slices, 128-byte swizzle) into a
-//               three-stage shared-memory ring (mbarrier expect-tx), refilling
-//               a slot as soon as the MMAs that read it have completed;
+//               per operand: 64 k x 128 rows x S slices, 128-byte swizzle) into
+//               a shared-memory ring (2 stages of 96 KB for S = 3, 4 of 32 KB
+//               for S = 1; mbarrier expect-tx), refilling a slot as soon as
+//               the MMAs that read it have completed;
 //   warp 1      allocates tensor memory; one thread issues the tcgen05.mma
-//               (M = 128, N = 64, K = 16) and the tcgen05.commit;
-//   warps 2-5   drain: warp w reads accumulator lanes 32 (w % 4).. (one row
-//               per thread, 64 columns), adds into the compensated sums and,
-//               at the end of a unit, writes C (or its split-K partial sums).
-// The accumulators are double-buffered in tensor memory (2 x 2 x 64
-// columns), so the drain of one chunk overlaps the MMAs of the next.
+//               (M = 128, N = 128, K = 16) and the tcgen05.commit;
+//   warps 2-9   drain: warp w reads accumulator lanes 32 (w % 4).. (one row
+//               per thread) and columns 64 ((w - 2) / 4).. (64 columns), adds
+//               into the compensated sums and, at the end of a unit, writes C
+//               (or its split-K partial sums).
+// The accumulators are double-buffered in tensor memory (2 x 2 x 128
+// columns, all 512), so the drain of one chunk overlaps the MMAs of the next.
+// The 128-column tile halves the operand bytes per flop of the earlier
+// 128 x 64 tile, whose reads from L2 and HBM bounded it.
 // Every mbarrier wait is bounded; on timeout the status word gets
 // RQRCP_INFO_TIMEOUT, each role stops, in-flight copies and MMAs are waited
 // for (bounded) and the tensor memory is freed.
@@ -49,13 +53,16 @@ namespace {
 using namespace tc;
 
 constexpr int XBM = 128;          // tile rows (A role), UMMA M
-constexpr int XBN = 64;           // tile columns (B role), UMMA N
+constexpr int XBN = 128;          // tile columns (B role), UMMA N
 constexpr int XBK = 64;           // k per pipeline stage: one 128-byte swizzle row
-constexpr int XNST = 3;           // shared-memory ring stages
-constexpr int XNT = 192;          // warp 0 TMA, warp 1 MMA issue, warps 2..5 drain
+constexpr int XNDW = 8;           // drain warps: two per tensor-memory lane quadrant
+constexpr int XDC = XBN / 2;      // columns a drain thread owns
+constexpr int XNT = 64 + 32 * XNDW;  // warp 0 TMA, warp 1 MMA issue, warps 2.. drain
 constexpr int XCH = 2;            // MMA k-steps per drained chunk (S = 3): 32 k
 constexpr int XTILE_A = XBM * 128;  // bytes of one A slice tile (128 rows x 64 k)
-constexpr int XTILE_B = XBN * 128;  // bytes of one B slice tile (64 rows x 64 k)
+constexpr int XTILE_B = XBN * 128;  // bytes of one B slice tile (128 rows x 64 k)
+// shared-memory ring stages: 2 x 96 KB for S = 3, 4 x 32 KB for S = 1
+__host__ __device__ constexpr int xnst(int S) { return S == 3 ? 2 : 4; }
 constexpr uint32_t XIDESC = idesc_bf16_f32(XBM, XBN);
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
@@ -156,7 +163,8 @@ __global__ void __launch_bounds__(XNT, 1)
     tcx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     TcxArgs g) {
   constexpr int NACC = (S == 3) ? 2 : 1;
-  constexpr uint32_t TCOLS = (S == 3) ? 256u : 128u;
+  constexpr int XNST = xnst(S);
+  constexpr uint32_t TCOLS = (uint32_t)(2 * NACC * XBN);  // two buffers of NACC accumulators
   constexpr uint32_t STAGE_A = (uint32_t)S * XTILE_A;
   constexpr uint32_t STAGE_TX = (uint32_t)S * (XTILE_A + XTILE_B);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -174,7 +182,7 @@ __global__ void __launch_bounds__(XNT, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&tfull[i], 1);
-      mbar_init(&tempty[i], 4);
+      mbar_init(&tempty[i], XNDW);
     }
     mbar_init(&done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -287,8 +295,11 @@ __global__ void __launch_bounds__(XNT, 1)
     __syncwarp();
   } else {
     // ------------------------------------------------ drain and epilogue
+    // warp w reads tensor-memory lanes 32 (w % 4).. (its quadrant); the two
+    // warps of a quadrant take columns 0..63 and 64..127 of the tile
     const int quad = warp & 3;
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * quad) << 16);
+    const int half = (warp - 2) / 4;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(XDC * half);
     const int64_t MN = g.M * g.N;
     int buf = 0;
     uint32_t tpar = 0u;  // parity of the tfull[] uses
@@ -298,10 +309,17 @@ __global__ void __launch_bounds__(XNT, 1)
       const int tn = rest % g.tiles_n, z = rest / g.tiles_n;
       const int kb = z * g.kt_per_split, ke = min(g.KT, kb + g.kt_per_split);
       const int nch = (S == 3) ? (ke - kb) * (XBK / 16) / XCH : (ke > kb ? 1 : 0);
-      // compensated sums: value = hi - cc
-      float hi[XBN], cc[XBN];
+      // compensated sums: value = hi - cc.  The compensation cc is below half
+      // an ulp of hi, so it is kept as bfloat16 (8 bits of it are plenty: the
+      // error of the stored compensation is below 2^-10 ulp of the sum per
+      // chunk), two per register, which keeps the drain thread's state within
+      // the register budget of a 320-thread CTA.
+      float hi[XDC];
+      __nv_bfloat162 ccp[XDC / 2];
 #pragma unroll
-      for (int c = 0; c < XBN; ++c) hi[c] = cc[c] = 0.0f;
+      for (int c = 0; c < XDC; ++c) hi[c] = 0.0f;
+#pragma unroll
+      for (int c = 0; c < XDC / 2; ++c) ccp[c] = __floats2bfloat162_rn(0.0f, 0.0f);
       for (int ch = 0; ch < nch; ++ch) {
         if (!mbar_wait(&tfull[buf], (tpar >> buf) & 1u) || s_fail) {
           ok = false;
@@ -311,21 +329,27 @@ __global__ void __launch_bounds__(XNT, 1)
         const uint32_t tb = lane_base + (uint32_t)(buf * NACC * XBN);
         if (S == 3) {
 #pragma unroll
-          for (int c0 = 0; c0 < XBN; c0 += 32) {
-            float v[32], w[32];
-            tmem_ld32x2(tb + c0, tb + XBN + c0, v, w);
+          for (int c0 = 0; c0 < XDC; c0 += 16) {
+            float v[16], w[16];
+            tmem_ld16x2(tb + c0, tb + XBN + c0, v, w);
 #pragma unroll
-            for (int e = 0; e < 32; ++e) {
-              // Kahan step with the chunk's leading and correction parts
-              const float y = (v[e] - cc[c0 + e]) + w[e];
-              const float t = hi[c0 + e] + y;
-              cc[c0 + e] = (t - hi[c0 + e]) - y;
-              hi[c0 + e] = t;
+            for (int e = 0; e < 16; e += 2) {
+              // Kahan steps with the chunk's leading and correction parts
+              const float2 cf = __bfloat1622float2(ccp[(c0 + e) / 2]);
+              const float y0 = (v[e] - cf.x) + w[e];
+              const float t0 = hi[c0 + e] + y0;
+              const float n0 = (t0 - hi[c0 + e]) - y0;
+              hi[c0 + e] = t0;
+              const float y1 = (v[e + 1] - cf.y) + w[e + 1];
+              const float t1 = hi[c0 + e + 1] + y1;
+              const float n1 = (t1 - hi[c0 + e + 1]) - y1;
+              hi[c0 + e + 1] = t1;
+              ccp[(c0 + e) / 2] = __floats2bfloat162_rn(n0, n1);
             }
           }
         } else {
 #pragma unroll
-          for (int c0 = 0; c0 < XBN; c0 += 16) {
+          for (int c0 = 0; c0 < XDC; c0 += 16) {
             float v[16];
             tmem_ld16(tb + c0, v);
 #pragma unroll
@@ -340,16 +364,17 @@ __global__ void __launch_bounds__(XNT, 1)
       }
       if (!ok) break;
       const int64_t r = (int64_t)tm * XBM + 32 * quad + lane;
-      const int64_t c0 = (int64_t)tn * XBN;
-      const int nval = (int)imin64(XBN, g.N - c0);
+      const int64_t c0 = (int64_t)tn * XBN + XDC * half;
+      const int nval = (int)imax64(0, imin64(XDC, g.N - c0));
       if (r < g.M) {
         if (g.part != nullptr) {
           float* ph = g.part + (int64_t)(2 * z) * MN + r + c0 * g.M;
 #pragma unroll
-          for (int c = 0; c < XBN; ++c) {
+          for (int c = 0; c < XDC; ++c) {
             if (c < nval) {
+              const float2 cf = __bfloat1622float2(ccp[c / 2]);
               ph[0] = hi[c];
-              ph[MN] = -cc[c];
+              ph[MN] = -((c & 1) ? cf.y : cf.x);
             }
             ph += g.M;
           }
@@ -359,7 +384,7 @@ __global__ void __launch_bounds__(XNT, 1)
           const int64_t ldc = g.ldc;
           const float alpha = g.alpha, beta = g.beta;
 #pragma unroll
-          for (int cb = 0; cb < XBN; cb += 16) {
+          for (int cb = 0; cb < XDC; cb += 16) {
             float cv[16];
 #pragma unroll
             for (int e = 0; e < 16; ++e)
@@ -369,7 +394,8 @@ __global__ void __launch_bounds__(XNT, 1)
               const int c = cb + e;
               if (c < nval) {
                 const float out = fmaf(alpha, hi[c], beta * cv[e]);
-                __stcs(cp + c * ldc, fmaf(-alpha, cc[c], out));
+                const float2 cf = __bfloat1622float2(ccp[c / 2]);
+                __stcs(cp + c * ldc, fmaf(-alpha, (c & 1) ? cf.y : cf.x, out));
               }
             }
           }
@@ -452,7 +478,7 @@ cudaError_t split_operand(const float* X, int64_t ld, bool kc, int64_t R, int64_
 
 template <int S>
 size_t gemm_smem() {
-  return (size_t)XNST * S * (XTILE_A + XTILE_B) + 1024;
+  return (size_t)xnst(S) * S * (XTILE_A + XTILE_B) + 1024;
 }
 
 template <int S>
