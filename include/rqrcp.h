@@ -179,8 +179,10 @@ int rqrcp_factor_host(rqrcp_handle_t handle, int64_t m, int64_t n, const double*
  * The sketch B = Omega A is a BF16 product with FP32 accumulation (it only
  * steers pivots); the trailing update W = T^T Y^T A2, A2 -= Y W runs as
  * split-BF16 x3 tensor-core products (rqrcp_gemm_bf16x, FP32-level); the
- * sample QRCP with its norm downdates, the Householder panel, T and the
- * sample update stay in FP64, and R's diagonal is returned in FP64.
+ * sample QRCP generates its reflectors and downdates its norms in FP64 (the
+ * BF16-accurate sample itself is held and transformed in FP32), and the
+ * Householder panel, T and the sample update stay in FP64; R's diagonal is
+ * returned in FP64.
  *   dA     : in/out, m x n FP32, lda >= m; on exit R (FP32-rounded) on and
  *            above the diagonal and the reflectors below it
  *   d_jpvt : out, n int64;  d_tau : out, min(m, n) FP64
@@ -217,8 +219,9 @@ int trqrcp(rqrcp_handle_t handle, int64_t m, int64_t n, const double* dA, int64_
 
 /*
  * Mixed-precision TRQRCP (Alg. 6) on an FP32 matrix: BF16 sketch, the
- * products with A, Y and W^T as split-BF16 x3 tensor-core GEMMs, FP64 sample
- * QRCP, panel, T and R diagonal.  Outputs as in trqrcp with dY (m x k, ldy)
+ * products with A, Y and W^T as split-BF16 x3 tensor-core GEMMs; the sample
+ * QRCP's reflectors and norm downdates, the panel, T and R's diagonal in FP64
+ * (the sample held and transformed in FP32).  Outputs as in trqrcp with dY (m x k, ldy)
  * and dR (k x n, ldr) in FP32, d_tau and d_rdiag (k) in FP64.
  */
 int trqrcp_mixed(rqrcp_handle_t handle, int64_t m, int64_t n, const float* dA, int64_t lda,
@@ -252,7 +255,8 @@ typedef struct rqrcp_problem {
  * (sorted longest-first by algorithmic flops) and runs all of Alg. 6 on it:
  * Omega from Philox stream 1 with an FP32 Box-Muller transform, the sample
  * B = Omega A and every product with A, Y and W^T as FP32 products on the CUDA
- * cores, the sample QRCP, the Householder panel, T and the sample update of
+ * cores, the sample QRCP's reflectors and norm downdates (the sample held and
+ * transformed in FP32), the Householder panel, T and the sample update of
  * Eq. (3) in FP64.  Outputs per problem are laid out as trqrcp_mixed's (jpvt,
  * tau and rdiag FP64; Y and R FP32); they agree with trqrcp_mixed within FP32
  * rounding, not bit for bit (its products use the split-BF16 tensor-core GEMM).

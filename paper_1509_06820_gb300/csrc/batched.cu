@@ -17,8 +17,11 @@
 //   Omega     Philox4x32-10 stream 1 (as everywhere in this library), the
 //             Box-Muller transform in FP32 (it only steers pivots)
 //   B = Omega A                         FP32 products, stored FP64
-//   sample QRCP (Alg. 1 halted)        FP64, the same device code as the
-//                                       cooperative sample kernel
+//   sample QRCP (Alg. 1 halted)        reflectors generated and norms
+//                                       downdated in FP64, the sample held
+//                                       and the reflectors applied in FP32
+//                                       (the same device code as the
+//                                       cooperative sample kernel)
 //   A_hat = A(:, sel) - Y1 W1^T(:, sel) FP32 products, FP64 panel
 //   panel QR + T (Sec. 2.2)             FP64, the same device code as the
 //                                       cooperative panel kernel; reflectors
@@ -510,7 +513,7 @@ __device__ bool run_problem(const BatchKernelArgs& a, char* ts, TeamCtl* ctl, Gr
     {
       SampleQrcpArgs sa{Bblk, ell, ell, nc, bJ, swaps, at<double>(ts, L.cand),
                         at<double>(ts, L.candcol), bar, st};
-      sq::sample_qrcp_body(sa, g, G, smem);
+      sq::sample_qrcp_body<float>(sa, g, G, smem);
     }
     TEAM_SYNC();
     tr.mark(1);
@@ -821,7 +824,7 @@ constexpr size_t kBatchSmem = 200 * 1024;
 bool batch_fits(int64_t m, int64_t n, int b, int ell, int G) {
   if (b < 1 || b > MAXB || ell > 192 || G < 1) return false;
   const int64_t cs = (n + G - 1) / G, cp = (m + G - 1) / G;
-  if (sq::sample_qrcp_smem_bytes(ell, cs) > kBatchSmem) return false;
+  if (sq::sample_qrcp_smem_bytes(ell, cs, sizeof(float)) > kBatchSmem) return false;
   if (pn::panel_smem_bytes(cp, b) > kBatchSmem) return false;
   if (((size_t)b * b + b) * 8 > kBatchSmem) return false;
   return true;

@@ -126,6 +126,10 @@ struct SampleQrcpArgs {
   // many extra CTAs that do not exist (with a poll bound of a few ms), so the
   // first barrier runs out, RQRCP_INFO_TIMEOUT is set and every CTA returns
   int phantom = 0;
+  // nonzero: the sample is held and the reflectors applied in FP32 (a sample
+  // that is single-precision accurate to begin with); the reflectors are
+  // generated and the norms downdated in FP64 either way
+  int f32 = 0;
 };
 cudaError_t launch_sample_qrcp(const SampleQrcpArgs& a, int num_sms, cudaStream_t st);
 bool sample_qrcp_fits(int ell, int64_t nc, int num_sms);

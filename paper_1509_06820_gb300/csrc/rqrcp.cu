@@ -388,12 +388,13 @@ int begin(rqrcp_handle_t h, char op, int64_t m, int64_t n, int64_t k, int b, int
 }
 
 // ---------------------------------------------------------------- blocks
-int sample_step(Call& cl, double* Bblk, int ell, int64_t nc, int bJ) {
+int sample_step(Call& cl, double* Bblk, int ell, int64_t nc, int bJ, int f32 = 0) {
   double fl = 0.0;
   for (int i = 0; i < bJ && i < ell; ++i) fl += 4.0 * (ell - i) * (double)(nc - i - 1);
   PhaseScope ps(cl.h, PH_SAMPLE, fl);
   rq::SampleQrcpArgs a{Bblk, ell, ell, nc, bJ, cl.w.swaps, cl.w.cand, cl.w.candcol, cl.bar,
                        cl.status};
+  a.f32 = f32;
   CKL(1, rq::launch_sample_qrcp(a, cl.h->num_sms, cl.st));
   return RQRCP_OK;
 }
@@ -1346,7 +1347,7 @@ int rqrcp_factor_mixed(rqrcp_handle_t h, int64_t m, int64_t n, float* dA, int64_
     const int bJ = (int)std::min<int64_t>(b, k - j0);
     const int64_t nc = n - j0, n2 = nc - bJ, mJ = m - j0;
     double* Bblk = w.B + j0 * ell;
-    if ((r = sample_step(cl, Bblk, ell, nc, bJ))) return r;
+    if ((r = sample_step(cl, Bblk, ell, nc, bJ, 1))) return r;
     {
       PhaseScope ps(cl.h, PH_PERM, 0.0);
       CKL(3, rq::launch_apply_swaps_f32(dA, lda, m, j0, w.swaps, bJ, d_jpvt, w.map, w.permbuf32,
@@ -1442,7 +1443,7 @@ int trqrcp_mixed_run(Call& cl, int64_t m, int64_t n, const float* dA, int64_t ld
     const int bJ = (int)std::min<int64_t>(b, k - j0);
     const int64_t nc = n - j0, n2 = nc - bJ, mJ = m - j0;
     double* Bblk = w.B + j0 * ell;
-    if ((r = sample_step(cl, Bblk, ell, nc, bJ))) return r;
+    if ((r = sample_step(cl, Bblk, ell, nc, bJ, 1))) return r;
     {
       PhaseScope ps(cl.h, PH_PERM, 0.0);
       CKL(3, rq::launch_apply_swaps_f32(Wt, k, j0, j0, w.swaps, bJ, d_jpvt, w.map, w.permbuf32, cl.st));

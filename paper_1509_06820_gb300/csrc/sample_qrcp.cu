@@ -27,9 +27,10 @@ namespace {
 
 using namespace sq;
 
+template <typename T>
 __global__ void __launch_bounds__(NT, 1) sample_qrcp_kernel(SampleQrcpArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  sample_qrcp_body(a, blockIdx.x, gridDim.x, smem_raw);
+  sample_qrcp_body<T>(a, blockIdx.x, gridDim.x, smem_raw);
 }
 
 size_t smem_bytes(int ell, int64_t chunk) { return sample_qrcp_smem_bytes(ell, chunk); }
@@ -54,16 +55,19 @@ bool sample_qrcp_fits(int ell, int64_t nc, int num_sms) {
 cudaError_t launch_sample_qrcp(const SampleQrcpArgs& a, int num_sms, cudaStream_t st) {
   const int G = sample_grid(a.nc, num_sms);
   const int64_t chunk = (a.nc + G - 1) / G;
-  const size_t smem = smem_bytes(a.ell, chunk);
+  const size_t smem = sample_qrcp_smem_bytes(a.ell, chunk, a.f32 ? 4 : 8);
   if (a.ell > MAX_ELL || smem > kSmemLimit) return cudaErrorInvalidValue;
-  static std::atomic<uint64_t> attr_done{0};
-  cudaError_t e = ensure_smem_attr(sample_qrcp_kernel, (int)kSmemLimit, attr_done);
+  static std::atomic<uint64_t> attr_done_d{0}, attr_done_f{0};
+  const void* kern = a.f32 ? (const void*)sample_qrcp_kernel<float>
+                           : (const void*)sample_qrcp_kernel<double>;
+  cudaError_t e = a.f32 ? ensure_smem_attr(sample_qrcp_kernel<float>, (int)kSmemLimit, attr_done_f)
+                        : ensure_smem_attr(sample_qrcp_kernel<double>, (int)kSmemLimit, attr_done_d);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), st);
   if (e != cudaSuccess) return e;
   SampleQrcpArgs args = a;
   void* params[] = {&args};
-  return cudaLaunchCooperativeKernel((const void*)sample_qrcp_kernel, dim3((unsigned)G),
+  return cudaLaunchCooperativeKernel(kern, dim3((unsigned)G),
                                      dim3(NT), params, smem, st);
 }
 

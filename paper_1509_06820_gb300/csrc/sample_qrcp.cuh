@@ -17,6 +17,16 @@ constexpr int LPC = 8;                 // lanes per column
 constexpr int GROUPS = NT / LPC;       // columns processed concurrently
 constexpr int MAX_ELL = 192;
 constexpr double TOL3Z = 1.4901161193847656e-08;  // sqrt(2^-52)
+// the same safeguard for a sample held in single precision: sqrt(2^-23)
+constexpr double TOL3Z_F32 = 3.4526698300124393e-04;
+
+// Sum over groups of W lanes of a warp, in the type of the sample.
+template <int W, typename T>
+__device__ __forceinline__ T lane_group_sum(T v) {
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
 struct Cand {
   long long key; // order-preserving integer image of the norm (see sort_key);
@@ -51,7 +61,13 @@ __device__ __forceinline__ Cand warp_argmax(Cand c) {
 
 // The sample QRCP on CTA g of a group of G co-resident CTAs (the whole grid
 // of the standalone kernel, or one team of the persistent batched kernel);
-// smem_raw: sample_qrcp_smem_bytes(ell, chunk) bytes of dynamic shared memory.
+// smem_raw: sample_qrcp_smem_bytes(ell, chunk, sizeof(T)) bytes of dynamic
+// shared memory.  T is the type the sample is held and the reflectors are
+// applied in: double, or float for a sample that is only single-precision
+// accurate to begin with (the mixed-precision and served paths, whose sketch
+// is BF16 or FP32).  The reflectors are generated in FP64 and the norms are
+// kept and downdated in FP64 either way.
+template <typename T>
 __device__ __forceinline__ void sample_qrcp_body(const SampleQrcpArgs& a, int g, int G,
                                                  unsigned char* smem_raw) {
   const int ell = a.ell;
@@ -59,12 +75,14 @@ __device__ __forceinline__ void sample_qrcp_body(const SampleQrcpArgs& a, int g,
   const int64_t c_lo = (int64_t)g * chunk;
   const int ncol = (int)imax64(0, imin64(a.nc, c_lo + chunk) - c_lo);
 
-  double* col = reinterpret_cast<double*>(smem_raw);          // ell x chunk
-  double* vn = col + (size_t)ell * chunk;                       // chunk
+  double* vn = reinterpret_cast<double*>(smem_raw);             // chunk
   double* vn0 = vn + chunk;                                     // chunk
   long long* lpos = reinterpret_cast<long long*>(vn0 + chunk);  // chunk
   double* xv = reinterpret_cast<double*>(lpos + chunk);         // MAX_ELL (reflector v)
-  int* done = reinterpret_cast<int*>(xv + MAX_ELL);             // chunk
+  T* xt = reinterpret_cast<T*>(xv + MAX_ELL);                   // MAX_ELL (v in type T)
+  T* col = xt + MAX_ELL;                                        // ell x chunk
+  int* done = reinterpret_cast<int*>(col + (size_t)ell * chunk);  // chunk
+  constexpr double tol3z = sizeof(T) == 4 ? TOL3Z_F32 : TOL3Z;
   __shared__ Cand red[2];
   __shared__ double s_scal[4];
 
@@ -74,7 +92,7 @@ __device__ __forceinline__ void sample_qrcp_body(const SampleQrcpArgs& a, int g,
   // load the owned columns, logical position = index
   for (int64_t e = tid; e < (int64_t)ncol * ell; e += NT) {
     const int64_t c = e / ell, r = e % ell;
-    col[e] = __ldcg(a.B + (c_lo + c) * a.ldb + r);
+    col[e] = (T)__ldcg(a.B + (c_lo + c) * a.ldb + r);
   }
   for (int c = tid; c < ncol; c += NT) {
     lpos[c] = c_lo + c;
@@ -87,7 +105,10 @@ __device__ __forceinline__ void sample_qrcp_body(const SampleQrcpArgs& a, int g,
     const bool act = c < ncol;
     double s = 0.0;
     if (act)
-      for (int r = lig; r < ell; r += LPC) s = fma(col[r + c * ell], col[r + c * ell], s);
+      for (int r = lig; r < ell; r += LPC) {
+        const double x = col[r + c * ell];
+        s = fma(x, x, s);
+      }
     s = group_sum<LPC>(s);
     if (act && lig == 0) {
       double nv = sqrt(s);
@@ -154,7 +175,11 @@ __device__ __forceinline__ void sample_qrcp_body(const SampleQrcpArgs& a, int g,
       __syncwarp();  // every lane has read alpha before lane 0 overwrites it
       double beta, tau, scale;
       house_scalars_sq(alpha, s, &beta, &tau, &scale);
-      for (int r = i + tid; r < ell; r += 32) xv[r] = (r == i) ? 1.0 : xv[r] * scale;
+      for (int r = i + tid; r < ell; r += 32) {
+        const double v = (r == i) ? 1.0 : xv[r] * scale;
+        xv[r] = v;
+        xt[r] = (T)v;
+      }
       if (tid == 0) {
         s_scal[0] = beta;
         s_scal[1] = tau;
@@ -175,9 +200,9 @@ __device__ __forceinline__ void sample_qrcp_body(const SampleQrcpArgs& a, int g,
     __syncthreads();
     if (g == w.who && my_pivot >= 0) {
       // finish the pivot column: S(i, i) = beta, zeros below, position i
-      for (int r = i + 1 + tid; r < ell; r += NT) col[r + my_pivot * ell] = 0.0;
+      for (int r = i + 1 + tid; r < ell; r += NT) col[r + my_pivot * ell] = (T)0;
       if (tid == 0) {
-        col[i + my_pivot * ell] = beta;
+        col[i + my_pivot * ell] = (T)beta;
         done[my_pivot] = 1;
         lpos[my_pivot] = i;
       }
@@ -186,17 +211,18 @@ __device__ __forceinline__ void sample_qrcp_body(const SampleQrcpArgs& a, int g,
     // ---- apply H = I - tau v v^T to the trailing columns (LPC lanes per
     // column, rounds of GROUPS columns keep the shuffles warp-uniform)
     if (tau != 0.0) {
+      const T taut = (T)tau;
       for (int base = 0; base < ncol; base += GROUPS) {
         const int c = base + grp;
         const bool act = c < ncol && !done[c];
         if (__any_sync(0xffffffffu, act)) {
-          double* cc = col + (size_t)(act ? c : 0) * ell;
-          double s = 0.0;
+          T* cc = col + (size_t)(act ? c : 0) * ell;
+          T s = (T)0;
           if (act)
-            for (int r = i + lig; r < ell; r += LPC) s = fma(xv[r], cc[r], s);
-          s = group_sum<LPC>(s) * tau;
+            for (int r = i + lig; r < ell; r += LPC) s = fma(xt[r], cc[r], s);
+          s = lane_group_sum<LPC>(s) * taut;
           if (act)
-            for (int r = i + lig; r < ell; r += LPC) cc[r] = fma(-s, xv[r], cc[r]);
+            for (int r = i + lig; r < ell; r += LPC) cc[r] = fma(-s, xt[r], cc[r]);
         }
       }
       __syncthreads();
@@ -207,10 +233,10 @@ __device__ __forceinline__ void sample_qrcp_body(const SampleQrcpArgs& a, int g,
     int need_any = 0;
     for (int c = tid; c < ncol; c += NT) {
       if (done[c] || vn[c] == 0.0) continue;
-      const double rr = fabs(col[i + (size_t)c * ell]) / vn[c];
+      const double rr = fabs((double)col[i + (size_t)c * ell]) / vn[c];
       const double f = fmax(0.0, (1.0 - rr) * (1.0 + rr));
       const double q = vn[c] / vn0[c];
-      if (f * q * q <= TOL3Z) {
+      if (f * q * q <= tol3z) {
         vn[c] = -1.0;  // recompute below
         need_any = 1;
       } else {
@@ -223,8 +249,11 @@ __device__ __forceinline__ void sample_qrcp_body(const SampleQrcpArgs& a, int g,
         const bool act = c < ncol && !done[c] && vn[c] < 0.0;
         double t = 0.0;
         if (act) {
-          const double* cc = col + (size_t)c * ell;
-          for (int r = i + 1 + lig; r < ell; r += LPC) t = fma(cc[r], cc[r], t);
+          const T* cc = col + (size_t)c * ell;
+          for (int r = i + 1 + lig; r < ell; r += LPC) {
+            const double x = cc[r];
+            t = fma(x, x, t);
+          }
         }
         t = group_sum<LPC>(t);
         if (act && lig == 0) {
@@ -240,12 +269,14 @@ __device__ __forceinline__ void sample_qrcp_body(const SampleQrcpArgs& a, int g,
   // permuted (logical) order
   for (int c = 0; c < ncol; ++c) {
     const long long L = lpos[c];
-    for (int r = tid; r < ell; r += NT) a.B[L * a.ldb + r] = col[r + (size_t)c * ell];
+    for (int r = tid; r < ell; r += NT) a.B[L * a.ldb + r] = (double)col[r + (size_t)c * ell];
   }
 }
 
-__host__ __device__ inline size_t sample_qrcp_smem_bytes(int ell, int64_t chunk) {
-  return (size_t)chunk * ((size_t)ell * 8 + 8 + 8 + 8 + 4) + MAX_ELL * 8 + 16;
+// dynamic shared memory of sample_qrcp_body<T> (tsize = sizeof(T))
+__host__ __device__ inline size_t sample_qrcp_smem_bytes(int ell, int64_t chunk,
+                                                        size_t tsize = 8) {
+  return (size_t)chunk * ((size_t)ell * tsize + 8 + 8 + 8 + 4) + MAX_ELL * (8 + tsize) + 16;
 }
 
 }  // namespace sq
