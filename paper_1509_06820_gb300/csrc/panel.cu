@@ -3,7 +3,8 @@
 // upper-triangular compact-WY factor T with Q = I - Y T Y^T (Sec. 2.2).
 //
 // One cooperative launch.  CTA g keeps a contiguous range of panel rows in
-// shared memory.  Column j costs one grid barrier: before it every CTA
+// shared memory, staged by one TMA 2-D tile load when the panel's layout
+// allows it (see launch_panel), else by plain loads.  Column j costs one grid barrier: before it every CTA
 // publishes, over its rows below row j, the dot products of column j with
 // columns j..b_J-1 (the j-th entry is the squared tail norm), and the owner
 // of row j publishes that row.  After it every CTA adds the partial sums in
@@ -27,8 +28,15 @@ namespace {
 using namespace pn;
 
 __global__ void __launch_bounds__(NT, 1) panel_kernel(PanelArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   panel_body(a, blockIdx.x, gridDim.x, smem_raw);
+}
+
+// The same with the rows staged by a TMA tile load (see launch_panel).
+__global__ void __launch_bounds__(NT, 1)
+    panel_kernel_tma(const __grid_constant__ CUtensorMap tm, PanelArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  panel_body(a, blockIdx.x, gridDim.x, smem_raw, &tm);
 }
 
 }  // namespace
@@ -62,12 +70,29 @@ cudaError_t launch_panel(const PanelArgs& a, int num_sms, cudaStream_t st) {
   const int64_t chunk = (a.mJ + G - 1) / G;
   const size_t smem = panel_smem(chunk, a.bJ);
   if (smem > kPanelSmemLimit) return cudaErrorInvalidValue;
-  static std::atomic<uint64_t> attr_done{0};
-  cudaError_t e = ensure_smem_attr(panel_kernel, (int)kPanelSmemLimit, attr_done);
+  // TMA staging when the tile's alignment rules hold: base 16-byte aligned,
+  // leading dimension even (16-byte column stride), an even row chunk (its
+  // first row x 8 bytes a multiple of 16) of at most 256 rows, and the
+  // shared-memory tile within the limit
+  const int64_t chunk_t = tma_chunk(chunk);
+  const bool tma = (a.ld % 2 == 0) && ((reinterpret_cast<uintptr_t>(a.P) & 15) == 0) &&
+                   chunk_t <= 256 && panel_smem(chunk_t, a.bJ) <= kPanelSmemLimit;
+  CUtensorMap tm;
+  const bool use_tma =
+      tma && tc::make_map_f64_2d(&tm, a.P, (uint64_t)a.mJ, (uint64_t)a.bJ, (uint64_t)a.ld,
+                                 (int)chunk_t, a.bJ) == cudaSuccess;
+  static std::atomic<uint64_t> attr_done{0}, attr_done_t{0};
+  cudaError_t e = use_tma ? ensure_smem_attr(panel_kernel_tma, (int)kPanelSmemLimit, attr_done_t)
+                          : ensure_smem_attr(panel_kernel, (int)kPanelSmemLimit, attr_done);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), st);
   if (e != cudaSuccess) return e;
   PanelArgs args = a;
+  if (use_tma) {
+    void* params[] = {&tm, &args};
+    return cudaLaunchCooperativeKernel((const void*)panel_kernel_tma, dim3((unsigned)G), dim3(NT),
+                                       params, panel_smem(chunk_t, a.bJ), st);
+  }
   void* params[] = {&args};
   return cudaLaunchCooperativeKernel((const void*)panel_kernel, dim3((unsigned)G), dim3(NT), params,
                                      smem, st);

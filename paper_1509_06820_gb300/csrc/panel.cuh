@@ -5,6 +5,7 @@
 #pragma once
 
 #include "kernels.cuh"
+#include "tcgen05.cuh"
 
 namespace rq {
 namespace pn {
@@ -14,16 +15,30 @@ constexpr int MAXB = 128;
 constexpr int PARTS = 8;   // threads per column in the partial-sum reduction
 constexpr int RB = 40;     // loads in flight per thread in that reduction
 
+// Row chunk of a TMA-staged panel: the plain chunk rounded up to 2 (mod 4).
+// Even, so a CTA's first row is 16-byte aligned for the tile load; 2 (mod 4),
+// so the tile's pitch spreads a warp's column-strided accesses over eight of
+// the sixteen 8-byte banks (an odd pitch, used for plain loads, spreads them
+// over all sixteen).
+__host__ __device__ inline int64_t tma_chunk(int64_t chunk) { return chunk + ((6 - chunk % 4) % 4); }
+
 // The panel QR and T on CTA g of a group of G co-resident CTAs (the whole
 // grid of the standalone kernel, or one team of the persistent batched
 // kernel); smem_raw: panel_smem_bytes(chunk, bJ) bytes of dynamic shared memory.
+// tmap: when given, the CTA's rows are staged into shared memory by one TMA
+// 2-D tile load (box: chunk rows x bJ columns with chunk = tma_chunk(...), the
+// tile's pitch chunk); otherwise by plain loads into a layout of odd pitch.
 __device__ __forceinline__ void panel_body(const PanelArgs& a, int g, int G,
-                                           unsigned char* smem_raw) {
+                                           unsigned char* smem_raw,
+                                           const CUtensorMap* tmap = nullptr) {
   const int bJ = a.bJ;
-  const int64_t chunk = (a.mJ + G - 1) / G;
+  const int64_t chunk0 = (a.mJ + G - 1) / G;
+  const int64_t chunk = tmap ? tma_chunk(chunk0) : chunk0;
   const int64_t r_lo = (int64_t)g * chunk;
   const int nrow = (int)imax64(0, imin64(a.mJ, r_lo + chunk) - r_lo);
-  const int64_t ldp = chunk | 1;  // odd: rows of one column in distinct banks
+  // plain loads: odd pitch, so rows of one column sit in distinct banks; TMA:
+  // the box's pitch
+  const int64_t ldp = tmap ? chunk : (chunk | 1);
   double* Ps = reinterpret_cast<double*>(smem_raw);  // chunk x bJ, ld = ldp
   __shared__ double s_tot[MAXB];
   __shared__ double s_w[MAXB];
@@ -32,9 +47,31 @@ __device__ __forceinline__ void panel_body(const PanelArgs& a, int g, int G,
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nwarps = NT / 32;
 
-  for (int64_t e = tid; e < (int64_t)nrow * bJ; e += NT) {
-    const int64_t r = e % nrow, c = e / nrow;
-    Ps[r + c * ldp] = __ldcg(a.P + (r_lo + r) + c * a.ld);
+  if (tmap != nullptr) {
+    // one TMA tile per CTA (rows past the panel read as zero), completion
+    // counted on an mbarrier; the wait is bounded
+    __shared__ __align__(8) uint64_t s_mbar;
+    if (tid == 0) {
+      tc::mbar_init(&s_mbar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+      tc::mbar_expect_tx(&s_mbar, (uint32_t)(chunk * bJ * 8));
+      tc::tma_load_2d(Ps, tmap, (int)r_lo, 0, &s_mbar);
+    }
+    if (!tc::mbar_wait(&s_mbar, 0u)) {
+      if (tid == 0) {
+        atomicExch(&a.bar->abort, 1u);
+        atomicOr(a.status, RQRCP_INFO_TIMEOUT);
+      }
+      return;
+    }
+  } else {
+    for (int64_t e = tid; e < (int64_t)nrow * bJ; e += NT) {
+      const int64_t r = e % nrow, c = e / nrow;
+      Ps[r + c * ldp] = __ldcg(a.P + (r_lo + r) + c * a.ld);
+    }
   }
   __syncthreads();
 

@@ -1,4 +1,5 @@
-// Device helpers shared by the tcgen05 GEMMs (tc_gemm.cu, oz_gemm.cu):
+// Device helpers shared by the tcgen05 GEMMs (tc_gemm.cu, oz_gemm.cu) and
+// the TMA-staged panel (panel.cu):
 // mbarriers with bounded waits, TMA tile loads, tensor-memory fences, loads
 // and allocation, the shared-memory matrix descriptor of the 128-byte-swizzled
 // K-major layout, the BF16 MMA, and the host-side tensor-map encoder.
@@ -55,6 +56,16 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// 2-D tile load (no swizzle): box {box0, box1} at coordinates (c0, c1).
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -214,6 +225,25 @@ inline cudaError_t make_map_bf16_3d(CUtensorMap* map, const __nv_bfloat16* base,
   const cuuint32_t es[3] = {1, 1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(base), dims,
                   strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// 2-D FP64 map of a column-major rows x cols block (leading dimension ld
+// elements) with a box of box_rows x box_cols and no swizzle: one box lands
+// in shared memory as box_cols columns of box_rows contiguous doubles; rows
+// beyond the block read as zero.  Requirements checked by the caller: base
+// 16-byte aligned, ld even, box_rows even and at most 256, box_cols <= 256.
+inline cudaError_t make_map_f64_2d(CUtensorMap* map, const double* base, uint64_t rows,
+                                   uint64_t cols, uint64_t ld, int box_rows, int box_cols) {
+  EncodeTiledFn fn = encode_fn();
+  if (fn == nullptr) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 8};
+  const cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)box_cols};
+  const cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(base), dims,
+                  strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
