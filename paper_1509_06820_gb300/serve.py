@@ -428,7 +428,8 @@ class RingServer:
 
     def plan(self, req):
         b, p = self.tuner.choose(req.m, req.n, req.k) if self.tuner else (min(req.k, 64), 8)
-        req.b, req.p = min(b, req.k), p
+        # within the sizes the server was started for
+        req.b, req.p = min(b, req.k, self.limits[3]), min(p, self.limits[4])
         req.bucket = (req.m, req.n, req.k)
         return req
 
