@@ -272,8 +272,8 @@ typedef struct rqrcp_problem {
  * Limits: b <= 128, b + p <= 192, the sample of one block (l x n) and the panel
  * (m x b) held in the shared memory of the team's G CTAs (about 200 KB each).
  * Device conditions of all problems are ORed into the handle's info word.
- * The call waits for the handle's earlier work before it refills the staging
- * buffer (except during stream capture); team scratch and the device table
+ * The call waits for the previous call's table copy before it refills the
+ * staging buffer (except during stream capture); team scratch and the device table
  * grow on demand (a device allocation, not allowed during capture): reserve
  * them first with rqrcp_reserve_batched.  A captured launch reads the staging
  * buffer when it runs, so replay it before the next trqrcp_batched call on the

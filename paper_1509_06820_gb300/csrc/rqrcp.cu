@@ -55,6 +55,8 @@ struct rqrcp_handle_s {
   bool ring_running = false;
   bool bt_trace_clear = true;       // the batched phase timers restart at the next launch
   int bt_server_teams = 0;          // teams of the serving launch
+  cudaEvent_t bt_copy_ev = nullptr; // completion of the last table copy from the staging
+  bool bt_copy_pending = false;
   // rqrcp_factor_host: copy stream, its events, device pivots and tau
   cudaStream_t io_st = nullptr;
   std::vector<cudaEvent_t> io_ev;
@@ -543,6 +545,7 @@ int rqrcp_destroy(rqrcp_handle_t h) {
   if (h->bt_ctl) cudaFree(h->bt_ctl);
   if (h->bt_table) cudaFree(h->bt_table);
   if (h->bt_stage) cudaFreeHost(h->bt_stage);
+  if (h->bt_copy_ev) cudaEventDestroy(h->bt_copy_ev);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   if (h->io_st) cudaStreamSynchronize(h->io_st);
   for (cudaEvent_t e : h->io_ev) cudaEventDestroy(e);
@@ -1687,13 +1690,15 @@ int trqrcp_batched(rqrcp_handle_t h, int nprob, const rqrcp_problem* probs, int 
   });
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess) cs = cudaStreamCaptureStatusNone;
-  // the staging buffer may still feed the copy of the previous batch
-  if (cs == cudaStreamCaptureStatusNone) {
-    cudaError_t e = cudaStreamSynchronize(h->stream);
+  // the staging buffer may still feed the copy of the previous batch: wait
+  // for that copy (not for the whole stream)
+  if (cs == cudaStreamCaptureStatusNone && h->bt_copy_pending) {
+    cudaError_t e = cudaEventSynchronize(h->bt_copy_ev);
     if (e != cudaSuccess) {
       h->err = std::string("trqrcp_batched: ") + cudaGetErrorString(e);
       return RQRCP_ERR_CUDA;
     }
+    h->bt_copy_pending = false;
   }
   std::copy(qs.begin(), qs.end(), h->bt_stage);
   double fl = 0.0;
@@ -1703,6 +1708,11 @@ int trqrcp_batched(rqrcp_handle_t h, int nprob, const rqrcp_problem* probs, int 
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->bt_table, h->bt_stage, sizeof(rqrcp_problem) * nprob,
                         cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+    if (!h->bt_copy_ev) e = cudaEventCreateWithFlags(&h->bt_copy_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(h->bt_copy_ev, h->stream);
+    if (e == cudaSuccess) h->bt_copy_pending = true;
+  }
   rq::BatchLaunch bl = batch_launch(h, nt);
   bl.table = h->bt_table;
   bl.nprob = nprob;
