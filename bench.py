@@ -84,12 +84,14 @@ def parse():
     ap.add_argument("--legs", default="qr,e2e,cpu,emulated,rsrqrcp,qrcp,quality,mixed,truncated,serving",
                     help="comma-separated extra legs to run after the FP64 step")
     ap.add_argument("--case", choices=["panel", "gemm_bf16x", "gemm_f64x", "qrcp", "sample", "mixed",
-                                       "fp64peak", "batched", "serve"],
+                                       "rqrcp", "qr", "fp64peak", "batched", "serve"],
                     default=None,
                     help="run one small kernel case (for profiling) instead of the benchmark")
     ap.add_argument("--shape", default=None,
                     help="--case gemm_*: transA,transB,M,N,K (e.g. T,N,128,8000,8192)")
     ap.add_argument("--m", type=int, default=16384, help="--case panel: rows")
+    ap.add_argument("--emulated", action="store_true",
+                    help="--case rqrcp / qr: FP64 trailing update as tensor-core slice products")
     ap.add_argument("--reps", type=int, default=1, help="--case: timed repetitions")
     ap.add_argument("--team", type=int, default=16,
                     help="--case batched / serve: CTAs per team (serve: 0 = autotuned)")
@@ -808,6 +810,21 @@ def run_case(args):
             A.t().copy_(A0.t())
             rq.rqrcp_factor_mixed(A, args.b, args.p, 1, handle=h)
         out.update({"n": n, "b": args.b, "p": args.p})
+    elif args.case in ("rqrcp", "qr"):
+        import synth
+        n = args.n
+        if args.emulated:
+            h.set_fp64_emulation(True)
+        A0 = synth.graded_device(n, dev)
+        A = rq.empty_colmajor(n, n, dev)
+
+        def call():
+            A.t().copy_(A0.t())
+            if args.case == "rqrcp":
+                rq.rqrcp_factor(A, args.b, args.p, 1, handle=h)
+            else:
+                rq.qr_factor(A, args.b, handle=h)
+        out.update({"n": n, "b": args.b, "p": args.p, "emulated": args.emulated})
     elif args.case == "sample":
         ell, n = args.b + args.p, args.n
         B0 = rq.colmajor(torch.randn((ell, n), generator=g, device=dev, dtype=torch.float64))

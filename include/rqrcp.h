@@ -441,7 +441,7 @@ int rqrcp_sample_qrcp(rqrcp_handle_t handle, int ell, int64_t nc, int steps, dou
  * memory -- code running during CUDA graph stream capture, latency-critical
  * loops that must stay out of the driver's allocator, processes whose device
  * memory is owned by a pool or arena -- it runs the same sample QRCP with its
- * scratch in a fixed device array compiled into the library (about 467 KB,
+ * scratch in a fixed device array compiled into the library (about 477 KB,
  * held by every GPU that loads the library until exit), so it needs no
  * handle and calls no cudaMalloc/cudaFree.
  *   ell, nc, steps, dB, ldb, d_swaps : as rqrcp_sample_qrcp (ell <= 192)

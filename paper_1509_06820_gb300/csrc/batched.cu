@@ -521,10 +521,14 @@ __device__ bool run_problem(const BatchKernelArgs& a, char* ts, TeamCtl* ctl, Gr
     if (g == 0 && tid < 32) {
       int* pos = reinterpret_cast<int*>(smem);
       int* src = pos + 2 * MAXB;
+      int* sw = src + 2 * MAXB;
       int cnt = 0;
       const int lane = tid;
+      // the whole swap list in one round of loads (the loop is sequential)
+      for (int t = lane; t < bJ; t += 32) sw[t] = (int)__ldcg(swaps + t);
+      __syncwarp();
       for (int i = 0; i < bJ; ++i) {
-        const int s = (int)__ldcg(swaps + i);
+        const int s = sw[i];
         if (s == i) continue;
         // entries holding positions i and s (or -1)
         int ei = -1, es = -1;
@@ -807,7 +811,7 @@ size_t batch_team_bytes(const BatchLimits& lim, int G, BatchLayout* L) {
   l.map = take(sizeof(int) * (1 + 4 * b));
   l.cbuf = take(sizeof(float) * 2 * (2 * b) * k);
   l.jbuf = take(sizeof(int64_t) * 2 * b);
-  l.cand = take(sizeof(double) * 2 * G * 2);
+  l.cand = take(sizeof(double) * 2 * G * 4);
   l.candcol = take(sizeof(double) * 2 * G * ell);
   l.ppart = take(sizeof(double) * panel_partial_doubles(G, (int)b));
   l.rowj = take(sizeof(double) * 2 * b);

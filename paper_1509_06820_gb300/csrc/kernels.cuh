@@ -118,7 +118,7 @@ struct SampleQrcpArgs {
   int64_t nc;
   int steps;          // bJ
   int64_t* swaps;     // out: steps entries, partner position of each swap
-  double* cand;       // scratch: 2 * grid * 2 doubles (value, position)
+  double* cand;       // scratch: 2 * grid * 4 doubles (key, position, alpha, sigma2)
   double* candcol;    // scratch: 2 * grid * l doubles
   GridBarrier* bar;
   int* status;

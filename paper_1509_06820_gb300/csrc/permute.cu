@@ -16,16 +16,22 @@ namespace {
 
 // map layout: map[0] = number of moves; moves at map[1 + 2t] (dest), map[2 + 2t] (src);
 // the jpvt staging buffer follows at map[1 + 8*steps].
+constexpr int kMaxSwapSteps = 128;  // the largest block size
+
 __global__ void compose_swaps(const int64_t* __restrict__ swaps, int steps, int64_t* map) {
   // touched positions and the original position each holds, in shared
   // memory; one warp: the lanes search the touched list together
-  __shared__ int64_t pos[256];
-  __shared__ int64_t content[256];
+  __shared__ int64_t pos[2 * kMaxSwapSteps];
+  __shared__ int64_t content[2 * kMaxSwapSteps];
+  __shared__ int64_t sw[kMaxSwapSteps];
   if (blockIdx.x != 0 || threadIdx.x >= 32) return;
   const int lane = threadIdx.x;
+  // the whole swap list in one round of loads (the loop below is sequential)
+  for (int t = lane; t < steps; t += 32) sw[t] = swaps[t];
+  __syncwarp();
   int ntouch = 0;  // identical in every lane
   for (int i = 0; i < steps; ++i) {
-    const int64_t s = swaps[i];
+    const int64_t s = sw[i];
     if (s == i) continue;
     int ia = -1, ib = -1;  // positions are unique in pos[]: at most one hit each
     for (int t0 = 0; t0 < ntouch; t0 += 32) {
@@ -147,6 +153,7 @@ template <typename T, typename V>
 cudaError_t apply_swaps_t(T* A, int64_t lda, int64_t m, int64_t col0, const int64_t* swaps,
                           int steps, int64_t* jpvt, int64_t* map, T* buf, cudaStream_t st) {
   if (steps <= 0) return cudaSuccess;
+  if (steps > kMaxSwapSteps) return cudaErrorInvalidValue;
   compose_swaps<<<1, 32, 0, st>>>(swaps, steps, map);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -83,7 +83,7 @@ struct Work {
   int64_t* swaps = nullptr;   // b
   int64_t* map = nullptr;     // 1 + 10 b
   double* permbuf = nullptr;  // rows x 2b (column moves)
-  double* cand = nullptr;     // 2 x sms x 2
+  double* cand = nullptr;     // 2 x sms x 4
   double* candcol = nullptr;  // 2 x sms x l
   double* ppart = nullptr;    // panel partial sums
   double* rowj = nullptr;     // 2 b
@@ -166,7 +166,7 @@ Work carve(char op, int64_t m, int64_t n, int64_t k, int b, int p, int sms, char
     w.map = c.take<int64_t>(1 + 10 * bb);
     const int64_t prow = (op == 'R') ? m : k;
     w.permbuf = c.take<double>((size_t)std::max<int64_t>(prow, 1) * 2 * bb);
-    w.cand = c.take<double>((size_t)2 * sms * 2);
+    w.cand = c.take<double>((size_t)2 * sms * 4);
     w.candcol = c.take<double>((size_t)2 * sms * ell);
     w.W11 = c.take<double>((size_t)bb * bb);
   }
@@ -864,8 +864,24 @@ int rqrcp_factor_core(Call& cl, int64_t m, int64_t n, double* dA, int64_t lda, i
       // Eq. (3): B1 = S12 - S11 R11^{-1} R12, B2 = S22 (in place)
       CKL(1, rq::launch_w11(Bblk, ell, P, lda, bJ, w.W11, cl.flag, cl.status, cl.st));
       double* Bnext = Bblk + (int64_t)bJ * ell;
-      CK(gemm(cl, 'N', 'N', 2, bJ, n2, bJ, -1.0, w.W11, bJ, dA + j0 + (j0 + bJ) * lda, lda, 1.0,
-              Bnext, ell, cl.flag, 0));
+      const double* R12 = dA + j0 + (j0 + bJ) * lda;
+      if (w.slA != nullptr) {
+        // FP64 emulation: S12 -= W11 R12 as slice products on the tensor
+        // cores (not gated: W11 = 0 when the flag is raised, and the
+        // re-sample below then overwrites S12)
+        CKL(rq::oz_slice_launches(false, bJ),
+            rq::launch_oz_slice(w.W11, bJ, false, 0, bJ, bJ, w.slB, w.exB, cl.st));
+        CKL(rq::oz_slice_launches(true, bJ),
+            rq::launch_oz_slice(R12, lda, true, 0, n2, bJ, w.slA, w.exA, cl.st));
+        float* part = reinterpret_cast<float*>(w.skpart);
+        const size_t pcap = 2 * w.skcap;
+        rq::OzGemmArgs su{bJ,   n2,    rq::oz_kpad(bJ), w.slB, w.exB, w.slA,        w.exA, -1.0,
+                          1.0,  Bnext, ell,             cl.status, part, pcap,      cl.h->num_sms};
+        CKL(rq::oz_launches(bJ, n2, su.Kp, cl.h->num_sms, pcap), rq::launch_oz_gemm(su, cl.st));
+      } else {
+        CK(gemm(cl, 'N', 'N', 2, bJ, n2, bJ, -1.0, w.W11, bJ, R12, lda, 1.0, Bnext, ell, cl.flag,
+                0));
+      }
       // exactly singular R11: fresh sample of the trailing matrix (Alg. 5 step)
       const int64_t mt = m - j0 - bJ;
       CKL(1, rq::launch_gaussian(seed, kResampleStreamBase + J, ell, mt, w.omega, ell, cl.flag, cl.st));

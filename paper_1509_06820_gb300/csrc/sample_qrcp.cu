@@ -4,20 +4,26 @@
 // One cooperative launch per block of pivots.  CTA g owns a contiguous range
 // of sample columns and keeps them in shared memory for the whole launch;
 // columns never move between CTAs.  Each pivot step costs one grid barrier:
-//   1. every CTA publishes its best trailing column (norm, logical position)
-//      and that column's values;
+//   1. every CTA publishes its best trailing column: a record (norm, logical
+//      position, the column's row i and the sum of squares of its rows
+//      below i) and those rows;
 //   2. after the barrier every CTA picks the same winner (largest norm, lowest
-//      logical position on a tie), builds the same Householder reflector from
-//      the published column, records the swap in its own bookkeeping, applies
-//      the reflector to its trailing columns (8 lanes per column, shuffle
-//      reductions), downdates their norms and computes its next candidate.
+//      logical position on a tie), forms the reflector's scalars from the
+//      winner's record while the winner's rows load, records the swap in its
+//      own bookkeeping, applies the reflector to its trailing columns (4
+//      lanes per column in FP64, 8 in FP32, shuffle reductions), downdates
+//      their norms and computes its next candidate.
 // Swaps are tracked as logical positions; at the end every column is written
 // back to B at its final logical position, so B holds S = [S11 S12; 0 S22]
 // in the permuted order and `swaps` the partner position of each step.
 //
 // Norm update (reading of Alg. 1's trailing-norm step once row j is final):
-// nrm *= sqrt(max(0, 1 - (|s_ij|/nrm)^2)), recomputed exactly from rows
-// j+1.. when f * (nrm/nrm_ref)^2 <= sqrt(eps); identical to the oracle.
+// the oracle's nrm *= sqrt(f), f = max(0, 1 - (|s_ij|/nrm)^2), with an exact
+// recomputation from rows j+1.. when f * (nrm/nrm_ref)^2 <= sqrt(eps), kept
+// here on squared norms: nrm^2 -= s_ij^2, recomputed when
+// nrm^2 <= sqrt(eps) nrm_ref^2 -- the same quantities and the same test with
+// no division or square root (FP64 costs ~16 issue cycles per warp
+// instruction on this GPU); the two differ only in rounding.
 #include <mutex>
 
 #include "sample_qrcp.cuh"
@@ -84,8 +90,8 @@ cudaError_t launch_sample_qrcp(const SampleQrcpArgs& a, int num_sms, cudaStream_
 // (the candidate norms and columns, the grid barrier and a fallback status
 // word) lives in the file-scope device array below instead of handle memory.
 //
-// * Size: kNoAllocScratchDoubles doubles (2*152*2 + 2*152*192 + 8, about
-//   467 KB).  Every GPU that loads this library holds the array until the
+// * Size: kNoAllocScratchDoubles doubles (2*152*4 + 2*152*192 + 8, about
+//   477 KB).  Every GPU that loads this library holds the array until the
 //   process exits.  It covers ell <= 192 sample rows with at most 152 CTAs;
 //   larger ell is rejected.
 // * The array's host-side name is only a stand-in for the symbol; the first
@@ -102,7 +108,7 @@ cudaError_t launch_sample_qrcp(const SampleQrcpArgs& a, int num_sms, cudaStream_
 namespace {
 
 constexpr int kNoAllocMaxGrid = 152;  // CTAs (one per SM, capped)
-constexpr int64_t kNoAllocCand = 2LL * kNoAllocMaxGrid * 2;
+constexpr int64_t kNoAllocCand = 2LL * kNoAllocMaxGrid * 4;
 constexpr int64_t kNoAllocCandCol = 2LL * kNoAllocMaxGrid * MAX_ELL;
 // candidates, candidate columns, then 8 doubles for the barrier
 constexpr int64_t kNoAllocScratchDoubles = kNoAllocCand + kNoAllocCandCol + 8;

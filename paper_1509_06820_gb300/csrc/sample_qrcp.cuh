@@ -65,19 +65,25 @@ __device__ __forceinline__ Cand warp_argmax(Cand c) {
 // shared memory.  T is the type the sample is held and the reflectors are
 // applied in: double, or float for a sample that is only single-precision
 // accurate to begin with (the mixed-precision and served paths, whose sketch
-// is BF16 or FP32).  The reflectors are generated in FP64 and the norms are
-// kept and downdated in FP64 either way.
+// is BF16 or FP32).  The reflectors are generated in FP64 and the squared
+// norms are kept and downdated in FP64 either way.
 template <typename T>
 __device__ __forceinline__ void sample_qrcp_body(const SampleQrcpArgs& a, int g, int G,
                                                  unsigned char* smem_raw) {
+  // lanes per column in the reflector apply: FP64 is issue-bound, so fewer
+  // lanes (fewer shuffle-add levels per column); FP32 is latency-bound
+  constexpr int LPA = sizeof(T) == 4 ? 8 : 4;
+  constexpr int GRA = NT / LPA;
   const int ell = a.ell;
   const int64_t chunk = (a.nc + G - 1) / G;
   const int64_t c_lo = (int64_t)g * chunk;
   const int ncol = (int)imax64(0, imin64(a.nc, c_lo + chunk) - c_lo);
 
+  // vn: squared trailing norms (downdated); thr: tol3z x the squared norm at
+  // its last exact computation (the recompute threshold)
   double* vn = reinterpret_cast<double*>(smem_raw);             // chunk
-  double* vn0 = vn + chunk;                                     // chunk
-  long long* lpos = reinterpret_cast<long long*>(vn0 + chunk);  // chunk
+  double* thr = vn + chunk;                                     // chunk
+  long long* lpos = reinterpret_cast<long long*>(thr + chunk);  // chunk
   double* xv = reinterpret_cast<double*>(lpos + chunk);         // MAX_ELL (reflector v)
   T* xt = reinterpret_cast<T*>(xv + MAX_ELL);                   // MAX_ELL (v in type T)
   T* col = xt + MAX_ELL;                                        // ell x chunk
@@ -99,7 +105,8 @@ __device__ __forceinline__ void sample_qrcp_body(const SampleQrcpArgs& a, int g,
     done[c] = 0;
   }
   __syncthreads();
-  // exact initial norms (rounds of GROUPS columns keep the shuffles warp-uniform)
+  // exact initial squared norms (rounds of GROUPS columns keep the shuffles
+  // warp-uniform)
   for (int base = 0; base < ncol; base += GROUPS) {
     const int c = base + grp;
     const bool act = c < ncol;
@@ -111,17 +118,18 @@ __device__ __forceinline__ void sample_qrcp_body(const SampleQrcpArgs& a, int g,
       }
     s = group_sum<LPC>(s);
     if (act && lig == 0) {
-      double nv = sqrt(s);
-      if (!isfinite(nv)) atomicOr(a.status, RQRCP_INFO_NONFINITE);
-      vn[c] = nv;
-      vn0[c] = nv;
+      if (!isfinite(s)) atomicOr(a.status, RQRCP_INFO_NONFINITE);
+      vn[c] = s;
+      thr[c] = tol3z * s;
     }
   }
   __syncthreads();
 
   for (int i = 0; i < a.steps; ++i) {
-    // ---- local candidate: warp 0 scans the owned columns
-    double* cand = a.cand + (size_t)(i & 1) * G * 2;
+    // ---- local candidate: warp 0 scans the owned columns and publishes the
+    // best one's record (key, logical position, alpha = its row i, sigma2 =
+    // the sum of squares of its rows i+1..) and its rows i+1..
+    double* cand = a.cand + (size_t)(i & 1) * G * 4;
     double* ccol = a.candcol + (size_t)(i & 1) * G * ell;
     if (tid < 32) {
       Cand mine{sort_key(-2.0), LLONG_MAX, -1};
@@ -131,16 +139,28 @@ __device__ __forceinline__ void sample_qrcp_body(const SampleQrcpArgs& a, int g,
         if (better(t, mine)) mine = t;
       }
       mine = warp_argmax(mine);
+      double alpha = 0.0, s = 0.0;
+      if (mine.who >= 0) {
+        const T* pc = col + (size_t)mine.who * ell;
+        for (int r = i + 1 + tid; r < ell; r += 32) {
+          const double x = pc[r];
+          s = fma(x, x, s);
+        }
+        s = warp_sum(s);
+        alpha = pc[i];
+      }
       if (tid == 0) {
         red[0] = mine;
-        cand[2 * g] = __longlong_as_double(mine.key);       // bit pattern
-        cand[2 * g + 1] = __longlong_as_double(mine.pos);
+        cand[4 * g] = __longlong_as_double(mine.key);  // bit pattern
+        cand[4 * g + 1] = __longlong_as_double(mine.pos);
+        cand[4 * g + 2] = alpha;
+        cand[4 * g + 3] = s;
       }
     }
     __syncthreads();
     const int my_pivot = red[0].who;  // local column index of this CTA's candidate
     if (my_pivot >= 0)
-      for (int r = tid; r < ell; r += NT) ccol[(size_t)g * ell + r] = col[r + my_pivot * ell];
+      for (int r = i + 1 + tid; r < ell; r += NT) ccol[(size_t)g * ell + r] = col[r + my_pivot * ell];
     if (!grid_barrier(a.bar, G + a.phantom, a.status,
                       a.phantom ? kBarrierTestPolls : kBarrierMaxPolls)) {
       // the wait ran out (RQRCP_INFO_TIMEOUT is set): leave valid swap
@@ -152,35 +172,57 @@ __device__ __forceinline__ void sample_qrcp_body(const SampleQrcpArgs& a, int g,
     }
 
     // ---- global winner (identical in every CTA): warp 0 scans the G
-    // candidates, then builds the reflector from the winner's rows i..ell-1
+    // records, starts loading the winner's rows i+1.. and forms the reflector
+    // scalars from the winner's alpha and sigma2 while those loads are in flight
     if (tid < 32) {
       Cand w{sort_key(-3.0), LLONG_MAX, -1};
+      double wa = 0.0, ws = 0.0;
       for (int q = tid; q < G; q += 32) {
-        Cand t{__double_as_longlong(__ldcg(cand + 2 * q)),
-               __double_as_longlong(__ldcg(cand + 2 * q + 1)), q};
-        if (better(t, w)) w = t;
+        const double2 kp = __ldcg(reinterpret_cast<const double2*>(cand + 4 * q));
+        const double2 as = __ldcg(reinterpret_cast<const double2*>(cand + 4 * q + 2));
+        const Cand t{__double_as_longlong(kp.x), __double_as_longlong(kp.y), q};
+        if (better(t, w)) {
+          w = t;
+          wa = as.x;
+          ws = as.y;
+        }
       }
-      w = warp_argmax(w);
-      // the winner's rows i..ell-1; each lane rescales the rows it loaded
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        Cand d;
+        d.key = __shfl_xor_sync(0xffffffffu, w.key, o);
+        d.pos = __shfl_xor_sync(0xffffffffu, w.pos, o);
+        d.who = __shfl_xor_sync(0xffffffffu, w.who, o);
+        const double da = __shfl_xor_sync(0xffffffffu, wa, o);
+        const double ds = __shfl_xor_sync(0xffffffffu, ws, o);
+        if (better(d, w)) {
+          w = d;
+          wa = da;
+          ws = ds;
+        }
+      }
       const double* wc = ccol + (size_t)w.who * ell;
-      double s = 0.0;
-      for (int r = i + tid; r < ell; r += 32) {
-        const double x = __ldcg(wc + r);
-        xv[r] = x;
-        if (r > i) s = fma(x, x, s);
+      constexpr int RPL = MAX_ELL / 32;
+      double xr[RPL];
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) {
+        const int r = i + 1 + tid + 32 * q;
+        xr[q] = r < ell ? __ldcg(wc + r) : 0.0;
       }
-      s = warp_sum(s);
-      __syncwarp();
-      const double alpha = xv[i];
-      __syncwarp();  // every lane has read alpha before lane 0 overwrites it
       double beta, tau, scale;
-      house_scalars_sq(alpha, s, &beta, &tau, &scale);
-      for (int r = i + tid; r < ell; r += 32) {
-        const double v = (r == i) ? 1.0 : xv[r] * scale;
-        xv[r] = v;
-        xt[r] = (T)v;
+      house_scalars_sq(wa, ws, &beta, &tau, &scale);
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) {
+        const int r = i + 1 + tid + 32 * q;
+        if (r < ell) {
+          const double v = xr[q] * scale;
+          xv[r] = v;
+          xt[r] = (T)v;
+        }
       }
       if (tid == 0) {
+        xv[i] = 1.0;
+        xt[i] = (T)1;
         s_scal[0] = beta;
         s_scal[1] = tau;
         red[1] = w;
@@ -208,39 +250,41 @@ __device__ __forceinline__ void sample_qrcp_body(const SampleQrcpArgs& a, int g,
       }
     }
     __syncthreads();
-    // ---- apply H = I - tau v v^T to the trailing columns (LPC lanes per
-    // column, rounds of GROUPS columns keep the shuffles warp-uniform)
+    // ---- apply H = I - tau v v^T to the trailing columns (LPA lanes per
+    // column, rounds of GRA columns keep the shuffles warp-uniform)
     if (tau != 0.0) {
       const T taut = (T)tau;
-      for (int base = 0; base < ncol; base += GROUPS) {
-        const int c = base + grp;
+      const int ga = tid / LPA, la = tid % LPA;
+      for (int base = 0; base < ncol; base += GRA) {
+        const int c = base + ga;
         const bool act = c < ncol && !done[c];
         if (__any_sync(0xffffffffu, act)) {
           T* cc = col + (size_t)(act ? c : 0) * ell;
           T s = (T)0;
           if (act)
-            for (int r = i + lig; r < ell; r += LPC) s = fma(xt[r], cc[r], s);
-          s = lane_group_sum<LPC>(s) * taut;
+            for (int r = i + la; r < ell; r += LPA) s = fma(xt[r], cc[r], s);
+          s = lane_group_sum<LPA>(s) * taut;
           if (act)
-            for (int r = i + lig; r < ell; r += LPC) cc[r] = fma(-s, xt[r], cc[r]);
+            for (int r = i + la; r < ell; r += LPA) cc[r] = fma(-s, xt[r], cc[r]);
         }
       }
       __syncthreads();
     }
-    // ---- downdate the norms, one thread per column; a column whose
-    // downdated norm lost too many digits is recomputed exactly from rows
-    // i+1.. (rare: a second pass only when some column needs it)
+    // ---- downdate the squared norms, one thread per column: sigma2 -= x_i^2
+    // (the same test as nrm^2 (1 - (x_i/nrm)^2) / nrm_ref^2 <= tol3z, with no
+    // division or square root); a column that lost too many digits is
+    // recomputed exactly from rows i+1.. (rare: a second pass only when some
+    // column needs it)
     int need_any = 0;
     for (int c = tid; c < ncol; c += NT) {
       if (done[c] || vn[c] == 0.0) continue;
-      const double rr = fabs((double)col[i + (size_t)c * ell]) / vn[c];
-      const double f = fmax(0.0, (1.0 - rr) * (1.0 + rr));
-      const double q = vn[c] / vn0[c];
-      if (f * q * q <= tol3z) {
+      const double x = col[i + (size_t)c * ell];
+      const double v2 = fma(-x, x, vn[c]);
+      if (v2 <= thr[c]) {
         vn[c] = -1.0;  // recompute below
         need_any = 1;
       } else {
-        vn[c] *= sqrt(f);
+        vn[c] = v2;
       }
     }
     if (__syncthreads_or(need_any)) {
@@ -257,8 +301,8 @@ __device__ __forceinline__ void sample_qrcp_body(const SampleQrcpArgs& a, int g,
         }
         t = group_sum<LPC>(t);
         if (act && lig == 0) {
-          vn[c] = sqrt(t);
-          vn0[c] = vn[c];
+          vn[c] = t;
+          thr[c] = tol3z * t;
         }
       }
       __syncthreads();

@@ -3,9 +3,9 @@
 // and R11 are) by forward substitution over the columns of R11, one thread
 // per row of S11; the host then enqueues the GEMM S12 -= W11 R12 in place in
 // the sample buffer (S22 already sits below it).  If R11 has an exactly zero
-// diagonal entry the formula is undefined: the kernel raises the re-sample
-// flag, which gates that GEMM off and gates on a fresh sketch of the trailing
-// matrix (an Alg. 5 step).
+// diagonal entry the formula is undefined: the kernel sets W11 = 0 and raises
+// the re-sample flag, which gates that GEMM off and gates on a fresh sketch of
+// the trailing matrix (an Alg. 5 step).
 #include "kernels.cuh"
 
 namespace rq {
@@ -59,6 +59,11 @@ __global__ void w11_kernel(const double* __restrict__ S, int ell, const double* 
       *flag = 1;
       atomicOr(status, RQRCP_INFO_RESAMPLED);
     }
+    // W11 = 0: a product that is not gated by the flag leaves S12 unchanged
+    // for the re-sample to overwrite
+    const int r = blockIdx.x * W11_ROWS + warp;
+    if (r < bJ)
+      for (int c = lane; c < bJ; c += 32) W[r + c * bJ] = 0.0;
     return;
   }
   if (blockIdx.x == 0 && tid == 0) *flag = 0;
