@@ -188,14 +188,22 @@ struct PanelArgs {
   int bJ;
   double* tau;
   double* T;          // out, bJ x bJ, column-major, zeros below the diagonal
-  double* partial;    // scratch: grid * (bJ + 1) * 2 doubles + grid * bJ * bJ
-  double* rowj;       // scratch: bJ doubles
+  double* partial;    // scratch: panel_partial_doubles(grid, bJ) doubles
+  double* rowj;       // scratch: 2 bJ doubles
+  // with group > 1, ceil(grid / group) unsigned arrival counters follow the
+  // barrier word (zeroed with it by the launcher)
   GridBarrier* bar;
   int* status;
   // mixed precision: round the reflectors below the diagonal to FP32 values
   // before the Gram, and set tau_i = 2 / v_i^T v_i (kept 0 where the column
   // had a zero tail), so that T and tau describe exactly the stored vectors
   int round_f32;
+  // the column dots' grid reduction in two levels: the last CTA of each group
+  // of `group` consecutive CTAs to publish adds the group's partial sums, and
+  // every CTA then adds the groups' sums (0 or 1: every CTA adds all CTAs'
+  // partial sums).  launch_panel sets it (8 for grids of 32 CTAs or more);
+  // the barrier word must then be followed by ceil(grid / 8) unsigned ints.
+  int group = 0;
 };
 cudaError_t launch_panel(const PanelArgs& a, int num_sms, cudaStream_t st);
 size_t panel_partial_doubles(int grid, int bJ);

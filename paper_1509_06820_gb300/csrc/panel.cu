@@ -49,13 +49,16 @@ int panel_grid(int64_t mJ, int bJ, int num_sms) {
 }
 
 size_t panel_partial_doubles(int grid, int bJ) {
-  return (size_t)2 * grid * bJ + (size_t)grid * bJ * bJ + (size_t)bJ * bJ;
+  return (size_t)2 * grid * bJ + (size_t)grid * bJ * bJ + (size_t)bJ * bJ + (size_t)2 * grid * bJ;
 }
 
 static size_t panel_smem(int64_t chunk, int bJ) { return pn::panel_smem_bytes(chunk, bJ); }
 
 // dynamic shared memory limit: 227 KB per CTA less the kernel's static arrays
 constexpr size_t kPanelSmemLimit = 200 * 1024;
+constexpr int kPanelGroup = 8;
+// arrival counters that fit after the barrier word in the handle's state area
+constexpr int kPanelMaxGroups = 40;
 
 bool panel_fits(int64_t mJ, int bJ, int num_sms) {
   if (bJ < 1 || bJ > MAXB) return false;
@@ -89,9 +92,15 @@ cudaError_t launch_panel(const PanelArgs& a, int num_sms, cudaStream_t st) {
   cudaError_t e = use_tma ? ensure_smem_attr(panel_kernel_tma, (int)kPanelSmemLimit, attr_done_t)
                           : ensure_smem_attr(panel_kernel, (int)kPanelSmemLimit, attr_done);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), st);
-  if (e != cudaSuccess) return e;
+  // the column dots' reduction in two levels (groups of 8 CTAs) on grids of
+  // 32 CTAs or more: every CTA then reads ceil(G / 8) sums per column instead
+  // of G partial sums (the one-level form reads G^2 per column over the grid)
   PanelArgs args = a;
+  const int ngrp_g = (G + kPanelGroup - 1) / kPanelGroup;
+  args.group = (G >= 32 && ngrp_g <= kPanelMaxGroups) ? kPanelGroup : 0;
+  const int ngrp = args.group ? ngrp_g : 0;
+  e = cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier) + sizeof(unsigned) * ngrp, st);
+  if (e != cudaSuccess) return e;
   if (use_tma) {
     void* params[] = {&tm, &args};
     return cudaLaunchCooperativeKernel((const void*)panel_kernel_tma, dim3((unsigned)G), dim3(NT),

@@ -14,6 +14,10 @@ constexpr int NT = 256;
 constexpr int MAXB = 128;
 constexpr int PARTS = 8;   // threads per column in the partial-sum reduction
 constexpr int RB = 40;     // loads in flight per thread in that reduction
+constexpr int MAXGROUP = 16;  // largest CTA group of the two-level reduction
+// the two-level form pays for its extra round trips (the group's arrival
+// counter, its partial sums) only while many columns remain
+constexpr int GROUP_MIN_COLS = 64;
 
 // Row chunk of a TMA-staged panel: the plain chunk rounded up to 2 (mod 4).
 // Even, so a CTA's first row is 16-byte aligned for the tile load; 2 (mod 4),
@@ -75,8 +79,19 @@ __device__ __forceinline__ void panel_body(const PanelArgs& a, int g, int G,
   }
   __syncthreads();
 
-  // 2 x G x bJ (column dots), G x bJ x bJ (Gram partials), bJ x bJ (Gram)
+  // 2 x G x bJ (column dots), G x bJ x bJ (Gram partials), bJ x bJ (Gram),
+  // 2 x ceil(G / group) x bJ (the groups' sums of the column dots)
   double* part_base = a.partial;
+  // two-level reduction of the column dots: CTA g belongs to group g / C of
+  // cq consecutive CTAs; the last of them to publish adds the group's partial
+  // sums in increasing CTA order (no waiting: an arrival counter per group,
+  // after the barrier word, says which CTA is last)
+  const int C = (a.group > 1 && a.group <= MAXGROUP) ? a.group : 1;
+  const int ngrp = (G + C - 1) / C;
+  const int grp_q = g / C, grp_q0 = grp_q * C, grp_cq = min(C, G - grp_q0);
+  double* gsum_base = part_base + (size_t)2 * G * bJ + (size_t)G * bJ * bJ + (size_t)bJ * bJ;
+  unsigned* grp_cnt = reinterpret_cast<unsigned*>(a.bar + 1);
+  __shared__ int s_last;
   // partial dots of column j with columns j..bJ-1 over owned rows below row j
   auto publish = [&](int j) {
     double* part = part_base + (size_t)(j & 1) * G * bJ + (size_t)g * bJ;
@@ -103,54 +118,96 @@ __device__ __forceinline__ void panel_body(const PanelArgs& a, int g, int G,
       double* rowj = a.rowj + (size_t)(j & 1) * bJ;
       for (int c = j + tid; c < bJ; c += NT) rowj[c] = Ps[(j - r_lo) + c * ldp];
     }
+    if (C > 1 && bJ - j >= GROUP_MIN_COLS) {
+      // every group member adds one to the counter per grouped step, so the
+      // last of a step sees a multiple of cq, less one
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        const unsigned old = atomicAdd(grp_cnt + grp_q, 1u);
+        s_last = (old % (unsigned)grp_cq) == (unsigned)(grp_cq - 1);
+      }
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+        const double* pq = part_base + (size_t)(j & 1) * G * bJ + (size_t)grp_q0 * bJ;
+        double* gs = gsum_base + ((size_t)(j & 1) * ngrp + grp_q) * bJ;
+        for (int c = j + tid; c < bJ; c += NT) {
+          double v[MAXGROUP];
+#pragma unroll
+          for (int u = 0; u < MAXGROUP; ++u) v[u] = u < grp_cq ? __ldcg(pq + (size_t)u * bJ + c) : 0.0;
+          double t = v[0];
+#pragma unroll
+          for (int u = 1; u < MAXGROUP; ++u)
+            if (u < grp_cq) t += v[u];
+          gs[c] = t;
+        }
+      }
+    }
   };
 
   publish(0);
   for (int j = 0; j < bJ; ++j) {
     if (!grid_barrier(a.bar, G, a.status)) return;
-    // fixed-order reduction of the partial dots: PARTS threads per column,
-    // thread pp adds CTAs q = pp, pp + PARTS, ... in increasing order with up
-    // to RB loads in flight, then the PARTS sums are added in order
-    const double* part = part_base + (size_t)(j & 1) * G * bJ;
+    // fixed-order reduction of the partial dots (or of the groups' sums):
+    // PARTS threads per column, thread pp adds sources q = pp, pp + PARTS, ...
+    // in increasing order with up to RB loads in flight, then the PARTS sums
+    // are added in order
     const int ncols = bJ - j;
+    const bool grouped = C > 1 && ncols >= GROUP_MIN_COLS;
+    const double* part = grouped ? gsum_base + (size_t)(j & 1) * ngrp * bJ
+                                 : part_base + (size_t)(j & 1) * G * bJ;
+    const int nsrc = grouped ? ngrp : G;
     const int parts = imin64(PARTS, imax64(1, NT / ncols));
-    for (int e = tid; e < parts * ncols; e += NT) {
-      const int c = j + e % ncols, pp = e / ncols;
+    // warp-uniform rounds, so that the adds stop (by warp vote) at each
+    // thread's own source count: FP64 adds are the cost here
+    const int total = parts * ncols;
+    for (int e0 = warp * 32; e0 < total; e0 += NT) {
+      const int e = e0 + lane;
+      const bool act = e < total;
+      const int c = j + (act ? e % ncols : 0), pp = act ? e / ncols : 0;
+      const int cnt = act ? (nsrc - pp + parts - 1) / parts : 0;  // sources pp, pp + parts, ...
       double s = 0.0;
-      for (int q0 = pp; q0 < G; q0 += RB * parts) {
+      for (int u0 = 0; __any_sync(0xffffffffu, u0 < cnt); u0 += RB) {
         double v[RB];
 #pragma unroll
-        for (int u = 0; u < RB; ++u) {
-          const int q = q0 + u * parts;
-          v[u] = (q < G) ? __ldcg(part + (size_t)q * bJ + c) : 0.0;
-        }
+        for (int u = 0; u < RB; ++u)
+          v[u] = (u0 + u < cnt) ? __ldcg(part + (size_t)(pp + (u0 + u) * parts) * bJ + c) : 0.0;
 #pragma unroll
-        for (int u = 0; u < RB; ++u) s += v[u];
+        for (int u = 0; u < RB; ++u) {
+          if (!__any_sync(0xffffffffu, u0 + u < cnt)) break;
+          if (u0 + u < cnt) s += v[u];
+        }
       }
-      s_part[pp][c] = s;
+      if (act) s_part[pp][c] = s;
     }
     __syncthreads();
     const double* rowj = a.rowj + (size_t)(j & 1) * bJ;
-    for (int c = j + tid; c < bJ; c += NT) {
-      double s = 0.0;
-      for (int pp = 0; pp < parts; ++pp) s += s_part[pp][c];
-      s_tot[c] = s;
-      s_w[c] = __ldcg(rowj + c);  // row j of the panel before this step
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double beta, tau, scale;
-      house_scalars_sq(s_w[j], s_tot[j], &beta, &tau, &scale);
-      s_scal[0] = beta;
-      s_scal[1] = tau;
-      s_scal[2] = scale;
-      if (g == 0) a.tau[j] = tau;
+    if (warp == 0) {
+      // column j: its total and alpha = row j, then the reflector's scalars
+      // (a dependent FP64 chain, overlapped with the other warps' work)
+      if (lane == 0) {
+        double sj = 0.0;
+        for (int pp = 0; pp < parts; ++pp) sj += s_part[pp][j];
+        double beta, tau, scale;
+        house_scalars_sq(__ldcg(rowj + j), sj, &beta, &tau, &scale);
+        s_scal[0] = beta;
+        s_scal[1] = tau;
+        s_scal[2] = scale;
+        if (g == 0) a.tau[j] = tau;
+      }
+    } else {
+      for (int c = j + 1 + tid - 32; c < bJ; c += NT - 32) {
+        double s = 0.0;
+        for (int pp = 0; pp < parts; ++pp) s += s_part[pp][c];
+        s_tot[c] = s;
+        s_w[c] = __ldcg(rowj + c);  // row j of the panel before this step
+      }
     }
     __syncthreads();
     const double beta = s_scal[0], tau = s_scal[1], scale = s_scal[2];
     // w_c = tau * v^T a_c for c > j (v_j = 1, v_r = scale x_r below)
     for (int c = j + 1 + tid; c < bJ; c += NT) s_w[c] = tau * (s_w[c] + scale * s_tot[c]);
-    __syncthreads();
     const int64_t jl = (int64_t)j - r_lo;  // local index of row j (may be outside)
     const int64_t rstart = imax64(0, jl + 1);
     // scale column j into v, then a_rc -= v_r w_c on owned rows below j

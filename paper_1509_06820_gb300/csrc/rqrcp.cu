@@ -21,7 +21,8 @@ struct rqrcp_handle_s {
   int dev_sms = 1;       // SMs of the device
   char* ws = nullptr;
   size_t ws_bytes = 0;
-  int* state = nullptr;  // [0] status word, [1] re-sample flag; barrier at byte 64
+  int* state = nullptr;  // [0] status word, [1] re-sample flag; barrier at byte 64,
+                         // then the panel's group arrival counters (up to 40)
   std::string err;
   // instrumentation
   bool prof = false;
@@ -135,9 +136,11 @@ struct Work {
   size_t tslcapB = 0;
   // FP64 emulation on the tensor cores: operand slices and exponents
   __nv_bfloat16* slA = nullptr;
+  size_t slcapA = 0;
   __nv_bfloat16* slB = nullptr;
-  int* exA = nullptr;
-  int* exB = nullptr;
+  size_t slcapB = 0;
+  int* exA = nullptr;  // exponents of slA's rows (also of the mixed modes' R12 slices)
+  int* exB = nullptr;  // exponents of slB's rows (also of the mixed modes' W11 slices)
   size_t bytes = 0;
 };
 
@@ -227,6 +230,8 @@ Work carve(char op, int64_t m, int64_t n, int64_t k, int b, int p, int sms, char
     w.tslcapB = std::max(rq::tc_slice_elems(n, m, 3), rq::tc_slice_elems(k, m, 3));
     w.tslA = c.take<__nv_bfloat16>(w.tslcapA);
     w.tslB = c.take<__nv_bfloat16>(w.tslcapB);
+    w.exA = c.take<int>(n);
+    w.exB = c.take<int>(bb);
   } else if (op == 'G') {
     // split-BF16 GEMM of op(A) (m x k) and op(B) (k x n)
     w.tccap = (size_t)32 * (size_t)std::min<int64_t>(m * n, (int64_t)sms * 128 * 128);
@@ -259,14 +264,18 @@ Work carve(char op, int64_t m, int64_t n, int64_t k, int b, int p, int sms, char
     w.tslcapB = rq::tc_slice_elems(n, m, 3);
     w.tslA = c.take<__nv_bfloat16>(w.tslcapA);
     w.tslB = c.take<__nv_bfloat16>(w.tslcapB);
+    w.exA = c.take<int>(n);
+    w.exB = c.take<int>(bb);
   }
   if (emul && (op == 'R' || op == 'Q')) {
     // slices of the trailing matrix A2^T (n rows of m) and of Y, W^T, and W^T itself
-    w.slA = c.take<__nv_bfloat16>(rq::oz_slice_elems(n, m));
+    w.slcapA = rq::oz_slice_elems(n, m);
+    w.slA = c.take<__nv_bfloat16>(w.slcapA);
     // Y sliced twice: b rows of m (as op(B) of Z^T), m rows of b (as op(A) of the update)
     // (and the l x m Omega of the sketch)
-    w.slB = c.take<__nv_bfloat16>(std::max(rq::oz_slice_elems(std::max<int64_t>(bb, ell), m),
-                                           rq::oz_slice_elems(m, bb)));
+    w.slcapB = std::max(rq::oz_slice_elems(std::max<int64_t>(bb, ell), m),
+                        rq::oz_slice_elems(m, bb));
+    w.slB = c.take<__nv_bfloat16>(w.slcapB);
     w.exA = c.take<int>(std::max(n, m));
     w.exB = c.take<int>(std::max(n, m));
   }
@@ -442,6 +451,33 @@ int trailing_update_emulated(Call& cl, const double* P, int64_t ld, int64_t mJ, 
   rq::OzGemmArgs u{mJ, n2, rq::oz_kpad(bJ), w.slB,  w.exB, w.slA,        w.exA, -1.0, 1.0,
                    A2, ld, cl.status,       part,   pcap,  cl.h->num_sms};
   CKL(rq::oz_launches(mJ, n2, u.Kp, cl.h->num_sms, pcap), rq::launch_oz_gemm(u, cl.st));
+  return RQRCP_OK;
+}
+
+// Eq. (3)'s product S12 -= W11 R12 (W11 bJ x bJ, R12 bJ x n2 with leading
+// dimension ldr, S12 bJ x n2 with leading dimension lds): FP64-accurate slice
+// products on the tensor cores (oz_gemm.cu) when the slice buffers given hold
+// both operands, else the FP64 GEMM gated off by the re-sample flag.  The
+// tensor-core product is not gated: W11 = 0 when the flag is raised, so it
+// leaves S12 unchanged.
+int sample_update_product(Call& cl, const double* W11, int bJ, const double* R12, int64_t ldr,
+                          int64_t n2, double* S12, int64_t lds, __nv_bfloat16* slW, size_t capW,
+                          int* exW, __nv_bfloat16* slR, size_t capR, int* exR) {
+  if (n2 <= 0) return RQRCP_OK;
+  if (slW != nullptr && slR != nullptr && exW != nullptr && exR != nullptr &&
+      rq::oz_slice_elems(bJ, bJ) <= capW && rq::oz_slice_elems(n2, bJ) <= capR) {
+    CKL(rq::oz_slice_launches(false, bJ),
+        rq::launch_oz_slice(W11, bJ, false, 0, bJ, bJ, slW, exW, cl.st));
+    CKL(rq::oz_slice_launches(true, bJ),
+        rq::launch_oz_slice(R12, ldr, true, 0, n2, bJ, slR, exR, cl.st));
+    float* part = reinterpret_cast<float*>(cl.w.skpart);
+    const size_t pcap = 2 * cl.w.skcap;
+    rq::OzGemmArgs su{bJ,  n2,  rq::oz_kpad(bJ), slW,       exW,  slR,  exR,  -1.0,
+                      1.0, S12, lds,             cl.status, part, pcap, cl.h->num_sms};
+    CKL(rq::oz_launches(bJ, n2, su.Kp, cl.h->num_sms, pcap), rq::launch_oz_gemm(su, cl.st));
+    return RQRCP_OK;
+  }
+  CK(gemm(cl, 'N', 'N', 2, bJ, n2, bJ, -1.0, W11, bJ, R12, ldr, 1.0, S12, lds, cl.flag, 0));
   return RQRCP_OK;
 }
 
@@ -864,24 +900,11 @@ int rqrcp_factor_core(Call& cl, int64_t m, int64_t n, double* dA, int64_t lda, i
       // Eq. (3): B1 = S12 - S11 R11^{-1} R12, B2 = S22 (in place)
       CKL(1, rq::launch_w11(Bblk, ell, P, lda, bJ, w.W11, cl.flag, cl.status, cl.st));
       double* Bnext = Bblk + (int64_t)bJ * ell;
-      const double* R12 = dA + j0 + (j0 + bJ) * lda;
-      if (w.slA != nullptr) {
-        // FP64 emulation: S12 -= W11 R12 as slice products on the tensor
-        // cores (not gated: W11 = 0 when the flag is raised, and the
-        // re-sample below then overwrites S12)
-        CKL(rq::oz_slice_launches(false, bJ),
-            rq::launch_oz_slice(w.W11, bJ, false, 0, bJ, bJ, w.slB, w.exB, cl.st));
-        CKL(rq::oz_slice_launches(true, bJ),
-            rq::launch_oz_slice(R12, lda, true, 0, n2, bJ, w.slA, w.exA, cl.st));
-        float* part = reinterpret_cast<float*>(w.skpart);
-        const size_t pcap = 2 * w.skcap;
-        rq::OzGemmArgs su{bJ,   n2,    rq::oz_kpad(bJ), w.slB, w.exB, w.slA,        w.exA, -1.0,
-                          1.0,  Bnext, ell,             cl.status, part, pcap,      cl.h->num_sms};
-        CKL(rq::oz_launches(bJ, n2, su.Kp, cl.h->num_sms, pcap), rq::launch_oz_gemm(su, cl.st));
-      } else {
-        CK(gemm(cl, 'N', 'N', 2, bJ, n2, bJ, -1.0, w.W11, bJ, R12, lda, 1.0, Bnext, ell, cl.flag,
-                0));
-      }
+      // with FP64 emulation on the tensor cores (the re-sample below then
+      // overwrites S12 when the flag is raised), else FP64
+      if ((r = sample_update_product(cl, w.W11, bJ, dA + j0 + (j0 + bJ) * lda, lda, n2, Bnext, ell,
+                                     w.slB, w.slcapB, w.exB, w.slA, w.slcapA, w.exA)))
+        return r;
       // exactly singular R11: fresh sample of the trailing matrix (Alg. 5 step)
       const int64_t mt = m - j0 - bJ;
       CKL(1, rq::launch_gaussian(seed, kResampleStreamBase + J, ell, mt, w.omega, ell, cl.flag, cl.st));
@@ -1393,13 +1416,16 @@ int rqrcp_factor_mixed(rqrcp_handle_t h, int64_t m, int64_t n, float* dA, int64_
       CK(tcgemm(cl, 'N', 'N', mJ, n2, bJ, -1.0f, w.Y32, m, w.W32, bJ, 1.0f, A2, lda, 3));
     }
     if (j0 + bJ < k) {
-      // Eq. (3) in FP64 with R11 from the FP64 panel and R12 widened from FP32;
-      // an exactly singular R11 keeps S12 (no re-sample in this mode)
+      // Eq. (3) with R11 from the FP64 panel and R12 widened from FP32, the
+      // product FP64-accurate on the tensor cores (the split-BF16 slice
+      // buffers are free here); an exactly singular R11 keeps S12 (no
+      // re-sample in this mode)
       PhaseScope ps(cl.h, PH_SUPD, (double)bJ * bJ * bJ / 3.0 + 2.0 * bJ * bJ * (double)n2);
       CKL(1, rq::launch_w11(Bblk, ell, w.P64, m, bJ, w.W11, cl.flag, cl.status, cl.st));
       CKL(1, rq::launch_convert_f32_f64(A2, lda, w.R12, bJ, bJ, n2, cl.st));
-      CK(gemm(cl, 'N', 'N', 2, bJ, n2, bJ, -1.0, w.W11, bJ, w.R12, bJ, 1.0,
-              Bblk + (int64_t)bJ * ell, ell, cl.flag, 0));
+      if ((r = sample_update_product(cl, w.W11, bJ, w.R12, bJ, n2, Bblk + (int64_t)bJ * ell, ell,
+                                     w.tslA, w.tslcapA, w.exB, w.tslB, w.tslcapB, w.exA)))
+        return r;
     }
   }
   return RQRCP_OK;
@@ -1512,8 +1538,9 @@ int trqrcp_mixed_run(Call& cl, int64_t m, int64_t n, const float* dA, int64_t ld
       PhaseScope ps(cl.h, PH_SUPD, (double)bJ * bJ * bJ / 3.0 + 2.0 * bJ * bJ * (double)n2);
       CKL(1, rq::launch_w11(Bblk, ell, w.P64, m, bJ, w.W11, cl.flag, cl.status, cl.st));
       CKL(1, rq::launch_convert_f32_f64(dR + j0 + (j0 + bJ) * ldr, ldr, w.R12, bJ, bJ, n2, cl.st));
-      CK(gemm(cl, 'N', 'N', 2, bJ, n2, bJ, -1.0, w.W11, bJ, w.R12, bJ, 1.0,
-              Bblk + (int64_t)bJ * ell, ell, cl.flag, 0));
+      if ((r = sample_update_product(cl, w.W11, bJ, w.R12, bJ, n2, Bblk + (int64_t)bJ * ell, ell,
+                                     w.tslA, w.tslcapA, w.exB, w.tslB, w.tslcapB, w.exA)))
+        return r;
     }
   }
   return RQRCP_OK;
