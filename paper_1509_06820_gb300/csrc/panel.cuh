@@ -16,8 +16,10 @@ constexpr int PARTS = 8;   // threads per column in the partial-sum reduction
 constexpr int RB = 40;     // loads in flight per thread in that reduction
 constexpr int MAXGROUP = 16;  // largest CTA group of the two-level reduction
 // the two-level form pays for its extra round trips (the group's arrival
-// counter, its partial sums) only while many columns remain
-constexpr int GROUP_MIN_COLS = 64;
+// counter, its partial sums) only while many columns remain; below it,
+// warps 1.. take at most G x 54 / 224 <= 37 sources per thread (one round of
+// RB loads)
+constexpr int GROUP_MIN_COLS = 56;
 
 // Row chunk of a TMA-staged panel: the plain chunk rounded up to 2 (mod 4).
 // Even, so a CTA's first row is 16-byte aligned for the tile load; 2 (mod 4),
@@ -44,7 +46,6 @@ __device__ __forceinline__ void panel_body(const PanelArgs& a, int g, int G,
   // the box's pitch
   const int64_t ldp = tmap ? chunk : (chunk | 1);
   double* Ps = reinterpret_cast<double*>(smem_raw);  // chunk x bJ, ld = ldp
-  __shared__ double s_tot[MAXB];
   __shared__ double s_w[MAXB];
   __shared__ double s_part[PARTS][MAXB];
   __shared__ double s_scal[4];
@@ -149,65 +150,66 @@ __device__ __forceinline__ void panel_body(const PanelArgs& a, int g, int G,
   publish(0);
   for (int j = 0; j < bJ; ++j) {
     if (!grid_barrier(a.bar, G, a.status)) return;
-    // fixed-order reduction of the partial dots (or of the groups' sums):
-    // PARTS threads per column, thread pp adds sources q = pp, pp + PARTS, ...
-    // in increasing order with up to RB loads in flight, then the PARTS sums
-    // are added in order
+    // fixed-order reduction of the partial dots (or of the groups' sums).
+    // Warp 0 adds column j's sources (lane-strided, then a shuffle tree) and
+    // forms the reflector's scalars from them -- a dependent FP64 chain --
+    // while warps 1.. add the other columns' sources: PARTS threads per
+    // column, thread pp adds sources q = pp, pp + PARTS, ... in increasing
+    // order with up to RB loads in flight; the PARTS sums are added in order.
     const int ncols = bJ - j;
     const bool grouped = C > 1 && ncols >= GROUP_MIN_COLS;
     const double* part = grouped ? gsum_base + (size_t)(j & 1) * ngrp * bJ
                                  : part_base + (size_t)(j & 1) * G * bJ;
     const int nsrc = grouped ? ngrp : G;
-    const int parts = imin64(PARTS, imax64(1, NT / ncols));
-    // warp-uniform rounds, so that the adds stop (by warp vote) at each
-    // thread's own source count: FP64 adds are the cost here
-    const int total = parts * ncols;
-    for (int e0 = warp * 32; e0 < total; e0 += NT) {
-      const int e = e0 + lane;
-      const bool act = e < total;
-      const int c = j + (act ? e % ncols : 0), pp = act ? e / ncols : 0;
-      const int cnt = act ? (nsrc - pp + parts - 1) / parts : 0;  // sources pp, pp + parts, ...
-      double s = 0.0;
-      for (int u0 = 0; __any_sync(0xffffffffu, u0 < cnt); u0 += RB) {
-        double v[RB];
-#pragma unroll
-        for (int u = 0; u < RB; ++u)
-          v[u] = (u0 + u < cnt) ? __ldcg(part + (size_t)(pp + (u0 + u) * parts) * bJ + c) : 0.0;
-#pragma unroll
-        for (int u = 0; u < RB; ++u) {
-          if (!__any_sync(0xffffffffu, u0 + u < cnt)) break;
-          if (u0 + u < cnt) s += v[u];
-        }
-      }
-      if (act) s_part[pp][c] = s;
-    }
-    __syncthreads();
     const double* rowj = a.rowj + (size_t)(j & 1) * bJ;
+    const int nc1 = ncols - 1;                            // columns after j
+    const int parts = imin64(PARTS, imax64(1, (NT - 32) / imax64(1, nc1)));
     if (warp == 0) {
-      // column j: its total and alpha = row j, then the reflector's scalars
-      // (a dependent FP64 chain, overlapped with the other warps' work)
+      const double alpha = __ldcg(rowj + j);
+      double sj = 0.0;
+      for (int q = lane; q < nsrc; q += 32) sj += __ldcg(part + (size_t)q * bJ + j);
+      sj = warp_sum(sj);
       if (lane == 0) {
-        double sj = 0.0;
-        for (int pp = 0; pp < parts; ++pp) sj += s_part[pp][j];
         double beta, tau, scale;
-        house_scalars_sq(__ldcg(rowj + j), sj, &beta, &tau, &scale);
+        house_scalars_sq(alpha, sj, &beta, &tau, &scale);
         s_scal[0] = beta;
         s_scal[1] = tau;
         s_scal[2] = scale;
         if (g == 0) a.tau[j] = tau;
       }
-    } else {
-      for (int c = j + 1 + tid - 32; c < bJ; c += NT - 32) {
+    } else if (nc1 > 0) {
+      for (int c = j + 1 + tid - 32; c < bJ; c += NT - 32) s_w[c] = __ldcg(rowj + c);  // row j
+      // warp-uniform rounds; the adds stop at the warp's largest source count
+      const int total = parts * nc1;
+      for (int e0 = (warp - 1) * 32; e0 < total; e0 += NT - 32) {
+        const int e = e0 + lane;
+        const bool act = e < total;
+        const int c = j + 1 + (act ? e % nc1 : 0), pp = act ? e / nc1 : 0;
+        const int cnt = act ? (nsrc - pp + parts - 1) / parts : 0;  // sources pp, pp + parts, ...
+        const int cmax = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
         double s = 0.0;
-        for (int pp = 0; pp < parts; ++pp) s += s_part[pp][c];
-        s_tot[c] = s;
-        s_w[c] = __ldcg(rowj + c);  // row j of the panel before this step
+        for (int u0 = 0; u0 < cmax; u0 += RB) {
+          double v[RB];
+#pragma unroll
+          for (int u = 0; u < RB; ++u)
+            v[u] = (u0 + u < cnt) ? __ldcg(part + (size_t)(pp + (u0 + u) * parts) * bJ + c) : 0.0;
+#pragma unroll
+          for (int u = 0; u < RB; ++u) {
+            if (u0 + u >= cmax) break;
+            if (u0 + u < cnt) s += v[u];
+          }
+        }
+        if (act) s_part[pp][c] = s;
       }
     }
     __syncthreads();
     const double beta = s_scal[0], tau = s_scal[1], scale = s_scal[2];
     // w_c = tau * v^T a_c for c > j (v_j = 1, v_r = scale x_r below)
-    for (int c = j + 1 + tid; c < bJ; c += NT) s_w[c] = tau * (s_w[c] + scale * s_tot[c]);
+    for (int c = j + 1 + tid; c < bJ; c += NT) {
+      double st = 0.0;
+      for (int pp = 0; pp < parts; ++pp) st += s_part[pp][c];
+      s_w[c] = tau * (s_w[c] + scale * st);
+    }
     const int64_t jl = (int64_t)j - r_lo;  // local index of row j (may be outside)
     const int64_t rstart = imax64(0, jl + 1);
     // scale column j into v, then a_rc -= v_r w_c on owned rows below j
