@@ -522,3 +522,27 @@ def test_max_sms_cap_keeps_parity(lib):
         h.set_max_sms(-1)
     h.set_max_sms(0)   # back to all SMs
     _check_rqrcp(lib, A, 32, 8, 1, handle=h)
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_factor_bitwise_reproducible(lib, mixed):
+    """Two runs of one factorization are bit for bit equal: every grid reduction
+    has a fixed order, including the panel's two-level sum of the column dots
+    (4096 rows on 128 CTAs in 16 groups of 8, b = 128, so the grouped form runs
+    for the first 73 columns of every panel), whose group sums are added in CTA
+    order by whichever CTA of the group publishes last."""
+    m, n, b, p = 4096, 768, 128, 16
+    A = synth.gaussian(m, n, seed=11)
+    runs = []
+    for _ in range(2):
+        if mixed:
+            dA = lib.colmajor(torch.from_numpy(A).float().cuda())
+            jp, tau, rd = lib.rqrcp_factor_mixed(dA, b, p, 3)
+            runs.append((dA, jp, tau, rd))
+        else:
+            dA = to_dev(A)
+            jp, tau = lib.rqrcp_factor(dA, b, p, 3)
+            runs.append((dA, jp, tau))
+    assert lib.sync_info() == 0
+    for x, y in zip(*runs):
+        assert torch.equal(x, y)
