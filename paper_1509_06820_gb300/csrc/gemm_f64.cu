@@ -43,6 +43,27 @@ __device__ __forceinline__ double load_b(const double* __restrict__ B, int64_t l
   return B[j + kk * ldb];
 }
 
+// One staged k-slice into the 4 x 4 register tile: rows tx + 16a for a < NA
+// (NA = 1 for a tile whose live rows all fall in a = 0, so that a ragged
+// last row tile -- e.g. rows 64..71 of the l = 72 sketch -- issues a quarter
+// of the FP64 FMAs instead of computing on zeros), columns ty + 16c.
+template <int NA>
+__device__ __forceinline__ void fma_slice(const double (*As)[BM], const double (*Bs)[BN], int tx,
+                                          int ty, double (&acc)[4][4]) {
+#pragma unroll
+  for (int kk = 0; kk < BK; ++kk) {
+    double av[NA], bv[4];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) av[a] = As[kk][tx + 16 * a];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][ty + 16 * c];
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][c] = fma(av[a], bv[c], acc[a][c]);
+  }
+}
+
 template <char TA, char TB, int AMODE>
 __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs g, int64_t kchunk, double* partial) {
   if (g.gate != nullptr && *g.gate != g.gate_run) return;
@@ -54,6 +75,7 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs g, int64_t kchunk, do
   const int64_t j0 = (int64_t)blockIdx.y * BN;
   const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
   const int64_t kend = imin64(g.K, kbeg + kchunk);
+  const bool thin = g.M - i0 <= 16;  // the same for the whole CTA
 
   double acc[4][4];
 #pragma unroll
@@ -77,18 +99,10 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs g, int64_t kchunk, do
       Bs[lk][lj] = load_b<TB>(g.B, g.ldb, kend, g.N, k0 + lk, j0 + lj, g.bcols);
     }
     __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      double av[4], bv[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = As[kk][tx + 16 * a];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][ty + 16 * c];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[a][c] = fma(av[a], bv[c], acc[a][c]);
-    }
+    if (thin)
+      fma_slice<1>(As, Bs, tx, ty, acc);
+    else
+      fma_slice<4>(As, Bs, tx, ty, acc);
     __syncthreads();
   }
 
