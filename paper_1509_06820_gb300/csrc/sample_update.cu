@@ -11,12 +11,15 @@
 namespace rq {
 namespace {
 
-constexpr int W11_ROWS = 8;  // rows of W11 per CTA, one warp each
-constexpr int W11_MAXQ = 4;  // columns per lane (b <= 128)
+constexpr int W11_ROWS = 2;     // rows of W11 per CTA, one warp each
+constexpr int W11_THREADS = 256;  // threads per CTA (all stage R11; W11_ROWS warps solve)
+constexpr int W11_MAXQ = 4;     // columns per lane (b <= 128)
 
-// W11 = S11 R11^{-1}: CTA c owns rows 8c..8c+7 of W11; R11's upper triangle
-// and the reciprocals of its diagonal are staged in shared memory; warp w
-// computes row r of W11 left to right by the right-looking recurrence
+// W11 = S11 R11^{-1}: CTA c owns rows 2c, 2c + 1 of W11 (two rows per SM: the
+// recurrence's FP64 FMAs of eight rows on one SM had waited on the SM's FP64
+// unit at every step); R11's upper triangle and the reciprocals of its
+// diagonal are staged in shared memory by the whole CTA; warp w < 2 computes
+// row r of W11 left to right by the right-looking recurrence
 //   W(r, j) = acc_j / R(j, j),  acc_c -= W(r, j) R(j, c) for c > j,
 // with acc_c = S(r, c) initially and lane l keeping acc_c for c = l (mod 32):
 // one shuffle, one multiply and a few FMAs per step, no reductions.
@@ -62,13 +65,13 @@ __global__ void w11_kernel(const double* __restrict__ S, int ell, const double* 
     // W11 = 0: a product that is not gated by the flag leaves S12 unchanged
     // for the re-sample to overwrite
     const int r = blockIdx.x * W11_ROWS + warp;
-    if (r < bJ)
+    if (warp < W11_ROWS && r < bJ)
       for (int c = lane; c < bJ; c += 32) W[r + c * bJ] = 0.0;
     return;
   }
   if (blockIdx.x == 0 && tid == 0) *flag = 0;
   const int r = blockIdx.x * W11_ROWS + warp;
-  if (r >= bJ) return;
+  if (warp >= W11_ROWS || r >= bJ) return;
   double acc[W11_MAXQ];
 #pragma unroll
   for (int q = 0; q < W11_MAXQ; ++q) {
@@ -103,7 +106,7 @@ cudaError_t launch_w11(const double* S, int ell, const double* R11, int64_t ldr,
   cudaError_t e = ensure_smem_attr(w11_kernel, (128 * 128 + 128) * (int)sizeof(double), attr_done);
   if (e != cudaSuccess) return e;
   const int grid = (bJ + W11_ROWS - 1) / W11_ROWS;
-  w11_kernel<<<grid, 32 * W11_ROWS, smem, st>>>(S, ell, R11, ldr, bJ, W11, flag, status);
+  w11_kernel<<<grid, W11_THREADS, smem, st>>>(S, ell, R11, ldr, bJ, W11, flag, status);
   return cudaGetLastError();
 }
 
