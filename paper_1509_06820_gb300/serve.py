@@ -29,6 +29,7 @@ Only host-side scheduling lives here: every numerical step runs in the CUDA
 kernels behind the C ABI.
 """
 import collections
+import gc
 import ctypes
 import math
 import time
@@ -325,27 +326,38 @@ def poisson_arrivals(rate, total, seed, size_range, k_range):
 def run_poisson(server, rate, duration, warmup=0.0, seed=7, size_range=(256, 4096),
                 k_range=(16, 128)):
     """Drive `server` (submit / poll / pending / running / done) with a Poisson
-    stream; latency = completion seen by the host - arrival."""
+    stream; latency = completion seen by the host - arrival.  The host loop is
+    the only thread that admits, publishes and observes completions, so the
+    cyclic garbage collector is held off while it runs (reference counting
+    still frees every request's tensors): a collection pass over the
+    thousands of finished requests stalls every request in flight."""
     arrivals = poisson_arrivals(rate, warmup + duration, seed, size_range, k_range)
     server.done = []
-    t0 = time.perf_counter()
     i = 0
     def busy():
         return bool(server.pending or server.running or getattr(server, "staged", None))
 
-    while i < len(arrivals) or busy():
-        now = time.perf_counter() - t0
-        while i < len(arrivals) and arrivals[i][0] <= now:
-            req = arrivals[i][1]
-            req.t_arrival = t0 + arrivals[i][0]
-            server.submit(req)
-            i += 1
-        server.poll()
-        if i < len(arrivals) and not busy():
-            wait = arrivals[i][0] - (time.perf_counter() - t0)
-            if wait > 50e-6:
-                time.sleep(min(wait, 200e-6))
-    t_end = time.perf_counter()
+    gc_was_enabled = gc.isenabled()
+    gc.collect()
+    gc.disable()
+    try:
+        t0 = time.perf_counter()
+        while i < len(arrivals) or busy():
+            now = time.perf_counter() - t0
+            while i < len(arrivals) and arrivals[i][0] <= now:
+                req = arrivals[i][1]
+                req.t_arrival = t0 + arrivals[i][0]
+                server.submit(req)
+                i += 1
+            server.poll()
+            if i < len(arrivals) and not busy():
+                wait = arrivals[i][0] - (time.perf_counter() - t0)
+                if wait > 50e-6:
+                    time.sleep(min(wait, 200e-6))
+        t_end = time.perf_counter()
+    finally:
+        if gc_was_enabled:
+            gc.enable()
     measured = [r for r in server.done if r.t_arrival - t0 >= warmup]
     lat = np.array([r.t_done - r.t_arrival for r in measured]) * 1e3
     span = max(r.t_done for r in measured) - min(r.t_arrival for r in measured)
@@ -470,9 +482,12 @@ class RingServer:
 
     def poll(self):
         info = ctypes.c_int(0)
+        info_ref = ctypes.byref(info)
+        server_poll = load().rqrcp_server_poll
+        h = self.handle.h
         still = []
         for req in self.running:
-            rc = load().rqrcp_server_poll(self.handle.h, req.slot[3], ctypes.byref(info))
+            rc = server_poll(h, req.slot[3], info_ref)
             if rc < 0:
                 raise RuntimeError(f"rqrcp_server_poll: {rc}")
             if rc == 1:
