@@ -42,7 +42,11 @@ __global__ void __launch_bounds__(NT, 1)
 }  // namespace
 
 int panel_grid(int64_t mJ, int bJ, int num_sms) {
-  int64_t G = (mJ + 31) / 32;
+  // rows per CTA: 32, or 16 for panels of 128 columns, whose per-column work
+  // shrinks faster than the reduction over more CTAs grows (measured: 2048 x
+  // 128 7.98 against 8.76 us per column; 64-column panels gain nothing)
+  const int64_t rows = bJ >= 128 ? 16 : 32;
+  int64_t G = (mJ + rows - 1) / rows;
   if (G > num_sms) G = num_sms;
   if (G < 1) G = 1;
   return (int)G;
