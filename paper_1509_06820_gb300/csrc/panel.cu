@@ -8,7 +8,10 @@
 // publishes, over its rows below row j, the dot products of column j with
 // columns j..b_J-1 (the j-th entry is the squared tail norm), and the owner
 // of row j publishes that row.  After it every CTA adds the partial sums in
-// the same fixed order, so all CTAs derive the same reflector
+// the same fixed order (while 56 or more columns remain, in two levels: the
+// last CTA of each group of 8 to publish has added its group's partials, in
+// CTA order, before the barrier, and every CTA adds the groups' sums), so all
+// CTAs derive the same reflector
 //   beta = -sign(alpha) ||x||, tau = (beta - alpha)/beta, v = x/(alpha - beta),
 // and the same w_c = tau v^T a_c = tau (a_jc + (x^T a_c)_tail/(alpha - beta)),
 // update their rows, and compute the partial sums of the next column.
